@@ -1,0 +1,443 @@
+"""FP64 CPU oracle for the Iterative Hessian Sketch (Cormode & Dickens,
+"Iterative Hessian Sketch in Input Sparsity Time", arXiv 1910.14166).
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and
+``bench.py``'s CPU-baseline / reference leg may import this package.  The GPU
+library never calls it and shares no code with it: the O(nnz) data passes and
+the hash live in ``ihs_oracle.c`` (plain C loops, FP64), the d-dimensional
+algebra below is plain NumPy/SciPy in FP64, each function citing the part of
+the paper it states.
+
+What is pinned, and by what (see tests/test_oracle.py):
+  * hash: published SplitMix64 outputs; uniformity; the sketch lemmas of
+    App. A (S S^T diagonal with the row counts, E[S S^T] = (n/m) I,
+    E[S^T S] = I with diag(S^T S) = 1 on every draw).
+  * sketch: brute-force S A with S materialised as a dense matrix.
+  * Gram: dense matmul of the materialised sketch; E over draws -> A^T A.
+  * residual / gradient: finite differences of f(x) = 1/2 ||Ax - b||^2 (Eq. 1).
+  * OLS step: identity sketch gives x_OPT (numpy lstsq) in one step (Eq. 2).
+  * l1-ball QP: brute force over all faces of the ball for d <= 6; KKT.
+  * x_OPT: Householder QR vs refined normal equations vs lstsq.
+  * IHS: geometric convergence at a rate below 1/2 (Thm. 1).
+  * ridge adjoint: central finite differences in FP64.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "ihs_oracle.c")
+_SO = os.path.join(_HERE, "libihs_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+u64 = ctypes.c_uint64
+i64 = ctypes.c_int64
+i32 = ctypes.c_int
+f64 = ctypes.c_double
+vp = ctypes.c_void_p
+
+
+def build_oracle(force: bool = False) -> str:
+    """Compile ihs_oracle.c with gcc (plain -O2, no fast-math, no FMA contraction)."""
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+        tmp = _SO + ".tmp%d" % os.getpid()
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math",
+                               "-shared", "-fPIC", "-o", tmp, _SRC])
+        os.replace(tmp, _SO)
+    return _SO
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            L = ctypes.CDLL(build_oracle())
+            L.orc_sm64_at.restype = u64
+            L.orc_sm64_at.argtypes = [u64, u64]
+            L.orc_hash.restype = i32
+            L.orc_hash.argtypes = [u64, i64, i32, i64, i64, vp, vp]
+            L.orc_sketch_dense.restype = None
+            L.orc_sketch_dense.argtypes = [i64, i64, vp, i64, i64, i32, vp, vp, vp]
+            L.orc_sketch_csr.restype = None
+            L.orc_sketch_csr.argtypes = [i64, i64, vp, vp, vp, i64, i32, vp, vp, vp]
+            L.orc_gram.restype = None
+            L.orc_gram.argtypes = [i64, i64, vp, f64, f64, vp]
+            L.orc_resid_grad_dense.restype = None
+            L.orc_resid_grad_dense.argtypes = [i64, i64, vp, i64, vp, vp, vp, vp]
+            L.orc_resid_grad_csr.restype = None
+            L.orc_resid_grad_csr.argtypes = [i64, i64, vp, vp, vp, vp, vp, vp, vp]
+            L.orc_sketch_adjoint.restype = None
+            L.orc_sketch_adjoint.argtypes = [i64, i64, i64, i32, vp, vp, vp, f64, vp]
+            _lib = L
+    return _lib
+
+
+def _p(a):
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+# --------------------------------------------------------------------------
+# Matrices: dense np.ndarray (n x d) or a CSR triple.
+# --------------------------------------------------------------------------
+class CSR:
+    """CSR matrix with int64 rowptr, int32 col, float64 val (the oracle's own copy)."""
+
+    def __init__(self, n, d, rowptr, col, val):
+        self.n, self.d = int(n), int(d)
+        self.rowptr = np.ascontiguousarray(rowptr, dtype=np.int64)
+        self.col = np.ascontiguousarray(col, dtype=np.int32)
+        self.val = np.ascontiguousarray(val, dtype=np.float64)
+
+    @property
+    def shape(self):
+        return (self.n, self.d)
+
+    def todense(self):
+        out = np.zeros((self.n, self.d))
+        for i in range(self.n):
+            a, b = self.rowptr[i], self.rowptr[i + 1]
+            out[i, self.col[a:b]] += self.val[a:b]
+        return out
+
+    def matvec(self, x):
+        rows = np.repeat(np.arange(self.n), np.diff(self.rowptr))
+        out = np.zeros(self.n)
+        np.add.at(out, rows, self.val * x[self.col])
+        return out
+
+    def gram(self):
+        """A^T A in FP64 (for x_OPT and the error metric)."""
+        d = self.d
+        rows = np.repeat(np.arange(self.n), np.diff(self.rowptr))
+        # A^T A = sum over rows of outer products; build via a dense column block product.
+        try:
+            import scipy.sparse as sp
+            M = sp.csr_matrix((self.val, self.col, self.rowptr), shape=(self.n, d))
+            return np.asarray((M.T @ M).todense())
+        except ImportError:  # plain fallback
+            G = np.zeros((d, d))
+            for i in range(self.n):
+                a, b = self.rowptr[i], self.rowptr[i + 1]
+                c, v = self.col[a:b], self.val[a:b]
+                G[np.ix_(c, c)] += np.outer(v, v)
+            return G
+
+    def rmatvec(self, r):
+        out = np.zeros(self.d)
+        rows = np.repeat(np.arange(self.n), np.diff(self.rowptr))
+        np.add.at(out, self.col, self.val * r[rows])
+        return out
+
+
+def as_f64(A):
+    if isinstance(A, CSR):
+        return A
+    return np.ascontiguousarray(A, dtype=np.float64)
+
+
+# --------------------------------------------------------------------------
+# Sketch draw and data passes (C loops).
+# --------------------------------------------------------------------------
+def sm64_at(state: int, j: int) -> int:
+    """Output j of a SplitMix64 generator started at `state` (Steele, Lea & Flood 2014)."""
+    return int(lib().orc_sm64_at(u64(state & 0xFFFFFFFFFFFFFFFF), u64(j)))
+
+
+def hash_draw(seed: int, t: int, s: int, m: int, n: int):
+    """Sketch S^{t} of Sec. 2: bucket (global row of S, int32 [s, n]) and sign (int8 [s, n])."""
+    bucket = np.empty((s, n), dtype=np.int32)
+    sign = np.empty((s, n), dtype=np.int8)
+    rc = lib().orc_hash(u64(seed & 0xFFFFFFFFFFFFFFFF), i64(t), i32(s), i64(m), i64(n),
+                        _p(bucket), _p(sign))
+    if rc != 0:
+        raise ValueError("invalid sketch shape: m=%d s=%d" % (m, s))
+    return bucket, sign
+
+
+def sketch(A, m: int, s: int, bucket, sign):
+    """Raw SA (unscaled +-1 entries), m x d FP64, by the streaming pass of Sec. 2."""
+    bucket = np.ascontiguousarray(bucket, dtype=np.int32)
+    sign = np.ascontiguousarray(sign, dtype=np.int8)
+    if isinstance(A, CSR):
+        SA = np.empty((m, A.d))
+        lib().orc_sketch_csr(A.n, A.d, _p(A.rowptr), _p(A.col), _p(A.val), m, s,
+                             _p(bucket), _p(sign), _p(SA))
+        return SA
+    A = as_f64(A)
+    n, d = A.shape
+    SA = np.empty((m, d))
+    lib().orc_sketch_dense(n, d, _p(A), d, m, s, _p(bucket), _p(sign), _p(SA))
+    return SA
+
+
+def gram(SA, scale: float, shift: float = 0.0):
+    """H = scale * SA^T SA + shift * I (Sec. 1), plain triple loop."""
+    SA = np.ascontiguousarray(SA, dtype=np.float64)
+    m, d = SA.shape
+    H = np.empty((d, d))
+    lib().orc_gram(m, d, _p(SA), f64(scale), f64(shift), _p(H))
+    return H
+
+
+def resid_grad(A, b, x, want_r: bool = False):
+    """r = b - A x and g = A^T r (Eq. 2's linear term), rows in order, FP64."""
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    n = b.shape[0]
+    r = np.empty(n) if want_r else None
+    if isinstance(A, CSR):
+        g = np.empty(A.d)
+        lib().orc_resid_grad_csr(A.n, A.d, _p(A.rowptr), _p(A.col), _p(A.val), _p(b), _p(x),
+                                 _p(r) if want_r else None, _p(g))
+    else:
+        A = as_f64(A)
+        g = np.empty(A.shape[1])
+        lib().orc_resid_grad_dense(A.shape[0], A.shape[1], _p(A), A.shape[1], _p(b), _p(x),
+                                   _p(r) if want_r else None, _p(g))
+    return (r, g) if want_r else g
+
+
+def sketch_adjoint(G, n: int, s: int, bucket, sign):
+    """S^T G for the normalised sketch (entries sign/sqrt(s)), n x d FP64."""
+    G = np.ascontiguousarray(G, dtype=np.float64)
+    m, d = G.shape
+    out = np.empty((n, d))
+    lib().orc_sketch_adjoint(n, d, m, s, _p(np.ascontiguousarray(bucket, dtype=np.int32)),
+                             _p(np.ascontiguousarray(sign, dtype=np.int8)), _p(G),
+                             f64(1.0 / np.sqrt(s)), _p(out))
+    return out
+
+
+def sketch_matrix(m: int, s: int, bucket, sign):
+    """Dense S (m x n) with entries sign/sqrt(s): only for brute-force pins on tiny n."""
+    n = bucket.shape[1]
+    S = np.zeros((m, n))
+    for k in range(s):
+        for i in range(n):
+            S[bucket[k, i], i] += sign[k, i] / np.sqrt(s)
+    return S
+
+
+# --------------------------------------------------------------------------
+# d-dimensional algebra (FP64, NumPy / SciPy primitives).
+# --------------------------------------------------------------------------
+def chol_solve(H, g):
+    """Solve H delta = g through the Cholesky factor H = L L^T (OLS step of Eq. 2)."""
+    from scipy.linalg import solve_triangular
+    L = np.linalg.cholesky(H)
+    y = solve_triangular(L, g, lower=True)
+    return solve_triangular(L.T, y, lower=False)
+
+
+def project_l1_ball(v, R):
+    """Euclidean projection onto {x : ||x||_1 <= R} (Duchi, Shalev-Shwartz,
+    Singer & Chandra 2008, sort-based)."""
+    if np.abs(v).sum() <= R:
+        return v.copy()
+    u = np.sort(np.abs(v))[::-1]
+    css = np.cumsum(u)
+    j = np.arange(1, v.size + 1)
+    rho = np.nonzero(u - (css - R) / j > 0)[0][-1]
+    theta = (css[rho] - R) / (rho + 1.0)
+    return np.sign(v) * np.maximum(np.abs(v) - theta, 0.0)
+
+
+def _l1_face_solve(H, c, R, S, sgn):
+    """Minimise 1/2 x^T H x - c^T x on {x_S^T sgn = R, x_{S^c} = 0}: the
+    bordered KKT system [H_SS sgn; sgn^T 0][z; mu] = [c_S; R]."""
+    k = len(S)
+    K = np.zeros((k + 1, k + 1))
+    K[:k, :k] = H[np.ix_(S, S)]
+    K[:k, k] = sgn
+    K[k, :k] = sgn
+    rhs = np.concatenate([c[S], [R]])
+    sol = np.linalg.solve(K, rhs)
+    return sol[:k], sol[k]
+
+
+def l1_kkt_residual(H, g, xt, R, x):
+    """Relative KKT violation of x for the l1-ball QP (0 at the exact solution)."""
+    c = H @ xt + g
+    grad = H @ x - c
+    scale = max(np.abs(c).max(), 1e-300)
+    if np.abs(x).sum() < R * (1 - 1e-12):
+        return np.abs(grad).max() / scale
+    S = np.nonzero(x)[0]
+    if S.size == 0:
+        return np.inf
+    mu = -np.mean(grad[S] * np.sign(x[S]))
+    on = np.abs(grad[S] + mu * np.sign(x[S])).max()
+    off = 0.0
+    mask = np.ones(x.size, bool)
+    mask[S] = False
+    if mask.any():
+        off = max(0.0, (np.abs(grad[mask]) - mu).max())
+    return max(on, off, max(0.0, -mu), abs(np.abs(x).sum() - R) / max(R, 1e-300)) / scale
+
+
+def l1_ball_qp(H, g, xt, R, tol=1e-13, max_rounds=200, inner=200):
+    """Exact minimiser of the l1-ball subproblem of Eq. 2:
+        argmin_{||x||_1 <= R} 1/2 (x - xt)^T H (x - xt) - g^T (x - xt).
+    The paper solves each subproblem "exactly" (Sec. 3); this oracle reads that
+    as: the unconstrained Newton point if it is feasible; otherwise FISTA (Beck
+    & Teboulle 2009) with the l1-ball projection locates the support and signs,
+    and the bordered KKT system on that face gives the exact point, accepted
+    only when its signs match and the off-support optimality holds."""
+    c = H @ xt + g
+    xu = chol_solve(H, c)
+    if np.abs(xu).sum() <= R:
+        return xu
+    Lip = np.linalg.eigvalsh(H)[-1]
+    x = project_l1_ball(xt, R)
+    y = x.copy()
+    tk = 1.0
+    for _ in range(max_rounds):
+        for _ in range(inner):
+            xn = project_l1_ball(y - (H @ y - c) / Lip, R)
+            tn = 0.5 * (1.0 + np.sqrt(1.0 + 4.0 * tk * tk))
+            y = xn + ((tk - 1.0) / tn) * (xn - x)
+            x, tk = xn, tn
+        S = np.nonzero(x)[0]
+        if S.size == 0:
+            continue
+        sgn = np.sign(x[S])
+        z, mu = _l1_face_solve(H, c, R, S, sgn)
+        if mu < 0 or np.any(z * sgn <= 0):
+            continue
+        xf = np.zeros_like(x)
+        xf[S] = z
+        grad = H @ xf - c
+        mask = np.ones(x.size, bool)
+        mask[S] = False
+        if (not mask.any()) or np.all(np.abs(grad[mask]) <= mu * (1.0 + 1e-9) + tol * np.abs(c).max()):
+            return xf
+    raise RuntimeError("l1-ball QP did not reach an exact KKT point")
+
+
+def l1_ball_qp_bruteforce(H, g, xt, R):
+    """Brute force for tiny d: the unconstrained point if feasible, else the
+    best point over every face of the l1 ball (all sign patterns in {-1,0,1}^d)."""
+    import itertools
+    d = H.shape[0]
+    c = H @ xt + g
+    q = lambda x: 0.5 * x @ H @ x - c @ x
+    xu = np.linalg.solve(H, c)
+    if np.abs(xu).sum() <= R:
+        return xu
+    best, bq = None, np.inf
+    for pat in itertools.product((-1, 0, 1), repeat=d):
+        pat = np.array(pat)
+        S = np.nonzero(pat)[0]
+        if S.size == 0:
+            continue
+        z, _ = _l1_face_solve(H, c, R, S, pat[S].astype(float))
+        if np.any(z * pat[S] < 0):
+            continue
+        x = np.zeros(d)
+        x[S] = z
+        if q(x) < bq:
+            best, bq = x, q(x)
+    return best
+
+
+# --------------------------------------------------------------------------
+# IHS (Eq. 2) and its fixed point.
+# --------------------------------------------------------------------------
+OLS, L1_BALL, RIDGE = 0, 1, 2
+
+
+def ihs(A, b, kind: int, param: float, m: int, s: int, seed: int, iters: int, x0=None,
+        t0: int = 0, keep_sketch: bool = False):
+    """Iterates x^0..x^iters of Eq. 2 with a fresh sketch per step.
+
+    Iteration t (t = t0, t0+1, ...) draws the sketch with counter t, builds
+    H = (1/s) (SA)^T SA (+ lam I for ridge) and g = A^T (b - A x^t) (- lam x^t
+    for ridge), then takes the QP step: Cholesky for OLS / ridge, the exact
+    l1-ball QP for LASSO.  x^0 = 0 unless x0 is given."""
+    A = as_f64(A)
+    n, d = A.shape
+    x = np.zeros(d) if x0 is None else np.array(x0, dtype=np.float64)
+    xs = [x.copy()]
+    sk = []
+    for t in range(t0, t0 + iters):
+        bucket, sign = hash_draw(seed, t, s, m, n)
+        SA = sketch(A, m, s, bucket, sign)
+        shift = param if kind == RIDGE else 0.0
+        H = gram(SA, 1.0 / s, shift)
+        g = resid_grad(A, b, x)
+        if kind == RIDGE:
+            g = g - param * x
+        if kind == L1_BALL:
+            x = l1_ball_qp(H, g, x, param)
+        else:
+            x = x + chol_solve(H, g)
+        xs.append(x.copy())
+        if keep_sketch:
+            sk.append((SA, H, g))
+    return (xs, sk) if keep_sketch else xs
+
+
+def ata(A):
+    A = as_f64(A)
+    if isinstance(A, CSR):
+        return A.gram()
+    return A.T @ A
+
+
+def atb(A, b):
+    A = as_f64(A)
+    if isinstance(A, CSR):
+        return A.rmatvec(b)
+    return A.T @ b
+
+
+def x_opt_ols_qr(A, b):
+    """x_OPT of Eq. 1 with C = R^d by Householder QR (numpy.linalg.qr)."""
+    Q, Rm = np.linalg.qr(as_f64(A))
+    from scipy.linalg import solve_triangular
+    return solve_triangular(Rm, Q.T @ b, lower=False)
+
+
+def x_opt_ols_normal(A, b, lam: float = 0.0, refine: int = 3):
+    """x_OPT from the normal equations (A^T A + lam I) x = A^T b, Cholesky in
+    FP64 plus `refine` rounds of iterative refinement with FP64 residuals."""
+    A = as_f64(A)
+    G = ata(A) + lam * np.eye(A.shape[1])
+    x = chol_solve(G, atb(A, b))
+    for _ in range(refine):
+        g = resid_grad(A, b, x) - lam * x
+        x = x + chol_solve(G, g)
+    return x
+
+
+def x_opt_l1(A, b, R):
+    """x_OPT of Eq. 1 over the l1 ball: the QP with H = A^T A, x^t = 0, g = A^T b."""
+    A = as_f64(A)
+    G = ata(A)
+    return l1_ball_qp(G, atb(A, b), np.zeros(A.shape[1]), R)
+
+
+def err_A(x, xopt, G):
+    """||x - x_OPT||_A / ||x_OPT||_A with ||v||_A = n^{-1/2} ||A v|| (Def. of
+    an eps-solution approximation); G = A^T A, the n^{-1/2} factors cancel."""
+    e = np.asarray(x) - xopt
+    return float(np.sqrt(max(e @ G @ e, 0.0)) / np.sqrt(xopt @ G @ xopt))
+
+
+def ridge_adjoint(A, b, lam, dLdx):
+    """Exact gradients of L(x(A, b)) for x = (A^T A + lam I)^{-1} A^T b:
+    v = (A^T A + lam I)^{-1} dL/dx,  dL/db = A v,  dL/dA = r v^T - (A v) x^T
+    with r = b - A x.  Dense FP64 solves."""
+    A = np.ascontiguousarray(A, dtype=np.float64)
+    G = A.T @ A + lam * np.eye(A.shape[1])
+    x = chol_solve(G, A.T @ b)
+    v = chol_solve(G, dLdx)
+    r = b - A @ x
+    Av = A @ v
+    return x, Av, np.outer(r, v) - np.outer(Av, x)

@@ -1,0 +1,198 @@
+/*
+ * ihs_oracle.c -- plain FP64 CPU oracle for the data passes of the Iterative
+ * Hessian Sketch with CountSketch / SJLT (Cormode & Dickens, "Iterative Hessian
+ * Sketch in Input Sparsity Time", arXiv 1910.14166).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the slow, obviously correct
+ * statement of what the GPU library computes.  Only tests, the smoke check and
+ * the benchmark's CPU-baseline leg may load it.  It shares no code, header or
+ * constant table with the CUDA library: the hash below is written from the
+ * published SplitMix64 definition, independently of the GPU's copy.
+ *
+ * Every loop here is the plain definition: no blocking, no reordering, one
+ * pass in ascending index order, all arithmetic in IEEE double.
+ *
+ * Functions (all exported with C linkage, plain pointers, row-major arrays):
+ *   orc_sm64_at       SplitMix64 stream output (Steele, Lea & Flood 2014)
+ *   orc_hash          CountSketch / SJLT bucket and sign per (block, row)  (Sec. 2)
+ *   orc_sketch_dense  SA = S A by streaming the rows of a dense A           (Sec. 2, "applied by streaming")
+ *   orc_sketch_csr    the same over a CSR matrix                            (Sec. 2)
+ *   orc_gram          H = scale * (SA)^T (SA) + shift * I                   (Sec. 1, approximate Hessian)
+ *   orc_resid_grad_dense / orc_resid_grad_csr
+ *                     r = b - A x,  g = A^T r                               (Eq. 2, linear term)
+ *   orc_sketch_adjoint  (S^T G) row by row                                  (adjoint of Sec. 2's map)
+ *
+ * Build: gcc -O2 -std=c11 -shared -fPIC -o libihs_oracle.so ihs_oracle.c
+ * (-O2 keeps IEEE semantics: no -ffast-math, no FMA contraction, see below).
+ */
+#include <stdint.h>
+#include <stddef.h>
+
+/* Keep a*b+c as two roundings so the oracle is plain IEEE double arithmetic. */
+#if defined(__GNUC__)
+#pragma GCC optimize("fp-contract=off")
+#endif
+
+/* SplitMix64 constants, from the published generator (Steele, Lea & Flood,
+ * "Fast splittable pseudorandom number generators", OOPSLA 2014): the state
+ * advances by the golden-gamma increment and each output is the state passed
+ * through the two xor-shift-multiply rounds of the finaliser. */
+#define SM64_GAMMA 0x9E3779B97F4A7C15ULL
+
+static uint64_t sm64_finalise(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  return z ^ (z >> 31);
+}
+
+/* Output number j (counting from 0) of a SplitMix64 generator whose initial
+ * state is `state`: the generator adds gamma before each output, so output j
+ * is the finaliser of state + (j + 1) * gamma (mod 2^64). */
+uint64_t orc_sm64_at(uint64_t state, uint64_t j) {
+  return sm64_finalise(state + (j + 1) * SM64_GAMMA);
+}
+
+/*
+ * Sketch draw (Sec. 2, CountSketch and SJLT definitions).  The paper asks
+ * for a uniformly random row h(i) per column i of S and a sign that is +1 or
+ * -1 with probability 1/2, and builds an SJLT from s independent CountSketches
+ * of m/s rows each.  It names no generator; this library's reading is a
+ * counter-based SplitMix64 chain:
+ *     key_seed = out(seed, 0);  key_t = out(key_seed, t);  key_tk = out(key_t, k);
+ *     w = out(key_tk, i)
+ * where out(x, j) = orc_sm64_at(x, j).  The bucket within block k is the
+ * multiply-shift range reduction of the high 32 bits, floor(hi32(w) * mb / 2^32)
+ * with mb = m / s (Lemire 2019), and the sign is -1 when bit 0 of w is set.
+ * The global row of S is k * mb + bucket.
+ *
+ * Output layout: bucket[k * n + i] (int32, global row in [0, m)),
+ *                sign[k * n + i]   (int8, +1 or -1).
+ * Returns 0, or -1 if s < 1, m % s != 0, or m/s exceeds 2^31 - 1.
+ */
+int orc_hash(uint64_t seed, int64_t t, int s, int64_t m, int64_t n,
+             int32_t* bucket, int8_t* sign) {
+  if (s < 1 || m < 1 || m % s != 0) return -1;
+  int64_t mb = m / s;
+  if (mb > 2147483647LL) return -1;
+  uint64_t key_seed = orc_sm64_at(seed, 0);
+  uint64_t key_t = orc_sm64_at(key_seed, (uint64_t)t);
+  for (int k = 0; k < s; ++k) {
+    uint64_t key_tk = orc_sm64_at(key_t, (uint64_t)k);
+    for (int64_t i = 0; i < n; ++i) {
+      uint64_t w = orc_sm64_at(key_tk, (uint64_t)i);
+      uint64_t hi = w >> 32;
+      uint64_t b = (hi * (uint64_t)mb) >> 32;
+      bucket[(int64_t)k * n + i] = (int32_t)((int64_t)k * mb + (int64_t)b);
+      sign[(int64_t)k * n + i] = (w & 1ULL) ? (int8_t)-1 : (int8_t)1;
+    }
+  }
+  return 0;
+}
+
+/*
+ * SA = S A for a dense row-major A (n x d, leading dimension lda), following
+ * the streaming description of Sec. 2: each row i of A is visited once per
+ * block k, in ascending i, and added with its sign into row bucket[k][i] of SA.
+ * The entries of S are the raw signs (+-1); the SJLT normalisation by the
+ * number of nonzeros per column (App. A, "normalise by the number of
+ * nonzeros") is applied later, once, as the Gram scale 1/s.
+ * SA is m x d row-major and is overwritten.
+ */
+void orc_sketch_dense(int64_t n, int64_t d, const double* A, int64_t lda,
+                      int64_t m, int s, const int32_t* bucket,
+                      const int8_t* sign, double* SA) {
+  for (int64_t q = 0; q < m * d; ++q) SA[q] = 0.0;
+  for (int k = 0; k < s; ++k) {
+    for (int64_t i = 0; i < n; ++i) {
+      int64_t row = bucket[(int64_t)k * n + i];
+      double sg = (double)sign[(int64_t)k * n + i];
+      for (int64_t j = 0; j < d; ++j) SA[row * d + j] += sg * A[i * lda + j];
+    }
+  }
+}
+
+/*
+ * The same product for a CSR matrix (rowptr[n+1], col[nnz], val[nnz]): on
+ * seeing nonzero A_ij, bucket h(i) of column j gains sign(i) * A_ij (Sec. 2).
+ * rowptr is int64.  SA is m x d row-major and is overwritten.
+ */
+void orc_sketch_csr(int64_t n, int64_t d, const int64_t* rowptr,
+                    const int32_t* col, const double* val, int64_t m, int s,
+                    const int32_t* bucket, const int8_t* sign, double* SA) {
+  for (int64_t q = 0; q < m * d; ++q) SA[q] = 0.0;
+  for (int k = 0; k < s; ++k) {
+    for (int64_t i = 0; i < n; ++i) {
+      int64_t row = bucket[(int64_t)k * n + i];
+      double sg = (double)sign[(int64_t)k * n + i];
+      for (int64_t p = rowptr[i]; p < rowptr[i + 1]; ++p)
+        SA[row * d + col[p]] += sg * val[p];
+    }
+  }
+}
+
+/*
+ * Approximate Hessian H = scale * (SA)^T (SA) + shift * I (Sec. 1: IHS
+ * replaces A^T A by the quadratic form of SA).  scale is 1/s for an SJLT with
+ * raw +-1 entries; shift is the ridge parameter (0 for OLS and LASSO).
+ * Full d x d output, row-major, plain triple loop over r = 0..m-1.
+ */
+void orc_gram(int64_t m, int64_t d, const double* SA, double scale,
+              double shift, double* H) {
+  for (int64_t a = 0; a < d; ++a) {
+    for (int64_t c = 0; c < d; ++c) {
+      double acc = 0.0;
+      for (int64_t r = 0; r < m; ++r) acc += SA[r * d + a] * SA[r * d + c];
+      H[a * d + c] = scale * acc + (a == c ? shift : 0.0);
+    }
+  }
+}
+
+/*
+ * Residual and gradient of f(x) = 1/2 ||Ax - b||^2 (Eq. 1): r = b - A x and
+ * g = A^T r = -grad f(x), the linear term of the IHS subproblem (Eq. 2).
+ * Rows in ascending order; r may be NULL.
+ */
+void orc_resid_grad_dense(int64_t n, int64_t d, const double* A, int64_t lda,
+                          const double* b, const double* x, double* r,
+                          double* g) {
+  for (int64_t j = 0; j < d; ++j) g[j] = 0.0;
+  for (int64_t i = 0; i < n; ++i) {
+    double ax = 0.0;
+    for (int64_t j = 0; j < d; ++j) ax += A[i * lda + j] * x[j];
+    double ri = b[i] - ax;
+    if (r) r[i] = ri;
+    for (int64_t j = 0; j < d; ++j) g[j] += A[i * lda + j] * ri;
+  }
+}
+
+void orc_resid_grad_csr(int64_t n, int64_t d, const int64_t* rowptr,
+                        const int32_t* col, const double* val, const double* b,
+                        const double* x, double* r, double* g) {
+  for (int64_t j = 0; j < d; ++j) g[j] = 0.0;
+  for (int64_t i = 0; i < n; ++i) {
+    double ax = 0.0;
+    for (int64_t p = rowptr[i]; p < rowptr[i + 1]; ++p) ax += val[p] * x[col[p]];
+    double ri = b[i] - ax;
+    if (r) r[i] = ri;
+    for (int64_t p = rowptr[i]; p < rowptr[i + 1]; ++p) g[col[p]] += val[p] * ri;
+  }
+}
+
+/*
+ * Adjoint of the sketch map: given G (m x d), (S^T G)_i = sum_k sign_k(i) *
+ * G[bucket_k(i), :] * entry_scale, with entry_scale = 1/sqrt(s) for the
+ * normalised SJLT.  Output n x d row-major.
+ */
+void orc_sketch_adjoint(int64_t n, int64_t d, int64_t m, int s,
+                        const int32_t* bucket, const int8_t* sign,
+                        const double* G, double entry_scale, double* out) {
+  (void)m;
+  for (int64_t i = 0; i < n; ++i) {
+    for (int64_t j = 0; j < d; ++j) out[i * d + j] = 0.0;
+    for (int k = 0; k < s; ++k) {
+      int64_t row = bucket[(int64_t)k * n + i];
+      double sg = (double)sign[(int64_t)k * n + i] * entry_scale;
+      for (int64_t j = 0; j < d; ++j) out[i * d + j] += sg * G[row * d + j];
+    }
+  }
+}

@@ -1,0 +1,405 @@
+"""Pins of the FP64 CPU oracle against facts fixed by the paper and by
+mathematics (no GPU).  Each test names what it pins and the passage it
+follows."""
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ---------------------------------------------------------------- hash ----
+def test_splitmix64_published_outputs():
+    """The sketch's generator is SplitMix64 from its published definition."""
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "splitmix64.txt")) if l[0] != "#"]
+    assert len(rows) == 8
+    for st, j, v in rows:
+        assert O.sm64_at(int(st), int(j)) == int(v)
+
+
+@pytest.mark.parametrize("m,s", [(40, 1), (40, 4), (7, 7), (1, 1)])
+def test_hash_shape_ranges(m, s):
+    """Sec. 2: block k of an SJLT is a CountSketch of m/s rows, stacked row-wise."""
+    n = 1000
+    bucket, sign = O.hash_draw(3, 2, s, m, n)
+    mb = m // s
+    for k in range(s):
+        assert bucket[k].min() >= k * mb and bucket[k].max() < (k + 1) * mb
+    assert set(np.unique(sign)) <= {-1, 1}
+
+
+def test_hash_rejects_bad_shape():
+    """SJLT needs m/s integral (Sec. 2)."""
+    with pytest.raises(ValueError):
+        O.hash_draw(0, 0, 3, 10, 5)
+
+
+def test_hash_uniform_and_balanced():
+    """Sec. 2: h(i) uniform over the m rows, signs +-1 with probability 1/2.
+    Chi-square over 64 buckets for 2^18 draws; sign fraction within 5 sigma."""
+    n, m = 1 << 18, 64
+    bucket, sign = O.hash_draw(11, 0, 1, m, n)
+    cnt = np.bincount(bucket[0], minlength=m)
+    e = n / m
+    chi2 = ((cnt - e) ** 2 / e).sum()
+    assert chi2 < 63 + 6 * np.sqrt(2 * 63)  # mean 63, sd sqrt(126)
+    frac = (sign == 1).mean()
+    assert abs(frac - 0.5) < 5 * 0.5 / np.sqrt(n)
+
+
+def test_hash_independent_across_iterations_and_blocks():
+    """A fresh sketch every iteration (App. A, iteration costs) and
+    independent blocks for the SJLT: draws for different (t, k) agree on about
+    1/mb of the rows, as independent uniform draws would."""
+    n, m, s = 20000, 80, 4
+    b0, _ = O.hash_draw(5, 0, s, m, n)
+    b1, _ = O.hash_draw(5, 1, s, m, n)
+    mb = m // s
+    same_t = ((b0 % mb) == (b1 % mb)).mean()
+    same_k = ((b0[0] % mb) == (b0[1] % mb)).mean()
+    for v in (same_t, same_k):
+        assert abs(v - 1 / mb) < 6 * np.sqrt(1 / mb / n)
+
+
+def test_countsketch_rows_orthogonal_lemma():
+    """Lemma (orthogonal rows): S S^T is diagonal with (S S^T)_ii = N_i, the
+    number of nonzeros in row i; for CountSketch sum_i N_i = n."""
+    n, m = 300, 16
+    bucket, sign = O.hash_draw(1, 0, 1, m, n)
+    S = O.sketch_matrix(m, 1, bucket, sign)
+    SS = S @ S.T
+    assert np.array_equal(SS, np.diag(np.diag(SS)))
+    assert np.array_equal(np.diag(SS), np.bincount(bucket[0], minlength=m).astype(float))
+    assert np.diag(SS).sum() == n
+
+
+def test_expected_SST_and_STS():
+    """Lemmas of App. A: E[S S^T] = (n/m) I_m and E[S^T S] = I_n; for an SJLT
+    normalised by its s nonzeros per column, diag(S^T S) = 1 on every draw."""
+    n, m, trials = 48, 8, 4000
+    acc_sst = np.zeros((m, m))
+    acc_sts = np.zeros((n, n))
+    for s in (1, 4):
+        acc_sst[:] = 0
+        acc_sts[:] = 0
+        for t in range(trials):
+            bucket, sign = O.hash_draw(2024, t, s, m, n)
+            S = O.sketch_matrix(m, s, bucket, sign)
+            STS = S.T @ S
+            assert np.array_equal(np.diag(STS), np.ones(n))  # exact: s * (1/sqrt(s))^2 = 1 for s = 1, 4
+            acc_sts += STS
+            acc_sst += S @ S.T
+        mean_sts = acc_sts / trials
+        off = mean_sts[~np.eye(n, dtype=bool)]
+        # off-diagonal entries: each draw contributes +-1/s w.p. 1/mb per block -> sd <= 1/sqrt(trials*mb)
+        assert np.abs(off).max() < 6 / np.sqrt(trials * (m // s))
+        assert abs(off.mean()) < 4 / np.sqrt(trials * (m // s) * off.size)
+        mean_sst = acc_sst / trials
+        assert np.allclose(np.diag(mean_sst), n / m, rtol=0.1)
+        assert np.abs(mean_sst[~np.eye(m, dtype=bool)]).max() < 0.15
+
+
+# -------------------------------------------------------------- sketch ----
+@pytest.mark.parametrize("s", [1, 2, 4])
+def test_sketch_equals_materialised_product(s):
+    """The streaming pass of Sec. 2 equals S A with S as a dense matrix."""
+    n, d, m = 333, 7, 24
+    rng = np.random.default_rng(0)
+    A = rng.standard_normal((n, d))
+    bucket, sign = O.hash_draw(9, 4, s, m, n)
+    S = O.sketch_matrix(m, s, bucket, sign) * np.sqrt(s)  # raw +-1 entries
+    SA = O.sketch(A, m, s, bucket, sign)
+    assert np.allclose(SA, S @ A, rtol=0, atol=1e-12)
+    # CSR path on the same values
+    rowptr, col, val = synth.csr_uniform(n, d, 3, 1, np.float64)
+    C = O.CSR(n, d, rowptr, col, val)
+    assert np.allclose(O.sketch(C, m, s, bucket, sign), S @ C.todense(), rtol=0, atol=1e-12)
+
+
+def test_sketch_adjoint_dot_product():
+    """<S A, G> = <A, S^T G> for the normalised sketch (adjoint of a linear map)."""
+    n, d, m, s = 500, 6, 32, 4
+    rng = np.random.default_rng(1)
+    A = rng.standard_normal((n, d))
+    G = rng.standard_normal((m, d))
+    bucket, sign = O.hash_draw(1, 0, s, m, n)
+    SA = O.sketch(A, m, s, bucket, sign) / np.sqrt(s)
+    STG = O.sketch_adjoint(G, n, s, bucket, sign)
+    assert abs((SA * G).sum() - (A * STG).sum()) < 1e-10 * np.abs(SA).sum()
+    S = O.sketch_matrix(m, s, bucket, sign)
+    assert np.allclose(STG, S.T @ G, atol=1e-13)
+
+
+# ---------------------------------------------------------------- gram ----
+def test_gram_against_matmul_and_expectation():
+    """H = (1/s) (SA)^T SA + shift I; averaged over draws it tends to A^T A
+    (E[S^T S] = I, App. A), error ~ 1/sqrt(trials)."""
+    n, d, m, s = 400, 5, 40, 2
+    rng = np.random.default_rng(2)
+    A = rng.standard_normal((n, d))
+    acc = np.zeros((d, d))
+    trials = 400
+    for t in range(trials):
+        bucket, sign = O.hash_draw(77, t, s, m, n)
+        SA = O.sketch(A, m, s, bucket, sign)
+        H = O.gram(SA, 1.0 / s, 0.25)
+        assert np.allclose(H, SA.T @ SA / s + 0.25 * np.eye(d), rtol=1e-13, atol=1e-12)
+        acc += H - 0.25 * np.eye(d)
+    G = A.T @ A
+    rel = np.linalg.norm(acc / trials - G) / np.linalg.norm(G)
+    assert rel < 3.0 * np.sqrt(d / m) / np.sqrt(trials) * 3
+
+
+# ------------------------------------------------------------ gradient ----
+def test_resid_grad_is_minus_gradient():
+    """g = A^T (b - A x) = -grad f(x) for f = 1/2 ||Ax - b||^2 (Eq. 1):
+    central differences in FP64; r = b - A x."""
+    n, d = 200, 6
+    rng = np.random.default_rng(3)
+    A = rng.standard_normal((n, d))
+    b = rng.standard_normal(n)
+    x = rng.standard_normal(d)
+    r, g = O.resid_grad(A, b, x, want_r=True)
+    assert np.allclose(r, b - A @ x, rtol=0, atol=1e-12)
+    f = lambda z: 0.5 * np.sum((A @ z - b) ** 2)
+    h = 1e-5
+    fd = np.array([(f(x + h * e) - f(x - h * e)) / (2 * h) for e in np.eye(d)])
+    assert np.allclose(-g, fd, rtol=1e-7, atol=1e-6)
+    rowptr, col, val = synth.csr_uniform(n, d, 2, 4, np.float64)
+    C = O.CSR(n, d, rowptr, col, val)
+    Ad = C.todense()
+    r2, g2 = O.resid_grad(C, b, x, want_r=True)
+    assert np.allclose(r2, b - Ad @ x, atol=1e-12) and np.allclose(g2, Ad.T @ (b - Ad @ x), atol=1e-11)
+
+
+def test_gradient_vanishes_at_xopt():
+    """At x_OPT of OLS the gradient is zero up to rounding."""
+    w = synth.make("ols_dense_fp64", n=4000)
+    xo = O.x_opt_ols_qr(w["A"], w["b"])
+    g = O.resid_grad(w["A"], w["b"], xo)
+    assert np.linalg.norm(g) <= 1e-12 * np.linalg.norm(w["A"]) * np.linalg.norm(w["b"])
+
+
+# ------------------------------------------------------------ OLS step ----
+def test_identity_sketch_gives_xopt_in_one_step():
+    """Eq. 2 with C = R^d and S = I (m = n, h(i) = i) is a Newton step on a
+    quadratic: x^1 = x^0 + (A^T A)^{-1} A^T (b - A x^0) = x_OPT."""
+    n, d = 300, 8
+    rng = np.random.default_rng(4)
+    A = rng.standard_normal((n, d))
+    b = rng.standard_normal(n)
+    bucket = np.arange(n, dtype=np.int32)[None, :]
+    sign = np.ones((1, n), np.int8)
+    SA = O.sketch(A, n, 1, bucket, sign)
+    H = O.gram(SA, 1.0)
+    x0 = rng.standard_normal(d)
+    x1 = x0 + O.chol_solve(H, O.resid_grad(A, b, x0))
+    xl = np.linalg.lstsq(A, b, rcond=None)[0]
+    assert np.allclose(x1, xl, rtol=1e-12, atol=1e-12)
+
+
+# --------------------------------------------------------------- x_OPT ----
+def test_xopt_solvers_agree():
+    """Householder QR, refined normal equations and LAPACK lstsq give the
+    same x_OPT on a 20000 x 50 problem."""
+    w = synth.make("ols_dense_fp64")
+    xq = O.x_opt_ols_qr(w["A"], w["b"])
+    xn = O.x_opt_ols_normal(w["A"], w["b"])
+    xl = np.linalg.lstsq(w["A"], w["b"], rcond=None)[0]
+    G = w["A"].T @ w["A"]
+    assert O.err_A(xq, xl, G) < 1e-13 and O.err_A(xn, xl, G) < 1e-13
+
+
+def test_err_metric_definition():
+    """||v||_A = n^{-1/2} ||A v|| (Sec. 1); err_A is the ratio of two of them."""
+    rng = np.random.default_rng(5)
+    A = rng.standard_normal((50, 4))
+    x, xo = rng.standard_normal(4), rng.standard_normal(4)
+    nA = lambda v: np.linalg.norm(A @ v) / np.sqrt(50)
+    assert abs(O.err_A(x, xo, A.T @ A) - nA(x - xo) / nA(xo)) < 1e-14
+
+
+# ---------------------------------------------------------- l1-ball QP ----
+@pytest.mark.parametrize("seed", range(12))
+def test_l1_qp_against_bruteforce(seed):
+    """The exact l1-ball subproblem of Eq. 2 (Sec. 3: 'solved exactly') equals
+    brute force over every face of the ball, d <= 6."""
+    rng = np.random.default_rng(100 + seed)
+    d = 2 + seed % 5
+    M = rng.standard_normal((3 * d, d))
+    H = M.T @ M + 0.1 * np.eye(d)
+    g = rng.standard_normal(d) * 3
+    xt = rng.standard_normal(d) * 0.3
+    R = 0.2 + rng.random() * 1.5
+    x = O.l1_ball_qp(H, g, xt, R)
+    xb = O.l1_ball_qp_bruteforce(H, g, xt, R)
+    assert np.allclose(x, xb, rtol=1e-10, atol=1e-12)
+    assert np.abs(x).sum() <= R * (1 + 1e-12)
+    assert O.l1_kkt_residual(H, g, xt, R, x) < 1e-13
+
+
+def test_l1_projection_properties():
+    """Projection onto the l1 ball (Duchi et al. 2008): feasible, idempotent,
+    on the boundary when the input is outside, and the variational
+    inequality <v - p, y - p> <= 0 for feasible y."""
+    rng = np.random.default_rng(6)
+    for _ in range(50):
+        v = rng.standard_normal(9) * 3
+        R = rng.random() * 4 + 0.1
+        p = O.project_l1_ball(v, R)
+        assert np.abs(p).sum() <= R * (1 + 1e-12)
+        assert np.allclose(O.project_l1_ball(p, R), p)
+        if np.abs(v).sum() > R:
+            assert abs(np.abs(p).sum() - R) < 1e-12
+        for _ in range(5):
+            y = O.project_l1_ball(rng.standard_normal(9) * 5, R)
+            assert (v - p) @ (y - p) <= 1e-10
+
+
+def test_l1_qp_kkt_at_dimension_200():
+    """The QP at the lasso workload's dimension reaches an exact KKT point."""
+    rng = np.random.default_rng(7)
+    d = 200
+    M = rng.standard_normal((2000, d))
+    H = M.T @ M / 2000 * 1000
+    xs = synth.sparse_truth(d, 20, 1)
+    g = H @ xs * 1.0 + rng.standard_normal(d)
+    R = 0.5 * np.abs(xs).sum()
+    x = O.l1_ball_qp(H, g, np.zeros(d), R)
+    assert O.l1_kkt_residual(H, g, np.zeros(d), R, x) < 1e-12
+
+
+# ------------------------------------------------------- IHS iteration ----
+def _gaussian_rate(m, d):
+    """E||e'||^2/||e||^2 for a Gaussian sketch (inverse-Wishart moments); a
+    reference value for the per-step contraction, derived here, not printed
+    in the paper."""
+    return np.sqrt(1 - 2 * m / (m - d - 1) + m * m * (m - 1) / ((m - d) * (m - d - 1) * (m - d - 3)))
+
+
+def test_ihs_ols_converges_geometrically():
+    """Thm. 1: the error in the A-seminorm contracts by a factor eps0 < 1/2
+    per step, reaching 1e-10 in Theta(log 1/eps) steps.  20000 x 50,
+    CountSketch m = 10 d."""
+    w = synth.make("ols_dense_fp64")
+    A, b = w["A"], w["b"]
+    G = A.T @ A
+    xo = O.x_opt_ols_qr(A, b)
+    xs = O.ihs(A, b, O.OLS, 0.0, 500, 1, 0, 30)
+    err = np.array([O.err_A(x, xo, G) for x in xs])
+    assert err[0] == 1.0
+    ratios = err[1:20] / err[:19]
+    med = np.median(ratios)
+    ref = _gaussian_rate(500, 50)
+    assert med < 0.5 and 0.7 * ref < med < 1.3 * ref
+    assert err[30] <= 1e-10
+
+
+def test_ihs_lasso_converges_to_xopt():
+    """Eq. 2 over the l1 ball converges to the constrained x_OPT (Thm. 1),
+    here on a 20000 x 200 CSR lasso with SJLT s = 4, m = 2000."""
+    w = synth.make("lasso_csr_fp64", n=20000)
+    C = O.CSR(w["n"], w["d"], w["rowptr"], w["col"], w["val"])
+    xo = O.x_opt_l1(C, w["b"], w["param"])
+    G = C.gram()
+    xs = O.ihs(C, w["b"], O.L1_BALL, w["param"], 2000, 4, 0, 25)
+    err = [O.err_A(x, xo, G) for x in xs]
+    assert err[-1] < 1e-10
+    assert np.abs(xs[-1]).sum() <= w["param"] * (1 + 1e-12)
+
+
+def test_ihs_ridge_converges():
+    """Ridge (sketched Hessian plus lam I, exact gradient minus lam x)
+    converges to (A^T A + lam I)^{-1} A^T b."""
+    w = synth.make("ridge_dense", n=8192, d=32, m=320)
+    A = w["A"].astype(np.float64)
+    xo = O.x_opt_ols_normal(A, w["b"], lam=w["param"])
+    xs = O.ihs(A, w["b"], O.RIDGE, w["param"], 320, 1, 0, 30)
+    assert O.err_A(xs[-1], xo, A.T @ A) < 1e-10
+
+
+def test_resume_is_exact():
+    """Counter-based sketches make a resumed run identical: 10 steps equal
+    4 steps then 6 more from x^4 starting at counter 4."""
+    w = synth.make("ols_dense_fp64", n=3000, d=10, m=100)
+    xs = O.ihs(w["A"], w["b"], O.OLS, 0.0, 100, 1, 3, 10)
+    ys = O.ihs(w["A"], w["b"], O.OLS, 0.0, 100, 1, 3, 6, x0=xs[4], t0=4)
+    assert np.array_equal(xs[10], ys[6])
+
+
+# ------------------------------------------------------------- adjoint ----
+def test_ridge_adjoint_against_central_differences():
+    """dL/db = A v and dL/dA = r v^T - (A v) x^T for L = ||x(A, b) - x_t||^2,
+    x = (A^T A + lam I)^{-1} A^T b; central differences h = 1e-6 in FP64."""
+    rng = np.random.default_rng(8)
+    n, d, lam = 60, 5, 1e-3
+    A = rng.standard_normal((n, d))
+    b = rng.standard_normal(n)
+    xt = rng.standard_normal(d)
+
+    def loss(A_, b_):
+        x = np.linalg.solve(A_.T @ A_ + lam * np.eye(d), A_.T @ b_)
+        return np.sum((x - xt) ** 2)
+
+    x, dLdb, dLdA = O.ridge_adjoint(A, b, lam, None if False else 2 * (np.linalg.solve(A.T @ A + lam * np.eye(d), A.T @ b) - xt))
+    h = 1e-6
+    fd_b = np.array([(loss(A, b + h * e) - loss(A, b - h * e)) / (2 * h) for e in np.eye(n)])
+    assert np.linalg.norm(fd_b - dLdb) <= 1e-6 * np.linalg.norm(dLdb)
+    fd_A = np.zeros_like(A)
+    for i in range(n):
+        for j in range(d):
+            E = np.zeros_like(A)
+            E[i, j] = h
+            fd_A[i, j] = (loss(A + E, b) - loss(A - E, b)) / (2 * h)
+    assert np.linalg.norm(fd_A - dLdA) <= 1e-6 * np.linalg.norm(dLdA)
+
+
+# ----------------------------------------------- planted-mistake checks ----
+def test_pins_catch_planted_mistakes(monkeypatch):
+    """A dropped sign, a transposed Gram or an off-by-one gradient term in the
+    oracle each fails one of the pins above (mistakes planted on the CPU)."""
+    n, d, m = 200, 5, 16
+    rng = np.random.default_rng(9)
+    A = rng.standard_normal((n, d))
+    b = rng.standard_normal(n)
+    bucket, sign = O.hash_draw(9, 4, 1, m, n)
+    S = O.sketch_matrix(m, 1, bucket, sign)
+    # dropped sign
+    SA_bad = O.sketch(A, m, 1, bucket, np.ones_like(sign))
+    assert not np.allclose(SA_bad, S @ A)
+    # gradient missing the residual's b term fails the finite-difference pin
+    x = rng.standard_normal(d)
+    g_bad = -(A.T @ (A @ x))
+    f = lambda z: 0.5 * np.sum((A @ z - b) ** 2)
+    fd = np.array([(f(x + 1e-5 * e) - f(x - 1e-5 * e)) / 2e-5 for e in np.eye(d)])
+    assert not np.allclose(-g_bad, fd, rtol=1e-7, atol=1e-6)
+    # a step with the wrong sign diverges instead of contracting
+    H = O.gram(O.sketch(A, m, 1, bucket, sign), 1.0)
+    x1 = x - O.chol_solve(H, O.resid_grad(A, b, x))
+    xo = np.linalg.lstsq(A, b, rcond=None)[0]
+    assert O.err_A(x1, xo, A.T @ A) > O.err_A(x, xo, A.T @ A)
+
+
+# --------------------------------------------------------------- synth ----
+def test_synth_recipes():
+    """Input recipes: exact nnz per row, distinct sorted columns, AR(1)
+    correlation rho^|i-j|, Zipf column frequencies."""
+    rowptr, col, val = synth.csr_uniform(5000, 200, 2, 0)
+    assert np.all(np.diff(rowptr) == 2)
+    c = col.reshape(-1, 2)
+    assert np.all(c[:, 0] < c[:, 1])
+    A = synth.dense_ar1(200000, 6, 0.5, 0)
+    C = np.corrcoef(A.T.astype(np.float64))
+    for k in range(1, 4):
+        assert abs(C[0, k] - 0.5 ** k) < 0.01
+    rowptr, col, val = synth.csr_zipf(100000, 1000, 5, 1.1, 0)
+    c = col.reshape(-1, 5)
+    assert np.all(np.diff(c, axis=1) > 0)
+    freq = np.bincount(col, minlength=1000) / col.size
+    # the hottest column holds roughly p_1 of the draws (rejection of repeats lowers it a little)
+    p1 = synth.zipf_probs(1000, 1.1)[0]
+    assert 0.6 * p1 < freq.max() < 1.05 * p1
