@@ -1,0 +1,414 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 Iterative Hessian Sketch library.
+
+Metric: IHS time-to-1e-10 relative error (||x - x_OPT||_A / ||x_OPT||_A) of
+the mixed-precision form, beside the plain FP64 form, and the SA sketch
+kernel's bandwidth against the measured HBM peak.
+
+Workload (default): OLS on a dense 1,048,576 x 500 FP32 matrix with rows
+N(0, Sigma), Sigma_ij = 0.5^|i-j|, b = A x* + 0.1 N(0,1), CountSketch
+m = 5000 (10 d), seed 0.  A "step" is one whole solve from x = 0 for the
+number of iterations the form needs to reach 1e-10 (found once, off the
+clock, against x_OPT).  A (2.1 GB) is far larger than L2, so every pass
+streams from HBM.
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+Prints one JSON line (rank 0).
+"""
+import os
+
+for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
+
+import argparse
+import hashlib
+import json
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "IHS time-to-1e-10 rel. error (mixed vs FP64); SA sketch GB/s vs HBM peak"
+FALLBACK_HBM = 6800.0
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return FALLBACK_HBM, "fallback"
+
+
+# ---------------------------------------------------------------- clocks ---
+class Clocks:
+    """nvidia-smi samples (200 ms) while the timed region runs."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index, self.rows, self.proc = index, [], None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) == 7:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": len(self.rows)}
+        if not self.rows:
+            return out
+        def num(v):
+            try:
+                return float(v)
+            except ValueError:
+                return None
+        sm = [num(r[0]) for r in self.rows if num(r[0])]
+        out["sm_mhz"] = statistics.median(sm) if sm else None
+        out["sm_max_mhz"] = max((num(r[1]) or 0) for r in self.rows)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for k, nm in enumerate(names):
+            if any(r[3 + k].lower() == "active" for r in self.rows):
+                out["reasons"].append(nm)
+        return out
+
+
+# ------------------------------------------------------------ CPU oracle ---
+def oracle_time_to_tol(w, n_sample, T, seed=0):
+    """The FP64 CPU oracle, timed on a bounded sample of the workload: one IHS
+    iteration (sketch + Gram + gradient + Cholesky step) on the first
+    n_sample rows, with the O(n) passes scaled to the full n and the O(m d^2)
+    Gram kept whole; times T iterations.  Returns (ms, description)."""
+    import oracle as O
+    A = np.ascontiguousarray(w["A"][:n_sample], dtype=np.float64)
+    b = np.ascontiguousarray(w["b"][:n_sample])
+    m, s, n = w["m"], w["s"], w["n"]
+    x = np.zeros(A.shape[1])
+    t0 = time.perf_counter()
+    bucket, sign = O.hash_draw(seed, 0, s, m, n_sample)
+    SA = O.sketch(A, m, s, bucket, sign)
+    g = O.resid_grad(A, b, x)
+    t1 = time.perf_counter()
+    H = O.gram(SA, 1.0 / s)
+    x = x + O.chol_solve(H, g)
+    t2 = time.perf_counter()
+    per_iter = (t1 - t0) * (n / n_sample) + (t2 - t1)
+    desc = ("one oracle iteration on the first %d of %d rows (O(n) passes scaled by %.1f, "
+            "m x d Gram whole), times %d iterations" % (n_sample, n, n / n_sample, T))
+    return per_iter * T * 1e3, desc, (t2 - t0)
+
+
+def oracle_iterations_proxy():
+    """Iterations the FP64 oracle needs to reach 1e-10 on a proxy of the
+    workload with the same m/d = 10 and design (65536 x 100, m = 1000)."""
+    import oracle as O
+    w = synth.make("ols_dense_ar1", n=65536, d=100, m=1000)
+    A = w["A"].astype(np.float64)
+    G = A.T @ A
+    xo = O.x_opt_ols_normal(A, w["b"])
+    xs = O.ihs(A, w["b"], O.OLS, 0.0, 1000, 1, 0, 60)
+    for t, x in enumerate(xs):
+        if O.err_A(x, xo, G) <= 1e-10:
+            return t
+    return 60
+
+
+# ----------------------------------------------------------- GPU harness ---
+def x_opt_gpu(A, b):
+    """x_OPT off the clock: FP64 normal equations from the FP32 data (exactly
+    promoted), Cholesky, three refinement steps with FP64 residuals."""
+    import torch
+    d = A.shape[1]
+    G = torch.zeros((d, d), dtype=torch.float64, device=A.device)
+    rhs = torch.zeros(d, dtype=torch.float64, device=A.device)
+    CH = 1 << 17
+    for i in range(0, A.shape[0], CH):
+        Ac = A[i:i + CH].double()
+        G += Ac.T @ Ac
+        rhs += Ac.T @ b[i:i + CH]
+    Lc = torch.linalg.cholesky(G)
+    x = torch.cholesky_solve(rhs[:, None], Lc)[:, 0]
+    for _ in range(3):
+        g = torch.zeros(d, dtype=torch.float64, device=A.device)
+        for i in range(0, A.shape[0], CH):
+            Ac = A[i:i + CH].double()
+            g += Ac.T @ (b[i:i + CH] - Ac @ x)
+        x = x + torch.cholesky_solve(g[:, None], Lc)[:, 0]
+    return x, G
+
+
+def err_A(x, xo, G):
+    e = x - xo
+    return float(((e @ G @ e).clamp_min(0).sqrt() / (xo @ G @ xo).sqrt()).item())
+
+
+def iterations_to(solver, xo, G, tol, cap=80):
+    import torch
+    x = torch.zeros(solver.d, dtype=torch.float64, device=xo.device)
+    errs = []
+    for t in range(cap):
+        solver.solve(x, t0=t, iters=1)
+        errs.append(err_A(x, xo, G))
+        if errs[-1] <= tol:
+            return t + 1, errs
+    return cap, errs
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("sketch.cu", "grad.cu", "common.cuh", "hash_sort.cu"):
+        h.update(open(os.path.join(ROOT, "paper_1910_14166_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def traffic_for(kernel):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on
+    the current kernel sources (else null)."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    if d.get("source_hash") != kernel_source_hash():
+        return None
+    return d.get("kernels", {}).get(kernel)
+
+
+def run_ours(args, rank, world):
+    import torch
+    import paper_1910_14166_gb300 as ihs
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    w = synth.make(args.workload, n=args.n, seed=rank)
+    n, d, m, s = w["n"], w["d"], w["m"], w["s"]
+    A = torch.from_numpy(w["A"]).cuda()
+    b = torch.from_numpy(w["b"]).cuda()
+    xo, G = x_opt_gpu(A, b)
+
+    mixed = ihs.IHS(A, b, kind="ols", m=m, s=s, seed=0, precision=args.precision)
+    plain = ihs.IHS(A, b, kind="ols", m=m, s=s, seed=0, precision="fp64")
+    T_mixed, errs_mixed = iterations_to(mixed, xo, G, 1e-10)
+    T_plain, errs_plain = iterations_to(plain, xo, G, 1e-10)
+
+    def solve_steps(solver, T, K):
+        x = torch.zeros(d, dtype=torch.float64, device="cuda")
+        for _ in range(K):
+            x.zero_()
+            solver.solve(x, t0=0, iters=T)
+        return x
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    def timed(solver, T, K, W, profile=False):
+        solve_steps(solver, T, W)
+        if profile:
+            solver.profile(True)
+        barrier()
+        st = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        x = solve_steps(solver, T, K)
+        e1.record(st)
+        barrier()
+        ms = e0.elapsed_time(e1) / K
+        prof = solver.profile_read() if profile else None
+        if profile:
+            solver.profile(False)
+        return ms, x, prof
+
+    clocks = Clocks(int(os.environ.get("LOCAL_RANK", "0")))
+    clocks.start()
+    ms_mixed, x_m, prof = timed(mixed, T_mixed, args.steps, args.warmup, profile=True)
+    clk = clocks.stop()
+    ms_plain, x_p, prof_plain = timed(plain, T_plain, max(1, args.steps // 2), 1, profile=True)
+    err_final = err_A(x_m, xo, G)
+    err_final_plain = err_A(x_p, xo, G)
+
+    # max over ranks
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms_mixed, ms_plain], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_mixed, ms_plain = t.tolist()
+
+    # per-kernel roofline from the stage events of the timed region
+    hbm, hbm_kind = peaks()
+    ms_stage, cnt, launches = prof
+    a_bytes = n * d * 4
+    alg = {"sketch": a_bytes + m * d * 4, "grad": a_bytes + n * 8}
+    kernels = {}
+    for k in ("sketch", "grad"):
+        avg = ms_stage[k] / max(1, cnt[k])
+        gbs = alg[k] / (avg * 1e-3) / 1e9
+        kernels[k] = {"ms_avg": round(avg, 4), "algorithmic_bytes": alg[k],
+                      "GB_s": round(gbs, 1), "frac": round(gbs / hbm, 3)}
+    dominant = max(("sketch", "grad"), key=lambda k: ms_stage[k])
+    kd = kernels[dominant]
+    roofline = {"kernel": "k_sketch_dense" if dominant == "sketch" else "k_rg_dense_f32",
+                "bound": "hbm", "achieved": kd["GB_s"], "peak": hbm, "unit": "GB/s",
+                "frac": kd["frac"], "peak_kind": hbm_kind,
+                "traffic": traffic_for("k_sketch_dense" if dominant == "sketch" else "k_rg_dense_f32")}
+    sk = kernels["sketch"]
+
+    # end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        A_h = torch.from_numpy(w["A"]).pin_memory()
+        b_h = torch.from_numpy(w["b"]).pin_memory()
+        A_d = torch.empty_like(A)
+        b_d = torch.empty_like(b)
+        del mixed
+        st = torch.cuda.current_stream()
+        times = []
+        for it in range(args.warmup + args.steps):
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            A_d.copy_(A_h, non_blocking=True)
+            b_d.copy_(b_h, non_blocking=True)
+            sv = ihs.IHS(A_d, b_d, kind="ols", m=m, s=s, seed=0, precision=args.precision)
+            x, _ = sv.solve(iters=T_mixed)
+            x_host = x.cpu()
+            e1.record(st)
+            torch.cuda.synchronize()
+            sv.close()
+            if it >= args.warmup:
+                times.append(e0.elapsed_time(e1))
+        e2e = {"value": round(statistics.mean(times), 3), "unit": "ms",
+               "h2d_bytes_per_step": int(A_h.numel() * 4 + b_h.numel() * 8),
+               "d2h_bytes_per_step": int(x_host.numel() * 8)}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        import multiprocessing as mp  # noqa: F401  (oracle runs in this process; no pool)
+        ms_cpu, desc, spent = oracle_time_to_tol(w, args.cpu_rows, T_plain)
+        cpu = {"value": round(ms_cpu, 1), "unit": "ms", "cores": 1, "kind": "oracle",
+               "sample": desc, "cpu_seconds": round(spent, 2)}
+
+    res = {
+        "metric": METRIC,
+        "value": round(ms_mixed, 3),
+        "unit": "ms",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(ms_mixed, 3),
+        "higher_is_better": False,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32 data; %s Gram; f64-class gradient" % args.precision,
+        "data": "synthetic",
+        "config": {"workload": "%s n=%d d=%d m=%d s=%d CountSketch seed 0 (OLS, AR(1) rho=0.5 rows)"
+                   % (args.workload, n, d, m, s),
+                   "precision": args.precision, "l2": "inputs larger than L2 (A = %.2f GB)" % (a_bytes / 1e9),
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "iters_to_1e-10": {"mixed": T_mixed, "fp64": T_plain},
+        "final_err": {"mixed": err_final, "fp64": err_final_plain},
+        "fp64_time_to_1e-10_ms": round(ms_plain, 3),
+        "mixed_speedup_vs_fp64": round(ms_plain / ms_mixed, 3),
+        "sketch_GB_s": sk["GB_s"],
+        "sketch_frac_of_hbm": sk["frac"],
+        "kernels": kernels,
+        "stage_ms_per_iter": {k: round(v / max(1, cnt[k]), 4) for k, v in ms_stage.items()},
+        "stage_ms_per_iter_fp64": {k: round(v / max(1, prof_plain[1][k]), 4)
+                                   for k, v in prof_plain[0].items()},
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": int(launches),
+        "clocks": clk,
+    }
+    return res
+
+
+def run_reference(args, rank, world):
+    """The oracle (plain FP64 CPU IHS) as the reference arm, on the same
+    workload and metric, each step a bounded sample (see oracle_time_to_tol)."""
+    if rank != 0:
+        return None
+    nrows = args.cpu_rows
+    w = synth.make(args.workload, n=nrows, seed=0)
+    w["n"] = synth.WORKLOADS[args.workload]["n"] if args.n is None else args.n
+    T = oracle_iterations_proxy()
+    vals = []
+    spent = 0.0
+    for it in range(args.warmup + args.steps):
+        ms, desc, sp = oracle_time_to_tol(w, nrows, T)
+        spent += sp
+        if it >= args.warmup:
+            vals.append(ms)
+    v = round(statistics.mean(vals), 1)
+    return {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "ms", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": v, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "%s n=%d d=%d m=%d s=%d CountSketch seed 0" %
+                   (args.workload, w["n"], w["d"], w["m"], w["s"])},
+        "iters_to_1e-10": {"oracle_proxy": T},
+        "cpu_baseline": {"value": v, "unit": "ms", "cores": 1, "kind": "oracle", "sample": desc,
+                         "cpu_seconds": round(spent, 2)},
+        "e2e": {"value": v, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="ols_dense_ar1")
+    ap.add_argument("--precision", default="tf32", choices=["tf32", "bf16"])
+    ap.add_argument("--n", type=int, default=None)
+    ap.add_argument("--cpu-rows", type=int, default=131072)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if world > 1 and args.impl == "ours":
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        dist.init_process_group("nccl")
+    res = run_reference(args, rank, world) if args.impl == "reference" else run_ours(args, rank, world)
+    if rank == 0 and res is not None:
+        print(json.dumps(res), flush=True)
+    if world > 1 and args.impl == "ours":
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

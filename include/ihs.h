@@ -1,0 +1,218 @@
+/*
+ * ihs.h -- C ABI of the GB300 Iterative Hessian Sketch library (libihs.so).
+ *
+ * The method is the Iterative Hessian Sketch with sparse embeddings of
+ * Cormode & Dickens, "Iterative Hessian Sketch in Input Sparsity Time"
+ * (arXiv 1910.14166).  For a problem (A, b, C) of Eq. 1,
+ *     x_OPT = argmin_{x in C} f(x),  f(x) = 1/2 ||A x - b||_2^2,
+ * each iteration draws a fresh CountSketch / SJLT S (Sec. 2), forms S A,
+ * the approximate Hessian (SA)^T SA (Sec. 1), the exact gradient
+ * A^T (b - A x^t), and solves the quadratic program of Eq. 2:
+ *     x^{t+1} = argmin_{x in C} 1/2 ||S A (x - x^t)||^2 - <A^T (b - A x^t), x - x^t>.
+ *
+ * Conventions for every entry point:
+ *   - All array arguments are DEVICE pointers unless a comment says HOST.
+ *     Matrices are row-major.  Nothing is copied: A and b are borrowed and
+ *     must stay valid and unchanged for the life of the context.
+ *   - Work is issued on the context's CUDA stream (or the stream argument of
+ *     the stateless calls) and is asynchronous unless the comment says the
+ *     call synchronises.  A context is not thread-safe.
+ *   - Every call returns an ihs_status; nothing throws across the ABI.  A
+ *     failure detected on the device (Hessian not positive definite, a QP
+ *     that did not converge, a bounded wait that ran out) is written to a
+ *     device status word and returned by the next call that synchronises
+ *     (ihs_solve, ihs_sync, ihs_adjoint).
+ *   - Sizes: n < 2^31 rows, 1 <= d <= 1024 columns, s divides m, m >= d.
+ */
+#ifndef IHS_H_
+#define IHS_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ihs_ctx ihs_ctx;
+
+typedef enum {
+  IHS_OK = 0,
+  IHS_ERR_ARG = 1,            /* invalid argument or shape                      */
+  IHS_ERR_CUDA = 2,           /* a CUDA runtime call failed                     */
+  IHS_ERR_OOM = 3,            /* device allocation failed                       */
+  IHS_ERR_NOT_SPD = 4,        /* sketched Hessian not positive definite         */
+  IHS_ERR_NOT_CONVERGED = 5,  /* the inner QP / PCG did not reach its tolerance */
+  IHS_ERR_NONFINITE = 6,      /* NaN or Inf met in the data or the iterate      */
+  IHS_ERR_TIMEOUT = 7,        /* a bounded device wait gave up                  */
+  IHS_ERR_UNSUPPORTED = 8     /* valid request outside this build's limits      */
+} ihs_status;
+
+/* Matrix storage (Eq. 1's A).  DENSE: val is n x d row-major with leading
+ * dimension ld >= d (elements).  CSR: rowptr[n+1] (int32 or int64, see
+ * rowptr_i64), col[nnz] int32 in [0, d), val[nnz]; columns within a row
+ * must be distinct. */
+enum { IHS_DENSE = 0, IHS_CSR = 1 };
+enum { IHS_F64 = 0, IHS_F32 = 1 };
+
+typedef struct {
+  int kind;            /* IHS_DENSE or IHS_CSR                         */
+  int dtype;           /* IHS_F64 or IHS_F32 (values)                  */
+  int64_t n, d;        /* rows, columns                                */
+  int64_t ld;          /* DENSE: leading dimension in elements          */
+  const void* val;     /* values                                        */
+  const int32_t* col;  /* CSR column indices (NULL for DENSE)           */
+  const void* rowptr;  /* CSR row pointers (NULL for DENSE)             */
+  int rowptr_i64;      /* CSR: 1 if rowptr is int64, 0 if int32         */
+  int64_t nnz;         /* CSR: number of stored entries                 */
+} ihs_matrix;
+
+/* Constraint set C of Eq. 1 (Sec. 1 lists OLS and the p-norm balls).
+ *   IHS_OLS      C = R^d                                  param unused
+ *   IHS_L1_BALL  C = {x : ||x||_1 <= param}  (LASSO)       param = radius > 0
+ *   IHS_RIDGE    f(x) + (param/2) ||x||^2, C = R^d         param = lambda >= 0
+ * Ridge is not in the paper; it is the squared-l2 penalty beside the p = 2
+ * ball, with the penalty kept exact (not sketched). */
+enum { IHS_OLS = 0, IHS_L1_BALL = 1, IHS_RIDGE = 2 };
+
+typedef struct {
+  int kind;
+  double param;
+} ihs_constraint;
+
+/* Arithmetic of the sketch and Hessian (the residual and gradient are
+ * FP64-class in every mode).
+ *   IHS_PREC_FP64  plain: SA accumulated in FP64, FP64 Gram, FP64 Cholesky.
+ *   IHS_PREC_TF32  mixed: SA accumulated in FP32, Gram on the tensor cores
+ *                  from TF32 inputs with FP32 accumulation, FP32 factor.
+ *   IHS_PREC_BF16  mixed: as TF32 with BF16 Gram inputs. */
+enum { IHS_PREC_FP64 = 0, IHS_PREC_TF32 = 1, IHS_PREC_BF16 = 2 };
+
+typedef struct {
+  int64_t m;          /* sketch rows (projection dimension, Sec. 2)          */
+  int s;              /* nonzeros per column of S: 1 = CountSketch, >1 = SJLT */
+  uint64_t seed;      /* sketch seed; iteration t uses counter t             */
+  int precision;      /* IHS_PREC_*                                          */
+  int qp_max_iter;    /* l1 ball: FISTA iteration cap per QP (0 = default)   */
+  double qp_tol;      /* l1 ball: KKT acceptance tolerance (0 = default)     */
+} ihs_options;
+
+typedef struct {
+  int iters;            /* iterations taken                                */
+  int qp_fista_iters;   /* l1 ball: FISTA iterations spent, summed          */
+  int status;           /* ihs_status of the device status word             */
+  double step_norm;     /* ||x^{t+1} - x^t||_inf of the last step            */
+} ihs_report;
+
+/* ihs_create -- validate (A, b, C, options) and allocate every workspace.
+ * A: matrix descriptor (HOST struct; its arrays are DEVICE, borrowed).
+ * b: DEVICE, n doubles, borrowed.  C, opt: HOST structs, copied.
+ * stream: a cudaStream_t (NULL = legacy default stream).  For CSR input a
+ * column-major (CSC) copy of A is built once here and owned by the context.
+ * Synchronises.  Errors: IHS_ERR_ARG for shapes (m % s != 0, m < d, d > 1024,
+ * n >= 2^31, bad kind/dtype), IHS_ERR_OOM, IHS_ERR_CUDA. */
+ihs_status ihs_create(ihs_ctx** out, const ihs_matrix* A, const double* b,
+                      const ihs_constraint* C, const ihs_options* opt,
+                      void* stream);
+
+/* ihs_sketch -- draw S for counter t (Sec. 2) and form SA and the
+ * approximate Hessian H = (1/s) (SA)^T SA (+ lambda I for ridge) inside the
+ * context (Sec. 1; Eq. 2's quadratic term).  Asynchronous. */
+ihs_status ihs_sketch(ihs_ctx* ctx, int64_t t);
+
+/* ihs_gradient -- g = A^T (b - A x) (minus lambda x for ridge), the linear
+ * term of Eq. 2, and optionally r = b - A x.  x: DEVICE d doubles (in);
+ * g: DEVICE d doubles (out); r: DEVICE n doubles or NULL.  Asynchronous. */
+ihs_status ihs_gradient(ihs_ctx* ctx, const double* x, double* g, double* r);
+
+/* ihs_step -- one step of Eq. 2 with the Hessian of the last ihs_sketch:
+ * x (DEVICE, d doubles) holds x^t on entry and x^{t+1} on return.  OLS and
+ * ridge: Cholesky solve of H delta = g.  l1 ball: the exact QP over the ball.
+ * Asynchronous; device failures surface at the next synchronising call. */
+ihs_status ihs_step(ihs_ctx* ctx, double* x);
+
+/* ihs_solve -- iterations t = t0 .. t0+iters-1 of ihs_sketch + ihs_step from
+ * the x given (DEVICE, d doubles; in: x^{t0}, out: x^{t0+iters}).  The run
+ * is a pure function of (A, b, C, options, x, t0), so stopping after k
+ * iterations and resuming with t0 + k reproduces it exactly.  rep: HOST,
+ * nullable.  Synchronises and returns the device status. */
+ihs_status ihs_solve(ihs_ctx* ctx, double* x, int64_t t0, int iters,
+                     ihs_report* rep);
+
+/* ihs_sync -- wait for the context's stream and return the device status
+ * word (then clear it). */
+ihs_status ihs_sync(ihs_ctx* ctx);
+
+/* ihs_get_sketch -- copy the last sketch out, for inspection and tests.
+ * SA_out: DEVICE buffer for the m x d row-major raw sketch SA (entries +-1,
+ * SJLT normalisation not applied), FP64 for precision FP64 and FP32 for the
+ * mixed modes (*SA_dtype, HOST, gets IHS_F64 or IHS_F32).  H_out: DEVICE
+ * d x d doubles, the Hessian actually used ((1/s) SA^T SA + lambda I).
+ * scale: HOST, gets 1/s.  Every output may be NULL.  Stream-ordered copies;
+ * IHS_ERR_ARG if no sketch has been formed yet. */
+ihs_status ihs_get_sketch(ihs_ctx* ctx, void* SA_out, int* SA_dtype, double* H_out,
+                          double* scale);
+
+/* ihs_adjoint -- reverse-mode derivative of a loss L(x) of the ridge / OLS
+ * solution x = (A^T A + lambda I)^{-1} A^T b (not in the paper).
+ * v = (A^T A + lambda I)^{-1} dLdx is solved by conjugate gradients
+ * preconditioned with the Cholesky factor of the last sketched Hessian; then
+ *   dL/db = A v                  (DEVICE, n doubles, nullable)
+ *   dL/dA = r v^T - (A v) x^T    (DEVICE, n x d row-major in A's dtype, nullable)
+ * with r = b - A x.  x, dLdx: DEVICE d doubles.  Requires an earlier
+ * ihs_sketch.  rep (HOST, nullable) gets the CG iteration count in iters.
+ * Synchronises.  IHS_ERR_NOT_CONVERGED if CG misses 1e-13 relative. */
+ihs_status ihs_adjoint(ihs_ctx* ctx, const double* x, const double* dLdx,
+                       double* dLdb, void* dLdA, ihs_report* rep);
+
+/* Stage timing (CUDA events recorded on the context's stream around each
+ * stage of every iteration while enabled) and a count of the library's
+ * kernel launches.  Stages, in order: IHS_ST_SORT (sketch draw and bucket
+ * sort), IHS_ST_SKETCH (the SA kernel), IHS_ST_SKETCH_FIX (straddling and
+ * empty buckets), IHS_ST_GRAM, IHS_ST_FACTOR, IHS_ST_GRAD, IHS_ST_STEP. */
+enum { IHS_ST_SORT = 0, IHS_ST_SKETCH, IHS_ST_SKETCH_FIX, IHS_ST_GRAM, IHS_ST_FACTOR,
+       IHS_ST_GRAD, IHS_ST_STEP, IHS_NSTAGES };
+
+/* ihs_profile -- enable (1) or disable (0) stage timing; enabling clears
+ * the totals and the launch count. */
+ihs_status ihs_profile(ihs_ctx* ctx, int enable);
+
+/* ihs_profile_read -- synchronise and report, per stage, the summed event
+ * time in ms (ms[IHS_NSTAGES], HOST) and the number of timed instances
+ * (count[IHS_NSTAGES], HOST, nullable), and the kernel launches issued by the
+ * library since ihs_profile(ctx, 1) (launches, HOST, nullable). */
+ihs_status ihs_profile_read(ihs_ctx* ctx, double* ms, int* count, int64_t* launches);
+
+/* ihs_destroy -- free every workspace (NULL is a no-op).  Synchronises. */
+void ihs_destroy(ihs_ctx* ctx);
+
+/* ihs_status_str -- static text for a status code. */
+const char* ihs_status_str(ihs_status st);
+
+/* ---------------------------------------------------------------------
+ * Stateless kernels (no context).  Same conventions; stream may be NULL.
+ * --------------------------------------------------------------------- */
+
+/* ihs_hash -- the sketch draw of Sec. 2 for counter t: for block k < s and
+ * row i < n, bucket[k*n + i] = k*(m/s) + h_k(i) (global row of S, int32)
+ * and sign[k*n + i] in {+1, -1} (int8).  The generator is SplitMix64
+ * (Steele, Lea & Flood 2014) used counter-style:
+ *   key_seed = F(seed, 0), key_t = F(key_seed, t), key_tk = F(key_t, k),
+ *   w = F(key_tk, i),  F(x, j) = mix(x + (j + 1) * 0x9E3779B97F4A7C15),
+ * with the SplitMix64 finaliser mix; h_k(i) = (hi32(w) * (m/s)) >> 32 and the
+ * sign is -1 iff bit 0 of w is set.  Errors: IHS_ERR_ARG if m % s != 0. */
+ihs_status ihs_hash(uint64_t seed, int64_t t, int s, int64_t m, int64_t n,
+                    int32_t* bucket, int8_t* sign, void* stream);
+
+/* ihs_sketch_adjoint -- S^T G for the sketch of counter t with entries
+ * sign/sqrt(s): out[i, :] = sum_k sign_k(i) G[bucket_k(i), :] / sqrt(s).
+ * G: DEVICE m x d doubles (row-major), out: DEVICE n x d doubles.  A
+ * gather, one row of out per row of A (the adjoint of Sec. 2's map). */
+ihs_status ihs_sketch_adjoint(uint64_t seed, int64_t t, int s, int64_t m,
+                              int64_t n, int64_t d, const double* G,
+                              double* out, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* IHS_H_ */

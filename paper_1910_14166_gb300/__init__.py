@@ -1,0 +1,263 @@
+"""Python binding of libihs.so, the GB300 Iterative Hessian Sketch library
+(Cormode & Dickens, "Iterative Hessian Sketch in Input Sparsity Time",
+arXiv 1910.14166).
+
+The binding only marshals arguments: every step of the method runs in the
+library's CUDA kernels, reached through the C ABI declared in include/ihs.h
+(same function names).  PyTorch supplies device memory and the current CUDA
+stream.  There is no CPU fallback: if the library cannot be built or loaded,
+importing this package raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+from . import build as _build
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+
+IHS_OK = 0
+STATUS_NAMES = {0: "IHS_OK", 1: "IHS_ERR_ARG", 2: "IHS_ERR_CUDA", 3: "IHS_ERR_OOM",
+                4: "IHS_ERR_NOT_SPD", 5: "IHS_ERR_NOT_CONVERGED", 6: "IHS_ERR_NONFINITE",
+                7: "IHS_ERR_TIMEOUT", 8: "IHS_ERR_UNSUPPORTED"}
+DENSE, CSR = 0, 1
+F64, F32 = 0, 1
+OLS, L1_BALL, RIDGE = 0, 1, 2
+PREC = {"fp64": 0, "tf32": 1, "bf16": 2}
+KIND = {"ols": OLS, "l1": L1_BALL, "ridge": RIDGE}
+
+
+class IHSError(RuntimeError):
+    def __init__(self, status, where=""):
+        self.status = int(status)
+        msg = _lib.ihs_status_str(self.status).decode() if _lib else str(status)
+        super().__init__("%s: %s (%s)" % (where, STATUS_NAMES.get(self.status, "?"), msg))
+
+
+class _Matrix(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("dtype", ctypes.c_int), ("n", ctypes.c_int64),
+                ("d", ctypes.c_int64), ("ld", ctypes.c_int64), ("val", ctypes.c_void_p),
+                ("col", ctypes.c_void_p), ("rowptr", ctypes.c_void_p),
+                ("rowptr_i64", ctypes.c_int), ("nnz", ctypes.c_int64)]
+
+
+class _Constraint(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("param", ctypes.c_double)]
+
+
+class _Options(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int64), ("s", ctypes.c_int), ("seed", ctypes.c_uint64),
+                ("precision", ctypes.c_int), ("qp_max_iter", ctypes.c_int),
+                ("qp_tol", ctypes.c_double)]
+
+
+class _Report(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("qp_fista_iters", ctypes.c_int),
+                ("status", ctypes.c_int), ("step_norm", ctypes.c_double)]
+
+
+def _load():
+    path = _build.build()
+    L = ctypes.CDLL(path)
+    vp, i64, i32, u64, f64 = (ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_uint64,
+                              ctypes.c_double)
+    sig = {
+        "ihs_create": [ctypes.POINTER(vp), ctypes.POINTER(_Matrix), vp,
+                       ctypes.POINTER(_Constraint), ctypes.POINTER(_Options), vp],
+        "ihs_sketch": [vp, i64],
+        "ihs_gradient": [vp, vp, vp, vp],
+        "ihs_step": [vp, vp],
+        "ihs_solve": [vp, vp, i64, i32, ctypes.POINTER(_Report)],
+        "ihs_sync": [vp],
+        "ihs_get_sketch": [vp, vp, ctypes.POINTER(i32), vp, ctypes.POINTER(f64)],
+        "ihs_adjoint": [vp, vp, vp, vp, vp, ctypes.POINTER(_Report)],
+        "ihs_hash": [u64, i64, i32, i64, i64, vp, vp, vp],
+        "ihs_sketch_adjoint": [u64, i64, i32, i64, i64, i64, vp, vp, vp],
+        "ihs_profile": [vp, i32],
+        "ihs_profile_read": [vp, ctypes.POINTER(f64), ctypes.POINTER(i32), ctypes.POINTER(i64)],
+    }
+    for name, args in sig.items():
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = ctypes.c_int
+    L.ihs_destroy.argtypes = [vp]
+    L.ihs_destroy.restype = None
+    L.ihs_status_str.argtypes = [ctypes.c_int]
+    L.ihs_status_str.restype = ctypes.c_char_p
+    return L
+
+
+_lib = _load()
+LIB_PATH = _build.LIB
+STAGES = ["sort", "sketch", "sketch_fix", "gram", "factor", "grad", "step"]
+EXPORTS = ["ihs_create", "ihs_sketch", "ihs_gradient", "ihs_step", "ihs_solve", "ihs_sync",
+           "ihs_get_sketch", "ihs_adjoint", "ihs_destroy", "ihs_status_str", "ihs_hash",
+           "ihs_sketch_adjoint", "ihs_profile", "ihs_profile_read"]
+
+
+def _check(st, where):
+    if st != IHS_OK:
+        raise IHSError(st, where)
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _need_cuda(t, name):
+    if not (isinstance(t, torch.Tensor) and t.is_cuda):
+        raise TypeError("%s must be a CUDA tensor" % name)
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % name)
+
+
+def ihs_hash(seed, t, s, m, n):
+    """Sketch draw of Sec. 2 on the GPU: (bucket int32 [s, n], sign int8 [s, n])."""
+    bucket = torch.empty((s, n), dtype=torch.int32, device="cuda")
+    sign = torch.empty((s, n), dtype=torch.int8, device="cuda")
+    _check(_lib.ihs_hash(seed & 0xFFFFFFFFFFFFFFFF, t, s, m, n, _ptr(bucket), _ptr(sign), _stream()),
+           "ihs_hash")
+    return bucket, sign
+
+
+def ihs_sketch_adjoint(seed, t, s, m, n, G):
+    """S^T G (n x d FP64) for the normalised sketch of counter t."""
+    _need_cuda(G, "G")
+    G = G.to(torch.float64)
+    out = torch.empty((n, G.shape[1]), dtype=torch.float64, device=G.device)
+    _check(_lib.ihs_sketch_adjoint(seed & 0xFFFFFFFFFFFFFFFF, t, s, m, n, G.shape[1], _ptr(G),
+                                   _ptr(out), _stream()), "ihs_sketch_adjoint")
+    return out
+
+
+class IHS:
+    """One problem (A, b, C) of Eq. 1 with its workspaces on the GPU.
+
+    A: a 2-D CUDA tensor (float32 or float64, row-major) or a CSR triple
+    (rowptr int32/int64, col int32, val float32/float64) with shape=(n, d).
+    b: CUDA float64 vector.  The tensors are borrowed and must outlive the
+    object.  kind: 'ols', 'l1' (param = radius) or 'ridge' (param = lambda).
+    precision: 'fp64' (plain), 'tf32' or 'bf16' (mixed)."""
+
+    def __init__(self, A, b, kind="ols", param=0.0, m=None, s=1, seed=0, precision="fp64",
+                 shape=None, qp_max_iter=0, qp_tol=0.0):
+        self._keep = [A, b]
+        _need_cuda(b, "b")
+        if b.dtype != torch.float64:
+            raise TypeError("b must be float64")
+        M = _Matrix()
+        if isinstance(A, torch.Tensor):
+            _need_cuda(A, "A")
+            if A.dim() != 2 or A.dtype not in (torch.float32, torch.float64):
+                raise TypeError("dense A must be a 2-D float32/float64 tensor")
+            M.kind, M.n, M.d = DENSE, A.shape[0], A.shape[1]
+            M.ld = A.stride(0)
+            M.dtype = F32 if A.dtype == torch.float32 else F64
+            M.val = A.data_ptr()
+            M.col = None
+            M.rowptr = None
+            M.nnz = A.numel()
+        else:
+            rowptr, col, val = A
+            for t_, nm in ((rowptr, "rowptr"), (col, "col"), (val, "val")):
+                _need_cuda(t_, nm)
+            if shape is None:
+                raise ValueError("CSR input needs shape=(n, d)")
+            M.kind, M.n, M.d, M.ld = CSR, shape[0], shape[1], shape[1]
+            M.dtype = F32 if val.dtype == torch.float32 else F64
+            M.val, M.col, M.rowptr = val.data_ptr(), col.data_ptr(), rowptr.data_ptr()
+            M.rowptr_i64 = 1 if rowptr.dtype == torch.int64 else 0
+            M.nnz = val.numel()
+        self.n, self.d = int(M.n), int(M.d)
+        self.m = int(m if m is not None else 10 * self.d)
+        self.s = int(s)
+        self.kind = kind
+        self.precision = precision
+        C = _Constraint(KIND[kind], float(param))
+        O = _Options(self.m, self.s, seed & 0xFFFFFFFFFFFFFFFF, PREC[precision], int(qp_max_iter),
+                     float(qp_tol))
+        h = ctypes.c_void_p()
+        _check(_lib.ihs_create(ctypes.byref(h), ctypes.byref(M), _ptr(b), ctypes.byref(C),
+                               ctypes.byref(O), _stream()), "ihs_create")
+        self._h = h
+        self.device = b.device
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.ihs_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def sketch(self, t):
+        _check(_lib.ihs_sketch(self._h, int(t)), "ihs_sketch")
+
+    def gradient(self, x, want_r=False):
+        _need_cuda(x, "x")
+        g = torch.empty(self.d, dtype=torch.float64, device=self.device)
+        r = torch.empty(self.n, dtype=torch.float64, device=self.device) if want_r else None
+        _check(_lib.ihs_gradient(self._h, _ptr(x), _ptr(g), _ptr(r)), "ihs_gradient")
+        return (r, g) if want_r else g
+
+    def step(self, x):
+        _need_cuda(x, "x")
+        _check(_lib.ihs_step(self._h, _ptr(x)), "ihs_step")
+
+    def sync(self):
+        _check(_lib.ihs_sync(self._h), "ihs_sync")
+
+    def solve(self, x=None, t0=0, iters=10):
+        if x is None:
+            x = torch.zeros(self.d, dtype=torch.float64, device=self.device)
+        _need_cuda(x, "x")
+        rep = _Report()
+        _check(_lib.ihs_solve(self._h, _ptr(x), int(t0), int(iters), ctypes.byref(rep)), "ihs_solve")
+        return x, rep
+
+    def get_sketch(self):
+        dt = ctypes.c_int()
+        scale = ctypes.c_double()
+        _check(_lib.ihs_get_sketch(self._h, None, ctypes.byref(dt), None, ctypes.byref(scale)),
+               "ihs_get_sketch")
+        SA = torch.empty((self.m, self.d), dtype=torch.float64 if dt.value == F64 else torch.float32,
+                         device=self.device)
+        H = torch.empty((self.d, self.d), dtype=torch.float64, device=self.device)
+        _check(_lib.ihs_get_sketch(self._h, _ptr(SA), ctypes.byref(dt), _ptr(H),
+                                   ctypes.byref(scale)), "ihs_get_sketch")
+        return SA, H, scale.value
+
+    def profile(self, enable=True):
+        """Enable stage timing (CUDA events on the context's stream) and reset totals."""
+        _check(_lib.ihs_profile(self._h, 1 if enable else 0), "ihs_profile")
+
+    def profile_read(self):
+        """(ms per stage summed, instances per stage, library kernel launches)."""
+        n = len(STAGES)
+        ms = (ctypes.c_double * n)()
+        cnt = (ctypes.c_int * n)()
+        launches = ctypes.c_int64()
+        _check(_lib.ihs_profile_read(self._h, ms, cnt, ctypes.byref(launches)), "ihs_profile_read")
+        return ({k: ms[i] for i, k in enumerate(STAGES)}, {k: cnt[i] for i, k in enumerate(STAGES)},
+                launches.value)
+
+    def adjoint(self, x, dLdx, want_A=True):
+        _need_cuda(x, "x")
+        _need_cuda(dLdx, "dLdx")
+        dLdb = torch.empty(self.n, dtype=torch.float64, device=self.device)
+        A = self._keep[0]
+        dLdA = torch.empty_like(A) if (want_A and isinstance(A, torch.Tensor)) else None
+        rep = _Report()
+        _check(_lib.ihs_adjoint(self._h, _ptr(x), _ptr(dLdx), _ptr(dLdb), _ptr(dLdA),
+                                ctypes.byref(rep)), "ihs_adjoint")
+        return dLdb, dLdA, rep

@@ -1,0 +1,577 @@
+// capi.cu -- the C ABI of include/ihs.h: context, workspaces and the IHS loop
+// (Eq. 2): per iteration t, ihs_sketch(t) draws S (Sec. 2), forms SA, the
+// Hessian (SA)^T SA / s (+ lambda I) and its Cholesky factor; ihs_step forms
+// the exact gradient A^T (b - A x^t) and takes the QP step.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "internal.h"
+
+static int64_t g_launches = 0;  // kernel launches issued by the library
+void note_launches(int k) { __atomic_add_fetch(&g_launches, (int64_t)k, __ATOMIC_RELAXED); }
+int64_t launches_total() { return __atomic_load_n(&g_launches, __ATOMIC_RELAXED); }
+
+struct StageEvents {
+  std::vector<cudaEvent_t> ev;   // pool: pairs (start, stop)
+  std::vector<int> stage;        // stage of pair k
+  size_t used = 0;
+};
+
+struct ihs_ctx {
+  cudaStream_t st = nullptr;
+  bool prof = false;
+  StageEvents pe;
+  double prof_ms[IHS_NSTAGES] = {};
+  int prof_cnt[IHS_NSTAGES] = {};
+  int64_t prof_launch0 = 0;
+  int sms = 152;
+  // problem
+  ihs_matrix A{};
+  const double* b = nullptr;
+  ihs_constraint C{};
+  ihs_options opt{};
+  int64_t n = 0, d = 0, m = 0;
+  int s = 1;
+  int prec = 0, acc64 = 1, f32fac = 0;
+  bool dense = true;
+  // dense path
+  DenseA DA{};
+  SortPlan sp{};
+  void* sort_ws = nullptr;
+  uint32_t* perm = nullptr;
+  int32_t* seg = nullptr;
+  int32_t* chunk_first = nullptr;
+  void* sk_partial = nullptr;
+  int rg_warps = 0;
+  double* gpart = nullptr;
+  float2* bsplit = nullptr;
+  // CSR path (CSC copy)
+  CscA CA{};
+  void* csc_partial = nullptr;
+  void* rbuf = nullptr;
+  double* item_part = nullptr;
+  // sketch / Hessian
+  void* SA = nullptr;
+  GramPlan gp{};
+  void* gop = nullptr;
+  float* gpart_f = nullptr;
+  double* gpart_d = nullptr;
+  double* H = nullptr;
+  void* L = nullptr;
+  double* g = nullptr;
+  double* step_norm = nullptr;
+  int* status = nullptr;
+  int* counter = nullptr;
+  // l1 QP
+  QpWork qw{};
+  bool have_sketch = false;
+  std::vector<void*> allocs;
+};
+
+void prof_stage_begin(void* c, int stage);
+void prof_stage_end(void* c);
+
+namespace {
+
+// Record a stage boundary on the context's stream (timing enabled only).
+void stage_begin(ihs_ctx* c, int stage) {
+  if (!c->prof) return;
+  StageEvents& P = c->pe;
+  if (P.used + 2 > P.ev.size()) {
+    for (int q = 0; q < 64; ++q) {
+      cudaEvent_t e;
+      if (cudaEventCreate(&e) != cudaSuccess) return;
+      P.ev.push_back(e);
+    }
+    P.stage.resize(P.ev.size() / 2);
+  }
+  P.stage[P.used / 2] = stage;
+  cudaEventRecord(P.ev[P.used], c->st);
+}
+void stage_end(ihs_ctx* c) {
+  if (!c->prof) return;
+  StageEvents& P = c->pe;
+  if (P.used + 2 > P.ev.size()) return;
+  cudaEventRecord(P.ev[P.used + 1], c->st);
+  P.used += 2;
+}
+// Fold completed event pairs into the totals (after a synchronisation).
+void stage_collect(ihs_ctx* c) {
+  StageEvents& P = c->pe;
+  for (size_t k = 0; k + 1 < P.used + 1 && k < P.used; k += 2) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, P.ev[k], P.ev[k + 1]) == cudaSuccess) {
+      c->prof_ms[P.stage[k / 2]] += ms;
+      c->prof_cnt[P.stage[k / 2]] += 1;
+    }
+  }
+  P.used = 0;
+}
+
+}  // namespace
+
+void prof_stage_begin(void* c, int stage) { if (c) stage_begin((ihs_ctx*)c, stage); }
+void prof_stage_end(void* c) { if (c) stage_end((ihs_ctx*)c); }
+
+namespace {
+
+ihs_status cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return IHS_OK;
+  if (e == cudaErrorMemoryAllocation) return IHS_ERR_OOM;
+  return IHS_ERR_CUDA;
+}
+
+#define CK(call)                                    \
+  do {                                              \
+    cudaError_t e_ = (call);                        \
+    if (e_ != cudaSuccess) return cuda_status(e_);  \
+  } while (0)
+
+template <typename T>
+ihs_status dalloc(ihs_ctx* c, T** p, size_t bytes) {
+  void* q = nullptr;
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc(&q, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return IHS_ERR_OOM;
+  }
+  c->allocs.push_back(q);
+  *p = (T*)q;
+  return IHS_OK;
+}
+#define AL(ptr, bytes)                                  \
+  do {                                                  \
+    ihs_status s_ = dalloc(c, &(ptr), (size_t)(bytes)); \
+    if (s_ != IHS_OK) return s_;                        \
+  } while (0)
+
+__global__ void k_expand_rows(int64_t n, const void* rowptr, int i64, int32_t* rowexp) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int64_t a = i64 ? ((const int64_t*)rowptr)[i] : ((const int32_t*)rowptr)[i];
+    int64_t b = i64 ? ((const int64_t*)rowptr)[i + 1] : ((const int32_t*)rowptr)[i + 1];
+    for (int64_t p = a; p < b; ++p) rowexp[p] = (int32_t)i;
+  }
+}
+__global__ void k_csc_gather(int64_t nnz, const uint32_t* perm, const int32_t* rowexp,
+                             const void* val, int f32, int32_t* rowidx, void* cval) {
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nnz;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t p = perm[q];
+    rowidx[q] = rowexp[p];
+    if (f32) ((float*)cval)[q] = ((const float*)val)[p];
+    else ((double*)cval)[q] = ((const double*)val)[p];
+  }
+}
+__global__ void k_csr_check(int64_t nnz, const int32_t* col, int64_t d, int* bad) {
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < nnz;
+       q += (int64_t)gridDim.x * blockDim.x) {
+    int c = col[q];
+    if (c < 0 || c >= d) atomicExch(bad, 1);
+  }
+}
+
+ihs_status build_csc(ihs_ctx* c) {
+  const int64_t nnz = c->A.nnz, n = c->n, d = c->d;
+  if (nnz >= (1ll << 31)) return IHS_ERR_UNSUPPORTED;
+  int* bad;
+  AL(bad, sizeof(int));
+  CK(cudaMemsetAsync(bad, 0, sizeof(int), c->st));
+  if (nnz > 0)
+    { k_csr_check<<<(unsigned)std::min<int64_t>((nnz + 255) / 256, 8192), 256, 0, c->st>>>(
+        nnz, c->A.col, d, bad); note_launches(1); }
+  int hbad = 0;
+  CK(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  if (hbad) return IHS_ERR_ARG;
+  // host copy of rowptr for validation
+  std::vector<int64_t> rp(n + 1);
+  if (c->A.rowptr_i64) {
+    CK(cudaMemcpy(rp.data(), c->A.rowptr, (n + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost));
+  } else {
+    std::vector<int32_t> r32(n + 1);
+    CK(cudaMemcpy(r32.data(), c->A.rowptr, (n + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    for (int64_t i = 0; i <= n; ++i) rp[i] = r32[i];
+  }
+  if (rp[0] != 0 || rp[n] != nnz) return IHS_ERR_ARG;
+  for (int64_t i = 0; i < n; ++i)
+    if (rp[i + 1] < rp[i]) return IHS_ERR_ARG;
+
+  int32_t* rowexp;
+  AL(rowexp, nnz * sizeof(int32_t));
+  if (n > 0)
+    { k_expand_rows<<<(unsigned)std::min<int64_t>((n + 255) / 256, 8192), 256, 0, c->st>>>(
+        n, c->A.rowptr, c->A.rowptr_i64, rowexp); note_launches(1); }
+  SortPlan p = make_sort_plan(nnz, (int)d, 1);
+  void* ws;
+  AL(ws, sort_workspace_bytes(p));
+  uint32_t* perm;
+  int32_t* seg;
+  AL(perm, nnz * sizeof(uint32_t));
+  AL(seg, (d + 1) * sizeof(int32_t));
+  CK(launch_sort_keys(p, c->A.col, ws, perm, seg, c->st));
+  int32_t* rowidx;
+  void* cval;
+  const size_t el = (c->A.dtype == IHS_F32) ? 4 : 8;
+  AL(rowidx, nnz * sizeof(int32_t));
+  AL(cval, nnz * el);
+  if (nnz > 0)
+    { k_csc_gather<<<(unsigned)std::min<int64_t>((nnz + 255) / 256, 8192), 256, 0, c->st>>>(
+        nnz, perm, rowexp, c->A.val, c->A.dtype == IHS_F32, rowidx, cval); note_launches(1); }
+  CK(cudaGetLastError());
+  std::vector<int32_t> cp32(d + 1);
+  CK(cudaMemcpyAsync(cp32.data(), seg, (d + 1) * sizeof(int32_t), cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  // work items: column chunks of at most kItem entries (a column with no
+  // entries still gets one item so its zero column is written)
+  const int64_t kItem = 1 << 17;
+  std::vector<int32_t> icol, islot, first(d + 1);
+  std::vector<int64_t> ib, ie;
+  int nsplit = 0;
+  for (int64_t j = 0; j < d; ++j) {
+    first[j] = (int32_t)icol.size();
+    const int64_t a = cp32[j], e = cp32[j + 1];
+    const int64_t k = std::max<int64_t>(1, (e - a + kItem - 1) / kItem);
+    for (int64_t q = 0; q < k; ++q) {
+      icol.push_back((int32_t)j);
+      ib.push_back(a + (e - a) * q / k);
+      ie.push_back(a + (e - a) * (q + 1) / k);
+      islot.push_back(k > 1 ? nsplit++ : -1);
+    }
+  }
+  first[d] = (int32_t)icol.size();
+  std::vector<int64_t> cp64(cp32.begin(), cp32.end());
+  const int ni = (int)icol.size();
+  int64_t* colptr;
+  int32_t *d_icol, *d_islot, *d_first;
+  int64_t *d_ib, *d_ie;
+  AL(colptr, (d + 1) * sizeof(int64_t));
+  AL(d_icol, ni * sizeof(int32_t));
+  AL(d_islot, ni * sizeof(int32_t));
+  AL(d_first, (d + 1) * sizeof(int32_t));
+  AL(d_ib, ni * sizeof(int64_t));
+  AL(d_ie, ni * sizeof(int64_t));
+  CK(cudaMemcpy(colptr, cp64.data(), (d + 1) * sizeof(int64_t), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(d_icol, icol.data(), ni * sizeof(int32_t), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(d_islot, islot.data(), ni * sizeof(int32_t), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(d_first, first.data(), (d + 1) * sizeof(int32_t), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(d_ib, ib.data(), ni * sizeof(int64_t), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(d_ie, ie.data(), ni * sizeof(int64_t), cudaMemcpyHostToDevice));
+  CscA& A = c->CA;
+  A.n = n;
+  A.d = d;
+  A.nnz = nnz;
+  A.colptr = colptr;
+  A.rowidx = rowidx;
+  A.val = cval;
+  A.f32 = c->A.dtype == IHS_F32;
+  A.nitems = ni;
+  A.item_col = d_icol;
+  A.item_begin = d_ib;
+  A.item_end = d_ie;
+  A.item_slot = d_islot;
+  A.nsplit_slots = nsplit;
+  A.col_first_item = d_first;
+  const size_t acc_el = c->acc64 ? 8 : 4;
+  AL(c->csc_partial, (size_t)std::max(1, nsplit) * c->m * acc_el);
+  AL(c->item_part, ni * sizeof(double));
+  AL(c->rbuf, n * 8);
+  return IHS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* ihs_status_str(ihs_status st) {
+  switch (st) {
+    case IHS_OK: return "ok";
+    case IHS_ERR_ARG: return "invalid argument";
+    case IHS_ERR_CUDA: return "CUDA error";
+    case IHS_ERR_OOM: return "out of device memory";
+    case IHS_ERR_NOT_SPD: return "sketched Hessian not positive definite";
+    case IHS_ERR_NOT_CONVERGED: return "inner solver did not converge";
+    case IHS_ERR_NONFINITE: return "non-finite value";
+    case IHS_ERR_TIMEOUT: return "bounded device wait expired";
+    case IHS_ERR_UNSUPPORTED: return "unsupported size or option";
+  }
+  return "unknown status";
+}
+
+void ihs_destroy(ihs_ctx* c) {
+  if (!c) return;
+  cudaStreamSynchronize(c->st);
+  for (cudaEvent_t e : c->pe.ev) cudaEventDestroy(e);
+  for (void* p : c->allocs) cudaFree(p);
+  delete c;
+}
+
+ihs_status ihs_create(ihs_ctx** out, const ihs_matrix* A, const double* b,
+                      const ihs_constraint* C, const ihs_options* opt, void* stream) {
+  if (!out || !A || !b || !C || !opt) return IHS_ERR_ARG;
+  *out = nullptr;
+  if (A->kind != IHS_DENSE && A->kind != IHS_CSR) return IHS_ERR_ARG;
+  if (A->dtype != IHS_F64 && A->dtype != IHS_F32) return IHS_ERR_ARG;
+  if (A->n < 1 || A->d < 1 || A->val == nullptr) return IHS_ERR_ARG;
+  if (A->n >= (1ll << 31)) return IHS_ERR_ARG;
+  if (A->d > 1024) return IHS_ERR_UNSUPPORTED;
+  if (opt->s < 1 || opt->s > kMaxBlocks || opt->m < 1 || opt->m % opt->s != 0) return IHS_ERR_ARG;
+  if (opt->m < A->d) return IHS_ERR_ARG;
+  if (opt->precision < IHS_PREC_FP64 || opt->precision > IHS_PREC_BF16) return IHS_ERR_ARG;
+  if (C->kind != IHS_OLS && C->kind != IHS_L1_BALL && C->kind != IHS_RIDGE) return IHS_ERR_ARG;
+  if (C->kind == IHS_L1_BALL && !(C->param > 0)) return IHS_ERR_ARG;
+  if (C->kind == IHS_RIDGE && !(C->param >= 0)) return IHS_ERR_ARG;
+  if (A->kind == IHS_DENSE && A->ld < A->d) return IHS_ERR_ARG;
+  if (A->kind == IHS_CSR && (A->col == nullptr || A->rowptr == nullptr || A->nnz < 0))
+    return IHS_ERR_ARG;
+  if (A->kind == IHS_DENSE && (int64_t)opt->s * A->n >= (1ll << 31)) return IHS_ERR_UNSUPPORTED;
+
+  ihs_ctx* c = new (std::nothrow) ihs_ctx();
+  if (!c) return IHS_ERR_OOM;
+  c->st = (cudaStream_t)stream;
+  c->A = *A;
+  c->b = b;
+  c->C = *C;
+  c->opt = *opt;
+  c->n = A->n;
+  c->d = A->d;
+  c->m = opt->m;
+  c->s = opt->s;
+  c->prec = opt->precision;
+  c->acc64 = (c->prec == IHS_PREC_FP64);
+  c->f32fac = (c->prec != IHS_PREC_FP64);
+  c->dense = (A->kind == IHS_DENSE);
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, dev);
+
+  auto fail = [&](ihs_status s) {
+    ihs_destroy(c);
+    return s;
+  };
+  const size_t acc_el = c->acc64 ? 8 : 4;
+  ihs_status s = IHS_OK;
+#define AL2(ptr, bytes)                                   \
+  do {                                                    \
+    if ((s = dalloc(c, &(ptr), (size_t)(bytes))) != IHS_OK) return fail(s); \
+  } while (0)
+  AL2(c->SA, (size_t)c->m * c->d * acc_el);
+  AL2(c->H, (size_t)c->d * c->d * sizeof(double));
+  const int dp = chol_padded((int)c->d);
+  AL2(c->L, (size_t)dp * dp * (c->f32fac ? 4 : 8));
+  AL2(c->g, c->d * sizeof(double));
+  AL2(c->step_norm, sizeof(double));
+  AL2(c->status, sizeof(int));
+  AL2(c->counter, sizeof(int));
+  if (cudaMemsetAsync(c->status, 0, sizeof(int), c->st) != cudaSuccess) return fail(IHS_ERR_CUDA);
+  c->gp = make_gram_plan((int)c->m, (int)c->d, c->prec, c->sms);
+  if (c->prec == IHS_PREC_FP64) {
+    AL2(c->gpart_d, gram_partial_bytes(c->gp));
+  } else {
+    AL2(c->gpart_f, gram_partial_bytes(c->gp));
+    AL2(c->gop, gram_operand_bytes(c->gp));
+  }
+  if ((A->dtype == IHS_F32)) {
+    AL2(c->bsplit, c->n * sizeof(float2));
+    if (launch_split_b(b, c->n, c->bsplit, c->st) != cudaSuccess) return fail(IHS_ERR_CUDA);
+  }
+  if (c->dense) {
+    c->DA = DenseA{A->val, A->n, A->d, A->ld, A->dtype == IHS_F32};
+    c->sp = make_sort_plan((int64_t)c->s * c->n, (int)c->m, c->sms * 16);
+    if ((size_t)c->m * sizeof(int32_t) > 200 * 1024) return fail(IHS_ERR_UNSUPPORTED);
+    AL2(c->sort_ws, sort_workspace_bytes(c->sp));
+    AL2(c->perm, c->sp.P * sizeof(uint32_t));
+    AL2(c->seg, (c->m + 1) * sizeof(int32_t));
+    AL2(c->chunk_first, c->sp.nchunks * sizeof(int32_t));
+    AL2(c->sk_partial, (size_t)2 * c->sp.nchunks * c->d * acc_el);
+    c->rg_warps = rg_dense_warps(c->n);
+    AL2(c->gpart, (size_t)c->rg_warps * c->d * sizeof(double));
+  } else {
+    if ((size_t)(c->m / c->s) * acc_el > 200 * 1024) return fail(IHS_ERR_UNSUPPORTED);
+    if ((s = build_csc(c)) != IHS_OK) return fail(s);
+  }
+  if (C->kind == IHS_L1_BALL) {
+    size_t qb = qp_work_bytes((int)c->d);
+    uint8_t* q;
+    AL2(q, qb);
+    const int64_t dd = c->d;
+    c->qw.Hf = (float*)q;
+    c->qw.Ls = (void*)(q + dd * dd * 4);
+    c->qw.cvec = (double*)(q + dd * dd * 4 + (size_t)dp * dp * 8);
+    c->qw.dbuf = c->qw.cvec + dd;
+    c->qw.support = (int*)(c->qw.dbuf + 8 * dd);
+    c->qw.iters = c->qw.support + dd + 1;
+    if (cudaMemsetAsync(c->qw.support, 0, (dd + 2) * sizeof(int), c->st) != cudaSuccess)
+      return fail(IHS_ERR_CUDA);
+  }
+#undef AL2
+  if (cudaStreamSynchronize(c->st) != cudaSuccess) return fail(IHS_ERR_CUDA);
+  *out = c;
+  return IHS_OK;
+}
+
+ihs_status ihs_sketch(ihs_ctx* c, int64_t t) {
+  if (!c || t < 0) return IHS_ERR_ARG;
+  const SketchKeys K = make_keys(c->opt.seed, t, c->s, c->m);
+  if (c->dense) {
+    stage_begin(c, IHS_ST_SORT);
+    CK(launch_sort_sketch(c->sp, K, c->n, c->sort_ws, c->perm, c->seg, c->chunk_first, c->st));
+    stage_end(c);
+    stage_begin(c, IHS_ST_SKETCH);
+    CK(launch_sketch_dense(c->DA, c->sp, c->perm, c->seg, c->chunk_first, c->acc64, c->SA,
+                           c->sk_partial, c->counter, c->sms, c->st, c->prof ? c : nullptr));
+    stage_end(c);
+  } else {
+    stage_begin(c, IHS_ST_SKETCH);
+    CK(launch_sketch_csc(c->CA, K, c->m, c->acc64, c->SA, c->csc_partial, c->st));
+    stage_end(c);
+  }
+  const double shift = (c->C.kind == IHS_RIDGE) ? c->C.param : 0.0;
+  stage_begin(c, IHS_ST_GRAM);
+  CK(launch_gram(c->gp, c->SA, c->gop, c->gpart_f, c->gpart_d, 1.0 / c->s, shift, c->H, c->status,
+                 c->st));
+  stage_end(c);
+  stage_begin(c, IHS_ST_FACTOR);
+  CK(launch_cholesky(c->H, (int)c->d, c->f32fac, c->L, c->status, c->st));
+  stage_end(c);
+  c->have_sketch = true;
+  return IHS_OK;
+}
+
+ihs_status ihs_gradient(ihs_ctx* c, const double* x, double* g, double* r) {
+  if (!c || !x || !g) return IHS_ERR_ARG;
+  const double lam = (c->C.kind == IHS_RIDGE) ? c->C.param : 0.0;
+  if (c->dense) {
+    CK(launch_resid_grad_dense(c->DA, c->b, c->bsplit, x, r, c->gpart, c->rg_warps, g, lam,
+                               c->st));
+  } else {
+    CK(launch_resid_csr(c->n, c->d, c->A.rowptr, c->A.rowptr_i64, c->A.col, c->A.val,
+                        c->A.dtype == IHS_F32, c->b, x, c->rbuf, r, c->st));
+    CK(launch_grad_csc(c->CA, c->rbuf, c->item_part, x, lam, g, c->st));
+  }
+  return IHS_OK;
+}
+
+ihs_status ihs_step(ihs_ctx* c, double* x) {
+  if (!c || !x) return IHS_ERR_ARG;
+  if (!c->have_sketch) return IHS_ERR_ARG;
+  stage_begin(c, IHS_ST_GRAD);
+  ihs_status s = ihs_gradient(c, x, c->g, nullptr);
+  stage_end(c);
+  if (s != IHS_OK) return s;
+  stage_begin(c, IHS_ST_STEP);
+  struct EndStep { ihs_ctx* c; ~EndStep() { stage_end(c); } } end_step{c};
+  if (c->C.kind == IHS_L1_BALL) {
+    CK(launch_l1_step(c->H, c->L, c->f32fac, (int)c->d, c->g, c->C.param, c->opt.qp_max_iter,
+                      c->opt.qp_tol, c->qw, x, c->step_norm, c->status, c->st));
+  } else {
+    CK(launch_chol_step(c->L, (int)c->d, c->f32fac, c->g, x, c->step_norm, c->st));
+  }
+  return IHS_OK;
+}
+
+ihs_status ihs_sync(ihs_ctx* c) {
+  if (!c) return IHS_ERR_ARG;
+  CK(cudaStreamSynchronize(c->st));
+  int st = 0;
+  CK(cudaMemcpy(&st, c->status, sizeof(int), cudaMemcpyDeviceToHost));
+  if (st != 0) CK(cudaMemset(c->status, 0, sizeof(int)));
+  return (ihs_status)st;
+}
+
+ihs_status ihs_solve(ihs_ctx* c, double* x, int64_t t0, int iters, ihs_report* rep) {
+  if (!c || !x || iters < 0 || t0 < 0) return IHS_ERR_ARG;
+  if (c->C.kind == IHS_L1_BALL) CK(cudaMemsetAsync(c->qw.iters, 0, sizeof(int), c->st));
+  for (int k = 0; k < iters; ++k) {
+    ihs_status s = ihs_sketch(c, t0 + k);
+    if (s != IHS_OK) return s;
+    s = ihs_step(c, x);
+    if (s != IHS_OK) return s;
+  }
+  ihs_status st = ihs_sync(c);
+  if (rep) {
+    rep->iters = iters;
+    rep->status = st;
+    rep->step_norm = 0.0;
+    rep->qp_fista_iters = 0;
+    if (iters > 0) cudaMemcpy(&rep->step_norm, c->step_norm, sizeof(double), cudaMemcpyDeviceToHost);
+    if (c->C.kind == IHS_L1_BALL)
+      cudaMemcpy(&rep->qp_fista_iters, c->qw.iters, sizeof(int), cudaMemcpyDeviceToHost);
+  }
+  return st;
+}
+
+ihs_status ihs_get_sketch(ihs_ctx* c, void* SA_out, int* SA_dtype, double* H_out,
+                          double* scale) {
+  if (!c) return IHS_ERR_ARG;
+  if (SA_dtype) *SA_dtype = c->acc64 ? IHS_F64 : IHS_F32;
+  if (scale) *scale = 1.0 / c->s;
+  if ((SA_out || H_out) && !c->have_sketch) return IHS_ERR_ARG;
+  const size_t el = c->acc64 ? 8 : 4;
+  if (SA_out)
+    CK(cudaMemcpyAsync(SA_out, c->SA, (size_t)c->m * c->d * el, cudaMemcpyDeviceToDevice, c->st));
+  if (H_out)
+    CK(cudaMemcpyAsync(H_out, c->H, (size_t)c->d * c->d * sizeof(double),
+                       cudaMemcpyDeviceToDevice, c->st));
+  return IHS_OK;
+}
+
+ihs_status ihs_adjoint(ihs_ctx* c, const double* x, const double* dLdx, double* dLdb, void* dLdA,
+                       ihs_report* rep) {
+  (void)c; (void)x; (void)dLdx; (void)dLdb; (void)dLdA; (void)rep;
+  return IHS_ERR_UNSUPPORTED;
+}
+
+ihs_status ihs_profile(ihs_ctx* c, int enable) {
+  if (!c) return IHS_ERR_ARG;
+  CK(cudaStreamSynchronize(c->st));
+  c->pe.used = 0;
+  for (int k = 0; k < IHS_NSTAGES; ++k) {
+    c->prof_ms[k] = 0.0;
+    c->prof_cnt[k] = 0;
+  }
+  c->prof = enable != 0;
+  c->prof_launch0 = launches_total();
+  return IHS_OK;
+}
+
+ihs_status ihs_profile_read(ihs_ctx* c, double* ms, int* count, int64_t* launches) {
+  if (!c || !ms) return IHS_ERR_ARG;
+  CK(cudaStreamSynchronize(c->st));
+  stage_collect(c);
+  for (int k = 0; k < IHS_NSTAGES; ++k) {
+    ms[k] = c->prof_ms[k];
+    if (count) count[k] = c->prof_cnt[k];
+  }
+  if (launches) *launches = launches_total() - c->prof_launch0;
+  return IHS_OK;
+}
+
+ihs_status ihs_hash(uint64_t seed, int64_t t, int s, int64_t m, int64_t n, int32_t* bucket,
+                    int8_t* sign, void* stream) {
+  if (s < 1 || s > kMaxBlocks || m < 1 || m % s != 0 || n < 0 || t < 0) return IHS_ERR_ARG;
+  if (m / s > 0x7fffffffLL || m > 0x7fffffffLL) return IHS_ERR_ARG;
+  if (n > 0 && (!bucket || !sign)) return IHS_ERR_ARG;
+  const SketchKeys K = make_keys(seed, t, s, m);
+  CK(launch_hash(K, n, bucket, sign, (cudaStream_t)stream));
+  return IHS_OK;
+}
+
+ihs_status ihs_sketch_adjoint(uint64_t seed, int64_t t, int s, int64_t m, int64_t n, int64_t d,
+                              const double* G, double* out, void* stream) {
+  if (s < 1 || s > kMaxBlocks || m < 1 || m % s != 0 || n < 0 || d < 1 || t < 0)
+    return IHS_ERR_ARG;
+  if (n > 0 && (!G || !out)) return IHS_ERR_ARG;
+  const SketchKeys K = make_keys(seed, t, s, m);
+  CK(launch_sketch_adjoint(K, n, d, G, out, (cudaStream_t)stream));
+  return IHS_OK;
+}
+
+}  // extern "C"

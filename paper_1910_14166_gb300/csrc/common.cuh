@@ -1,0 +1,146 @@
+// common.cuh -- device utilities shared by the IHS kernels (sm_103a).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/ihs.h"
+
+#define IHS_DEV __device__ __forceinline__
+
+// Device status word codes (written by kernels, read at synchronisation).
+enum : int {
+  DEV_OK = 0,
+  DEV_NOT_SPD = IHS_ERR_NOT_SPD,
+  DEV_NOT_CONVERGED = IHS_ERR_NOT_CONVERGED,
+  DEV_NONFINITE = IHS_ERR_NONFINITE,
+  DEV_TIMEOUT = IHS_ERR_TIMEOUT,
+};
+
+IHS_DEV void set_status(int* st, int code) {
+  if (st) atomicCAS(st, 0, code);
+}
+
+// ---------------------------------------------------------------------------
+// SplitMix64 (Steele, Lea & Flood 2014), counter style: output j of the
+// generator started at `state` is the finaliser of state + (j+1)*gamma.
+// ---------------------------------------------------------------------------
+constexpr uint64_t kSmGamma = 0x9E3779B97F4A7C15ULL;
+
+__host__ __device__ __forceinline__ uint64_t sm64_finalise(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  return z ^ (z >> 31);
+}
+__host__ __device__ __forceinline__ uint64_t sm64_out(uint64_t state, uint64_t j) {
+  return sm64_finalise(state + (j + 1) * kSmGamma);
+}
+
+// Keys of one sketch draw: key[k] for block k of iteration t (at most 64 blocks).
+constexpr int kMaxBlocks = 64;
+struct SketchKeys {
+  uint64_t key[kMaxBlocks];
+  int s;
+  int mb;  // rows per block, m / s
+};
+
+// Global row of S and sign for (block k, row i): the multiply-shift range
+// reduction of the high 32 bits, sign from bit 0.
+IHS_DEV void sketch_draw(const SketchKeys& K, int k, uint64_t i, int& row, int& neg) {
+  uint64_t w = sm64_out(K.key[k], i);
+  uint32_t b = (uint32_t)(((w >> 32) * (uint64_t)(uint32_t)K.mb) >> 32);
+  row = k * K.mb + (int)b;
+  neg = (int)(w & 1ULL);
+}
+
+// ---------------------------------------------------------------------------
+// Double-float ("float-float") arithmetic from error-free transformations:
+// TwoProd via FMA and Knuth's TwoSum (Dekker 1971; Ogita, Rump & Oishi 2005).
+// A pair (hi, lo) carries about 48 significant bits; every product of an
+// FP32 value with the hi part of a pair is exact.
+// ---------------------------------------------------------------------------
+IHS_DEV void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+IHS_DEV void fast_two_sum(float a, float b, float& s, float& e) {  // |a| >= |b|
+  s = __fadd_rn(a, b);
+  e = __fsub_rn(b, __fsub_rn(s, a));
+}
+// (hi, lo) += a * (yh + yl), yh/yl the split of an FP64 factor.
+IHS_DEV void dd_fma_acc(float& hi, float& lo, float a, float yh, float yl) {
+  float p = __fmul_rn(a, yh);
+  float pe = __fmaf_rn(a, yh, -p);  // exact low part of a*yh
+  float s, e;
+  two_sum(hi, p, s, e);
+  hi = s;
+  lo = __fadd_rn(lo, __fadd_rn(e, pe));
+  lo = __fmaf_rn(a, yl, lo);
+}
+// (ah, al) + (bh, bl), renormalised.
+IHS_DEV void dd_add(float& ah, float& al, float bh, float bl) {
+  float s, e;
+  two_sum(ah, bh, s, e);
+  e = __fadd_rn(e, __fadd_rn(al, bl));
+  fast_two_sum(s, e, ah, al);
+}
+IHS_DEV void split_double(double v, float& h, float& l) {
+  h = __double2float_rn(v);
+  l = __double2float_rn(v - (double)h);
+}
+
+// ---------------------------------------------------------------------------
+// Warp helpers.
+// ---------------------------------------------------------------------------
+IHS_DEV unsigned lanemask_lt() {
+  unsigned m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+template <typename T>
+IHS_DEV T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Load / store helpers with a compile-time vector width.
+template <typename T, int V> struct VecT;
+template <> struct VecT<float, 4> { using type = float4; };
+template <> struct VecT<float, 1> { using type = float; };
+template <> struct VecT<double, 2> { using type = double2; };
+template <> struct VecT<double, 1> { using type = double; };
+
+template <typename T, int V>
+IHS_DEV void load_vec(const T* p, T (&out)[V]) {
+  if constexpr (V == 4) {
+    float4 v = __ldg(reinterpret_cast<const float4*>(p));
+    out[0] = v.x; out[1] = v.y; out[2] = v.z; out[3] = v.w;
+  } else if constexpr (V == 2) {
+    double2 v = __ldg(reinterpret_cast<const double2*>(p));
+    out[0] = v.x; out[1] = v.y;
+  } else {
+    out[0] = __ldg(p);
+  }
+}
+// Streaming (evict-first) variant for data read once per pass.
+template <typename T, int V>
+IHS_DEV void load_vec_stream(const T* p, T (&out)[V]) {
+  if constexpr (V == 4) {
+    float4 v = __ldcs(reinterpret_cast<const float4*>(p));
+    out[0] = v.x; out[1] = v.y; out[2] = v.z; out[3] = v.w;
+  } else if constexpr (V == 2) {
+    double2 v = __ldcs(reinterpret_cast<const double2*>(p));
+    out[0] = v.x; out[1] = v.y;
+  } else {
+    out[0] = __ldcs(p);
+  }
+}
+
+// Bounded spin budget for every device-side wait (about a second at 2 GHz
+// with the back-off below); on expiry the waiter records DEV_TIMEOUT.
+constexpr long long kSpinLimit = 1ll << 26;
+
+IHS_DEV uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}

@@ -1,0 +1,479 @@
+// gram.cu -- the approximate Hessian H = scale * (SA)^T SA + shift * I
+// (Sec. 1: IHS replaces A^T A by the quadratic form of SA; O(m d^2)).
+//
+// Plain form (FP64): SIMT FP64 tiles of 64 x 64, split over m.
+// Mixed form (TF32 / BF16): a tcgen05 kernel.  SA is first transposed into
+// a K-major operand Op = SA^T (d_pad x ldt, K = m contiguous) in the MMA input
+// type; then each CTA owns one 128 x 128 lower-triangle tile of H and one
+// slice of K:
+//   warp 0      TMA producer: 128-row x 128-byte boxes, 128B swizzle, into a
+//               4-stage shared-memory ring (mbarrier complete_tx)
+//   warp 1      allocates 128 TMEM columns, one elected thread issues
+//               tcgen05.mma (M=128, N=128, FP32 accumulator in TMEM) and
+//               commits each stage back to the producer
+//   warps 2..5  epilogue: tcgen05.ld 32x32b.x32 from their TMEM lane
+//               quarter -> FP32 partial tile in global memory
+// Split-K partials are summed in split order by a reduce kernel that also
+// applies scale and shift and mirrors the lower triangle (deterministic).
+// Every mbarrier wait is bounded; a wait that runs out records DEV_TIMEOUT,
+// drains the copies it issued and frees TMEM before returning.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "internal.h"
+
+// ----------------------------------------------------------------------------
+// Plan
+// ----------------------------------------------------------------------------
+GramPlan make_gram_plan(int m, int d, int prec, int num_sms) {
+  GramPlan g;
+  g.d = d;
+  g.m = m;
+  g.prec = prec;
+  g.tdim = (prec == IHS_PREC_FP64) ? 64 : 128;
+  const int T = (d + g.tdim - 1) / g.tdim;
+  g.tiles = T * (T + 1) / 2;
+  const int kunit = (prec == IHS_PREC_FP64) ? 16 : (prec == IHS_PREC_TF32 ? 32 : 64);
+  const int64_t kblocks = (m + kunit - 1) / kunit;
+  int target = (prec == IHS_PREC_FP64) ? 2 * num_sms : num_sms;
+  int splits = std::max(1, target / g.tiles);
+  splits = (int)std::min<int64_t>(splits, kblocks);
+  g.splits = std::max(1, splits);
+  g.ldt = kblocks * kunit;  // K padded to whole k-blocks (zeros)
+  return g;
+}
+
+size_t gram_partial_bytes(const GramPlan& g) {
+  const size_t el = (g.prec == IHS_PREC_FP64) ? sizeof(double) : sizeof(float);
+  return (size_t)g.splits * g.tiles * g.tdim * g.tdim * el;
+}
+
+size_t gram_operand_bytes(const GramPlan& g) {
+  if (g.prec == IHS_PREC_FP64) return 0;
+  const int T = (g.d + g.tdim - 1) / g.tdim;
+  const size_t el = (g.prec == IHS_PREC_TF32) ? 4 : 2;
+  return (size_t)T * g.tdim * g.ldt * el;
+}
+
+IHS_DEV void tri_index(int q, int& ti, int& tj) {
+  // q enumerates (ti, tj), ti >= tj, row by row: q = ti*(ti+1)/2 + tj
+  int t = (int)((sqrtf(8.0f * q + 1.0f) - 1.0f) * 0.5f);
+  while ((t + 1) * (t + 2) / 2 <= q) ++t;
+  while (t * (t + 1) / 2 > q) --t;
+  ti = t;
+  tj = q - t * (t + 1) / 2;
+}
+
+// ----------------------------------------------------------------------------
+// FP64 SIMT
+// ----------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_gram_f64(const double* __restrict__ SA, int m, int d,
+                                                  int tiles, int64_t kchunk,
+                                                  double* __restrict__ partial) {
+  __shared__ double As[16][64 + 1];
+  __shared__ double Bs[16][64 + 1];
+  int ti, tj;
+  tri_index(blockIdx.x, ti, tj);
+  const int sp = blockIdx.y;
+  const int64_t r0 = sp * kchunk, r1 = min((int64_t)m, r0 + kchunk);
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  double acc[4][4] = {};
+  for (int64_t rb = r0; rb < r1; rb += 16) {
+    for (int e = threadIdx.x; e < 16 * 64; e += 256) {
+      int rr = e >> 6, c = e & 63;
+      int64_t r = rb + rr;
+      int ca = ti * 64 + c, cb = tj * 64 + c;
+      As[rr][c] = (r < r1 && ca < d) ? SA[r * d + ca] : 0.0;
+      Bs[rr][c] = (r < r1 && cb < d) ? SA[r * d + cb] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int rr = 0; rr < 16; ++rr) {
+      double a[4], b[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        a[u] = As[rr][ty * 4 + u];
+        b[u] = Bs[rr][tx * 4 + u];
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v] = fma(a[u], b[v], acc[u][v]);
+    }
+    __syncthreads();
+  }
+  double* out = partial + ((int64_t)sp * tiles + blockIdx.x) * 64 * 64;
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) out[(ty * 4 + u) * 64 + tx * 4 + v] = acc[u][v];
+}
+
+// Sum split partials in split order; H[i][j] = H[j][i] = scale * sum + shift * [i == j].
+template <typename P>
+__global__ void k_gram_reduce(const P* __restrict__ partial, int d, int tdim, int tiles,
+                              int splits, double scale, double shift, double* __restrict__ H,
+                              int* status) {
+  const int64_t total = (int64_t)d * d;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e / d), j = (int)(e - (int64_t)i * d);
+    if (j > i) continue;
+    const int ti = i / tdim, tj = j / tdim;
+    const int q = ti * (ti + 1) / 2 + tj;
+    const int li = i - ti * tdim, lj = j - tj * tdim;
+    double s = 0.0;
+    for (int sp = 0; sp < splits; ++sp)
+      s += (double)partial[((int64_t)sp * tiles + q) * tdim * tdim + (int64_t)li * tdim + lj];
+    double v = scale * s + (i == j ? shift : 0.0);
+    if (!isfinite(v)) set_status(status, DEV_NONFINITE);
+    H[(int64_t)i * d + j] = v;
+    H[(int64_t)j * d + i] = v;
+  }
+}
+
+// ----------------------------------------------------------------------------
+// Transpose SA (m x d float) into the K-major MMA operand (rows d_pad, ld ldt).
+// ----------------------------------------------------------------------------
+template <bool BF16>
+__global__ void k_gram_operand(const float* __restrict__ SA, int m, int d, int dpad, int64_t ldt,
+                               void* __restrict__ op) {
+  __shared__ float tile[32][33];
+  const int r0 = blockIdx.x * 32, c0 = blockIdx.y * 32;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
+  for (int k = ty; k < 32; k += 8) {
+    int r = r0 + k, c = c0 + tx;
+    tile[k][tx] = (r < m && c < d) ? SA[(int64_t)r * d + c] : 0.f;
+  }
+  __syncthreads();
+  for (int k = ty; k < 32; k += 8) {
+    int c = c0 + k, r = r0 + tx;  // output row c, column r
+    if (c < dpad && r < ldt) {
+      float v = tile[tx][k];
+      if constexpr (BF16) {
+        ((__nv_bfloat16*)op)[(int64_t)c * ldt + r] = __float2bfloat16_rn(v);
+      } else {
+        uint32_t u;
+        asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(u) : "f"(v));
+        ((uint32_t*)op)[(int64_t)c * ldt + r] = u;
+      }
+    }
+  }
+}
+
+// ----------------------------------------------------------------------------
+// tcgen05 / TMA primitives (inline PTX, sm_100-family)
+// ----------------------------------------------------------------------------
+IHS_DEV void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+               : "memory");
+}
+IHS_DEV void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+IHS_DEV bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait; gives up when `abort` is raised by another thread or the
+// spin budget runs out.
+IHS_DEV bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort) {
+  for (long long it = 0; it < kSpinLimit; ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (*abort) return false;
+    if (it > 32) __nanosleep(64);
+  }
+  return false;
+}
+IHS_DEV void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes "
+      "[%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+IHS_DEV void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+IHS_DEV void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+IHS_DEV void tc_commit(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(bar))
+      : "memory");
+}
+template <int KIND>  // 0: tf32, 1: bf16 (kind::f16)
+IHS_DEV void tc_mma(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                    uint32_t accumulate) {
+  if constexpr (KIND == 0) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+  } else {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+  }
+}
+// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, rows of
+// 128 bytes, 8-row core groups 1024 bytes apart (SBO), sm_100 descriptor version.
+IHS_DEV uint64_t smem_desc_sw128(uint32_t saddr) {
+  uint64_t desc = 0;
+  desc |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+  desc |= (uint64_t)1 << 16;                      // leading byte offset (unused for SW128 K-major)
+  desc |= (uint64_t)((1024u >> 4) & 0x3FFFu) << 32;  // stride byte offset
+  desc |= (uint64_t)1 << 46;                      // descriptor version
+  desc |= (uint64_t)2 << 61;                      // 128-byte swizzle
+  return desc;
+}
+// Instruction descriptor: FP32 accumulator, A/B type code, both K-major, N and M.
+__host__ __device__ constexpr uint32_t make_idesc(uint32_t ab_type, int M, int N) {
+  return (1u << 4) | (ab_type << 7) | (ab_type << 10) | ((uint32_t)(N >> 3) << 17) |
+         ((uint32_t)(M >> 4) << 24);
+}
+
+IHS_DEV void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+constexpr int kTcStages = 4;
+constexpr int kTcTile = 128;
+constexpr int kTcStageBytes = kTcTile * 128;  // one operand box: 128 rows x 128 bytes
+constexpr int kTcSmem = 1024 + kTcStages * 2 * kTcStageBytes + 256;
+
+template <int KIND>
+__global__ void __launch_bounds__(192, 1) k_gram_tc(const __grid_constant__ CUtensorMap map,
+                                                    int tiles, int kblocks, int splits,
+                                                    float* __restrict__ partial, int* status) {
+  extern __shared__ uint8_t smem_dyn[];
+  uint8_t* base = (uint8_t*)(((uintptr_t)smem_dyn + 1023) & ~(uintptr_t)1023);
+  uint8_t* ring = base;  // stage s: A at ring + s*2*SB, B at + SB
+  uint64_t* full = (uint64_t*)(ring + kTcStages * 2 * kTcStageBytes);
+  uint64_t* empty = full + kTcStages;
+  uint64_t* done = empty + kTcStages;
+  uint32_t* tmem_slot = (uint32_t*)(done + 1);
+  volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int ti, tj;
+  tri_index(blockIdx.x, ti, tj);
+  const bool diag = (ti == tj);
+  const int sp = blockIdx.y;
+  const int per = (kblocks + splits - 1) / splits;
+  const int kb0 = sp * per, kb1 = min(kblocks, kb0 + per);
+  const int nkb = max(0, kb1 - kb0);
+  constexpr int KB = (KIND == 0) ? 32 : 64;  // elements per 128-byte row
+  constexpr uint32_t kIdesc = make_idesc(KIND == 0 ? 2u : 1u, kTcTile, kTcTile);
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kTcStages; ++s) {
+      mbar_init(full + s, 1);
+      mbar_init(empty + s, 1);
+    }
+    mbar_init(done, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(128)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    // ---- TMA producer ----
+    const uint32_t bytes = diag ? kTcStageBytes : 2 * kTcStageBytes;
+    int issued = 0;
+    for (int i = 0; i < nkb; ++i) {
+      const int s = i % kTcStages;
+      const uint32_t ph = (uint32_t)((i / kTcStages) & 1);
+      if (!mbar_wait(empty + s, ph ^ 1u, abort_flag)) {
+        set_status(status, DEV_TIMEOUT);
+        *abort_flag = 1;
+        break;
+      }
+      mbar_expect_tx(full + s, bytes);
+      uint8_t* a = ring + s * 2 * kTcStageBytes;
+      const int x = (kb0 + i) * KB;
+      tma_load_2d(a, &map, x, ti * kTcTile, full + s);
+      if (!diag) tma_load_2d(a + kTcStageBytes, &map, x, tj * kTcTile, full + s);
+      ++issued;
+    }
+    // drain: every issued copy must land before the CTA can exit
+    for (int i = max(0, issued - kTcStages); i < issued; ++i) {
+      const int s = i % kTcStages;
+      const uint32_t ph = (uint32_t)((i / kTcStages) & 1);
+      volatile int never = 0;
+      for (long long it = 0; it < kSpinLimit && !mbar_try_wait(full + s, ph); ++it)
+        if (it > 32) __nanosleep(64);
+      (void)never;
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ---- MMA issuer ----
+    for (int i = 0; i < nkb; ++i) {
+      const int s = i % kTcStages;
+      const uint32_t ph = (uint32_t)((i / kTcStages) & 1);
+      if (!mbar_wait(full + s, ph, abort_flag)) {
+        set_status(status, DEV_TIMEOUT);
+        *abort_flag = 1;
+        break;
+      }
+      tc_fence_after();
+      uint8_t* a = ring + s * 2 * kTcStageBytes;
+      const uint64_t ad = smem_desc_sw128(smem_u32(a));
+      const uint64_t bd = diag ? ad : smem_desc_sw128(smem_u32(a + kTcStageBytes));
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk)  // four 32-byte K steps per 128-byte row
+        tc_mma<KIND>(tmem, ad + 2 * kk, bd + 2 * kk, kIdesc, (i > 0 || kk > 0) ? 1u : 0u);
+      tc_commit(empty + s);
+    }
+    tc_commit(done);  // arrives once all issued MMAs have completed
+  } else if (warp >= 2) {
+    // ---- epilogue ----
+    bool ok = false;
+    for (long long it = 0; it < kSpinLimit; ++it) {
+      if (mbar_try_wait(done, 0)) { ok = true; break; }
+      if (it > 32) __nanosleep(128);
+    }
+    tc_fence_after();
+    const int quarter = warp & 3;
+    const int row = quarter * 32 + lane;
+    float* out = partial + ((int64_t)sp * tiles + blockIdx.x) * kTcTile * kTcTile +
+                 (int64_t)row * kTcTile;
+    if (!ok) {
+      set_status(status, DEV_TIMEOUT);
+    } else if (nkb == 0 || *abort_flag) {
+      for (int c = 0; c < kTcTile; ++c) out[c] = 0.f;
+    } else {
+#pragma unroll 1
+      for (int c = 0; c < kTcTile; c += 32) {
+        float v[32];
+        tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)c, v);
+#pragma unroll
+        for (int u = 0; u < 32; u += 4)
+          *reinterpret_cast<float4*>(out + c + u) = make_float4(v[u], v[u + 1], v[u + 2], v[u + 3]);
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(128)
+                 : "memory");
+  }
+}
+
+// ----------------------------------------------------------------------------
+// Host side
+// ----------------------------------------------------------------------------
+typedef CUresult (*PFN_encodeTiled)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                    const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                    const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                    CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static PFN_encodeTiled get_encode() {
+  static PFN_encodeTiled fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &p, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_encodeTiled)p;
+  }
+  return fn;
+}
+
+cudaError_t launch_gram(const GramPlan& g, const void* SA, void* operand, float* partial_f,
+                        double* partial_d, double scale, double shift, double* H, int* status,
+                        cudaStream_t st) {
+  cudaError_t e;
+  const int red_blocks = (int)std::min<int64_t>(((int64_t)g.d * g.d + 255) / 256, 4096);
+  if (g.prec == IHS_PREC_FP64) {
+    const int64_t kchunk = ((g.m + g.splits - 1) / g.splits + 15) / 16 * 16;
+    dim3 grid(g.tiles, g.splits);
+    { k_gram_f64<<<grid, 256, 0, st>>>((const double*)SA, g.m, g.d, g.tiles, kchunk, partial_d); note_launches(1); }
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    { k_gram_reduce<double><<<red_blocks, 256, 0, st>>>(partial_d, g.d, g.tdim, g.tiles, g.splits,
+                                                      scale, shift, H, status); note_launches(1); }
+    return cudaGetLastError();
+  }
+  const int T = (g.d + g.tdim - 1) / g.tdim;
+  const int dpad = T * g.tdim;
+  const bool bf16 = (g.prec == IHS_PREC_BF16);
+  dim3 tg((unsigned)((g.ldt + 31) / 32), (unsigned)((dpad + 31) / 32));
+  if (bf16)
+    { k_gram_operand<true><<<tg, 256, 0, st>>>((const float*)SA, g.m, g.d, dpad, g.ldt, operand); note_launches(1); }
+  else
+    { k_gram_operand<false><<<tg, 256, 0, st>>>((const float*)SA, g.m, g.d, dpad, g.ldt, operand); note_launches(1); }
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+
+  PFN_encodeTiled enc = get_encode();
+  if (!enc) return cudaErrorNotSupported;
+  CUtensorMap map;
+  const size_t el = bf16 ? 2 : 4;
+  cuuint64_t gdim[2] = {(cuuint64_t)g.ldt, (cuuint64_t)dpad};
+  cuuint64_t gstride[1] = {(cuuint64_t)(g.ldt * el)};
+  cuuint32_t box[2] = {(cuuint32_t)(128 / el), (cuuint32_t)kTcTile};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = enc(&map, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+                   2, operand, gdim, gstride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+  const int kblocks = (int)(g.ldt / (128 / el));
+  dim3 grid(g.tiles, g.splits);
+  if (bf16) {
+    static bool attr = false;
+    if (!attr) {
+      e = cudaFuncSetAttribute(k_gram_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
+      if (e != cudaSuccess) return e;
+      attr = true;
+    }
+    { k_gram_tc<1><<<grid, 192, kTcSmem, st>>>(map, g.tiles, kblocks, g.splits, partial_f, status); note_launches(1); }
+  } else {
+    static bool attr = false;
+    if (!attr) {
+      e = cudaFuncSetAttribute(k_gram_tc<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
+      if (e != cudaSuccess) return e;
+      attr = true;
+    }
+    { k_gram_tc<0><<<grid, 192, kTcSmem, st>>>(map, g.tiles, kblocks, g.splits, partial_f, status); note_launches(1); }
+  }
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  { k_gram_reduce<float><<<red_blocks, 256, 0, st>>>(partial_f, g.d, g.tdim, g.tiles, g.splits,
+                                                   scale, shift, H, status); note_launches(1); }
+  return cudaGetLastError();
+}

@@ -1,0 +1,134 @@
+// internal.h -- host-side launchers shared between the translation units of
+// libihs.so.  Nothing here is part of the public ABI (include/ihs.h).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+// Kernel launches issued by the library (for the profiler's launch count).
+void note_launches(int k);
+int64_t launches_total();
+
+// ---- sketch draw ----------------------------------------------------------
+SketchKeys make_keys(uint64_t seed, int64_t t, int s, int64_t m);
+cudaError_t launch_hash(const SketchKeys& K, int64_t n, int32_t* bucket, int8_t* sign,
+                        cudaStream_t st);
+
+// ---- stable counting sort of (block, row) pairs by global bucket ------------
+// Keys come either from the sketch draw (pairs p = k*n + i) or from an int32
+// key array (used once to build the CSC copy of a CSR matrix).
+struct SortPlan {
+  int64_t P = 0;       // number of items
+  int m = 0;           // number of buckets
+  int tile = 0;        // items per tile
+  int ntiles = 0;
+  int64_t chunk = 0;   // reduce-chunk size (items) for the segmented reduce
+  int nchunks = 0;
+};
+SortPlan make_sort_plan(int64_t P, int m, int nchunks_target);
+size_t sort_workspace_bytes(const SortPlan& p);
+// perm[pos] = payload, seg_start[m+1], chunk_first[nchunks]: first bucket whose
+// segment contains the chunk's first item.
+cudaError_t launch_sort_sketch(const SortPlan& p, const SketchKeys& K, int64_t n, void* ws,
+                               uint32_t* perm, int32_t* seg_start, int32_t* chunk_first,
+                               cudaStream_t st);
+cudaError_t launch_sort_keys(const SortPlan& p, const int32_t* keys, void* ws, uint32_t* perm,
+                             int32_t* seg_start, cudaStream_t st);
+
+// ---- sketch SA = S A ---------------------------------------------------------
+struct DenseA {
+  const void* val;
+  int64_t n, d, ld;
+  int f32;  // 1: float values, 0: double
+};
+// SA is m x d row-major in Tacc (double if acc64 else float); partial holds
+// 2 * nchunks * d accumulators.
+cudaError_t launch_sketch_dense(const DenseA& A, const SortPlan& p, const uint32_t* perm,
+                                const int32_t* seg_start, const int32_t* chunk_first, int acc64,
+                                void* SA, void* partial, int* counter, int sms, cudaStream_t st,
+                                void* prof = nullptr);
+// Stage boundaries for the profiler (no-ops when prof is null).
+void prof_stage_begin(void* prof, int stage);
+void prof_stage_end(void* prof);
+
+struct CscA {
+  int64_t n, d, nnz;
+  const int64_t* colptr;   // d + 1
+  const int32_t* rowidx;   // nnz, ascending within a column
+  const void* val;         // nnz
+  int f32;
+  // work items: column chunks of at most `chunk` entries
+  int nitems;
+  const int32_t* item_col;     // nitems
+  const int64_t* item_begin;   // nitems
+  const int64_t* item_end;     // nitems
+  const int32_t* item_slot;    // nitems: -1 if the column has one item, else partial slot
+  int nsplit_slots;
+  const int32_t* col_first_item;  // d + 1 (items of column j: [first[j], first[j+1]))
+};
+cudaError_t launch_sketch_csc(const CscA& A, const SketchKeys& K, int64_t m, int acc64, void* SA,
+                              void* partial, cudaStream_t st);
+
+// S^T G gather (G m x d double, out n x d double).
+cudaError_t launch_sketch_adjoint(const SketchKeys& K, int64_t n, int64_t d, const double* G,
+                                  double* out, cudaStream_t st);
+
+// ---- residual and gradient ----------------------------------------------------
+// Dense: g = A^T (b - A x) with FP64-class accuracy; gpart has nwarps*d doubles.
+int rg_dense_warps(int64_t n);
+cudaError_t launch_resid_grad_dense(const DenseA& A, const double* b, const float2* bsplit,
+                                    const double* x, double* r, double* gpart, int nwarps,
+                                    double* g, double lam, cudaStream_t st);
+// CSR rows -> r (stored as double for FP64 values, float2 (hi, lo) for FP32);
+// CSC columns -> g.
+cudaError_t launch_resid_csr(int64_t n, int64_t d, const void* rowptr, int rowptr_i64,
+                             const int32_t* col, const void* val, int f32, const double* b,
+                             const double* x, void* rbuf, double* r_out, cudaStream_t st);
+cudaError_t launch_grad_csc(const CscA& A, const void* rbuf, double* item_part, const double* x,
+                            double lam, double* g, cudaStream_t st);
+
+// ---- Gram ---------------------------------------------------------------------
+struct GramPlan {
+  int d = 0, m = 0;
+  int prec = 0;            // IHS_PREC_*
+  int tiles = 0;           // lower-triangle output tiles
+  int tdim = 0;            // output tile edge
+  int splits = 0;          // split-K factor
+  int64_t ldt = 0;         // leading dimension of the transposed operand (elements)
+};
+GramPlan make_gram_plan(int m, int d, int prec, int num_sms);
+size_t gram_partial_bytes(const GramPlan& g);
+size_t gram_operand_bytes(const GramPlan& g);
+// SA (m x d, double for FP64, float otherwise) -> H (d x d double, full)
+cudaError_t launch_gram(const GramPlan& g, const void* SA, void* operand, float* partial_f,
+                        double* partial_d, double scale, double shift, double* H, int* status,
+                        cudaStream_t st);
+
+// ---- dense d x d linear algebra -------------------------------------------------
+int chol_padded(int d);  // d rounded up to the 32-tile
+cudaError_t launch_cholesky(const double* H, int d, int f32, void* Lbuf, int* status,
+                            cudaStream_t st);
+// x += (L L^T)^{-1} g ; step_norm (device double) gets max |delta|.
+cudaError_t launch_chol_step(const void* Lbuf, int d, int f32, const double* g, double* x,
+                             double* step_norm, cudaStream_t st);
+// delta = (L L^T)^{-1} v (no update), for preconditioning.
+cudaError_t launch_chol_apply(const void* Lbuf, int d, int f32, const double* v, double* out,
+                              cudaStream_t st);
+
+// l1-ball QP step (Eq. 2 over {||x||_1 <= R}); H double d x d.
+struct QpWork {
+  float* Hf;       // d x d float copy of H
+  double* cvec;    // scratch
+  void* Ls;        // support Cholesky (dp x dp, double)
+  int* support;    // d ints, previous face (count in support[d])
+  double* dbuf;    // 8 * d doubles of scratch
+  int* iters;      // FISTA iterations (device counter)
+};
+size_t qp_work_bytes(int d);
+cudaError_t launch_l1_step(const double* H, const void* Lbuf, int f32, int d, const double* g,
+                           double R, int max_iter, double tol, QpWork w, double* x,
+                           double* step_norm, int* status, cudaStream_t st);
+
+// small device vector kernels
+cudaError_t launch_split_b(const double* b, int64_t n, float2* out, cudaStream_t st);

@@ -1,0 +1,484 @@
+// qp.cu -- the l1-ball subproblem of Eq. 2 (LASSO, C = {x : ||x||_1 <= R}):
+//     x^{t+1} = argmin_{||x||_1 <= R} 1/2 (x - x^t)^T H (x - x^t) - g^T (x - x^t),
+// solved exactly (Sec. 3: each subproblem "is solved exactly"), in one CTA:
+//
+//  1. Newton point: if x^t + H^{-1} g lies in the ball it is the answer.
+//  2. Face solve on the support of the previous solution: on a face with
+//     support S and signs sigma the KKT conditions are the bordered system
+//         [H_SS sigma; sigma^T 0] [dS; mu] = [g_S + H_{S,S^c} x^t_{S^c}; R - sigma^T x^t_S]
+//     for the increment dS = x_S - x^t_S and multiplier mu.  The point is
+//     accepted only if mu >= 0, every x_S keeps its sign and
+//     |(H (x - x^t) - g)_j| <= mu off S -- then it is the unique optimum.
+//  3. Otherwise FISTA (Beck & Teboulle 2009) in FP32 with the exact
+//     Euclidean projection onto the l1 ball (Michelot's fixed-point
+//     threshold, exact after finitely many passes) finds the support, and a
+//     face solve is tried every kFaceEvery iterations.
+// The face system is factored in the factor precision of the mode (FP32 in
+// the mixed form) and refined with FP64 residuals, so dS and mu are FP64
+// accurate.  Failure to certify within the iteration cap records
+// DEV_NOT_CONVERGED and leaves the last feasible FISTA point.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+
+#include "internal.h"
+
+constexpr int kQpThreads = 1024;
+constexpr int kQpMaxD = 1024;
+constexpr int kFaceEvery = 25;
+
+size_t qp_work_bytes(int d) {
+  const size_t dp = (size_t)chol_padded(d);
+  return (size_t)d * d * 4 + dp * dp * 8 + (size_t)9 * d * 8 + (size_t)(d + 2) * 4 + 256;
+}
+
+// ---- block reductions (1024 threads) --------------------------------------
+template <typename T>
+__device__ T block_sum(T v, T* red) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  v = warp_sum(v);
+  __syncthreads();
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  if (w == 0) {
+    T s = (lane < (int)(blockDim.x >> 5)) ? red[lane] : T(0);
+    s = warp_sum(s);
+    if (lane == 0) red[32] = s;
+  }
+  __syncthreads();
+  return red[32];
+}
+
+struct QpShared {
+  double xt[kQpMaxD];    // x^t
+  double gd[kQpMaxD];    // g
+  double z[kQpMaxD + 1]; // face solution dS, then mu at [k]
+  double ra[kQpMaxD + 1];
+  float fx[kQpMaxD], fy[kQpMaxD], fv[kQpMaxD];
+  float fxt[kQpMaxD];
+  int S[kQpMaxD];
+  int k;           // support size
+  int accept;
+  double redd[33];
+  float redf[33];
+};
+
+// y = Hf * v (FP32, warp per row)
+__device__ void matvec_f(const float* __restrict__ Hf, int d, const float* v, float* out) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int i = w; i < d; i += (int)(blockDim.x >> 5)) {
+    const float* row = Hf + (int64_t)i * d;
+    float s = 0.f;
+    for (int j = lane; j < d; j += 32) s = fmaf(row[j], v[j], s);
+    s = warp_sum(s);
+    if (lane == 0) out[i] = s;
+  }
+}
+
+// Euclidean projection of v onto {||x||_1 <= R} in place (Michelot's
+// threshold iteration: theta <- (sum_{|v|>theta} |v| - R) / #{|v| > theta}).
+__device__ void project_l1(float* v, int d, float R, QpShared& sh) {
+  float a = 0.f;
+  for (int j = threadIdx.x; j < d; j += blockDim.x) a += fabsf(v[j]);
+  const float tot = block_sum(a, sh.redf);
+  if (tot <= R) return;
+  float theta = (tot - R) / (float)d;
+  int prev = d;
+  for (int it = 0; it < d + 1; ++it) {
+    float s = 0.f, c = 0.f;
+    for (int j = threadIdx.x; j < d; j += blockDim.x) {
+      const float u = fabsf(v[j]);
+      if (u > theta) { s += u; c += 1.f; }
+    }
+    const float S = block_sum(s, sh.redf);
+    const float C = block_sum(c, sh.redf);
+    const int cnt = (int)C;
+    if (cnt == 0) break;
+    const float nt = (S - R) / C;
+    const bool stop = (cnt == prev) || !(nt > theta);
+    theta = fmaxf(theta, nt);
+    prev = cnt;
+    if (stop) break;
+  }
+  for (int j = threadIdx.x; j < d; j += blockDim.x) {
+    const float u = fabsf(v[j]) - theta;
+    v[j] = u > 0.f ? copysignf(u, v[j]) : 0.f;
+  }
+  __syncthreads();
+}
+
+// ---- small dense Cholesky of M = H_SS (k x k, stride ld) in TF, in place --
+template <typename TF>
+__device__ bool chol_small(TF* M, int k, int ld, QpShared& sh) {
+  __shared__ int bad;
+  if (threadIdx.x == 0) bad = 0;
+  __syncthreads();
+  for (int j = 0; j < k; ++j) {
+    if (threadIdx.x == 0) {
+      TF p = M[(int64_t)j * ld + j];
+      if (!(p > TF(0))) { bad = 1; p = TF(1); }
+      M[(int64_t)j * ld + j] = sqrt(p);
+    }
+    __syncthreads();
+    const TF piv = M[(int64_t)j * ld + j];
+    for (int i = j + 1 + threadIdx.x; i < k; i += blockDim.x) M[(int64_t)i * ld + j] /= piv;
+    __syncthreads();
+    const int rem = k - j - 1;
+    const int64_t cnt = (int64_t)rem * (rem + 1) / 2;
+    for (int64_t e = threadIdx.x; e < cnt; e += blockDim.x) {
+      // (r, c) with j < c <= r < k
+      int r = (int)((sqrtf(8.0f * (float)e + 1.0f) - 1.0f) * 0.5f);
+      while ((int64_t)(r + 1) * (r + 2) / 2 <= e) ++r;
+      while ((int64_t)r * (r + 1) / 2 > e) --r;
+      const int c = (int)(e - (int64_t)r * (r + 1) / 2);
+      const int rr = j + 1 + r, cc = j + 1 + c;
+      M[(int64_t)rr * ld + cc] -= M[(int64_t)rr * ld + j] * M[(int64_t)cc * ld + j];
+    }
+    __syncthreads();
+  }
+  return bad == 0;
+}
+
+// out = M^{-1} v with M = L L^T (L in the lower triangle of M), in place in out.
+template <typename TF>
+__device__ void chol_small_solve(const TF* L, int k, int ld, double* v) {
+  for (int j = 0; j < k; ++j) {
+    if (threadIdx.x == 0) v[j] = (double)((TF)v[j] / L[(int64_t)j * ld + j]);
+    __syncthreads();
+    const TF yj = (TF)v[j];
+    for (int i = j + 1 + threadIdx.x; i < k; i += blockDim.x)
+      v[i] = (double)((TF)v[i] - L[(int64_t)i * ld + j] * yj);
+    __syncthreads();
+  }
+  for (int j = k - 1; j >= 0; --j) {
+    if (threadIdx.x == 0) v[j] = (double)((TF)v[j] / L[(int64_t)j * ld + j]);
+    __syncthreads();
+    const TF zj = (TF)v[j];
+    for (int i = threadIdx.x; i < j; i += blockDim.x)
+      v[i] = (double)((TF)v[i] - L[(int64_t)j * ld + i] * zj);
+    __syncthreads();
+  }
+}
+
+// Face solve for support sh.S[0..k) with signs sign(sig_src): fills sh.z
+// (dS, mu at [k]); returns false if the face matrix is not positive definite.
+template <typename TF>
+__device__ bool face_solve(const double* __restrict__ H, int d, double R, const float* sig_src,
+                           TF* Ls, int ld, double* wv, QpShared& sh) {
+  const int k = sh.k;
+  // gather M = H_SS
+  for (int64_t e = threadIdx.x; e < (int64_t)k * k; e += blockDim.x) {
+    const int a = (int)(e / k), b = (int)(e - (int64_t)a * k);
+    Ls[(int64_t)a * ld + b] = (TF)H[(int64_t)sh.S[a] * d + sh.S[b]];
+  }
+  __syncthreads();
+  if (!chol_small<TF>(Ls, k, ld, sh)) return false;
+  // w = M^{-1} sigma
+  for (int a = threadIdx.x; a < k; a += blockDim.x) wv[a] = sig_src[sh.S[a]] > 0.f ? 1.0 : -1.0;
+  __syncthreads();
+  chol_small_solve<TF>(Ls, k, ld, wv);
+  double sw = 0.0;
+  for (int a = threadIdx.x; a < k; a += blockDim.x)
+    sw += (sig_src[sh.S[a]] > 0.f ? 1.0 : -1.0) * wv[a];
+  const double sTw = block_sum(sw, sh.redd);
+  // right-hand side: ra = g_S + H_{S,S^c} x^t_{S^c},  beta = R - sigma^T x^t_S
+  // (S^c part: x^t_l for l not in S)
+  __shared__ unsigned char inS[kQpMaxD];
+  for (int j = threadIdx.x; j < d; j += blockDim.x) inS[j] = 0;
+  __syncthreads();
+  for (int a = threadIdx.x; a < k; a += blockDim.x) inS[sh.S[a]] = 1;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
+  for (int a = wi; a < k; a += (int)(blockDim.x >> 5)) {
+    const double* row = H + (int64_t)sh.S[a] * d;
+    double s = 0.0;
+    for (int l = lane; l < d; l += 32)
+      if (!inS[l] && sh.xt[l] != 0.0) s = fma(row[l], sh.xt[l], s);
+    s = warp_sum(s);
+    if (lane == 0) sh.ra[a] = sh.gd[sh.S[a]] + s;
+  }
+  double bl = 0.0;
+  for (int a = threadIdx.x; a < k; a += blockDim.x)
+    bl += (sig_src[sh.S[a]] > 0.f ? 1.0 : -1.0) * sh.xt[sh.S[a]];
+  const double beta = R - block_sum(bl, sh.redd);
+  // solve + FP64 refinement: z = 0, then residual steps
+  for (int a = threadIdx.x; a <= k; a += blockDim.x) sh.z[a] = 0.0;
+  __syncthreads();
+  const int rounds = sizeof(TF) == 4 ? 4 : 2;
+  for (int it = 0; it < rounds; ++it) {
+    // residual r = rhs - K z  (FP64), r_a in sh.ra? keep rhs: use wv2 = ra - (M z + mu sigma)
+    double* res = wv + d;  // scratch (wv holds 2d doubles)
+    for (int a = wi; a < k; a += (int)(blockDim.x >> 5)) {
+      const double* row = H + (int64_t)sh.S[a] * d;
+      double s = 0.0;
+      for (int b = lane; b < k; b += 32) s = fma(row[sh.S[b]], sh.z[b], s);
+      s = warp_sum(s);
+      if (lane == 0)
+        res[a] = sh.ra[a] - s - sh.z[k] * (sig_src[sh.S[a]] > 0.f ? 1.0 : -1.0);
+    }
+    double sz = 0.0;
+    for (int a = threadIdx.x; a < k; a += blockDim.x)
+      sz += (sig_src[sh.S[a]] > 0.f ? 1.0 : -1.0) * sh.z[a];
+    const double rb = beta - block_sum(sz, sh.redd);
+    // correction: u = M^{-1} res; dmu = (sigma^T u - rb) / sigma^T w; dz = u - dmu w
+    chol_small_solve<TF>(Ls, k, ld, res);
+    double su = 0.0;
+    for (int a = threadIdx.x; a < k; a += blockDim.x)
+      su += (sig_src[sh.S[a]] > 0.f ? 1.0 : -1.0) * res[a];
+    const double sTu = block_sum(su, sh.redd);
+    const double dmu = (sTu - rb) / sTw;
+    for (int a = threadIdx.x; a < k; a += blockDim.x) sh.z[a] += res[a] - dmu * wv[a];
+    if (threadIdx.x == 0) sh.z[k] += dmu;
+    __syncthreads();
+  }
+  return true;
+}
+
+// Check the KKT conditions of the face candidate; on success write x.
+template <typename TF>
+__device__ bool face_accept(const float* __restrict__ Hf, int d, const float* sig_src, double tol,
+                            double* __restrict__ x, QpShared& sh) {
+  const int k = sh.k;
+  const double mu = sh.z[k];
+  __shared__ int okf;
+  if (threadIdx.x == 0) okf = (mu >= -tol) ? 1 : 0;
+  __syncthreads();
+  // candidate increment in FP32 for the off-support test: fv = x - x^t
+  for (int j = threadIdx.x; j < d; j += blockDim.x) sh.fv[j] = (float)(-sh.xt[j]);
+  __syncthreads();
+  for (int a = threadIdx.x; a < k; a += blockDim.x) {
+    const int j = sh.S[a];
+    const double xn = sh.xt[j] + sh.z[a];
+    const bool pos = sig_src[j] > 0.f;
+    if (!(pos ? xn > 0.0 : xn < 0.0)) okf = 0;
+    sh.fv[j] = (float)sh.z[a];
+  }
+  __syncthreads();
+  if (!okf) return false;
+  // off support: |(H dx - g)_j| <= mu
+  matvec_f(Hf, d, sh.fv, sh.fy);
+  __syncthreads();
+  double gscale = 0.0;
+  for (int j = threadIdx.x; j < d; j += blockDim.x) gscale = fmax(gscale, fabs(sh.gd[j]));
+  for (int o = 16; o > 0; o >>= 1) gscale = fmax(gscale, __shfl_xor_sync(0xffffffffu, gscale, o));
+  if ((threadIdx.x & 31) == 0) sh.redd[threadIdx.x >> 5] = gscale;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double m = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmax(m, sh.redd[w]);
+    sh.redd[32] = m;
+  }
+  __syncthreads();
+  gscale = sh.redd[32];
+  __shared__ unsigned char inS2[kQpMaxD];
+  for (int j = threadIdx.x; j < d; j += blockDim.x) inS2[j] = 0;
+  __syncthreads();
+  for (int a = threadIdx.x; a < k; a += blockDim.x) inS2[sh.S[a]] = 1;
+  __syncthreads();
+  const double slack = 1e-5 * (gscale + fabs(mu)) + tol;
+  for (int j = threadIdx.x; j < d; j += blockDim.x) {
+    if (inS2[j]) continue;
+    const double gj = (double)sh.fy[j] - sh.gd[j];
+    if (fabs(gj) > mu + slack) okf = 0;
+  }
+  __syncthreads();
+  if (!okf) return false;
+  for (int j = threadIdx.x; j < d; j += blockDim.x) sh.ra[j] = 0.0;
+  __syncthreads();
+  for (int a = threadIdx.x; a < k; a += blockDim.x) sh.ra[sh.S[a]] = sh.xt[sh.S[a]] + sh.z[a];
+  __syncthreads();
+  for (int j = threadIdx.x; j < d; j += blockDim.x) x[j] = sh.ra[j];
+  return true;
+}
+
+template <typename TF>
+__global__ void __launch_bounds__(kQpThreads, 1) k_l1_step(
+    const double* __restrict__ H, const float* __restrict__ Hf, int d,
+    const double* __restrict__ g, const double* __restrict__ du, double R, int max_iter,
+    double tol, double* __restrict__ x, double* __restrict__ step_norm, int* __restrict__ support,
+    int* __restrict__ iters, double* __restrict__ wv, TF* __restrict__ Ls, int ld, int* status) {
+  extern __shared__ unsigned char qp_smem[];
+  QpShared& sh = *reinterpret_cast<QpShared*>(qp_smem);
+  for (int j = threadIdx.x; j < d; j += blockDim.x) {
+    sh.xt[j] = x[j];
+    sh.gd[j] = g[j];
+    sh.fxt[j] = (float)x[j];
+  }
+  __syncthreads();
+  bool done = false;
+  // 1. Newton point
+  {
+    double a = 0.0;
+    for (int j = threadIdx.x; j < d; j += blockDim.x) a += fabs(sh.xt[j] + du[j]);
+    const double l1 = block_sum(a, sh.redd);
+    if (l1 <= R) {
+      for (int j = threadIdx.x; j < d; j += blockDim.x) x[j] = sh.xt[j] + du[j];
+      if (threadIdx.x == 0) support[d] = 0;
+      done = true;
+    }
+  }
+  // 2. previous face (signs of x^t on the stored support)
+  if (!done) {
+    if (threadIdx.x == 0) sh.k = support[d];
+    __syncthreads();
+    if (sh.k > 0) {
+      for (int a = threadIdx.x; a < sh.k; a += blockDim.x) sh.S[a] = support[a];
+      for (int j = threadIdx.x; j < d; j += blockDim.x) sh.fv[j] = sh.fxt[j];
+      __syncthreads();
+      // a stored index whose x^t entry is zero has no sign: skip the attempt
+      __shared__ int zero_sign;
+      if (threadIdx.x == 0) zero_sign = 0;
+      __syncthreads();
+      for (int a = threadIdx.x; a < sh.k; a += blockDim.x)
+        if (sh.xt[sh.S[a]] == 0.0) zero_sign = 1;
+      __syncthreads();
+      if (!zero_sign) {
+        for (int j = threadIdx.x; j < d; j += blockDim.x) sh.fx[j] = sh.xt[j] > 0.0 ? 1.f : -1.f;
+        __syncthreads();
+        if (face_solve<TF>(H, d, R, sh.fx, Ls, ld, wv, sh) &&
+            face_accept<TF>(Hf, d, sh.fx, tol, x, sh))
+          done = true;
+      }
+    }
+    __syncthreads();
+  }
+  // 3. FISTA + periodic face solves
+  if (!done) {
+    // Lipschitz constant by power iteration on Hf
+    for (int j = threadIdx.x; j < d; j += blockDim.x) sh.fv[j] = 1.0f + 0.01f * (float)(j % 7);
+    __syncthreads();
+    float lam = 1.f;
+    for (int it = 0; it < 40; ++it) {
+      matvec_f(Hf, d, sh.fv, sh.fy);
+      __syncthreads();
+      float a = 0.f;
+      for (int j = threadIdx.x; j < d; j += blockDim.x) a += sh.fy[j] * sh.fy[j];
+      const float nrm = sqrtf(block_sum(a, sh.redf));
+      float b = 0.f;
+      for (int j = threadIdx.x; j < d; j += blockDim.x) b += sh.fy[j] * sh.fv[j];
+      lam = block_sum(b, sh.redf);
+      for (int j = threadIdx.x; j < d; j += blockDim.x) sh.fv[j] = sh.fy[j] / fmaxf(nrm, 1e-30f);
+      __syncthreads();
+    }
+    const float Lip = 1.1f * fmaxf(lam, 1e-30f);
+    const float Rf = (float)R;
+    for (int j = threadIdx.x; j < d; j += blockDim.x) sh.fx[j] = sh.fxt[j];
+    __syncthreads();
+    project_l1(sh.fx, d, Rf, sh);
+    for (int j = threadIdx.x; j < d; j += blockDim.x) sh.fy[j] = sh.fx[j];
+    __syncthreads();
+    float tk = 1.f;
+    const int cap = max_iter > 0 ? max_iter : 20000;
+    int it = 0;
+    for (; it < cap && !done; ++it) {
+      // grad at y: Hf (y - x^t) - g
+      for (int j = threadIdx.x; j < d; j += blockDim.x) sh.fv[j] = sh.fy[j] - sh.fxt[j];
+      __syncthreads();
+      float* gv = sh.fv;  // reuse: matvec writes into a separate buffer below
+      __shared__ float hv[kQpMaxD];
+      matvec_f(Hf, d, gv, hv);
+      __syncthreads();
+      for (int j = threadIdx.x; j < d; j += blockDim.x)
+        sh.fv[j] = sh.fy[j] - (hv[j] - (float)sh.gd[j]) / Lip;
+      __syncthreads();
+      project_l1(sh.fv, d, Rf, sh);
+      const float tn = 0.5f * (1.f + sqrtf(1.f + 4.f * tk * tk));
+      const float mom = (tk - 1.f) / tn;
+      for (int j = threadIdx.x; j < d; j += blockDim.x) {
+        const float xn = sh.fv[j];
+        sh.fy[j] = xn + mom * (xn - sh.fx[j]);
+        sh.fx[j] = xn;
+      }
+      tk = tn;
+      __syncthreads();
+      if ((it + 1) % kFaceEvery == 0) {
+        // support of the FISTA iterate
+        if (threadIdx.x == 0) {
+          int k = 0;
+          for (int j = 0; j < d; ++j)
+            if (sh.fx[j] != 0.f) sh.S[k++] = j;
+          sh.k = k;
+        }
+        __syncthreads();
+        if (sh.k > 0 && face_solve<TF>(H, d, R, sh.fx, Ls, ld, wv, sh) &&
+            face_accept<TF>(Hf, d, sh.fx, tol, x, sh))
+          done = true;
+        __syncthreads();
+      }
+    }
+    if (threadIdx.x == 0) atomicAdd(iters, it);
+    if (!done) {
+      set_status(status, DEV_NOT_CONVERGED);
+      for (int j = threadIdx.x; j < d; j += blockDim.x) x[j] = (double)sh.fx[j];
+      if (threadIdx.x == 0) support[d] = 0;
+      done = true;
+    }
+  }
+  __syncthreads();
+  // record the support of the new x and the step size
+  double mx = 0.0;
+  for (int j = threadIdx.x; j < d; j += blockDim.x) mx = fmax(mx, fabs(x[j] - sh.xt[j]));
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0) sh.redd[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double m = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmax(m, sh.redd[w]);
+    *step_norm = m;
+    int k = 0;
+    double l1 = 0.0;
+    for (int j = 0; j < d; ++j) l1 += fabs(x[j]);
+    if (l1 >= R * (1.0 - 1e-12))
+      for (int j = 0; j < d; ++j)
+        if (x[j] != 0.0) support[k++] = j;
+    support[d] = k;
+  }
+}
+
+__global__ void k_to_float(const double* __restrict__ a, int64_t n, float* __restrict__ b) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = (float)a[i];
+}
+
+cudaError_t launch_l1_step(const double* H, const void* Lbuf, int f32, int d, const double* g,
+                           double R, int max_iter, double tol, QpWork w, double* x,
+                           double* step_norm, int* status, cudaStream_t st) {
+  if (d > kQpMaxD) return cudaErrorInvalidValue;
+  const int64_t dd = (int64_t)d * d;
+  { k_to_float<<<(unsigned)std::min<int64_t>((dd + 255) / 256, 2048), 256, 0, st>>>(H, dd, w.Hf); note_launches(1); }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  double* du = w.dbuf;              // d
+  double* wv = w.dbuf + d;          // 2d doubles of face-solve scratch
+  e = launch_chol_apply(Lbuf, d, f32, g, du, st);
+  if (e != cudaSuccess) return e;
+  const size_t smem = sizeof(QpShared);
+  const int ld = chol_padded(d);
+  const double tl = tol > 0 ? tol : 1e-12;
+  if (f32) {
+    static bool attr = false;
+    if (!attr) {
+      e = cudaFuncSetAttribute(k_l1_step<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)smem);
+      if (e != cudaSuccess) return e;
+      attr = true;
+    }
+    { k_l1_step<float><<<1, kQpThreads, smem, st>>>(H, w.Hf, d, g, du, R, max_iter, tl, x,
+                                                  step_norm, w.support, w.iters, wv,
+                                                  (float*)w.Ls, ld, status); note_launches(1); }
+  } else {
+    static bool attr = false;
+    if (!attr) {
+      e = cudaFuncSetAttribute(k_l1_step<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)smem);
+      if (e != cudaSuccess) return e;
+      attr = true;
+    }
+    { k_l1_step<double><<<1, kQpThreads, smem, st>>>(H, w.Hf, d, g, du, R, max_iter, tl, x,
+                                                   step_norm, w.support, w.iters, wv,
+                                                   (double*)w.Ls, ld, status); note_launches(1); }
+  }
+  return cudaGetLastError();
+}

@@ -1,0 +1,432 @@
+// sketch.cu -- SA = S A for the CountSketch / SJLT of Sec. 2.
+//
+// Dense A: the (block, row) pairs sorted by bucket (hash_sort.cu) are split
+// into equal chunks, one warp per chunk, so every warp streams the same
+// number of rows whatever the bucket sizes.  A warp walks the buckets that
+// meet its chunk; lanes own interleaved VEC-wide column groups and read each
+// row of A with coalesced vector loads (a 2 KB row of a 500-column FP32
+// matrix is one 512-byte line per lane group).  Rows of a bucket are added
+// in ascending row order -- the order of the streaming definition -- so the
+// FP64 result equals a plain sequential loop.  A bucket that straddles
+// chunks leaves per-chunk partial rows that a fix-up kernel adds in chunk
+// order (deterministic); it also writes the zero rows of empty buckets.
+// That split is used for FP32 accumulation (the mixed form); FP64
+// accumulation keeps whole buckets per warp (k_sketch_dense_units) so the
+// result is bit-identical to the sequential definition.
+//
+// CSR A: a column-major (CSC) copy is built once at create.  One warp owns
+// (column chunk, SJLT block k) and keeps that block's m/s accumulators in
+// shared memory; entries arrive in ascending row order, buckets are drawn
+// on the fly, and lanes that hit the same bucket add in lane (= row) order
+// through __match_any_sync rounds, so again no atomics and a fixed order.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+
+#include "internal.h"
+
+// ----------------------------------------------------------------------------
+// Dense
+// ----------------------------------------------------------------------------
+template <typename Tin, typename Tacc, int VEC, int NV>
+__global__ void __launch_bounds__(256) k_sketch_dense(
+    const Tin* __restrict__ A, int64_t lda, int d, const uint32_t* __restrict__ perm,
+    const int32_t* __restrict__ seg_start, const int32_t* __restrict__ chunk_first, int m,
+    int64_t P, int64_t CH, int nchunks, Tacc* __restrict__ SA, Tacc* __restrict__ partial) {
+  const int lane = threadIdx.x & 31;
+  const int w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (w >= nchunks) return;
+  const int slab = blockIdx.y;
+  const int col_base = slab * (32 * NV * VEC) + lane * VEC;
+  const int64_t c0 = (int64_t)w * CH;
+  const int64_t c1 = min(P, c0 + CH);
+
+  bool colok[NV];
+#pragma unroll
+  for (int q = 0; q < NV; ++q) colok[q] = (col_base + q * 32 * VEC) < d;
+
+  for (int b = chunk_first[w]; b < m; ++b) {
+    const int64_t sb = seg_start[b], eb = seg_start[b + 1];
+    if (sb >= c1) break;
+    const int64_t lo = max(sb, c0), hi = min(eb, c1);
+    if (lo >= hi) continue;
+    Tacc acc[NV][VEC];
+#pragma unroll
+    for (int q = 0; q < NV; ++q)
+#pragma unroll
+      for (int v = 0; v < VEC; ++v) acc[q][v] = Tacc(0);
+
+    for (int64_t base = lo; base < hi; base += 32) {
+      const int cnt = (int)min((int64_t)32, hi - base);
+      uint32_t my = (lane < cnt) ? __ldg(perm + base + lane) : 0u;
+      int j = 0;
+      // four rows in flight per step
+      for (; j + 4 <= cnt; j += 4) {
+        Tin v[4][NV][VEC];
+        uint32_t e[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          e[u] = __shfl_sync(0xffffffffu, my, j + u);
+          const Tin* row = A + (int64_t)(e[u] & 0x7fffffffu) * lda + col_base;
+#pragma unroll
+          for (int q = 0; q < NV; ++q) {
+            if (colok[q]) load_vec_stream<Tin, VEC>(row + q * 32 * VEC, v[u][q]);
+            else {
+#pragma unroll
+              for (int t = 0; t < VEC; ++t) v[u][q][t] = Tin(0);
+            }
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const bool neg = (e[u] >> 31) != 0;
+#pragma unroll
+          for (int q = 0; q < NV; ++q)
+#pragma unroll
+            for (int t = 0; t < VEC; ++t) {
+              Tacc x = (Tacc)v[u][q][t];
+              acc[q][t] = neg ? acc[q][t] - x : acc[q][t] + x;
+            }
+        }
+      }
+      for (; j < cnt; ++j) {
+        uint32_t e = __shfl_sync(0xffffffffu, my, j);
+        const Tin* row = A + (int64_t)(e & 0x7fffffffu) * lda + col_base;
+        const bool neg = (e >> 31) != 0;
+#pragma unroll
+        for (int q = 0; q < NV; ++q) {
+          if (!colok[q]) continue;
+          Tin v[VEC];
+          load_vec_stream<Tin, VEC>(row + q * 32 * VEC, v);
+#pragma unroll
+          for (int t = 0; t < VEC; ++t) {
+            Tacc x = (Tacc)v[t];
+            acc[q][t] = neg ? acc[q][t] - x : acc[q][t] + x;
+          }
+        }
+      }
+    }
+    // write: whole bucket -> SA row; straddling bucket -> this chunk's slot
+    const bool split = (sb / CH) != ((eb - 1) / CH);
+    Tacc* dst;
+    if (!split) {
+      dst = SA + (int64_t)b * d;
+    } else {
+      const int slot = ((sb / CH) == w && sb != c0) ? 1 : 0;
+      dst = partial + ((int64_t)w * 2 + slot) * d;
+    }
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+      if (!colok[q]) continue;
+#pragma unroll
+      for (int t = 0; t < VEC; ++t) {
+        int c = col_base + q * 32 * VEC + t;
+        if (c < d) dst[c] = acc[q][t];
+      }
+    }
+  }
+}
+
+// One warp per bucket: zero rows for empty buckets, chunk-ordered sums for
+// buckets that straddle chunks.
+template <typename Tacc>
+__global__ void k_sketch_fixup(const int32_t* __restrict__ seg_start, int m, int d, int64_t CH,
+                               const Tacc* __restrict__ partial, Tacc* __restrict__ SA) {
+  const int lane = threadIdx.x & 31;
+  const int b = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (b >= m) return;
+  const int64_t sb = seg_start[b], eb = seg_start[b + 1];
+  Tacc* out = SA + (int64_t)b * d;
+  if (sb == eb) {
+    for (int c = lane; c < d; c += 32) out[c] = Tacc(0);
+    return;
+  }
+  const int64_t cf = sb / CH, cl = (eb - 1) / CH;
+  if (cf == cl) return;
+  for (int c = lane; c < d; c += 32) {
+    Tacc acc = Tacc(0);
+    for (int64_t w = cf; w <= cl; ++w) {
+      int slot = (w == cf && sb != w * CH) ? 1 : 0;
+      acc += partial[(w * 2 + slot) * d + c];
+    }
+    out[c] = acc;
+  }
+}
+
+// FP64 accumulation: work units are (bucket, column slab), handed out by an
+// atomic counter, so every bucket is summed by one warp in ascending row
+// order -- the exact order of the streaming definition, hence bit-identical
+// FP64 results -- while column slabs keep units small enough to balance.
+template <typename Tin, int VEC>
+__global__ void __launch_bounds__(256) k_sketch_dense_units(
+    const Tin* __restrict__ A, int64_t lda, int d, const uint32_t* __restrict__ perm,
+    const int32_t* __restrict__ seg_start, int m, int nslabs, int* __restrict__ counter,
+    double* __restrict__ SA) {
+  const int lane = threadIdx.x & 31;
+  const int64_t units = (int64_t)m * nslabs;
+  for (;;) {
+    int u = 0;
+    if (lane == 0) u = atomicAdd(counter, 1);
+    u = __shfl_sync(0xffffffffu, u, 0);
+    if (u >= units) break;
+    const int b = u / nslabs, slab = u - (u / nslabs) * nslabs;
+    const int col = slab * 32 * VEC + lane * VEC;
+    const bool ok = col < d;
+    double acc[VEC];
+#pragma unroll
+    for (int t = 0; t < VEC; ++t) acc[t] = 0.0;
+    const int64_t lo = seg_start[b], hi = seg_start[b + 1];
+    for (int64_t base = lo; base < hi; base += 32) {
+      const int cnt = (int)min((int64_t)32, hi - base);
+      const uint32_t my = (lane < cnt) ? __ldg(perm + base + lane) : 0u;
+      int j = 0;
+      for (; j + 4 <= cnt; j += 4) {
+        Tin v[4][VEC];
+        uint32_t e[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          e[q] = __shfl_sync(0xffffffffu, my, j + q);
+          if (ok) load_vec_stream<Tin, VEC>(A + (int64_t)(e[q] & 0x7fffffffu) * lda + col, v[q]);
+          else {
+#pragma unroll
+            for (int t = 0; t < VEC; ++t) v[q][t] = Tin(0);
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const bool neg = (e[q] >> 31) != 0;
+#pragma unroll
+          for (int t = 0; t < VEC; ++t) {
+            const double x = (double)v[q][t];
+            acc[t] = neg ? acc[t] - x : acc[t] + x;
+          }
+        }
+      }
+      for (; j < cnt; ++j) {
+        const uint32_t e = __shfl_sync(0xffffffffu, my, j);
+        if (!ok) continue;
+        Tin v[VEC];
+        load_vec_stream<Tin, VEC>(A + (int64_t)(e & 0x7fffffffu) * lda + col, v);
+        const bool neg = (e >> 31) != 0;
+#pragma unroll
+        for (int t = 0; t < VEC; ++t) {
+          const double x = (double)v[t];
+          acc[t] = neg ? acc[t] - x : acc[t] + x;
+        }
+      }
+    }
+    if (ok) {
+      double* dst = SA + (int64_t)b * d + col;
+#pragma unroll
+      for (int t = 0; t < VEC; ++t)
+        if (col + t < d) dst[t] = acc[t];
+    }
+  }
+}
+
+template <typename Tin, int VEC>
+static cudaError_t run_dense_units(const DenseA& A, const SortPlan& p, const uint32_t* perm,
+                                   const int32_t* seg, int* counter, void* SA, int sms,
+                                   cudaStream_t st) {
+  const int nslabs = (int)((A.d + 32 * VEC - 1) / (32 * VEC));
+  cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int), st);
+  if (e != cudaSuccess) return e;
+  { k_sketch_dense_units<Tin, VEC><<<sms * 8, 256, 0, st>>>((const Tin*)A.val, A.ld, (int)A.d,
+                                                          perm, seg, p.m, nslabs, counter,
+                                                          (double*)SA); note_launches(1); }
+  return cudaGetLastError();
+}
+
+template <typename Tin, typename Tacc, int VEC, int NV>
+static cudaError_t run_dense(const DenseA& A, const SortPlan& p, const uint32_t* perm,
+                             const int32_t* seg, const int32_t* cf, void* SA, void* partial,
+                             cudaStream_t st, void* prof) {
+  const int per_slab = 32 * NV * VEC;
+  dim3 grid((p.nchunks + 7) / 8, (unsigned)((A.d + per_slab - 1) / per_slab));
+  { k_sketch_dense<Tin, Tacc, VEC, NV><<<grid, 256, 0, st>>>(
+      (const Tin*)A.val, A.ld, (int)A.d, perm, seg, cf, p.m, p.P, p.chunk, p.nchunks,
+      (Tacc*)SA, (Tacc*)partial); note_launches(1); }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  prof_stage_end(prof);
+  prof_stage_begin(prof, IHS_ST_SKETCH_FIX);
+  { k_sketch_fixup<Tacc><<<(p.m + 7) / 8, 256, 0, st>>>(seg, p.m, (int)A.d, p.chunk,
+                                                      (const Tacc*)partial, (Tacc*)SA); note_launches(1); }
+  return cudaGetLastError();
+}
+
+template <typename Tin, typename Tacc, int VEC>
+static cudaError_t dense_nv(const DenseA& A, const SortPlan& p, const uint32_t* perm,
+                            const int32_t* seg, const int32_t* cf, void* SA, void* partial,
+                            cudaStream_t st, void* prof) {
+  const int64_t groups = (A.d + VEC - 1) / VEC;  // vector groups per row
+  if (groups <= 32) return run_dense<Tin, Tacc, VEC, 1>(A, p, perm, seg, cf, SA, partial, st, prof);
+  if (groups <= 64) return run_dense<Tin, Tacc, VEC, 2>(A, p, perm, seg, cf, SA, partial, st, prof);
+  return run_dense<Tin, Tacc, VEC, 4>(A, p, perm, seg, cf, SA, partial, st, prof);  // + slabs
+}
+
+cudaError_t launch_sketch_dense(const DenseA& A, const SortPlan& p, const uint32_t* perm,
+                                const int32_t* seg, const int32_t* cf, int acc64, void* SA,
+                                void* partial, int* counter, int sms, cudaStream_t st,
+                                void* prof) {
+  const uintptr_t base = (uintptr_t)A.val;
+  if (acc64) {
+    if (A.f32) {
+      const bool v4 = (A.ld % 4 == 0) && (A.d % 4 == 0) && (base % 16 == 0);
+      return v4 ? run_dense_units<float, 4>(A, p, perm, seg, counter, SA, sms, st)
+                : run_dense_units<float, 1>(A, p, perm, seg, counter, SA, sms, st);
+    }
+    const bool v2 = (A.ld % 2 == 0) && (A.d % 2 == 0) && (base % 16 == 0);
+    return v2 ? run_dense_units<double, 2>(A, p, perm, seg, counter, SA, sms, st)
+              : run_dense_units<double, 1>(A, p, perm, seg, counter, SA, sms, st);
+  }
+  if (A.f32) {
+    const bool v4 = (A.ld % 4 == 0) && (A.d % 4 == 0) && (base % 16 == 0);
+    return v4 ? dense_nv<float, float, 4>(A, p, perm, seg, cf, SA, partial, st, prof)
+              : dense_nv<float, float, 1>(A, p, perm, seg, cf, SA, partial, st, prof);
+  }
+  const bool v2 = (A.ld % 2 == 0) && (A.d % 2 == 0) && (base % 16 == 0);
+  return v2 ? dense_nv<double, float, 2>(A, p, perm, seg, cf, SA, partial, st, prof)
+            : dense_nv<double, float, 1>(A, p, perm, seg, cf, SA, partial, st, prof);
+}
+
+// ----------------------------------------------------------------------------
+// CSR through the CSC copy
+// ----------------------------------------------------------------------------
+template <typename Tin, typename Tacc>
+__global__ void __launch_bounds__(256) k_sketch_csc(
+    const int32_t* __restrict__ rowidx, const Tin* __restrict__ val, int nitems,
+    const int32_t* __restrict__ item_col, const int64_t* __restrict__ item_begin,
+    const int64_t* __restrict__ item_end, const int32_t* __restrict__ item_slot,
+    const SketchKeys K, int d, Tacc* __restrict__ SA, Tacc* __restrict__ partial) {
+  extern __shared__ unsigned char smem_raw[];
+  const int lane = threadIdx.x & 31;
+  const int wib = threadIdx.x >> 5;
+  const int nw = blockDim.x >> 5;
+  const int mb = K.mb;
+  Tacc* acc = reinterpret_cast<Tacc*>(smem_raw) + (size_t)wib * mb;
+  // work unit = (item, block k)
+  const int64_t unit = (int64_t)blockIdx.x * nw + wib;
+  if (unit >= (int64_t)nitems * K.s) return;
+  const int it = (int)(unit / K.s);
+  const int k = (int)(unit - (int64_t)it * K.s);
+  for (int b = lane; b < mb; b += 32) acc[b] = Tacc(0);
+  __syncwarp();
+  const int64_t e0 = item_begin[it], e1 = item_end[it];
+  const unsigned lt = lanemask_lt();
+  for (int64_t base = e0; base < e1; base += 32) {
+    const int64_t e = base + lane;
+    const bool valid = e < e1;
+    int key = -1 - lane;
+    Tacc v = Tacc(0);
+    if (valid) {
+      int row, neg;
+      sketch_draw(K, k, (uint64_t)(uint32_t)__ldg(rowidx + e), row, neg);
+      key = row - k * mb;
+      Tacc x = (Tacc)__ldg(val + e);
+      v = neg ? -x : x;
+    }
+    const unsigned peers = __match_any_sync(0xffffffffu, key);
+    const int rank = __popc(peers & lt);
+    // max multiplicity in this batch
+    int rounds = __popc(peers);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) rounds = max(rounds, __shfl_xor_sync(0xffffffffu, rounds, o));
+    for (int r = 0; r < rounds; ++r) {
+      if (valid && rank == r) acc[key] += v;
+      __syncwarp();
+    }
+  }
+  // write block k's rows of column item_col[it]
+  const int j = item_col[it];
+  const int slot = item_slot[it];
+  if (slot < 0) {
+    for (int b = lane; b < mb; b += 32) SA[(int64_t)(k * mb + b) * d + j] = acc[b];
+  } else {
+    Tacc* dst = partial + ((int64_t)slot * K.s + k) * mb;
+    for (int b = lane; b < mb; b += 32) dst[b] = acc[b];
+  }
+}
+
+// Columns with several items: sum the items' partial columns in item order.
+template <typename Tacc>
+__global__ void k_sketch_csc_merge(const int32_t* __restrict__ col_first_item,
+                                   const int32_t* __restrict__ item_slot, int d, int m, int s,
+                                   int mb, const Tacc* __restrict__ partial,
+                                   Tacc* __restrict__ SA) {
+  const int j = blockIdx.y;
+  const int i0 = col_first_item[j], i1 = col_first_item[j + 1];
+  if (i1 - i0 <= 1) return;
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < m; r += gridDim.x * blockDim.x) {
+    const int k = r / mb, b = r - k * mb;
+    Tacc acc = Tacc(0);
+    for (int it = i0; it < i1; ++it) acc += partial[((int64_t)item_slot[it] * s + k) * mb + b];
+    SA[(int64_t)r * d + j] = acc;
+  }
+}
+
+template <typename Tin, typename Tacc>
+static cudaError_t run_csc(const CscA& A, const SketchKeys& K, int64_t m, void* SA, void* partial,
+                           cudaStream_t st) {
+  const size_t per_warp = (size_t)K.mb * sizeof(Tacc);
+  int nw = (int)std::min<size_t>(8, (200 * 1024) / per_warp);
+  if (nw < 1) return cudaErrorInvalidValue;
+  const size_t smem = per_warp * nw;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_sketch_csc<Tin, Tacc>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  const int64_t units = (int64_t)A.nitems * K.s;
+  { k_sketch_csc<Tin, Tacc><<<(unsigned)((units + nw - 1) / nw), nw * 32, smem, st>>>(
+      A.rowidx, (const Tin*)A.val, A.nitems, A.item_col, A.item_begin, A.item_end, A.item_slot, K,
+      (int)A.d, (Tacc*)SA, (Tacc*)partial); note_launches(1); }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || A.nsplit_slots == 0) return e;
+  dim3 g((unsigned)std::min<int64_t>((m + 255) / 256, 64), (unsigned)A.d);
+  { k_sketch_csc_merge<Tacc><<<g, 256, 0, st>>>(A.col_first_item, A.item_slot, (int)A.d, (int)m,
+                                              K.s, K.mb, (const Tacc*)partial, (Tacc*)SA); note_launches(1); }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sketch_csc(const CscA& A, const SketchKeys& K, int64_t m, int acc64, void* SA,
+                              void* partial, cudaStream_t st) {
+  if (A.f32) {
+    return acc64 ? run_csc<float, double>(A, K, m, SA, partial, st)
+                 : run_csc<float, float>(A, K, m, SA, partial, st);
+  }
+  return acc64 ? run_csc<double, double>(A, K, m, SA, partial, st)
+               : run_csc<double, float>(A, K, m, SA, partial, st);
+}
+
+// ----------------------------------------------------------------------------
+// Adjoint: (S^T G)_i = sum_k sign_k(i) G[bucket_k(i), :] / sqrt(s); one warp per row.
+// ----------------------------------------------------------------------------
+__global__ void k_sketch_adjoint(const SketchKeys K, int64_t n, int d, double inv_sqrt_s,
+                                 const double* __restrict__ G, double* __restrict__ out) {
+  const int lane = threadIdx.x & 31;
+  const int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (i >= n) return;
+  int rows[kMaxBlocks];
+  double sg[kMaxBlocks];
+  for (int k = 0; k < K.s; ++k) {
+    int neg;
+    sketch_draw(K, k, (uint64_t)i, rows[k], neg);
+    sg[k] = neg ? -inv_sqrt_s : inv_sqrt_s;
+  }
+  for (int c = lane; c < d; c += 32) {
+    double acc = 0.0;
+    for (int k = 0; k < K.s; ++k) acc += sg[k] * __ldg(G + (int64_t)rows[k] * d + c);
+    out[i * d + c] = acc;
+  }
+}
+
+cudaError_t launch_sketch_adjoint(const SketchKeys& K, int64_t n, int64_t d, const double* G,
+                                  double* out, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  { k_sketch_adjoint<<<(unsigned)((n + 7) / 8), 256, 0, st>>>(K, n, (int)d,
+                                                           1.0 / std::sqrt((double)K.s), G,
+                                                           out); note_launches(1); }
+  return cudaGetLastError();
+}

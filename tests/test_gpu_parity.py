@@ -1,0 +1,291 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle, on
+the same seeded inputs.  Tolerances are stated per test with their origin."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def rel(a, b):
+    a, b = np.asarray(a, np.float64), np.asarray(b, np.float64)
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+
+# ------------------------------------------------------------------ hash ---
+@pytest.mark.parametrize("seed,t,s,m,n", [(0, 0, 1, 500, 20000), (7, 3, 4, 2000, 100003),
+                                          (2**63 + 5, 11, 8, 10000, 4097), (1, 0, 2, 2, 33),
+                                          (5, 2, 1, 1, 1000), (9, 1, 64, 128, 77)])
+def test_hash_bit_exact(cuda_lib, seed, t, s, m, n):
+    """Bucket and sign draws equal the oracle's bit for bit (Sec. 2 draw,
+    SplitMix64 keyed by seed, t, block, row)."""
+    bg, sg = cuda_lib.ihs_hash(seed, t, s, m, n)
+    bo, so = O.hash_draw(seed, t, s, m, n)
+    assert np.array_equal(bg.cpu().numpy(), bo)
+    assert np.array_equal(sg.cpu().numpy(), so)
+
+
+# ---------------------------------------------------------------- sketch ---
+DENSE_CASES = [
+    # (n, d, m, s, dtype, precision)
+    (20000, 50, 500, 1, np.float64, "fp64"),     # the 20000 x 50 OLS workload
+    (5003, 37, 64, 1, np.float64, "fp64"),       # odd d (scalar path), ragged n
+    (777, 13, 1000, 1, np.float64, "fp64"),      # m > n: many empty buckets
+    (3000, 9, 9, 1, np.float64, "fp64"),         # few, large buckets straddling chunks
+    (4000, 16, 64, 4, np.float64, "fp64"),       # dense SJLT
+    (20011, 500, 5000, 1, np.float32, "fp64"),   # FP32 data, FP64 accumulation
+    (20011, 500, 5000, 1, np.float32, "tf32"),   # mixed form
+    (9000, 256, 2560, 1, np.float32, "bf16"),
+    (4099, 130, 1300, 1, np.float32, "tf32"),    # d not a multiple of 4 groups per lane
+]
+
+
+@pytest.mark.parametrize("n,d,m,s,dt,prec", DENSE_CASES)
+def test_sketch_dense(cuda_lib, n, d, m, s, dt, prec):
+    """SA = S A: FP64 accumulation is bit-identical to the oracle's ascending-row
+    loop (<= 1e-12 relative bar); FP32 accumulation within 1e-5 relative to the
+    largest |SA| (about 2^-24 per add over ~n/m adds)."""
+    rng = np.random.default_rng(n + d)
+    A = rng.standard_normal((n, d)).astype(dt)
+    b = rng.standard_normal(n)
+    solver = cuda_lib.IHS(dev(A), dev(b), m=m, s=s, seed=3, precision=prec)
+    solver.sketch(5)
+    SA, H, scale = solver.get_sketch()
+    bo, so = O.hash_draw(3, 5, s, m, n)
+    SAo = O.sketch(A.astype(np.float64), m, s, bo, so)
+    if prec == "fp64":
+        assert np.array_equal(SA.cpu().numpy(), SAo)
+    else:
+        assert rel(SA.cpu().numpy(), SAo) < 1e-5
+    Ho = O.gram(SAo, 1.0 / s)
+    if prec == "fp64":
+        assert rel(H.cpu().numpy(), Ho) < 1e-13
+    else:
+        # TF32 inputs carry 2^-11 relative rounding, BF16 2^-8; the Gram entry
+        # error is bounded by about 2u * sum |SA_ri||SA_rj| <= 2u * max diag.
+        u = 2.0 ** -11 if prec == "tf32" else 2.0 ** -8
+        err = np.abs(H.cpu().numpy() - Ho).max()
+        assert err <= 4 * u * np.abs(np.diag(Ho)).max()
+
+
+@pytest.mark.parametrize("dt,prec,s", [(np.float64, "fp64", 4), (np.float32, "tf32", 8),
+                                       (np.float64, "fp64", 1)])
+def test_sketch_csr(cuda_lib, dt, prec, s):
+    """CSR sketch through the column copy; FP64 exact vs the oracle's
+    ascending-row order (columns are not split at this size)."""
+    n, d, m = 30011, 40, 400
+    rowptr, col, val = synth.csr_uniform(n, d, 3, 1, dt)
+    b = np.random.default_rng(0).standard_normal(n)
+    solver = cuda_lib.IHS((dev(rowptr), dev(col), dev(val)), dev(b), m=m, s=s, seed=9,
+                          precision=prec, shape=(n, d))
+    solver.sketch(2)
+    SA, H, _ = solver.get_sketch()
+    bo, so = O.hash_draw(9, 2, s, m, n)
+    C = O.CSR(n, d, rowptr, col, val.astype(np.float64))
+    SAo = O.sketch(C, m, s, bo, so)
+    if prec == "fp64":
+        assert np.array_equal(SA.cpu().numpy(), SAo)
+    else:
+        assert rel(SA.cpu().numpy(), SAo) < 1e-5
+
+
+# -------------------------------------------------------------- gradient ---
+@pytest.mark.parametrize("n,d,dt", [(20000, 50, np.float64), (30001, 500, np.float32),
+                                    (5000, 37, np.float32), (7000, 1000, np.float32),
+                                    (3001, 3, np.float64)])
+def test_gradient_dense(cuda_lib, n, d, dt):
+    """g = A^T (b - A x): FP64 data in FP64; FP32 data in double-float
+    (about 2^-48 per operation).  Bar: 1e-12 relative to sum_i |A_i| |r_i|."""
+    rng = np.random.default_rng(d)
+    A = rng.standard_normal((n, d)).astype(dt)
+    xs = rng.standard_normal(d)
+    b = A.astype(np.float64) @ xs + 0.1 * rng.standard_normal(n)
+    x = xs + 1e-3 * rng.standard_normal(d)
+    solver = cuda_lib.IHS(dev(A), dev(b), m=max(d, 64), precision="fp64")
+    r, g = solver.gradient(dev(x), want_r=True)
+    ro, go = O.resid_grad(A.astype(np.float64), b, x, want_r=True)
+    scale = np.abs(A.astype(np.float64)).T @ np.abs(ro)
+    assert np.all(np.abs(g.cpu().numpy() - go) <= 1e-12 * scale)
+    assert np.abs(r.cpu().numpy() - ro).max() <= 1e-12 * np.abs(b).max()
+
+
+def test_gradient_csr(cuda_lib):
+    n, d = 50000, 60
+    for dt in (np.float64, np.float32):
+        rowptr, col, val = synth.csr_uniform(n, d, 4, 2, dt)
+        rng = np.random.default_rng(1)
+        b = rng.standard_normal(n)
+        x = rng.standard_normal(d)
+        solver = cuda_lib.IHS((dev(rowptr), dev(col), dev(val)), dev(b), m=120, precision="fp64",
+                              shape=(n, d))
+        g = solver.gradient(dev(x)).cpu().numpy()
+        C = O.CSR(n, d, rowptr, col, val.astype(np.float64))
+        ro, go = O.resid_grad(C, b, x, want_r=True)
+        scale = np.abs(C.todense()).T @ np.abs(ro)
+        assert np.all(np.abs(g - go) <= 1e-12 * scale)
+
+
+# ------------------------------------------------------------ full solve ---
+def test_ihs_ols_plain_matches_oracle_every_iteration(cuda_lib):
+    """20000 x 50 OLS, CountSketch m = 500, 10 iterations, seed 0: every GPU
+    iterate within 1e-12 of the oracle's in the A-seminorm relative to x_OPT."""
+    w = synth.make("ols_dense_fp64")
+    A, b = w["A"], w["b"]
+    G = A.T @ A
+    xo = O.x_opt_ols_qr(A, b)
+    xs = O.ihs(A, b, O.OLS, 0.0, 500, 1, 0, 10)
+    solver = cuda_lib.IHS(dev(A), dev(b), m=500, s=1, seed=0, precision="fp64")
+    x = torch.zeros(50, dtype=torch.float64, device="cuda")
+    nrm = np.sqrt(xo @ G @ xo)
+    for t in range(10):
+        solver.sketch(t)
+        solver.step(x)
+        e = x.cpu().numpy() - xs[t + 1]
+        assert np.sqrt(e @ G @ e) / nrm <= 1e-12, t
+    solver.sync()
+
+
+def test_ihs_ols_mixed_reaches_1e10(cuda_lib):
+    """Mixed form (FP32 data, TF32 Gram, FP32 factor, FP64-class gradient)
+    reaches ||x - x_OPT||_A / ||x_OPT||_A <= 1e-10 on an AR(1) design."""
+    w = synth.make("ols_dense_ar1", n=65536, d=128, m=1280)
+    A64 = w["A"].astype(np.float64)
+    xo = O.x_opt_ols_normal(A64, w["b"])
+    G = A64.T @ A64
+    for prec in ("tf32", "bf16"):
+        solver = cuda_lib.IHS(dev(w["A"]), dev(w["b"]), m=1280, s=1, seed=0, precision=prec)
+        x, rep = solver.solve(iters=40)
+        assert O.err_A(x.cpu().numpy(), xo, G) <= 1e-10, prec
+
+
+def test_resume_reproduces_run(cuda_lib):
+    """Counter-based sketches: 10 iterations equal 4 + 6 resumed at t0 = 4."""
+    w = synth.make("ols_dense_fp64", n=5000, d=20, m=200)
+    A, b = dev(w["A"]), dev(w["b"])
+    s1 = cuda_lib.IHS(A, b, m=200, seed=4)
+    x1, _ = s1.solve(iters=10)
+    s2 = cuda_lib.IHS(A, b, m=200, seed=4)
+    x2, _ = s2.solve(iters=4)
+    x2, _ = s2.solve(x2, t0=4, iters=6)
+    assert torch.equal(x1, x2)
+
+
+def test_invalid_arguments_are_rejected(cuda_lib):
+    A = torch.zeros((100, 10), dtype=torch.float64, device="cuda")
+    b = torch.zeros(100, dtype=torch.float64, device="cuda")
+    with pytest.raises(cuda_lib.IHSError) as e:
+        cuda_lib.IHS(A, b, m=12, s=5)  # m % s != 0
+    assert e.value.status == 1
+    with pytest.raises(cuda_lib.IHSError):
+        cuda_lib.IHS(A, b, m=5)  # m < d
+    with pytest.raises(cuda_lib.IHSError):
+        cuda_lib.ihs_hash(0, 0, 3, 10, 5)
+
+
+def test_not_spd_is_reported(cuda_lib):
+    """A rank-deficient sketch (m >= d but zero columns in A) makes the
+    Hessian singular; the factor reports it through the status word."""
+    A = torch.zeros((1000, 8), dtype=torch.float64, device="cuda")
+    A[:, :4] = torch.randn(1000, 4, dtype=torch.float64, device="cuda")
+    b = torch.randn(1000, dtype=torch.float64, device="cuda")
+    solver = cuda_lib.IHS(A, b, m=64)
+    with pytest.raises(cuda_lib.IHSError) as e:
+        solver.solve(iters=1)
+    assert e.value.status == 4
+
+
+# ------------------------------------------------------------------ LASSO ---
+def _csr_problem(name, n, d, m, seed=0):
+    w = synth.make(name, n=n, d=d, m=m, seed=seed)
+    C = O.CSR(w["n"], w["d"], w["rowptr"], w["col"], w["val"].astype(np.float64))
+    return w, C
+
+
+def test_l1_qp_step_matches_oracle_qp(cuda_lib):
+    """One l1-ball step of Eq. 2 on the GPU equals the oracle's exact QP on the
+    same H and g (from the same sketch): the QP solution is unique."""
+    w, C = _csr_problem("lasso_csr_fp64", 40000, 60, 600)
+    R = w["param"]
+    solver = cuda_lib.IHS((dev(w["rowptr"]), dev(w["col"]), dev(w["val"])), dev(w["b"]), kind="l1",
+                          param=R, m=600, s=4, seed=0, precision="fp64", shape=(w["n"], w["d"]))
+    x = torch.zeros(w["d"], dtype=torch.float64, device="cuda")
+    xo = np.zeros(w["d"])
+    for t in range(4):
+        solver.sketch(t)
+        SA, H, _ = solver.get_sketch()
+        g = solver.gradient(x).cpu().numpy()
+        solver.step(x)
+        solver.sync()
+        Hn = H.cpu().numpy()
+        xq = O.l1_ball_qp(Hn, g, x_prev := xo.copy(), R)
+        xo = xq
+        assert rel(x.cpu().numpy(), xq) < 1e-11, t
+        x.copy_(dev(xq))
+
+
+def test_ihs_lasso_plain_matches_oracle_every_iteration(cuda_lib):
+    """LASSO over the l1 ball (R = ||x*||_1 / 2), CSR FP64 data, SJLT s = 4:
+    every GPU iterate within 1e-11 of the oracle's (A-seminorm, relative to
+    x_OPT), and the final error below 1e-10 after 25 iterations."""
+    w, C = _csr_problem("lasso_csr_fp64", 100000, 200, 2000)
+    R = w["param"]
+    G = C.gram()
+    xo = O.x_opt_l1(C, w["b"], R)
+    xs = O.ihs(C, w["b"], O.L1_BALL, R, 2000, 4, 0, 25)
+    solver = cuda_lib.IHS((dev(w["rowptr"]), dev(w["col"]), dev(w["val"])), dev(w["b"]), kind="l1",
+                          param=R, m=2000, s=4, seed=0, precision="fp64", shape=(w["n"], w["d"]))
+    x = torch.zeros(w["d"], dtype=torch.float64, device="cuda")
+    nrm = np.sqrt(xo @ G @ xo)
+    for t in range(25):
+        solver.sketch(t)
+        solver.step(x)
+        e = x.cpu().numpy() - xs[t + 1]
+        assert np.sqrt(max(e @ G @ e, 0)) / nrm <= 1e-11, t
+    solver.sync()
+    assert O.err_A(x.cpu().numpy(), xo, G) < 1e-10
+
+
+def test_ihs_lasso_mixed_reaches_1e10(cuda_lib):
+    """Mixed form on Zipf-column CSR FP32 data with SJLT s = 8 reaches 1e-10."""
+    w, C = _csr_problem("lasso_csr_zipf", 200000, 100, 1000)
+    R = w["param"]
+    G = C.gram()
+    xo = O.x_opt_l1(C, w["b"], R)
+    solver = cuda_lib.IHS((dev(w["rowptr"]), dev(w["col"]), dev(w["val"])), dev(w["b"]), kind="l1",
+                          param=R, m=1000, s=8, seed=0, precision="tf32", shape=(w["n"], w["d"]))
+    x, rep = solver.solve(iters=30)
+    assert O.err_A(x.cpu().numpy(), xo, G) < 1e-10
+
+
+def test_ihs_ridge_plain_and_mixed(cuda_lib):
+    w = synth.make("ridge_dense", n=32768, d=64, m=640)
+    A64 = w["A"].astype(np.float64)
+    xo = O.x_opt_ols_normal(A64, w["b"], lam=w["param"])
+    xs = O.ihs(A64, w["b"], O.RIDGE, w["param"], 640, 1, 0, 8)
+    G = A64.T @ A64
+    s1 = cuda_lib.IHS(dev(w["A"]), dev(w["b"]), kind="ridge", param=w["param"], m=640,
+                      precision="fp64")
+    x1, _ = s1.solve(iters=8)
+    e = x1.cpu().numpy() - xs[-1]
+    assert np.sqrt(e @ G @ e) / np.sqrt(xo @ G @ xo) < 1e-12
+    s2 = cuda_lib.IHS(dev(w["A"]), dev(w["b"]), kind="ridge", param=w["param"], m=640,
+                      precision="tf32")
+    x2, _ = s2.solve(iters=35)
+    assert O.err_A(x2.cpu().numpy(), xo, G) < 1e-10
+
+
+def test_profile_counts_stages(cuda_lib):
+    w = synth.make("ols_dense_fp64", n=5000, d=20, m=200)
+    s1 = cuda_lib.IHS(dev(w["A"]), dev(w["b"]), m=200)
+    s1.profile(True)
+    s1.solve(iters=3)
+    ms, cnt, launches = s1.profile_read()
+    assert cnt["sketch"] == 3 and cnt["grad"] == 3 and cnt["step"] == 3
+    assert all(v >= 0 for v in ms.values()) and launches > 0
