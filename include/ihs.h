@@ -211,6 +211,29 @@ ihs_status ihs_sketch_adjoint(uint64_t seed, int64_t t, int s, int64_t m,
                               int64_t n, int64_t d, const double* G,
                               double* out, void* stream);
 
+/* ihs_gradient_noalloc -- g = A^T (b - A x) - lambda x for a DENSE A, the
+ * same quantity as ihs_gradient, for callers that cannot allocate device
+ * memory when they call: code whose device memory is all handed to its own
+ * pool allocator, or latency-critical loops that cannot afford the implicit
+ * device-wide synchronisation of cudaMalloc.  It needs no context and
+ * allocates nothing (no cudaMalloc, cudaFree or allocating library call).
+ * The paper has no counterpart; this is a service of the library.
+ *   A: HOST descriptor of a DENSE matrix (IHS_F32 or IHS_F64, DEVICE values,
+ *      d <= 1024); b: DEVICE n doubles; x: DEVICE d doubles;
+ *   g: DEVICE d doubles (out); stream: cudaStream_t or NULL.
+ * Scratch: a fixed 4 MiB array of per-warp partial gradients inside the
+ * library (512 Ki doubles), held by every GPU that loads the library until
+ * the process exits; the number of warps is chosen so that warps * d fits.
+ * The first call on a device looks up that array's device address (once per
+ * device, with that device current); make the first call on each device
+ * before any stream capture.  Every call overwrites the slots it uses, so no
+ * clearing is needed, but calls that overlap on the GPU (in flight at the
+ * same time, e.g. on two streams) race on the shared array.
+ * Errors: IHS_ERR_ARG (not dense, bad shape or NULL pointer),
+ * IHS_ERR_UNSUPPORTED (d > 1024), IHS_ERR_CUDA.  Asynchronous. */
+ihs_status ihs_gradient_noalloc(const ihs_matrix* A, const double* b, const double* x,
+                                double lambda, double* g, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

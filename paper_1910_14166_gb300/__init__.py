@@ -78,6 +78,7 @@ def _load():
         "ihs_sketch_adjoint": [u64, i64, i32, i64, i64, i64, vp, vp, vp],
         "ihs_profile": [vp, i32],
         "ihs_profile_read": [vp, ctypes.POINTER(f64), ctypes.POINTER(i32), ctypes.POINTER(i64)],
+        "ihs_gradient_noalloc": [ctypes.POINTER(_Matrix), vp, vp, f64, vp, vp],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -95,7 +96,7 @@ LIB_PATH = _build.LIB
 STAGES = ["sort", "sketch", "sketch_fix", "gram", "factor", "grad", "step"]
 EXPORTS = ["ihs_create", "ihs_sketch", "ihs_gradient", "ihs_step", "ihs_solve", "ihs_sync",
            "ihs_get_sketch", "ihs_adjoint", "ihs_destroy", "ihs_status_str", "ihs_hash",
-           "ihs_sketch_adjoint", "ihs_profile", "ihs_profile_read"]
+           "ihs_sketch_adjoint", "ihs_profile", "ihs_profile_read", "ihs_gradient_noalloc"]
 
 
 def _check(st, where):
@@ -135,6 +136,25 @@ def ihs_sketch_adjoint(seed, t, s, m, n, G):
     _check(_lib.ihs_sketch_adjoint(seed & 0xFFFFFFFFFFFFFFFF, t, s, m, n, G.shape[1], _ptr(G),
                                    _ptr(out), _stream()), "ihs_sketch_adjoint")
     return out
+
+
+def ihs_gradient_noalloc(A, b, x, lam=0.0):
+    """g = A^T (b - A x) - lam x for a dense CUDA tensor A, through the entry
+    point that allocates no device memory inside the library (its scratch is
+    a fixed array in the library; see include/ihs.h).  Only the output g is
+    allocated here, by the caller's side (PyTorch)."""
+    for t_, nm in ((A, "A"), (b, "b"), (x, "x")):
+        _need_cuda(t_, nm)
+    if A.dim() != 2 or A.dtype not in (torch.float32, torch.float64):
+        raise TypeError("A must be a 2-D float32/float64 tensor")
+    M = _Matrix()
+    M.kind, M.n, M.d, M.ld = DENSE, A.shape[0], A.shape[1], A.stride(0)
+    M.dtype = F32 if A.dtype == torch.float32 else F64
+    M.val = A.data_ptr()
+    g = torch.empty(A.shape[1], dtype=torch.float64, device=A.device)
+    _check(_lib.ihs_gradient_noalloc(ctypes.byref(M), _ptr(b), _ptr(x), float(lam), _ptr(g),
+                                     _stream()), "ihs_gradient_noalloc")
+    return g
 
 
 class IHS:
