@@ -382,6 +382,21 @@ def run_reference(args, rank, world):
     }
 
 
+def run_iters_only(args):
+    """Profiling driver: create the solver on the workload and run exactly
+    args.ncu_iters iterations (no x_OPT, no timing).  Used under ncu."""
+    import torch
+    import paper_1910_14166_gb300 as ihs
+    w = synth.make(args.workload, n=args.n, seed=0)
+    A = torch.from_numpy(w["A"]).cuda()
+    b = torch.from_numpy(w["b"]).cuda()
+    sv = ihs.IHS(A, b, kind="ols", m=w["m"], s=w["s"], seed=0, precision=args.precision)
+    x, rep = sv.solve(iters=args.ncu_iters)
+    torch.cuda.synchronize()
+    print("iters_only ok: n=%d d=%d m=%d precision=%s iters=%d status=%d"
+          % (w["n"], w["d"], w["m"], args.precision, args.ncu_iters, rep.status))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -389,12 +404,17 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="ols_dense_ar1")
-    ap.add_argument("--precision", default="tf32", choices=["tf32", "bf16"])
+    ap.add_argument("--precision", default="tf32", choices=["tf32", "bf16", "fp64"])
+    ap.add_argument("--ncu-iters", type=int, default=0,
+                    help="profiling driver: run this many iterations and exit")
     ap.add_argument("--n", type=int, default=None)
     ap.add_argument("--cpu-rows", type=int, default=131072)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     args = ap.parse_args()
+    if args.ncu_iters:
+        run_iters_only(args)
+        return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     if world > 1 and args.impl == "ours":
