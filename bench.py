@@ -266,20 +266,33 @@ def run_ours(args, rank, world):
     hbm, hbm_kind = peaks()
     ms_stage, cnt, launches = prof
     a_bytes = n * d * 4
-    alg = {"sketch": a_bytes + m * d * 4, "grad": a_bytes + n * 8}
+    fused = cnt["grad"] == 0 and cnt["sketch"] > 0
+    if fused:
+        # one pass: A, the sorted pair list (4 B/row), b as a float pair (8 B/row), SA out
+        alg = {"sketch": a_bytes + m * d * 4 + n * 12}
+        names = {"sketch": "k_sketch_grad_fused"}
+    else:
+        alg = {"sketch": a_bytes + m * d * 4, "grad": a_bytes + n * 8}
+        names = {"sketch": "k_sketch_dense", "grad": "k_rg_dense_f32"}
     kernels = {}
-    for k in ("sketch", "grad"):
+    for k in alg:
         avg = ms_stage[k] / max(1, cnt[k])
-        gbs = alg[k] / (avg * 1e-3) / 1e9
-        kernels[k] = {"ms_avg": round(avg, 4), "algorithmic_bytes": alg[k],
-                      "GB_s": round(gbs, 1), "frac": round(gbs / hbm, 3)}
-    dominant = max(("sketch", "grad"), key=lambda k: ms_stage[k])
-    kd = kernels[dominant]
-    roofline = {"kernel": "k_sketch_dense" if dominant == "sketch" else "k_rg_dense_f32",
-                "bound": "hbm", "achieved": kd["GB_s"], "peak": hbm, "unit": "GB/s",
-                "frac": kd["frac"], "peak_kind": hbm_kind,
-                "traffic": traffic_for("k_sketch_dense" if dominant == "sketch" else "k_rg_dense_f32")}
-    sk = kernels["sketch"]
+        gbs = alg[k] / (avg * 1e-3) / 1e9 if avg > 0 else 0.0
+        kernels[names[k]] = {"ms_avg": round(avg, 4), "algorithmic_bytes": alg[k],
+                             "GB_s": round(gbs, 1), "frac": round(gbs / hbm, 3)}
+    dominant = max(alg, key=lambda k: ms_stage[k])
+    kd = kernels[names[dominant]]
+    roofline = {"kernel": names[dominant], "bound": "hbm", "achieved": kd["GB_s"], "peak": hbm,
+                "unit": "GB/s", "frac": kd["frac"], "peak_kind": hbm_kind,
+                "traffic": traffic_for(names[dominant])}
+    sk = kernels[names["sketch"]]
+
+    # the mixed form with SA and the gradient in two separate passes, for comparison
+    ms_two = None
+    if fused and not args.no_two_pass:
+        two = ihs.IHS(A, b, kind="ols", m=m, s=s, seed=0, precision=args.precision, fuse=False)
+        ms_two, _, _ = timed(two, T_mixed, max(1, args.steps // 2), 1)
+        del two
 
     # end to end through the public API with host buffers
     e2e = None
@@ -337,6 +350,7 @@ def run_ours(args, rank, world):
         "final_err": {"mixed": err_final, "fp64": err_final_plain},
         "fp64_time_to_1e-10_ms": round(ms_plain, 3),
         "mixed_speedup_vs_fp64": round(ms_plain / ms_mixed, 3),
+        "mixed_two_pass_ms": round(ms_two, 3) if ms_two else None,
         "sketch_GB_s": sk["GB_s"],
         "sketch_frac_of_hbm": sk["frac"],
         "kernels": kernels,
@@ -411,6 +425,7 @@ def main():
     ap.add_argument("--cpu-rows", type=int, default=131072)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-two-pass", action="store_true")
     args = ap.parse_args()
     if args.ncu_iters:
         run_iters_only(args)

@@ -94,7 +94,14 @@ typedef struct {
   int precision;      /* IHS_PREC_*                                          */
   int qp_max_iter;    /* l1 ball: FISTA iteration cap per QP (0 = default)   */
   double qp_tol;      /* l1 ball: KKT acceptance tolerance (0 = default)     */
+  int flags;          /* IHS_FLAG_* (0 = default)                           */
 } ihs_options;
+
+/* Option flags.  IHS_FLAG_NO_FUSE: in ihs_solve, form SA and the gradient in
+ * two separate passes over A even where the single fused pass applies (dense
+ * FP32 data, mixed precision, CountSketch, d <= 512); results agree to
+ * rounding, the fused pass reads A once instead of twice. */
+enum { IHS_FLAG_NO_FUSE = 1 };
 
 typedef struct {
   int iters;            /* iterations taken                                */

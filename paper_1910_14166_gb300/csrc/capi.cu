@@ -18,13 +18,18 @@ void note_launches(int k) { __atomic_add_fetch(&g_launches, (int64_t)k, __ATOMIC
 int64_t launches_total() { return __atomic_load_n(&g_launches, __ATOMIC_RELAXED); }
 
 struct StageEvents {
-  std::vector<cudaEvent_t> ev;   // pool: pairs (start, stop)
-  std::vector<int> stage;        // stage of pair k
+  std::vector<cudaEvent_t> ev;     // pool: pairs (start, stop)
+  std::vector<int> stage;          // stage of pair k
+  std::vector<cudaStream_t> strm;  // stream of pair k
   size_t used = 0;
 };
 
 struct ihs_ctx {
-  cudaStream_t st = nullptr;
+  cudaStream_t st = nullptr;   // caller's stream: gradient, step, adjoint
+  cudaStream_t st2 = nullptr;  // internal stream: sketch draw, SA, Gram, factor
+  cudaEvent_t ev_fac[2] = {};  // factor of buffer b ready
+  cudaEvent_t ev_use[2] = {};  // last step reading buffer b done
+  cudaEvent_t ev_join = nullptr;
   bool prof = false;
   StageEvents pe;
   double prof_ms[IHS_NSTAGES] = {};
@@ -44,9 +49,16 @@ struct ihs_ctx {
   DenseA DA{};
   SortPlan sp{};
   void* sort_ws = nullptr;
-  uint32_t* perm = nullptr;
+  uint32_t* perm = nullptr;        // sort output, buffer 0
   int32_t* seg = nullptr;
   int32_t* chunk_first = nullptr;
+  uint32_t* perm2 = nullptr;       // buffer 1 (fused pipeline)
+  int32_t* seg2 = nullptr;
+  int32_t* chunk_first2 = nullptr;
+  bool fused = false;              // ihs_solve uses the single fused pass
+  double* gcta = nullptr;          // per-CTA gradient partials of the fused pass
+  cudaEvent_t ev_sort[2] = {};
+  cudaEvent_t ev_read[2] = {};
   void* sk_partial = nullptr;
   int rg_warps = 0;
   double* gpart = nullptr;
@@ -56,18 +68,24 @@ struct ihs_ctx {
   void* csc_partial = nullptr;
   void* rbuf = nullptr;
   double* item_part = nullptr;
-  // sketch / Hessian
+  // sketch / Hessian (H, L, Dinv double-buffered: the next iteration's sketch
+  // chain runs while the current step still reads its factor)
   void* SA = nullptr;
   GramPlan gp{};
   void* gop = nullptr;
   float* gpart_f = nullptr;
   double* gpart_d = nullptr;
-  double* H = nullptr;
-  void* L = nullptr;
+  double* H[2] = {};
+  void* L[2] = {};
+  void* Dinv[2] = {};
+  unsigned* bar = nullptr;
+  int cur = 1;  // buffer of the last sketch
   double* g = nullptr;
   double* step_norm = nullptr;
   int* status = nullptr;
   int* counter = nullptr;
+  // adjoint workspace (allocated on first use): v, r, z, p, q (d each), scal[4]
+  double* cg = nullptr;
   // l1 QP
   QpWork qw{};
   bool have_sketch = false;
@@ -79,8 +97,8 @@ void prof_stage_end(void* c);
 
 namespace {
 
-// Record a stage boundary on the context's stream (timing enabled only).
-void stage_begin(ihs_ctx* c, int stage) {
+// Record a stage boundary on `s` (timing enabled only).
+void stage_begin(ihs_ctx* c, int stage, cudaStream_t s) {
   if (!c->prof) return;
   StageEvents& P = c->pe;
   if (P.used + 2 > P.ev.size()) {
@@ -90,21 +108,23 @@ void stage_begin(ihs_ctx* c, int stage) {
       P.ev.push_back(e);
     }
     P.stage.resize(P.ev.size() / 2);
+    P.strm.resize(P.ev.size() / 2);
   }
   P.stage[P.used / 2] = stage;
-  cudaEventRecord(P.ev[P.used], c->st);
+  P.strm[P.used / 2] = s;
+  cudaEventRecord(P.ev[P.used], s);
 }
 void stage_end(ihs_ctx* c) {
   if (!c->prof) return;
   StageEvents& P = c->pe;
   if (P.used + 2 > P.ev.size()) return;
-  cudaEventRecord(P.ev[P.used + 1], c->st);
+  cudaEventRecord(P.ev[P.used + 1], P.strm[P.used / 2]);
   P.used += 2;
 }
 // Fold completed event pairs into the totals (after a synchronisation).
 void stage_collect(ihs_ctx* c) {
   StageEvents& P = c->pe;
-  for (size_t k = 0; k + 1 < P.used + 1 && k < P.used; k += 2) {
+  for (size_t k = 0; k < P.used; k += 2) {
     float ms = 0.f;
     if (cudaEventElapsedTime(&ms, P.ev[k], P.ev[k + 1]) == cudaSuccess) {
       c->prof_ms[P.stage[k / 2]] += ms;
@@ -116,8 +136,17 @@ void stage_collect(ihs_ctx* c) {
 
 }  // namespace
 
-void prof_stage_begin(void* c, int stage) { if (c) stage_begin((ihs_ctx*)c, stage); }
-void prof_stage_end(void* c) { if (c) stage_end((ihs_ctx*)c); }
+void prof_stage_begin(void* c, int stage) {
+  if (!c) return;
+  ihs_ctx* x = (ihs_ctx*)c;
+  // continue on the stream of the stage that the launcher just closed
+  const StageEvents& P = x->pe;
+  cudaStream_t s = (P.used >= 2) ? P.strm[P.used / 2 - 1] : x->st2;
+  stage_begin(x, stage, s);
+}
+void prof_stage_end(void* c) {
+  if (c) stage_end((ihs_ctx*)c);
+}
 
 namespace {
 
@@ -308,7 +337,18 @@ const char* ihs_status_str(ihs_status st) {
 void ihs_destroy(ihs_ctx* c) {
   if (!c) return;
   cudaStreamSynchronize(c->st);
+  if (c->st2) cudaStreamSynchronize(c->st2);
   for (cudaEvent_t e : c->pe.ev) cudaEventDestroy(e);
+  for (int k = 0; k < 2; ++k) {
+    if (c->ev_fac[k]) cudaEventDestroy(c->ev_fac[k]);
+    if (c->ev_use[k]) cudaEventDestroy(c->ev_use[k]);
+  }
+  if (c->ev_join) cudaEventDestroy(c->ev_join);
+  for (int k = 0; k < 2; ++k) {
+    if (c->ev_sort[k]) cudaEventDestroy(c->ev_sort[k]);
+    if (c->ev_read[k]) cudaEventDestroy(c->ev_read[k]);
+  }
+  if (c->st2) cudaStreamDestroy(c->st2);
   for (void* p : c->allocs) cudaFree(p);
   delete c;
 }
@@ -362,10 +402,28 @@ ihs_status ihs_create(ihs_ctx** out, const ihs_matrix* A, const double* b,
   do {                                                    \
     if ((s = dalloc(c, &(ptr), (size_t)(bytes))) != IHS_OK) return fail(s); \
   } while (0)
+  if (cudaStreamCreateWithFlags(&c->st2, cudaStreamNonBlocking) != cudaSuccess)
+    return fail(IHS_ERR_CUDA);
+  for (int k = 0; k < 2; ++k) {
+    if (cudaEventCreateWithFlags(&c->ev_fac[k], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_use[k], cudaEventDisableTiming) != cudaSuccess)
+      return fail(IHS_ERR_CUDA);
+  }
+  if (cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess)
+    return fail(IHS_ERR_CUDA);
+  for (int k = 0; k < 2; ++k) {
+    if (cudaEventCreateWithFlags(&c->ev_sort[k], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_read[k], cudaEventDisableTiming) != cudaSuccess)
+      return fail(IHS_ERR_CUDA);
+  }
   AL2(c->SA, (size_t)c->m * c->d * acc_el);
-  AL2(c->H, (size_t)c->d * c->d * sizeof(double));
   const int dp = chol_padded((int)c->d);
-  AL2(c->L, (size_t)dp * dp * (c->f32fac ? 4 : 8));
+  for (int k = 0; k < 2; ++k) {
+    AL2(c->H[k], (size_t)c->d * c->d * sizeof(double));
+    AL2(c->L[k], (size_t)dp * dp * (c->f32fac ? 4 : 8));
+    AL2(c->Dinv[k], chol_dinv_bytes((int)c->d, c->f32fac));
+  }
+  AL2(c->bar, 4 * sizeof(unsigned));
   AL2(c->g, c->d * sizeof(double));
   AL2(c->step_norm, sizeof(double));
   AL2(c->status, sizeof(int));
@@ -393,6 +451,13 @@ ihs_status ihs_create(ihs_ctx** out, const ihs_matrix* A, const double* b,
     AL2(c->sk_partial, (size_t)2 * c->sp.nchunks * c->d * acc_el);
     c->rg_warps = rg_dense_warps(c->n);
     AL2(c->gpart, (size_t)c->rg_warps * c->d * sizeof(double));
+    c->fused = !c->acc64 && fused_supported(c->DA, c->s) && !(opt->flags & IHS_FLAG_NO_FUSE);
+    if (c->fused) {
+      AL2(c->perm2, c->sp.P * sizeof(uint32_t));
+      AL2(c->seg2, (c->m + 1) * sizeof(int32_t));
+      AL2(c->chunk_first2, c->sp.nchunks * sizeof(int32_t));
+      AL2(c->gcta, (size_t)fused_ctas(c->sp) * c->d * sizeof(double));
+    }
   } else {
     if ((size_t)(c->m / c->s) * acc_el > 200 * 1024) return fail(IHS_ERR_UNSUPPORTED);
     if ((s = build_csc(c)) != IHS_OK) return fail(s);
@@ -417,83 +482,196 @@ ihs_status ihs_create(ihs_ctx** out, const ihs_matrix* A, const double* b,
   return IHS_OK;
 }
 
-ihs_status ihs_sketch(ihs_ctx* c, int64_t t) {
-  if (!c || t < 0) return IHS_ERR_ARG;
+}  // extern "C"
+
+namespace {
+
+// The sketch chain of counter t into buffer `bf`, on the internal stream:
+// draw S and sort (dense), SA, Gram (+ lambda I), Cholesky factor.  Waits
+// for the last step that read buffer `bf`; records ev_fac[bf].
+ihs_status sketch_chain(ihs_ctx* c, int64_t t, int bf) {
+  cudaStream_t s2 = c->st2;
+  CK(cudaStreamWaitEvent(s2, c->ev_use[bf], 0));
   const SketchKeys K = make_keys(c->opt.seed, t, c->s, c->m);
   if (c->dense) {
-    stage_begin(c, IHS_ST_SORT);
-    CK(launch_sort_sketch(c->sp, K, c->n, c->sort_ws, c->perm, c->seg, c->chunk_first, c->st));
+    stage_begin(c, IHS_ST_SORT, s2);
+    CK(launch_sort_sketch(c->sp, K, c->n, c->sort_ws, c->perm, c->seg, c->chunk_first, s2));
     stage_end(c);
-    stage_begin(c, IHS_ST_SKETCH);
+    stage_begin(c, IHS_ST_SKETCH, s2);
     CK(launch_sketch_dense(c->DA, c->sp, c->perm, c->seg, c->chunk_first, c->acc64, c->SA,
-                           c->sk_partial, c->counter, c->sms, c->st, c->prof ? c : nullptr));
+                           c->sk_partial, c->counter, c->sms, s2, c->prof ? c : nullptr));
     stage_end(c);
   } else {
-    stage_begin(c, IHS_ST_SKETCH);
-    CK(launch_sketch_csc(c->CA, K, c->m, c->acc64, c->SA, c->csc_partial, c->st));
+    stage_begin(c, IHS_ST_SKETCH, s2);
+    CK(launch_sketch_csc(c->CA, K, c->m, c->acc64, c->SA, c->csc_partial, s2));
     stage_end(c);
   }
   const double shift = (c->C.kind == IHS_RIDGE) ? c->C.param : 0.0;
-  stage_begin(c, IHS_ST_GRAM);
-  CK(launch_gram(c->gp, c->SA, c->gop, c->gpart_f, c->gpart_d, 1.0 / c->s, shift, c->H, c->status,
-                 c->st));
+  stage_begin(c, IHS_ST_GRAM, s2);
+  CK(launch_gram(c->gp, c->SA, c->gop, c->gpart_f, c->gpart_d, 1.0 / c->s, shift, c->H[bf],
+                 c->status, s2));
   stage_end(c);
-  stage_begin(c, IHS_ST_FACTOR);
-  CK(launch_cholesky(c->H, (int)c->d, c->f32fac, c->L, c->status, c->st));
+  stage_begin(c, IHS_ST_FACTOR, s2);
+  CK(launch_cholesky(c->H[bf], (int)c->d, c->f32fac, c->L[bf], c->Dinv[bf], c->bar, c->status,
+                     s2));
   stage_end(c);
+  CK(cudaEventRecord(c->ev_fac[bf], s2));
+  return IHS_OK;
+}
+
+// The internal stream waits for everything issued so far on the caller's stream.
+ihs_status join_caller(ihs_ctx* c) {
+  CK(cudaEventRecord(c->ev_join, c->st));
+  CK(cudaStreamWaitEvent(c->st2, c->ev_join, 0));
+  return IHS_OK;
+}
+
+ihs_status gradient_on(ihs_ctx* c, const double* x, double* g, double* r, bool with_b) {
+  const double lam = (c->C.kind == IHS_RIDGE) ? c->C.param : 0.0;
+  if (c->dense) {
+    CK(launch_resid_grad_dense(c->DA, with_b ? c->b : nullptr, with_b ? c->bsplit : nullptr, x, r,
+                               c->gpart, c->rg_warps, g, lam, c->st));
+  } else {
+    CK(launch_resid_csr(c->n, c->d, c->A.rowptr, c->A.rowptr_i64, c->A.col, c->A.val,
+                        c->A.dtype == IHS_F32, with_b ? c->b : nullptr,
+                        with_b ? c->bsplit : nullptr, x, c->rbuf, r, c->st));
+    CK(launch_grad_csc(c->CA, c->rbuf, c->item_part, x, lam, g, c->st));
+  }
+  return IHS_OK;
+}
+
+// QP step of Eq. 2 with buffer bf (gradient already in c->g), on the caller's stream.
+ihs_status step_with(ihs_ctx* c, double* x, int bf) {
+  CK(cudaStreamWaitEvent(c->st, c->ev_fac[bf], 0));
+  stage_begin(c, IHS_ST_STEP, c->st);
+  cudaError_t e;
+  if (c->C.kind == IHS_L1_BALL)
+    e = launch_l1_step(c->H[bf], c->L[bf], c->Dinv[bf], c->f32fac, (int)c->d, c->g, c->C.param,
+                       c->opt.qp_max_iter, c->opt.qp_tol, c->qw, x, c->step_norm, c->status,
+                       c->st);
+  else
+    e = launch_chol_step(c->L[bf], c->Dinv[bf], (int)c->d, c->f32fac, c->g, x, c->step_norm,
+                         c->st);
+  stage_end(c);
+  CK(e);
+  CK(cudaEventRecord(c->ev_use[bf], c->st));
+  return IHS_OK;
+}
+
+// Fused pipeline, sort half: draw and sort the pairs of counter t into sort
+// buffer pb on the internal stream, after the fused pass that last read it.
+ihs_status fused_sort(ihs_ctx* c, int64_t t, int pb) {
+  cudaStream_t s2 = c->st2;
+  CK(cudaStreamWaitEvent(s2, c->ev_read[pb], 0));
+  const SketchKeys K = make_keys(c->opt.seed, t, c->s, c->m);
+  stage_begin(c, IHS_ST_SORT, s2);
+  CK(launch_sort_sketch(c->sp, K, c->n, c->sort_ws, pb ? c->perm2 : c->perm, pb ? c->seg2 : c->seg,
+                        pb ? c->chunk_first2 : c->chunk_first, s2));
+  stage_end(c);
+  CK(cudaEventRecord(c->ev_sort[pb], s2));
+  return IHS_OK;
+}
+
+// Fused pipeline, main half (caller's stream): one pass over A forming SA(t)
+// and g(x), then Gram, factor and step into x.
+ihs_status fused_iteration(ihs_ctx* c, double* x, int pb, int bf) {
+  cudaStream_t s1 = c->st;
+  CK(cudaStreamWaitEvent(s1, c->ev_sort[pb], 0));
+  const double lam = (c->C.kind == IHS_RIDGE) ? c->C.param : 0.0;
+  stage_begin(c, IHS_ST_SKETCH, s1);
+  cudaError_t e = launch_sketch_grad_fused(
+      c->DA, c->sp, pb ? c->perm2 : c->perm, pb ? c->seg2 : c->seg,
+      pb ? c->chunk_first2 : c->chunk_first, c->bsplit, x, (float*)c->SA, (float*)c->sk_partial,
+      c->gcta, c->g, lam, s1, c->prof ? c : nullptr);
+  stage_end(c);
+  CK(e);
+  CK(cudaEventRecord(c->ev_read[pb], s1));
+  stage_begin(c, IHS_ST_GRAM, s1);
+  CK(launch_gram(c->gp, c->SA, c->gop, c->gpart_f, c->gpart_d, 1.0 / c->s, lam, c->H[bf],
+                 c->status, s1));
+  stage_end(c);
+  stage_begin(c, IHS_ST_FACTOR, s1);
+  CK(launch_cholesky(c->H[bf], (int)c->d, c->f32fac, c->L[bf], c->Dinv[bf], c->bar, c->status,
+                     s1));
+  stage_end(c);
+  CK(cudaEventRecord(c->ev_fac[bf], s1));
+  return step_with(c, x, bf);
+}
+
+}  // namespace
+
+extern "C" {
+
+ihs_status ihs_sketch(ihs_ctx* c, int64_t t) {
+  if (!c || t < 0) return IHS_ERR_ARG;
+  ihs_status s = join_caller(c);
+  if (s != IHS_OK) return s;
+  const int bf = c->cur ^ 1;
+  if ((s = sketch_chain(c, t, bf)) != IHS_OK) return s;
+  c->cur = bf;
   c->have_sketch = true;
   return IHS_OK;
 }
 
 ihs_status ihs_gradient(ihs_ctx* c, const double* x, double* g, double* r) {
   if (!c || !x || !g) return IHS_ERR_ARG;
-  const double lam = (c->C.kind == IHS_RIDGE) ? c->C.param : 0.0;
-  if (c->dense) {
-    CK(launch_resid_grad_dense(c->DA, c->b, c->bsplit, x, r, c->gpart, c->rg_warps, g, lam,
-                               c->st));
-  } else {
-    CK(launch_resid_csr(c->n, c->d, c->A.rowptr, c->A.rowptr_i64, c->A.col, c->A.val,
-                        c->A.dtype == IHS_F32, c->b, x, c->rbuf, r, c->st));
-    CK(launch_grad_csc(c->CA, c->rbuf, c->item_part, x, lam, g, c->st));
-  }
-  return IHS_OK;
+  return gradient_on(c, x, g, r, true);
 }
 
 ihs_status ihs_step(ihs_ctx* c, double* x) {
   if (!c || !x) return IHS_ERR_ARG;
   if (!c->have_sketch) return IHS_ERR_ARG;
-  stage_begin(c, IHS_ST_GRAD);
-  ihs_status s = ihs_gradient(c, x, c->g, nullptr);
+  stage_begin(c, IHS_ST_GRAD, c->st);
+  ihs_status s = gradient_on(c, x, c->g, nullptr, true);
   stage_end(c);
   if (s != IHS_OK) return s;
-  stage_begin(c, IHS_ST_STEP);
-  struct EndStep { ihs_ctx* c; ~EndStep() { stage_end(c); } } end_step{c};
-  if (c->C.kind == IHS_L1_BALL) {
-    CK(launch_l1_step(c->H, c->L, c->f32fac, (int)c->d, c->g, c->C.param, c->opt.qp_max_iter,
-                      c->opt.qp_tol, c->qw, x, c->step_norm, c->status, c->st));
-  } else {
-    CK(launch_chol_step(c->L, (int)c->d, c->f32fac, c->g, x, c->step_norm, c->st));
-  }
-  return IHS_OK;
+  return step_with(c, x, c->cur);
 }
 
 ihs_status ihs_sync(ihs_ctx* c) {
   if (!c) return IHS_ERR_ARG;
   CK(cudaStreamSynchronize(c->st));
+  CK(cudaStreamSynchronize(c->st2));
   int st = 0;
   CK(cudaMemcpy(&st, c->status, sizeof(int), cudaMemcpyDeviceToHost));
   if (st != 0) CK(cudaMemset(c->status, 0, sizeof(int)));
   return (ihs_status)st;
 }
 
+// Pipelined loop: the sketch chain of t+1 (internal stream) is issued before
+// the step of t (caller's stream), so it overlaps with the gradient pass and
+// the step; double buffering keeps the step's factor intact.
 ihs_status ihs_solve(ihs_ctx* c, double* x, int64_t t0, int iters, ihs_report* rep) {
   if (!c || !x || iters < 0 || t0 < 0) return IHS_ERR_ARG;
   if (c->C.kind == IHS_L1_BALL) CK(cudaMemsetAsync(c->qw.iters, 0, sizeof(int), c->st));
-  for (int k = 0; k < iters; ++k) {
-    ihs_status s = ihs_sketch(c, t0 + k);
-    if (s != IHS_OK) return s;
-    s = ihs_step(c, x);
-    if (s != IHS_OK) return s;
+  ihs_status s = IHS_OK;
+  if (iters > 0 && c->fused) {
+    if ((s = join_caller(c)) != IHS_OK) return s;
+    if ((s = fused_sort(c, t0, 0)) != IHS_OK) return s;
+    int bf = c->cur ^ 1;
+    for (int k = 0; k < iters; ++k) {
+      const int pb = k & 1;
+      if (k + 1 < iters && (s = fused_sort(c, t0 + k + 1, pb ^ 1)) != IHS_OK) return s;
+      if ((s = fused_iteration(c, x, pb, bf)) != IHS_OK) return s;
+      c->cur = bf;
+      bf ^= 1;
+    }
+    c->have_sketch = true;
+  } else if (iters > 0) {
+    if ((s = join_caller(c)) != IHS_OK) return s;
+    int bf = c->cur ^ 1;
+    if ((s = sketch_chain(c, t0, bf)) != IHS_OK) return s;
+    for (int k = 0; k < iters; ++k) {
+      stage_begin(c, IHS_ST_GRAD, c->st);
+      s = gradient_on(c, x, c->g, nullptr, true);
+      stage_end(c);
+      if (s != IHS_OK) return s;
+      if (k + 1 < iters && (s = sketch_chain(c, t0 + k + 1, bf ^ 1)) != IHS_OK) return s;
+      if ((s = step_with(c, x, bf)) != IHS_OK) return s;
+      c->cur = bf;
+      bf ^= 1;
+    }
+    c->have_sketch = true;
   }
   ihs_status st = ihs_sync(c);
   if (rep) {
@@ -515,23 +693,74 @@ ihs_status ihs_get_sketch(ihs_ctx* c, void* SA_out, int* SA_dtype, double* H_out
   if (scale) *scale = 1.0 / c->s;
   if ((SA_out || H_out) && !c->have_sketch) return IHS_ERR_ARG;
   const size_t el = c->acc64 ? 8 : 4;
+  CK(cudaStreamWaitEvent(c->st, c->ev_fac[c->cur], 0));
   if (SA_out)
     CK(cudaMemcpyAsync(SA_out, c->SA, (size_t)c->m * c->d * el, cudaMemcpyDeviceToDevice, c->st));
   if (H_out)
-    CK(cudaMemcpyAsync(H_out, c->H, (size_t)c->d * c->d * sizeof(double),
+    CK(cudaMemcpyAsync(H_out, c->H[c->cur], (size_t)c->d * c->d * sizeof(double),
                        cudaMemcpyDeviceToDevice, c->st));
   return IHS_OK;
 }
 
 ihs_status ihs_adjoint(ihs_ctx* c, const double* x, const double* dLdx, double* dLdb, void* dLdA,
                        ihs_report* rep) {
-  (void)c; (void)x; (void)dLdx; (void)dLdb; (void)dLdA; (void)rep;
-  return IHS_ERR_UNSUPPORTED;
+  if (!c || !x || !dLdx) return IHS_ERR_ARG;
+  if (c->C.kind == IHS_L1_BALL) return IHS_ERR_UNSUPPORTED;
+  if (!c->have_sketch) return IHS_ERR_ARG;
+  if (dLdA && !c->dense) return IHS_ERR_UNSUPPORTED;
+  const int d = (int)c->d;
+  if (!c->cg) {
+    ihs_status s = dalloc(c, &c->cg, (size_t)(5 * d + 8) * sizeof(double));
+    if (s != IHS_OK) return s;
+  }
+  double *v = c->cg, *r = v + d, *z = r + d, *p = z + d, *q = p + d, *scal = q + d;
+  const int bf = c->cur;
+  CK(cudaStreamWaitEvent(c->st, c->ev_fac[bf], 0));
+  // PCG on (A^T A + lambda I) v = dL/dx with preconditioner (L L^T)^{-1}
+  CK(launch_cg_init(dLdx, d, v, r, scal, c->st));
+  double h[3] = {0, 0, 0};
+  CK(cudaMemcpyAsync(h, scal, 3 * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+  CK(cudaStreamSynchronize(c->st));
+  const double rhs2 = h[2];
+  const double tol2 = 1e-26 * rhs2;  // |r| <= 1e-13 |dL/dx|
+  int it = 0;
+  bool conv = (rhs2 == 0.0);
+  const int max_it = 200;
+  while (!conv && it < max_it) {
+    CK(launch_chol_apply(c->L[bf], c->Dinv[bf], d, c->f32fac, r, z, c->st));
+    CK(launch_cg_dir(r, z, d, p, scal, it == 0, c->st));
+    ihs_status s = gradient_on(c, p, q, nullptr, false);  // q = -(A^T A + lambda I) p
+    if (s != IHS_OK) return s;
+    CK(launch_cg_step(p, q, d, v, r, scal, c->st));
+    ++it;
+    double rr = 0.0;
+    CK(cudaMemcpyAsync(&rr, scal + 1, sizeof(double), cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    conv = rr <= tol2;
+  }
+  CK(cudaEventRecord(c->ev_use[bf], c->st));
+  // dL/db = A v  (the residual pass with b = 0 gives -A v)
+  if (dLdb) {
+    ihs_status s = gradient_on(c, v, q, dLdb, false);
+    if (s != IHS_OK) return s;
+    CK(launch_negate(dLdb, c->n, c->st));
+  }
+  if (dLdA) CK(launch_adjoint_dA(c->DA, c->b, x, v, dLdA, c->st));
+  ihs_status st = ihs_sync(c);
+  if (rep) {
+    rep->iters = it;
+    rep->status = st;
+    rep->qp_fista_iters = 0;
+    rep->step_norm = 0.0;
+  }
+  if (st != IHS_OK) return st;
+  return conv ? IHS_OK : IHS_ERR_NOT_CONVERGED;
 }
 
 ihs_status ihs_profile(ihs_ctx* c, int enable) {
   if (!c) return IHS_ERR_ARG;
   CK(cudaStreamSynchronize(c->st));
+  CK(cudaStreamSynchronize(c->st2));
   c->pe.used = 0;
   for (int k = 0; k < IHS_NSTAGES; ++k) {
     c->prof_ms[k] = 0.0;
@@ -545,6 +774,7 @@ ihs_status ihs_profile(ihs_ctx* c, int enable) {
 ihs_status ihs_profile_read(ihs_ctx* c, double* ms, int* count, int64_t* launches) {
   if (!c || !ms) return IHS_ERR_ARG;
   CK(cudaStreamSynchronize(c->st));
+  CK(cudaStreamSynchronize(c->st2));
   stage_collect(c);
   for (int k = 0; k < IHS_NSTAGES; ++k) {
     ms[k] = c->prof_ms[k];

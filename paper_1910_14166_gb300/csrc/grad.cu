@@ -98,7 +98,7 @@ __global__ void __launch_bounds__(kRgThreads) k_rg_dense_f32(
       dd_add(sh, sl, oh, ol);
     }
     // r_i = b_i - dot, as a float pair
-    float2 b2 = __ldg(bs + i);
+    const float2 b2 = bs ? __ldg(bs + i) : make_float2(0.f, 0.f);  // no b: r = -A x
     float rh = b2.x, rl = b2.y;
     dd_add(rh, rl, -sh, -sl);
     if (r_out && lane == 0) r_out[i] = (double)rh + (double)rl;
@@ -147,7 +147,7 @@ __global__ void __launch_bounds__(kRgThreads) k_rg_dense_f64(
       s = fma(a[q], xv[q], s);
     }
     s = warp_sum(s);
-    const double ri = b[i] - s;
+    const double ri = (b ? b[i] : 0.0) - s;
     if (r_out && lane == 0) r_out[i] = ri;
 #pragma unroll
     for (int q = 0; q < NQ; ++q) g[q] = fma(a[q], ri, g[q]);
@@ -235,7 +235,7 @@ cudaError_t launch_resid_grad_dense(const DenseA& A, const double* b, const floa
 template <typename RP>
 __global__ void k_resid_csr_f32(int64_t n, int d, const RP* __restrict__ rowptr,
                                 const int32_t* __restrict__ col, const float* __restrict__ val,
-                                const double* __restrict__ b, const double* __restrict__ x,
+                                const float2* __restrict__ bs, const double* __restrict__ x,
                                 float2* __restrict__ r2, double* __restrict__ r_out) {
   extern __shared__ float xs2[];
   float* xh = xs2;
@@ -250,8 +250,8 @@ __global__ void k_resid_csr_f32(int64_t n, int d, const RP* __restrict__ rowptr,
       const int c = __ldg(col + p);
       dd_fma_acc(sh, sl, __ldg(val + p), xh[c], xl[c]);
     }
-    float bh, bl;
-    split_double(b[i], bh, bl);
+    const float2 b2 = bs ? __ldg(bs + i) : make_float2(0.f, 0.f);
+    float bh = b2.x, bl = b2.y;
     dd_add(bh, bl, -sh, -sl);
     r2[i] = make_float2(bh, bl);
     if (r_out) r_out[i] = (double)bh + (double)bl;
@@ -268,7 +268,7 @@ __global__ void k_resid_csr_f64(int64_t n, const RP* __restrict__ rowptr,
     double s = 0.0;
     const int64_t p0 = rowptr[i], p1 = rowptr[i + 1];
     for (int64_t p = p0; p < p1; ++p) s = fma(__ldg(val + p), __ldg(x + __ldg(col + p)), s);
-    const double ri = b[i] - s;
+    const double ri = (b ? b[i] : 0.0) - s;
     r[i] = ri;
     if (r_out) r_out[i] = ri;
   }
@@ -276,18 +276,19 @@ __global__ void k_resid_csr_f64(int64_t n, const RP* __restrict__ rowptr,
 
 cudaError_t launch_resid_csr(int64_t n, int64_t d, const void* rowptr, int rowptr_i64,
                              const int32_t* col, const void* val, int f32, const double* b,
-                             const double* x, void* rbuf, double* r_out, cudaStream_t st) {
+                             const float2* bsplit, const double* x, void* rbuf, double* r_out,
+                             cudaStream_t st) {
   if (n == 0) return cudaSuccess;
   const int blocks = (int)std::min<int64_t>((n + 255) / 256, 152 * 8);
   if (f32) {
     const size_t smem = (size_t)2 * d * sizeof(float);
     if (rowptr_i64)
       { k_resid_csr_f32<int64_t><<<blocks, 256, smem, st>>>(n, (int)d, (const int64_t*)rowptr, col,
-                                                          (const float*)val, b, x, (float2*)rbuf,
+                                                          (const float*)val, bsplit, x, (float2*)rbuf,
                                                           r_out); note_launches(1); }
     else
       { k_resid_csr_f32<int32_t><<<blocks, 256, smem, st>>>(n, (int)d, (const int32_t*)rowptr, col,
-                                                          (const float*)val, b, x, (float2*)rbuf,
+                                                          (const float*)val, bsplit, x, (float2*)rbuf,
                                                           r_out); note_launches(1); }
   } else {
     if (rowptr_i64)
@@ -378,5 +379,12 @@ __global__ void k_split_b(const double* __restrict__ b, int64_t n, float2* __res
 cudaError_t launch_split_b(const double* b, int64_t n, float2* out, cudaStream_t st) {
   if (n == 0) return cudaSuccess;
   { k_split_b<<<(unsigned)std::min<int64_t>((n + 255) / 256, 4096), 256, 0, st>>>(b, n, out); note_launches(1); }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_reduce_partials(const double* part, int nparts, int d, const double* x,
+                                   double lam, double* g, cudaStream_t st) {
+  k_reduce_gpart<<<(d + 31) / 32, 256, 0, st>>>(part, nparts, d, x, lam, g);
+  note_launches(1);
   return cudaGetLastError();
 }

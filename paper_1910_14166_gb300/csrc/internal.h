@@ -70,6 +70,17 @@ struct CscA {
 cudaError_t launch_sketch_csc(const CscA& A, const SketchKeys& K, int64_t m, int acc64, void* SA,
                               void* partial, cudaStream_t st);
 
+cudaError_t launch_sketch_fixup_f32(const SortPlan& p, const int32_t* seg, int d,
+                                    const float* partial, float* SA, cudaStream_t st);
+// One pass over a dense FP32 A forming SA (FP32 accumulation, CountSketch)
+// and g = A^T (b - A x) - lam x together; gcta holds fused_ctas(p) * d doubles.
+bool fused_supported(const DenseA& A, int s);
+int fused_ctas(const SortPlan& p);
+cudaError_t launch_sketch_grad_fused(const DenseA& A, const SortPlan& p, const uint32_t* perm,
+                                     const int32_t* seg, const int32_t* cf, const float2* bsplit,
+                                     const double* x, float* SA, float* partial, double* gcta,
+                                     double* g, double lam, cudaStream_t st, void* prof);
+
 // S^T G gather (G m x d double, out n x d double).
 cudaError_t launch_sketch_adjoint(const SketchKeys& K, int64_t n, int64_t d, const double* G,
                                   double* out, cudaStream_t st);
@@ -84,9 +95,13 @@ cudaError_t launch_resid_grad_dense(const DenseA& A, const double* b, const floa
 // CSC columns -> g.
 cudaError_t launch_resid_csr(int64_t n, int64_t d, const void* rowptr, int rowptr_i64,
                              const int32_t* col, const void* val, int f32, const double* b,
-                             const double* x, void* rbuf, double* r_out, cudaStream_t st);
+                             const float2* bsplit, const double* x, void* rbuf, double* r_out,
+                             cudaStream_t st);
 cudaError_t launch_grad_csc(const CscA& A, const void* rbuf, double* item_part, const double* x,
                             double lam, double* g, cudaStream_t st);
+// g[c] = sum over parts (fixed order) of part[p][c] - lam x[c].
+cudaError_t launch_reduce_partials(const double* part, int nparts, int d, const double* x,
+                                   double lam, double* g, cudaStream_t st);
 
 // ---- Gram ---------------------------------------------------------------------
 struct GramPlan {
@@ -107,14 +122,17 @@ cudaError_t launch_gram(const GramPlan& g, const void* SA, void* operand, float*
 
 // ---- dense d x d linear algebra -------------------------------------------------
 int chol_padded(int d);  // d rounded up to the 32-tile
-cudaError_t launch_cholesky(const double* H, int d, int f32, void* Lbuf, int* status,
-                            cudaStream_t st);
+// Lbuf: dp x dp (lower: L, upper: L^T tiles); Dinv: dp/32 tiles of 32 x 32;
+// bar: 4 unsigned of barrier state (zeroed by the launcher).
+size_t chol_dinv_bytes(int d, int f32);
+cudaError_t launch_cholesky(const double* H, int d, int f32, void* Lbuf, void* Dinv, unsigned* bar,
+                            int* status, cudaStream_t st);
 // x += (L L^T)^{-1} g ; step_norm (device double) gets max |delta|.
-cudaError_t launch_chol_step(const void* Lbuf, int d, int f32, const double* g, double* x,
-                             double* step_norm, cudaStream_t st);
+cudaError_t launch_chol_step(const void* Lbuf, const void* Dinv, int d, int f32, const double* g,
+                             double* x, double* step_norm, cudaStream_t st);
 // delta = (L L^T)^{-1} v (no update), for preconditioning.
-cudaError_t launch_chol_apply(const void* Lbuf, int d, int f32, const double* v, double* out,
-                              cudaStream_t st);
+cudaError_t launch_chol_apply(const void* Lbuf, const void* Dinv, int d, int f32, const double* v,
+                              double* out, cudaStream_t st);
 
 // l1-ball QP step (Eq. 2 over {||x||_1 <= R}); H double d x d.
 struct QpWork {
@@ -126,9 +144,21 @@ struct QpWork {
   int* iters;      // FISTA iterations (device counter)
 };
 size_t qp_work_bytes(int d);
-cudaError_t launch_l1_step(const double* H, const void* Lbuf, int f32, int d, const double* g,
+cudaError_t launch_l1_step(const double* H, const void* Lbuf, const void* Dinv, int f32, int d,
+                           const double* g,
                            double R, int max_iter, double tol, QpWork w, double* x,
                            double* step_norm, int* status, cudaStream_t st);
+
+// ---- adjoint (ridge / OLS) -----------------------------------------------------
+cudaError_t launch_cg_init(const double* rhs, int d, double* v, double* r, double* scal,
+                           cudaStream_t st);
+cudaError_t launch_cg_dir(const double* r, const double* z, int d, double* p, double* scal,
+                          int first, cudaStream_t st);
+cudaError_t launch_cg_step(const double* p, const double* negq, int d, double* v, double* r,
+                           double* scal, cudaStream_t st);
+cudaError_t launch_negate(double* a, int64_t n, cudaStream_t st);
+cudaError_t launch_adjoint_dA(const DenseA& A, const double* b, const double* x, const double* v,
+                              void* out, cudaStream_t st);
 
 // small device vector kernels
 cudaError_t launch_split_b(const double* b, int64_t n, float2* out, cudaStream_t st);

@@ -1,15 +1,29 @@
 // linalg.cu -- the d x d step of Eq. 2 for OLS / ridge: Cholesky H = L L^T
 // and x^{t+1} = x^t + L^{-T} L^{-1} g.
 //
-// The factor is blocked in 32 x 32 tiles, right-looking, two launches per
-// tile column: a one-CTA kernel factors the diagonal tile and solves the
-// panel below it, then a grid of CTAs applies the rank-32 update to every
-// trailing lower tile in parallel.  Tiles are padded with the identity so
-// any d works.  The factor runs in FP64 (plain form) or FP32 (mixed form:
-// there the Hessian itself carries TF32/BF16 input rounding, so the
-// factorisation only has to be a good preconditioner; the iterate update
-// x += delta stays FP64).  A pivot that is not positive records
-// DEV_NOT_SPD in the status word.
+// Factor: one cooperative, persistent launch (all CTAs co-resident) doing a
+// blocked Cholesky on 32 x 32 tiles with a look-ahead schedule: between grid
+// barriers k-1 and k the CTAs share out, as one list of independent items,
+//   panel(k)   tile rows k..Tt-1 of column k.  Each such item first applies
+//              the rank-32 update of step k-1 to its own tiles, factors the
+//              32 x 32 diagonal tile itself in registers (redundantly, which
+//              saves a barrier), and solves x L_kk^T = a for its tile by a
+//              column sweep; the result also goes, transposed, into
+//              the unused upper triangle, tile (k, i);
+//   update(k-1) every trailing lower tile (i, j), k < j <= i:
+//              A_ij -= L_{i,k-1} L_{j,k-1}^T,
+// so a step costs one grid barrier.  A second small kernel then inverts the
+// diagonal tiles in parallel (D_k = L_kk^{-1}) for the solve.  Tiles are
+// padded with the identity so any d works.  The factor runs in FP64 (plain
+// form) or FP32 (mixed form: there the Hessian already carries TF32/BF16
+// input rounding, so the factor only has to be a good preconditioner; the
+// iterate update x += delta stays FP64).  A pivot that is not positive
+// records DEV_NOT_SPD; a barrier wait that exceeds its spin budget records
+// DEV_TIMEOUT and every CTA returns.
+//
+// Solve: one CTA, left-looking by tiles.  Forward: warp w forms row k0+w of
+// L times the solved part of y with coalesced row reads, then y_k = D_k t_k.
+// Backward: the same on the stored transpose, z_k = D_k^T t_k.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -17,6 +31,9 @@
 #include "internal.h"
 
 int chol_padded(int d) { return (d + 31) / 32 * 32; }
+size_t chol_dinv_bytes(int d, int f32) {
+  return (size_t)(chol_padded(d) / 32) * 1024 * (f32 ? 4 : 8);
+}
 
 template <typename T>
 __global__ void k_chol_init(const double* __restrict__ H, int d, int dp, T* __restrict__ L) {
@@ -31,166 +48,302 @@ __global__ void k_chol_init(const double* __restrict__ H, int d, int dp, T* __re
   }
 }
 
-template <typename T>
-__global__ void __launch_bounds__(512) k_chol_panel(T* __restrict__ L, int dp, int k,
-                                                    int* status) {
-  __shared__ T D[32][33];
-  const int ty = threadIdx.x >> 5, tx = threadIdx.x & 31;  // ty in [0, 16): rows ty, ty + 16
-  const int k0 = k * 32;
-  D[ty][tx] = L[(int64_t)(k0 + ty) * dp + k0 + tx];
-  D[ty + 16][tx] = L[(int64_t)(k0 + ty + 16) * dp + k0 + tx];
+// Grid-wide barrier (generation counter), bounded spin.  bar[0] = arrivals,
+// bar[1] = generation, bar[2] = abort flag; all zero before the launch.
+IHS_DEV bool grid_barrier(unsigned* bar, unsigned nblocks, int* status) {
+  __shared__ int ok;
   __syncthreads();
-  for (int j = 0; j < 32; ++j) {
-    if (threadIdx.x == 0) {
-      T p = D[j][j];
-      if (!(p > T(0))) {
-        set_status(status, DEV_NOT_SPD);
-        p = T(1);
+  if (threadIdx.x == 0) {
+    ok = 1;
+    volatile unsigned* gen = bar + 1;
+    volatile unsigned* abort_flag = bar + 2;
+    const unsigned g = *gen;
+    __threadfence();
+    if (atomicAdd(bar, 1u) == nblocks - 1) {
+      *(volatile unsigned*)bar = 0;
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      long long it = 0;
+      while (*gen == g) {
+        if (++it > kSpinLimit || *abort_flag) {
+          set_status(status, DEV_TIMEOUT);
+          *abort_flag = 1u;
+          ok = 0;
+          break;
+        }
+        if (it > 64) __nanosleep(32);
       }
-      D[j][j] = sqrt(p);
     }
-    __syncthreads();
-    if (threadIdx.x < 32 && tx > j) D[tx][j] = D[tx][j] / D[j][j];
-    __syncthreads();
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int r = ty + 16 * h;
-      if (r > j && tx > j && tx <= r) D[r][tx] -= D[r][j] * D[tx][j];
-    }
-    __syncthreads();
+    __threadfence();
   }
-#pragma unroll
-  for (int h = 0; h < 2; ++h) {
-    const int r = ty + 16 * h;
-    L[(int64_t)(k0 + r) * dp + k0 + tx] = (tx <= r) ? D[r][tx] : T(0);
-  }
-  __shared__ T R[32];
-  if (threadIdx.x < 32) R[threadIdx.x] = T(1) / D[threadIdx.x][threadIdx.x];
   __syncthreads();
-  // panel: rows below solve x L_kk^T = a
-  for (int row = k0 + 32 + threadIdx.x; row < dp; row += blockDim.x) {
-    T a[32];
-    T* pr = L + (int64_t)row * dp + k0;
-#pragma unroll
-    for (int c = 0; c < 32; ++c) a[c] = pr[c];
-#pragma unroll
-    for (int c = 0; c < 32; ++c) {
-      a[c] *= R[c];
-#pragma unroll
-      for (int q = c + 1; q < 32; ++q) a[q] -= a[c] * D[q][c];
-    }
-#pragma unroll
-    for (int c = 0; c < 32; ++c) pr[c] = a[c];
-  }
+  return ok != 0;
 }
 
+// Factor the 32 x 32 tile Dk (lower part valid) in place with warp 0, row r
+// in lane r's registers: column j is scaled by the pivot and the trailing
+// rows updated with the other lanes' entries fetched by shuffles; R gets the
+// reciprocals of the diagonal.  All threads of the CTA must call.
 template <typename T>
-__global__ void __launch_bounds__(256) k_chol_update(T* __restrict__ L, int dp, int k, int Tt) {
-  __shared__ T Pi[32][33];
-  __shared__ T Pj[32][33];
-  // lower tile (i, j), k < j <= i < Tt
-  const int q = blockIdx.x;
-  int ii = (int)((sqrtf(8.0f * q + 1.0f) - 1.0f) * 0.5f);
-  while ((ii + 1) * (ii + 2) / 2 <= q) ++ii;
-  while (ii * (ii + 1) / 2 > q) --ii;
-  const int jj = q - ii * (ii + 1) / 2;
-  const int i = k + 1 + ii, j = k + 1 + jj;
-  const int k0 = k * 32;
-  for (int e = threadIdx.x; e < 1024; e += 256) {
-    const int r = e >> 5, c = e & 31;
-    Pi[r][c] = L[(int64_t)(i * 32 + r) * dp + k0 + c];
-    Pj[r][c] = L[(int64_t)(j * 32 + r) * dp + k0 + c];
+__device__ void tile_factor(T (*Dk)[33], T* R, int* spd) {
+  const int lane = threadIdx.x & 31;
+  if (threadIdx.x < 32) {
+    T a[32];
+#pragma unroll
+    for (int c = 0; c < 32; ++c) a[c] = (c <= lane) ? Dk[lane][c] : T(0);
+    bool good = true;
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+      T pj = __shfl_sync(0xffffffffu, a[j], j);
+      if (!(pj > T(0))) {
+        good = false;
+        pj = T(1);
+      }
+      const T ljj = sqrt(pj);
+      const T rinv = T(1) / ljj;
+      const T lrj = (lane > j) ? a[j] * rinv : (lane == j ? ljj : T(0));
+      a[j] = lrj;
+      if (lane == j) R[j] = rinv;
+#pragma unroll
+      for (int c = 1; c < 32; ++c) {
+        if (c > j) {
+          const T lcj = __shfl_sync(0xffffffffu, lrj, c);
+          if (lane >= c) a[c] -= lrj * lcj;
+        }
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < 32; ++c) Dk[lane][c] = a[c];
+    if (lane == 0) *spd = good ? 1 : 0;
   }
   __syncthreads();
-  const int a = threadIdx.x >> 3, b0 = (threadIdx.x & 7) * 4;
+}
+
+// C (32 x 32 in smem) -= P Q^T, P, Q 32 x 32 in smem; 256 threads.
+template <typename T>
+__device__ void tile_sub_pqt(T (*C)[33], T (*P)[33], T (*Q)[33]) {
+  const int tid = threadIdx.x;
+  const int a = tid >> 3, b0 = (tid & 7) * 4;
   T acc[4] = {T(0), T(0), T(0), T(0)};
 #pragma unroll 8
-  for (int c = 0; c < 32; ++c) {
-    const T pa = Pi[a][c];
+  for (int cc = 0; cc < 32; ++cc) {
+    const T pa = P[a][cc];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) acc[u] += pa * Pj[b0 + u][c];
+    for (int v = 0; v < 4; ++v) acc[v] += pa * Q[b0 + v][cc];
   }
-  T* out = L + (int64_t)(i * 32 + a) * dp + j * 32 + b0;
 #pragma unroll
-  for (int u = 0; u < 4; ++u) out[u] -= acc[u];
+  for (int v = 0; v < 4; ++v) C[a][b0 + v] -= acc[v];
+  __syncthreads();
+}
+
+// Look-ahead schedule: between barriers k-1 and k the grid does, as one
+// list of independent items,
+//   panel(k)        tile rows k..Tt-1 of column k, each first applying the
+//                   rank-32 update of step k-1 to its own tiles, and
+//   update(k-1)     every trailing tile (i, j) with k < j <= i,
+// so a step costs one grid barrier.  The panel tile L_ik solves
+// x L_kk^T = a for its 32 rows at once by a column sweep in shared memory.
+template <typename T>
+__global__ void __launch_bounds__(256) k_chol_coop(T* __restrict__ L, int dp, int Tt, unsigned* bar,
+                                                   int* status) {
+  __shared__ T Dk[32][33];
+  __shared__ T Ta[32][33];
+  __shared__ T Tb[32][33];
+  __shared__ T Tc[32][33];
+  __shared__ T R[32];
+  __shared__ int spd;
+  const int tid = threadIdx.x;
+  const unsigned nb = gridDim.x;
+  for (int k = 0; k < Tt; ++k) {
+    const int k0 = k * 32, kp = (k - 1) * 32;
+    const int npanel = Tt - k;
+    const int u = Tt - k - 1;
+    const int nupd = (k >= 1) ? u * (u + 1) / 2 : 0;
+    for (int item = blockIdx.x; item < npanel + nupd; item += gridDim.x) {
+      if (item < npanel) {
+        const int c = item;
+        const int i0 = (k + c) * 32;
+        // all tile loads of the item at once
+        for (int e = tid; e < 1024; e += blockDim.x) {
+          const int r = e >> 5, q = e & 31;
+          Dk[r][q] = __ldcg(L + (int64_t)(k0 + r) * dp + k0 + q);
+          if (k >= 1) Tb[r][q] = __ldcg(L + (int64_t)(k0 + r) * dp + kp + q);  // L_{k,k-1}
+          if (c > 0) {
+            Ta[r][q] = __ldcg(L + (int64_t)(i0 + r) * dp + k0 + q);
+            if (k >= 1) Tc[r][q] = __ldcg(L + (int64_t)(i0 + r) * dp + kp + q);  // L_{i,k-1}
+          }
+        }
+        __syncthreads();
+        if (k >= 1) {
+          tile_sub_pqt(Dk, Tb, Tb);
+          if (c > 0) tile_sub_pqt(Ta, Tc, Tb);
+        }
+        tile_factor<T>(Dk, R, &spd);
+        if (c == 0) {
+          if (!spd && tid == 0) set_status(status, DEV_NOT_SPD);
+          for (int e = tid; e < 1024; e += blockDim.x) {
+            const int r = e >> 5, q = e & 31;
+            L[(int64_t)(k0 + r) * dp + k0 + q] = (q <= r) ? Dk[r][q] : T(0);
+          }
+        } else {
+          // column sweep: x_b = (a_b - sum_{q<b} x_q L_bq) / L_bb for all 32 rows at once
+          for (int b = 0; b < 32; ++b) {
+            if (tid < 32) Ta[tid][b] *= R[b];
+            __syncthreads();
+            for (int e = tid; e < 1024; e += blockDim.x) {
+              const int a = e >> 5, q = e & 31;
+              if (q > b) Ta[a][q] -= Ta[a][b] * Dk[q][b];
+            }
+            __syncthreads();
+          }
+          for (int e = tid; e < 1024; e += blockDim.x) {
+            const int a = e >> 5, b = e & 31;
+            L[(int64_t)(i0 + a) * dp + k0 + b] = Ta[a][b];
+            L[(int64_t)(k0 + a) * dp + i0 + b] = Ta[b][a];  // transpose into tile (k, i)
+          }
+        }
+        __syncthreads();
+      } else {
+        // update(k-1) of tile (i, j), k < j <= i
+        const int q = item - npanel;
+        int ii = (int)((sqrtf(8.0f * q + 1.0f) - 1.0f) * 0.5f);
+        while ((ii + 1) * (ii + 2) / 2 <= q) ++ii;
+        while (ii * (ii + 1) / 2 > q) --ii;
+        const int jj = q - ii * (ii + 1) / 2;
+        const int i0 = (k + 1 + ii) * 32, j0 = (k + 1 + jj) * 32;
+        for (int e = tid; e < 1024; e += blockDim.x) {
+          const int r = e >> 5, cc = e & 31;
+          Ta[r][cc] = __ldcg(L + (int64_t)(i0 + r) * dp + kp + cc);
+          Tb[r][cc] = __ldcg(L + (int64_t)(j0 + r) * dp + kp + cc);
+        }
+        __syncthreads();
+        const int a = tid >> 3, b0 = (tid & 7) * 4;
+        T acc[4] = {T(0), T(0), T(0), T(0)};
+#pragma unroll 8
+        for (int cc = 0; cc < 32; ++cc) {
+          const T pa = Ta[a][cc];
+#pragma unroll
+          for (int v = 0; v < 4; ++v) acc[v] += pa * Tb[b0 + v][cc];
+        }
+        T* out = L + (int64_t)(i0 + a) * dp + j0 + b0;
+#pragma unroll
+        for (int v = 0; v < 4; ++v) __stcg(out + v, __ldcg(out + v) - acc[v]);
+        __syncthreads();
+      }
+    }
+    if (k + 1 < Tt && !grid_barrier(bar, nb, status)) return;
+  }
+}
+
+// Inverses D_k = L_kk^{-1} of the diagonal tiles, one CTA (one warp) per
+// tile, lane c forming column c by forward substitution from shared memory.
+template <typename T>
+__global__ void __launch_bounds__(32) k_tile_inverse(const T* __restrict__ L, int dp,
+                                                     T* __restrict__ Dinv) {
+  __shared__ T Lk[32][33];
+  __shared__ T X[32][33];
+  const int k = blockIdx.x, lane = threadIdx.x, k0 = k * 32;
+  for (int r = 0; r < 32; ++r) Lk[r][lane] = L[(int64_t)(k0 + r) * dp + k0 + lane];
+  __syncwarp();
+  for (int r = 0; r < 32; ++r) {
+    T v;
+    if (r < lane) {
+      v = T(0);
+    } else {
+      T sacc = (r == lane) ? T(1) : T(0);
+      for (int q = lane; q < r; ++q) sacc -= Lk[r][q] * X[q][lane];
+      v = sacc / Lk[r][r];
+    }
+    X[r][lane] = v;
+  }
+  __syncwarp();
+  for (int r = 0; r < 32; ++r) Dinv[(int64_t)k * 1024 + r * 32 + lane] = X[r][lane];
 }
 
 template <typename T>
-static cudaError_t chol_impl(const double* H, int d, T* L, int* status, cudaStream_t st) {
-  const int dp = chol_padded(d), Tt = dp / 32;
+static cudaError_t chol_impl(const double* H, int d, T* L, T* Dinv, unsigned* bar, int* status,
+                             cudaStream_t st) {
+  int dp = chol_padded(d), Tt = dp / 32;
   const int blocks = (int)std::min<int64_t>(((int64_t)dp * dp + 255) / 256, 2048);
   { k_chol_init<T><<<blocks, 256, 0, st>>>(H, d, dp, L); note_launches(1); }
-  for (int k = 0; k < Tt; ++k) {
-    { k_chol_panel<T><<<1, 512, 0, st>>>(L, dp, k, status); note_launches(1); }
-    const int u = Tt - k - 1;
-    { if (u > 0) k_chol_update<T><<<u * (u + 1) / 2, 256, 0, st>>>(L, dp, k, Tt); note_launches(1); }
-  }
+  cudaError_t e = cudaMemsetAsync(bar, 0, 4 * sizeof(unsigned), st);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0, per = 0;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+    return e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_chol_coop<T>, 256, 0)) !=
+      cudaSuccess)
+    return e;
+  if (per < 1) return cudaErrorCooperativeLaunchTooLarge;
+  // one CTA per SM at most; no more CTAs than the largest phase has items
+  int grid = std::min(sms, std::max(Tt, Tt + (Tt - 2) * (Tt - 1) / 2));
+  grid = std::max(grid, 1);
+  void* args[] = {(void*)&L, (void*)&dp, (void*)&Tt, (void*)&bar, (void*)&status};
+  e = cudaLaunchCooperativeKernel((const void*)k_chol_coop<T>, dim3(grid), dim3(256), args, 0, st);
+  note_launches(1);
+  if (e != cudaSuccess) return e;
+  k_tile_inverse<T><<<Tt, 32, 0, st>>>(L, dp, Dinv);
+  note_launches(1);
   return cudaGetLastError();
 }
 
-cudaError_t launch_cholesky(const double* H, int d, int f32, void* Lbuf, int* status,
-                            cudaStream_t st) {
-  return f32 ? chol_impl<float>(H, d, (float*)Lbuf, status, st)
-             : chol_impl<double>(H, d, (double*)Lbuf, status, st);
+cudaError_t launch_cholesky(const double* H, int d, int f32, void* Lbuf, void* Dinv, unsigned* bar,
+                            int* status, cudaStream_t st) {
+  return f32 ? chol_impl<float>(H, d, (float*)Lbuf, (float*)Dinv, bar, status, st)
+             : chol_impl<double>(H, d, (double*)Lbuf, (double*)Dinv, bar, status, st);
 }
 
 // ----------------------------------------------------------------------------
-// Solve L L^T delta = v in one CTA (forward then backward substitution by 32
-// tiles: one warp solves the diagonal tile, all threads update the rest).
+// Solve L L^T delta = v in one CTA (32 warps), left-looking by 32-row tiles.
 // mode 0: x += delta, step_norm = max |delta|;  mode 1: out = delta.
 // ----------------------------------------------------------------------------
 template <typename T>
-__global__ void __launch_bounds__(1024) k_chol_solve(const T* __restrict__ L, int d, int dp,
+__global__ void __launch_bounds__(1024) k_chol_solve(const T* __restrict__ L,
+                                                     const T* __restrict__ Dinv, int d, int dp,
                                                      const double* __restrict__ v,
                                                      double* __restrict__ x,
-                                                     double* __restrict__ step_norm, int mode) {
+                                                     double* __restrict__ step_norm, int mode,
+                                                     int dinv_in_smem) {
   extern __shared__ unsigned char sm_raw[];
-  T* y = reinterpret_cast<T*>(sm_raw);
+  T* y = reinterpret_cast<T*>(sm_raw);  // dp: right-hand side, then the solution
+  T* Ds = y + dp;                       // Tt * 1024 when dinv_in_smem
+  __shared__ T t[32];
   __shared__ double red[32];
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const int Tt = dp / 32;
   for (int i = tid; i < dp; i += blockDim.x) y[i] = (i < d) ? (T)v[i] : T(0);
+  if (dinv_in_smem)
+    for (int e = tid; e < Tt * 1024; e += blockDim.x) Ds[e] = Dinv[e];
+  const T* Dk = dinv_in_smem ? Ds : Dinv;
   __syncthreads();
-  for (int kt = 0; kt < Tt; ++kt) {
-    const int k0 = kt * 32;
-    if (warp == 0) {
-      T yl = y[k0 + lane];
-      const T* Lr = L + (int64_t)(k0 + lane) * dp + k0;
-      for (int j = 0; j < 32; ++j) {
-        if (lane == j) yl = yl / Lr[j];
-        const T yj = __shfl_sync(0xffffffffu, yl, j);
-        if (lane > j) yl -= Lr[j] * yj;
-      }
-      y[k0 + lane] = yl;
-    }
+  // forward: y_k = D_k (v_k - sum_{j < k} L_kj y_j)
+  for (int k = 0; k < Tt; ++k) {
+    const int k0 = k * 32, r = k0 + w;
+    const T* Lr = L + (int64_t)r * dp;
+    T s = T(0);
+    for (int c = lane; c < k0; c += 32) s += Lr[c] * y[c];
+    s = warp_sum(s);
+    if (lane == 0) t[w] = y[r] - s;
     __syncthreads();
-    for (int r = k0 + 32 + tid; r < dp; r += blockDim.x) {
-      const T* Lr = L + (int64_t)r * dp + k0;
-      T s = T(0);
-#pragma unroll 8
-      for (int c = 0; c < 32; ++c) s += Lr[c] * y[k0 + c];
-      y[r] -= s;
-    }
+    T yv = Dk[(int64_t)k * 1024 + w * 32 + lane] * t[lane];
+    yv = warp_sum(yv);
+    if (lane == 0) y[r] = yv;
     __syncthreads();
   }
-  for (int kt = Tt - 1; kt >= 0; --kt) {
-    const int k0 = kt * 32;
-    if (warp == 0) {
-      T yl = y[k0 + lane];
-      for (int j = 31; j >= 0; --j) {
-        if (lane == j) yl = yl / L[(int64_t)(k0 + j) * dp + k0 + j];
-        const T zj = __shfl_sync(0xffffffffu, yl, j);
-        if (lane < j) yl -= L[(int64_t)(k0 + j) * dp + k0 + lane] * zj;
-      }
-      y[k0 + lane] = yl;
-    }
+  // backward: z_k = D_k^T (y_k - sum_{j > k} (L^T)_kj z_j), (L^T)_kj stored in tile (k, j)
+  for (int k = Tt - 1; k >= 0; --k) {
+    const int k0 = k * 32, r = k0 + w;
+    const T* Ur = L + (int64_t)r * dp;
+    T s = T(0);
+    for (int c = k0 + 32 + lane; c < dp; c += 32) s += Ur[c] * y[c];
+    s = warp_sum(s);
+    if (lane == 0) t[w] = y[r] - s;
     __syncthreads();
-    for (int r = tid; r < k0; r += blockDim.x) {
-      T s = T(0);
-#pragma unroll 8
-      for (int c = 0; c < 32; ++c) s += L[(int64_t)(k0 + c) * dp + r] * y[k0 + c];
-      y[r] -= s;
-    }
+    T zv = Dk[(int64_t)k * 1024 + lane * 32 + w] * t[lane];
+    zv = warp_sum(zv);
+    if (lane == 0) y[r] = zv;
     __syncthreads();
   }
   double mx = 0.0;
@@ -205,32 +358,46 @@ __global__ void __launch_bounds__(1024) k_chol_solve(const T* __restrict__ L, in
   }
   if (mode == 0) {
     for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    if (lane == 0) red[warp] = mx;
+    if (lane == 0) red[w] = mx;
     __syncthreads();
     if (tid == 0) {
       double m2 = 0.0;
-      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m2 = fmax(m2, red[w]);
+      for (int q = 0; q < (int)(blockDim.x >> 5); ++q) m2 = fmax(m2, red[q]);
       if (step_norm) *step_norm = m2;
     }
   }
 }
 
 template <typename T>
-static cudaError_t solve_impl(const T* L, int d, const double* v, double* x, double* step_norm,
-                              int mode, cudaStream_t st) {
+static cudaError_t solve_impl(const T* L, const T* Dinv, int d, const double* v, double* x,
+                              double* step_norm, int mode, cudaStream_t st) {
   const int dp = chol_padded(d);
-  { k_chol_solve<T><<<1, 1024, (size_t)dp * sizeof(T), st>>>(L, d, dp, v, x, step_norm, mode); note_launches(1); }
+  const size_t base = (size_t)dp * sizeof(T);
+  const size_t dinv = (size_t)(dp / 32) * 1024 * sizeof(T);
+  const int in_smem = (base + dinv) <= 200 * 1024;
+  const size_t smem = base + (in_smem ? dinv : 0);
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_chol_solve<T>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  k_chol_solve<T><<<1, 1024, smem, st>>>(L, Dinv, d, dp, v, x, step_norm, mode, in_smem);
+  note_launches(1);
   return cudaGetLastError();
 }
 
-cudaError_t launch_chol_step(const void* Lbuf, int d, int f32, const double* g, double* x,
-                             double* step_norm, cudaStream_t st) {
-  return f32 ? solve_impl<float>((const float*)Lbuf, d, g, x, step_norm, 0, st)
-             : solve_impl<double>((const double*)Lbuf, d, g, x, step_norm, 0, st);
+cudaError_t launch_chol_step(const void* Lbuf, const void* Dinv, int d, int f32, const double* g,
+                             double* x, double* step_norm, cudaStream_t st) {
+  return f32 ? solve_impl<float>((const float*)Lbuf, (const float*)Dinv, d, g, x, step_norm, 0, st)
+             : solve_impl<double>((const double*)Lbuf, (const double*)Dinv, d, g, x, step_norm, 0,
+                                  st);
 }
 
-cudaError_t launch_chol_apply(const void* Lbuf, int d, int f32, const double* v, double* out,
-                              cudaStream_t st) {
-  return f32 ? solve_impl<float>((const float*)Lbuf, d, v, out, nullptr, 1, st)
-             : solve_impl<double>((const double*)Lbuf, d, v, out, nullptr, 1, st);
+cudaError_t launch_chol_apply(const void* Lbuf, const void* Dinv, int d, int f32, const double* v,
+                              double* out, cudaStream_t st) {
+  return f32 ? solve_impl<float>((const float*)Lbuf, (const float*)Dinv, d, v, out, nullptr, 1, st)
+             : solve_impl<double>((const double*)Lbuf, (const double*)Dinv, d, v, out, nullptr, 1,
+                                  st);
 }

@@ -442,7 +442,8 @@ __global__ void k_to_float(const double* __restrict__ a, int64_t n, float* __res
     b[i] = (float)a[i];
 }
 
-cudaError_t launch_l1_step(const double* H, const void* Lbuf, int f32, int d, const double* g,
+cudaError_t launch_l1_step(const double* H, const void* Lbuf, const void* Dinv, int f32, int d,
+                           const double* g,
                            double R, int max_iter, double tol, QpWork w, double* x,
                            double* step_norm, int* status, cudaStream_t st) {
   if (d > kQpMaxD) return cudaErrorInvalidValue;
@@ -452,7 +453,7 @@ cudaError_t launch_l1_step(const double* H, const void* Lbuf, int f32, int d, co
   if (e != cudaSuccess) return e;
   double* du = w.dbuf;              // d
   double* wv = w.dbuf + d;          // 2d doubles of face-solve scratch
-  e = launch_chol_apply(Lbuf, d, f32, g, du, st);
+  e = launch_chol_apply(Lbuf, Dinv, d, f32, g, du, st);
   if (e != cudaSuccess) return e;
   const size_t smem = sizeof(QpShared);
   const int ld = chol_padded(d);

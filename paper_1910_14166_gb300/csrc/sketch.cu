@@ -430,3 +430,10 @@ cudaError_t launch_sketch_adjoint(const SketchKeys& K, int64_t n, int64_t d, con
                                                            out); note_launches(1); }
   return cudaGetLastError();
 }
+
+cudaError_t launch_sketch_fixup_f32(const SortPlan& p, const int32_t* seg, int d,
+                                    const float* partial, float* SA, cudaStream_t st) {
+  k_sketch_fixup<float><<<(p.m + 7) / 8, 256, 0, st>>>(seg, p.m, d, p.chunk, partial, SA);
+  note_launches(1);
+  return cudaGetLastError();
+}

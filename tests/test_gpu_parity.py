@@ -289,3 +289,26 @@ def test_profile_counts_stages(cuda_lib):
     ms, cnt, launches = s1.profile_read()
     assert cnt["sketch"] == 3 and cnt["grad"] == 3 and cnt["step"] == 3
     assert all(v >= 0 for v in ms.values()) and launches > 0
+
+
+def test_fused_pass_agrees_with_two_passes(cuda_lib):
+    """The single fused pass (SA and gradient from one read of A) gives the
+    same SA bit for bit and iterates within 1e-12 of the two-pass path, and
+    both reach 1e-10 against x_OPT."""
+    w = synth.make("ols_dense_ar1", n=50021, d=96, m=960)
+    A64 = w["A"].astype(np.float64)
+    xo = O.x_opt_ols_normal(A64, w["b"])
+    G = A64.T @ A64
+    A, b = dev(w["A"]), dev(w["b"])
+    fu = cuda_lib.IHS(A, b, m=960, precision="tf32", fuse=True)
+    tw = cuda_lib.IHS(A, b, m=960, precision="tf32", fuse=False)
+    x1, _ = fu.solve(iters=3)
+    x2, _ = tw.solve(iters=3)
+    S1, H1, _ = fu.get_sketch()
+    S2, H2, _ = tw.get_sketch()
+    assert torch.equal(S1, S2) and torch.equal(H1, H2)
+    e = (x1 - x2).cpu().numpy()
+    assert np.sqrt(e @ G @ e) / np.sqrt(xo @ G @ xo) < 1e-12
+    x1, _ = fu.solve(x1, t0=3, iters=30)
+    x2, _ = tw.solve(x2, t0=3, iters=30)
+    assert O.err_A(x1.cpu().numpy(), xo, G) < 1e-10 and O.err_A(x2.cpu().numpy(), xo, G) < 1e-10
