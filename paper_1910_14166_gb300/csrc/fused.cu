@@ -94,18 +94,21 @@ __global__ void __launch_bounds__(kFuThreads) k_sketch_grad_fused(
           for (int q = 0; q < NV; ++q)
 #pragma unroll
             for (int t = 0; t < 4; ++t) acc[q][t] = neg ? acc[q][t] - a[q][t] : acc[q][t] + a[q][t];
-          // residual: two independent float-pair chains, then a warp reduction
+          // residual: four independent float-pair chains, then a warp reduction
           float s0h = 0.f, s0l = 0.f, s1h = 0.f, s1l = 0.f;
+          float s2h = 0.f, s2l = 0.f, s3h = 0.f, s3l = 0.f;
 #pragma unroll
           for (int q = 0; q < NV; ++q) {
             const float4 vh = *reinterpret_cast<const float4*>(xh + colq[q]);
             const float4 vl = *reinterpret_cast<const float4*>(xl + colq[q]);
             dd_fma_acc(s0h, s0l, a[q][0], vh.x, vl.x);
             dd_fma_acc(s1h, s1l, a[q][1], vh.y, vl.y);
-            dd_fma_acc(s0h, s0l, a[q][2], vh.z, vl.z);
-            dd_fma_acc(s1h, s1l, a[q][3], vh.w, vl.w);
+            dd_fma_acc(s2h, s2l, a[q][2], vh.z, vl.z);
+            dd_fma_acc(s3h, s3l, a[q][3], vh.w, vl.w);
           }
           dd_add(s0h, s0l, s1h, s1l);
+          dd_add(s2h, s2l, s3h, s3l);
+          dd_add(s0h, s0l, s2h, s2l);
 #pragma unroll
           for (int o = 16; o > 0; o >>= 1) {
             const float oh = __shfl_xor_sync(0xffffffffu, s0h, o);

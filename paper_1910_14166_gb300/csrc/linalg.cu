@@ -6,14 +6,15 @@
 // barriers k-1 and k the CTAs share out, as one list of independent items,
 //   panel(k)   tile rows k..Tt-1 of column k.  Each such item first applies
 //              the rank-32 update of step k-1 to its own tiles, factors the
-//              32 x 32 diagonal tile itself in registers (redundantly, which
-//              saves a barrier), and solves x L_kk^T = a for its tile by a
-//              column sweep; the result also goes, transposed, into
+//              32 x 32 diagonal tile itself (redundantly, which saves a
+//              barrier) and solves x L_kk^T = a for its tile in the same
+//              register sweep; the result also goes, transposed, into
 //              the unused upper triangle, tile (k, i);
 //   update(k-1) every trailing lower tile (i, j), k < j <= i:
 //              A_ij -= L_{i,k-1} L_{j,k-1}^T,
-// so a step costs one grid barrier.  A second small kernel then inverts the
-// diagonal tiles in parallel (D_k = L_kk^{-1}) for the solve.  Tiles are
+// so a step costs one grid barrier.  The item that owns the diagonal tile
+// sweeps the identity alongside it, which yields D_k = L_kk^{-1} for the
+// solve in the same 32 steps.  Tiles are
 // padded with the identity so any d works.  The factor runs in FP64 (plain
 // form) or FP32 (mixed form: there the Hessian already carries TF32/BF16
 // input rounding, so the factor only has to be a good preconditioner; the
@@ -72,7 +73,7 @@ IHS_DEV bool grid_barrier(unsigned* bar, unsigned nblocks, int* status) {
           ok = 0;
           break;
         }
-        if (it > 64) __nanosleep(32);
+        if (it > 2048) __nanosleep(64);
       }
     }
     __threadfence();
@@ -81,17 +82,23 @@ IHS_DEV bool grid_barrier(unsigned* bar, unsigned nblocks, int* status) {
   return ok != 0;
 }
 
-// Factor the 32 x 32 tile Dk (lower part valid) in place with warp 0, row r
-// in lane r's registers: column j is scaled by the pivot and the trailing
-// rows updated with the other lanes' entries fetched by shuffles; R gets the
-// reciprocals of the diagonal.  All threads of the CTA must call.
+// Panel sweep with warp 0 over the tall block [Dk; Ta] (Ta optional): lane r
+// holds row r of the diagonal tile and row r of the panel tile in registers.
+// Column j: the pivot comes from lane j by a shuffle, the diagonal rows below
+// and every panel row are scaled by 1/L_jj, and the trailing columns of both
+// are updated with L_cj fetched from lane c.  This factors Dk = L_kk L_kk^T
+// and solves Ta <- Ta L_kk^{-T} in the same 32 steps, with no block-wide
+// barrier inside.  All threads of the CTA must call.
 template <typename T>
-__device__ void tile_factor(T (*Dk)[33], T* R, int* spd) {
+__device__ void panel_sweep(T (*Dk)[33], T (*Ta)[33], bool tall, int* spd) {
   const int lane = threadIdx.x & 31;
   if (threadIdx.x < 32) {
-    T a[32];
+    T a[32], bb[32];
 #pragma unroll
-    for (int c = 0; c < 32; ++c) a[c] = (c <= lane) ? Dk[lane][c] : T(0);
+    for (int c = 0; c < 32; ++c) {
+      a[c] = (c <= lane) ? Dk[lane][c] : T(0);
+      bb[c] = tall ? Ta[lane][c] : T(0);
+    }
     bool good = true;
 #pragma unroll
     for (int j = 0; j < 32; ++j) {
@@ -100,21 +107,25 @@ __device__ void tile_factor(T (*Dk)[33], T* R, int* spd) {
         good = false;
         pj = T(1);
       }
-      const T ljj = sqrt(pj);
-      const T rinv = T(1) / ljj;
-      const T lrj = (lane > j) ? a[j] * rinv : (lane == j ? ljj : T(0));
+      const T rinv = rsqrt(pj);
+      const T lrj = (lane > j) ? a[j] * rinv : (lane == j ? pj * rinv : T(0));
       a[j] = lrj;
-      if (lane == j) R[j] = rinv;
+      const T bj = bb[j] * rinv;
+      bb[j] = bj;
 #pragma unroll
       for (int c = 1; c < 32; ++c) {
         if (c > j) {
           const T lcj = __shfl_sync(0xffffffffu, lrj, c);
           if (lane >= c) a[c] -= lrj * lcj;
+          bb[c] -= bj * lcj;
         }
       }
     }
 #pragma unroll
-    for (int c = 0; c < 32; ++c) Dk[lane][c] = a[c];
+    for (int c = 0; c < 32; ++c) {
+      Dk[lane][c] = a[c];
+      if (tall) Ta[lane][c] = bb[c];
+    }
     if (lane == 0) *spd = good ? 1 : 0;
   }
   __syncthreads();
@@ -142,16 +153,15 @@ __device__ void tile_sub_pqt(T (*C)[33], T (*P)[33], T (*Q)[33]) {
 //   panel(k)        tile rows k..Tt-1 of column k, each first applying the
 //                   rank-32 update of step k-1 to its own tiles, and
 //   update(k-1)     every trailing tile (i, j) with k < j <= i,
-// so a step costs one grid barrier.  The panel tile L_ik solves
-// x L_kk^T = a for its 32 rows at once by a column sweep in shared memory.
+// so a step costs one grid barrier.  The diagonal factor and the panel tile's
+// solve x L_kk^T = a share one register sweep (panel_sweep).
 template <typename T>
-__global__ void __launch_bounds__(256) k_chol_coop(T* __restrict__ L, int dp, int Tt, unsigned* bar,
-                                                   int* status) {
+__global__ void __launch_bounds__(256) k_chol_coop(T* __restrict__ L, T* __restrict__ Dinv, int dp,
+                                                   int Tt, unsigned* bar, int* status) {
   __shared__ T Dk[32][33];
   __shared__ T Ta[32][33];
   __shared__ T Tb[32][33];
   __shared__ T Tc[32][33];
-  __shared__ T R[32];
   __shared__ int spd;
   const int tid = threadIdx.x;
   const unsigned nb = gridDim.x;
@@ -179,24 +189,20 @@ __global__ void __launch_bounds__(256) k_chol_coop(T* __restrict__ L, int dp, in
           tile_sub_pqt(Dk, Tb, Tb);
           if (c > 0) tile_sub_pqt(Ta, Tc, Tb);
         }
-        tile_factor<T>(Dk, R, &spd);
+        if (c == 0) {
+          // sweeping the identity alongside gives L_kk^{-T} in the same steps
+          for (int e = tid; e < 1024; e += blockDim.x) Ta[e >> 5][e & 31] = ((e >> 5) == (e & 31)) ? T(1) : T(0);
+          __syncthreads();
+        }
+        panel_sweep<T>(Dk, Ta, true, &spd);
         if (c == 0) {
           if (!spd && tid == 0) set_status(status, DEV_NOT_SPD);
           for (int e = tid; e < 1024; e += blockDim.x) {
             const int r = e >> 5, q = e & 31;
             L[(int64_t)(k0 + r) * dp + k0 + q] = (q <= r) ? Dk[r][q] : T(0);
+            Dinv[(int64_t)k * 1024 + e] = (q <= r) ? Ta[q][r] : T(0);  // (L_kk^{-T})^T
           }
         } else {
-          // column sweep: x_b = (a_b - sum_{q<b} x_q L_bq) / L_bb for all 32 rows at once
-          for (int b = 0; b < 32; ++b) {
-            if (tid < 32) Ta[tid][b] *= R[b];
-            __syncthreads();
-            for (int e = tid; e < 1024; e += blockDim.x) {
-              const int a = e >> 5, q = e & 31;
-              if (q > b) Ta[a][q] -= Ta[a][b] * Dk[q][b];
-            }
-            __syncthreads();
-          }
           for (int e = tid; e < 1024; e += blockDim.x) {
             const int a = e >> 5, b = e & 31;
             L[(int64_t)(i0 + a) * dp + k0 + b] = Ta[a][b];
@@ -236,31 +242,6 @@ __global__ void __launch_bounds__(256) k_chol_coop(T* __restrict__ L, int dp, in
   }
 }
 
-// Inverses D_k = L_kk^{-1} of the diagonal tiles, one CTA (one warp) per
-// tile, lane c forming column c by forward substitution from shared memory.
-template <typename T>
-__global__ void __launch_bounds__(32) k_tile_inverse(const T* __restrict__ L, int dp,
-                                                     T* __restrict__ Dinv) {
-  __shared__ T Lk[32][33];
-  __shared__ T X[32][33];
-  const int k = blockIdx.x, lane = threadIdx.x, k0 = k * 32;
-  for (int r = 0; r < 32; ++r) Lk[r][lane] = L[(int64_t)(k0 + r) * dp + k0 + lane];
-  __syncwarp();
-  for (int r = 0; r < 32; ++r) {
-    T v;
-    if (r < lane) {
-      v = T(0);
-    } else {
-      T sacc = (r == lane) ? T(1) : T(0);
-      for (int q = lane; q < r; ++q) sacc -= Lk[r][q] * X[q][lane];
-      v = sacc / Lk[r][r];
-    }
-    X[r][lane] = v;
-  }
-  __syncwarp();
-  for (int r = 0; r < 32; ++r) Dinv[(int64_t)k * 1024 + r * 32 + lane] = X[r][lane];
-}
-
 template <typename T>
 static cudaError_t chol_impl(const double* H, int d, T* L, T* Dinv, unsigned* bar, int* status,
                              cudaStream_t st) {
@@ -280,12 +261,10 @@ static cudaError_t chol_impl(const double* H, int d, T* L, T* Dinv, unsigned* ba
   // one CTA per SM at most; no more CTAs than the largest phase has items
   int grid = std::min(sms, std::max(Tt, Tt + (Tt - 2) * (Tt - 1) / 2));
   grid = std::max(grid, 1);
-  void* args[] = {(void*)&L, (void*)&dp, (void*)&Tt, (void*)&bar, (void*)&status};
+  void* args[] = {(void*)&L, (void*)&Dinv, (void*)&dp, (void*)&Tt, (void*)&bar, (void*)&status};
   e = cudaLaunchCooperativeKernel((const void*)k_chol_coop<T>, dim3(grid), dim3(256), args, 0, st);
   note_launches(1);
   if (e != cudaSuccess) return e;
-  k_tile_inverse<T><<<Tt, 32, 0, st>>>(L, dp, Dinv);
-  note_launches(1);
   return cudaGetLastError();
 }
 
