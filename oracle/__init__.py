@@ -18,7 +18,7 @@ What is pinned, and by what (see tests/test_oracle.py):
   * OLS step: identity sketch gives x_OPT (numpy lstsq) in one step (Eq. 2).
   * l1-ball QP: brute force over all faces of the ball for d <= 6; KKT.
   * x_OPT: Householder QR vs refined normal equations vs lstsq.
-  * IHS: geometric convergence at a rate below 1/2 (Thm. 1).
+  * IHS: geometric convergence at a rate below 1/2 (Thm. 2.2).
   * ridge adjoint: central finite differences in FP64.
 """
 from __future__ import annotations

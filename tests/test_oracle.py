@@ -282,7 +282,7 @@ def _gaussian_rate(m, d):
 
 
 def test_ihs_ols_converges_geometrically():
-    """Thm. 1: the error in the A-seminorm contracts by a factor eps0 < 1/2
+    """Thm. 2.2: the error in the A-seminorm contracts by a factor eps0 < 1/2
     per step, reaching 1e-10 in Theta(log 1/eps) steps.  20000 x 50,
     CountSketch m = 10 d."""
     w = synth.make("ols_dense_fp64")
@@ -300,7 +300,7 @@ def test_ihs_ols_converges_geometrically():
 
 
 def test_ihs_lasso_converges_to_xopt():
-    """Eq. 2 over the l1 ball converges to the constrained x_OPT (Thm. 1),
+    """Eq. 2 over the l1 ball converges to the constrained x_OPT (Thm. 2.2),
     here on a 20000 x 200 CSR lasso with SJLT s = 4, m = 2000."""
     w = synth.make("lasso_csr_fp64", n=20000)
     C = O.CSR(w["n"], w["d"], w["rowptr"], w["col"], w["val"])
