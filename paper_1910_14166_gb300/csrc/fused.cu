@@ -3,8 +3,9 @@
 // exact gradient g = A^T (b - A x^t).
 //
 // Rows arrive in bucket order (the sorted CountSketch pairs, split into equal
-// chunks, one warp per chunk, exactly as k_sketch_dense walks them), so each
-// row read from HBM is used three times while it sits in registers:
+// chunks, one warp per chunk, exactly as k_sketch_dense walks them), two rows
+// at a time, so each row read from HBM is used three times while it sits in
+// registers:
 //   SA[h(i)] += sign(i) A_i                      (FP32, bucket order)
 //   r_i = b_i - A_i x                            (float-pair, exact products)
 //   g  += A_i r_i                                (float-pair, per lane/column)
@@ -75,53 +76,90 @@ __global__ void __launch_bounds__(kFuThreads) k_sketch_grad_fused(
         const uint32_t my = (lane < cnt) ? __ldg(perm + base + lane) : 0u;
         // this lane's row of the batch: its b split, fetched once for the warp
         const float2 bmy = (lane < cnt) ? __ldg(bs + (my & 0x7fffffffu)) : make_float2(0.f, 0.f);
-        for (int j = 0; j < cnt; ++j) {
-          const uint32_t e = __shfl_sync(0xffffffffu, my, j);
-          const float* row = A + (int64_t)(e & 0x7fffffffu) * lda;
-          const bool neg = (e >> 31) != 0;
-          float a[NV][4];
+        // rows two at a time: both rows' loads in flight together, and one
+        // butterfly reduces both dot products (the first level exchanges the
+        // rows between half-warps, so lanes 0-15 end with row j, 16-31 with j+1)
+        for (int j = 0; j < cnt; j += 2) {
+          const bool two = (j + 1) < cnt;
+          const uint32_t e0 = __shfl_sync(0xffffffffu, my, j);
+          const uint32_t e1 = __shfl_sync(0xffffffffu, my, two ? j + 1 : j);
+          const float* row0 = A + (int64_t)(e0 & 0x7fffffffu) * lda;
+          const float* row1 = A + (int64_t)(e1 & 0x7fffffffu) * lda;
+          float a0[NV][4], a1[NV][4];
 #pragma unroll
           for (int q = 0; q < NV; ++q) {
             if (ok[q]) {
-              const float4 v = __ldcs(reinterpret_cast<const float4*>(row + colq[q]));
-              a[q][0] = v.x; a[q][1] = v.y; a[q][2] = v.z; a[q][3] = v.w;
+              const float4 v0 = __ldcs(reinterpret_cast<const float4*>(row0 + colq[q]));
+              a0[q][0] = v0.x; a0[q][1] = v0.y; a0[q][2] = v0.z; a0[q][3] = v0.w;
+              if (two) {
+                const float4 v1 = __ldcs(reinterpret_cast<const float4*>(row1 + colq[q]));
+                a1[q][0] = v1.x; a1[q][1] = v1.y; a1[q][2] = v1.z; a1[q][3] = v1.w;
+              } else {
+                a1[q][0] = a1[q][1] = a1[q][2] = a1[q][3] = 0.f;
+              }
             } else {
-              a[q][0] = a[q][1] = a[q][2] = a[q][3] = 0.f;
+#pragma unroll
+              for (int t = 0; t < 4; ++t) a0[q][t] = a1[q][t] = 0.f;
             }
           }
-          // sketch
+          // sketch: SA[h(i)] += sign(i) A_i, rows in order
+          const float sg0 = (e0 >> 31) ? -1.f : 1.f, sg1 = (e1 >> 31) ? -1.f : 1.f;
 #pragma unroll
           for (int q = 0; q < NV; ++q)
 #pragma unroll
-            for (int t = 0; t < 4; ++t) acc[q][t] = neg ? acc[q][t] - a[q][t] : acc[q][t] + a[q][t];
-          // residual: four independent float-pair chains, then a warp reduction
-          float s0h = 0.f, s0l = 0.f, s1h = 0.f, s1l = 0.f;
-          float s2h = 0.f, s2l = 0.f, s3h = 0.f, s3l = 0.f;
+            for (int t = 0; t < 4; ++t) acc[q][t] = __fmaf_rn(sg0, a0[q][t], acc[q][t]);
+          if (two) {
+#pragma unroll
+            for (int q = 0; q < NV; ++q)
+#pragma unroll
+              for (int t = 0; t < 4; ++t) acc[q][t] = __fmaf_rn(sg1, a1[q][t], acc[q][t]);
+          }
+          // residual partials: two float-pair chains per row
+          float p0h = 0.f, p0l = 0.f, q0h = 0.f, q0l = 0.f;
+          float p1h = 0.f, p1l = 0.f, q1h = 0.f, q1l = 0.f;
 #pragma unroll
           for (int q = 0; q < NV; ++q) {
             const float4 vh = *reinterpret_cast<const float4*>(xh + colq[q]);
             const float4 vl = *reinterpret_cast<const float4*>(xl + colq[q]);
-            dd_fma_acc(s0h, s0l, a[q][0], vh.x, vl.x);
-            dd_fma_acc(s1h, s1l, a[q][1], vh.y, vl.y);
-            dd_fma_acc(s2h, s2l, a[q][2], vh.z, vl.z);
-            dd_fma_acc(s3h, s3l, a[q][3], vh.w, vl.w);
+            dd_fma_acc(p0h, p0l, a0[q][0], vh.x, vl.x);
+            dd_fma_acc(q0h, q0l, a0[q][1], vh.y, vl.y);
+            dd_fma_acc(p0h, p0l, a0[q][2], vh.z, vl.z);
+            dd_fma_acc(q0h, q0l, a0[q][3], vh.w, vl.w);
+            dd_fma_acc(p1h, p1l, a1[q][0], vh.x, vl.x);
+            dd_fma_acc(q1h, q1l, a1[q][1], vh.y, vl.y);
+            dd_fma_acc(p1h, p1l, a1[q][2], vh.z, vl.z);
+            dd_fma_acc(q1h, q1l, a1[q][3], vh.w, vl.w);
           }
-          dd_add(s0h, s0l, s1h, s1l);
-          dd_add(s2h, s2l, s3h, s3l);
-          dd_add(s0h, s0l, s2h, s2l);
+          dd_add(p0h, p0l, q0h, q0l);
+          dd_add(p1h, p1l, q1h, q1l);
+          // level 16: keep my half's row, send the other row's partial
+          const bool hi_half = lane >= 16;
+          float kh = hi_half ? p1h : p0h, kl = hi_half ? p1l : p0l;
+          const float sh_ = hi_half ? p0h : p1h, sl_ = hi_half ? p0l : p1l;
+          dd_add(kh, kl, __shfl_xor_sync(0xffffffffu, sh_, 16), __shfl_xor_sync(0xffffffffu, sl_, 16));
 #pragma unroll
-          for (int o = 16; o > 0; o >>= 1) {
-            const float oh = __shfl_xor_sync(0xffffffffu, s0h, o);
-            const float ol = __shfl_xor_sync(0xffffffffu, s0l, o);
-            dd_add(s0h, s0l, oh, ol);
+          for (int o = 8; o > 0; o >>= 1) {
+            const float oh = __shfl_xor_sync(0xffffffffu, kh, o);
+            const float ol = __shfl_xor_sync(0xffffffffu, kl, o);
+            dd_add(kh, kl, oh, ol);
           }
-          float rh = __shfl_sync(0xffffffffu, bmy.x, j), rl = __shfl_sync(0xffffffffu, bmy.y, j);
-          dd_add(rh, rl, -s0h, -s0l);
+          // r = b - dot for both rows (lane 0 holds row j, lane 16 row j+1)
+          float r0h = __shfl_sync(0xffffffffu, bmy.x, j), r0l = __shfl_sync(0xffffffffu, bmy.y, j);
+          float r1h = __shfl_sync(0xffffffffu, bmy.x, two ? j + 1 : j);
+          float r1l = __shfl_sync(0xffffffffu, bmy.y, two ? j + 1 : j);
+          const float d0h = __shfl_sync(0xffffffffu, kh, 0), d0l = __shfl_sync(0xffffffffu, kl, 0);
+          const float d1h = __shfl_sync(0xffffffffu, kh, 16), d1l = __shfl_sync(0xffffffffu, kl, 16);
+          dd_add(r0h, r0l, -d0h, -d0l);
+          dd_add(r1h, r1l, -d1h, -d1l);
+          if (!two) r1h = r1l = 0.f;
           // gradient
 #pragma unroll
           for (int q = 0; q < NV; ++q)
 #pragma unroll
-            for (int t = 0; t < 4; ++t) dd_fma_acc(gh[q][t], gl[q][t], a[q][t], rh, rl);
+            for (int t = 0; t < 4; ++t) {
+              dd_fma_acc(gh[q][t], gl[q][t], a0[q][t], r0h, r0l);
+              dd_fma_acc(gh[q][t], gl[q][t], a1[q][t], r1h, r1l);
+            }
         }
       }
       const bool split = (sb / CH) != ((eb - 1) / CH);
