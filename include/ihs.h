@@ -101,7 +101,10 @@ typedef struct {
  * two separate passes over A even where the single fused pass applies (dense
  * FP32 data, mixed precision, CountSketch, d <= 512); results agree to
  * rounding, the fused pass reads A once instead of twice. */
-enum { IHS_FLAG_NO_FUSE = 1 };
+enum { IHS_FLAG_NO_FUSE = 1, IHS_FLAG_SERIAL = 2 };
+/* IHS_FLAG_SERIAL: issue the sketch chain (draw, sort, SA, Gram, factor) on
+ * the caller's stream too, instead of overlapping it with the gradient and
+ * step on an internal stream.  Same results; useful for timing stages. */
 
 typedef struct {
   int iters;            /* iterations taken                                */

@@ -167,7 +167,7 @@ class IHS:
     precision: 'fp64' (plain), 'tf32' or 'bf16' (mixed)."""
 
     def __init__(self, A, b, kind="ols", param=0.0, m=None, s=1, seed=0, precision="fp64",
-                 shape=None, qp_max_iter=0, qp_tol=0.0, fuse=True):
+                 shape=None, qp_max_iter=0, qp_tol=0.0, fuse=True, serial=False):
         self._keep = [A, b]
         _need_cuda(b, "b")
         if b.dtype != torch.float64:
@@ -202,7 +202,7 @@ class IHS:
         self.precision = precision
         C = _Constraint(KIND[kind], float(param))
         O = _Options(self.m, self.s, seed & 0xFFFFFFFFFFFFFFFF, PREC[precision], int(qp_max_iter),
-                     float(qp_tol), 0 if fuse else 1)
+                     float(qp_tol), (0 if fuse else 1) | (2 if serial else 0))
         h = ctypes.c_void_p()
         _check(_lib.ihs_create(ctypes.byref(h), ctypes.byref(M), _ptr(b), ctypes.byref(C),
                                ctypes.byref(O), _stream()), "ihs_create")

@@ -260,7 +260,7 @@ ihs_status build_csc(ihs_ctx* c) {
   CK(cudaStreamSynchronize(c->st));
   // work items: column chunks of at most kItem entries (a column with no
   // entries still gets one item so its zero column is written)
-  const int64_t kItem = 1 << 17;
+  const int64_t kItem = 1 << 14;
   std::vector<int32_t> icol, islot, first(d + 1);
   std::vector<int64_t> ib, ie;
   int nsplit = 0;
@@ -469,11 +469,12 @@ ihs_status ihs_create(ihs_ctx** out, const ihs_matrix* A, const double* b,
     const int64_t dd = c->d;
     c->qw.Hf = (float*)q;
     c->qw.Ls = (void*)(q + dd * dd * 4);
-    c->qw.cvec = (double*)(q + dd * dd * 4 + (size_t)dp * dp * 8);
-    c->qw.dbuf = c->qw.cvec + dd;
+    c->qw.evec = (float*)(q + dd * dd * 4 + (size_t)dp * dp * 8);
+    c->qw.dbuf = (double*)(q + dd * dd * 4 + (size_t)dp * dp * 8) + dd;
     c->qw.support = (int*)(c->qw.dbuf + 8 * dd);
     c->qw.iters = c->qw.support + dd + 1;
-    if (cudaMemsetAsync(c->qw.support, 0, (dd + 2) * sizeof(int), c->st) != cudaSuccess)
+    if (cudaMemsetAsync(c->qw.support, 0, (dd + 2) * sizeof(int), c->st) != cudaSuccess ||
+        cudaMemsetAsync(c->qw.evec, 0, dd * sizeof(float), c->st) != cudaSuccess)
       return fail(IHS_ERR_CUDA);
   }
 #undef AL2
@@ -490,7 +491,7 @@ namespace {
 // draw S and sort (dense), SA, Gram (+ lambda I), Cholesky factor.  Waits
 // for the last step that read buffer `bf`; records ev_fac[bf].
 ihs_status sketch_chain(ihs_ctx* c, int64_t t, int bf) {
-  cudaStream_t s2 = c->st2;
+  cudaStream_t s2 = (c->opt.flags & IHS_FLAG_SERIAL) ? c->st : c->st2;
   CK(cudaStreamWaitEvent(s2, c->ev_use[bf], 0));
   const SketchKeys K = make_keys(c->opt.seed, t, c->s, c->m);
   if (c->dense) {
@@ -561,7 +562,7 @@ ihs_status step_with(ihs_ctx* c, double* x, int bf) {
 // Fused pipeline, sort half: draw and sort the pairs of counter t into sort
 // buffer pb on the internal stream, after the fused pass that last read it.
 ihs_status fused_sort(ihs_ctx* c, int64_t t, int pb) {
-  cudaStream_t s2 = c->st2;
+  cudaStream_t s2 = (c->opt.flags & IHS_FLAG_SERIAL) ? c->st : c->st2;
   CK(cudaStreamWaitEvent(s2, c->ev_read[pb], 0));
   const SketchKeys K = make_keys(c->opt.seed, t, c->s, c->m);
   stage_begin(c, IHS_ST_SORT, s2);

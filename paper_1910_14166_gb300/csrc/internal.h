@@ -137,7 +137,8 @@ cudaError_t launch_chol_apply(const void* Lbuf, const void* Dinv, int d, int f32
 // l1-ball QP step (Eq. 2 over {||x||_1 <= R}); H double d x d.
 struct QpWork {
   float* Hf;       // d x d float copy of H
-  double* cvec;    // scratch
+  float* evec;     // d floats: top eigenvector estimate of H, kept across steps
+                   // (zero at creation: the power iteration then starts cold)
   void* Ls;        // support Cholesky (dp x dp, double)
   int* support;    // d ints, previous face (count in support[d])
   double* dbuf;    // 8 * d doubles of scratch

@@ -14,7 +14,9 @@
 //              A_ij -= L_{i,k-1} L_{j,k-1}^T,
 // so a step costs one grid barrier.  The item that owns the diagonal tile
 // sweeps the identity alongside it, which yields D_k = L_kk^{-1} for the
-// solve in the same 32 steps.  Tiles are
+// solve in the same 32 steps; L_kk itself is never written back (every panel
+// item of step k reads the diagonal tile while the step runs, and the solve
+// uses D_k only), so the diagonal tiles of L keep the updated H.  Tiles are
 // padded with the identity so any d works.  The factor runs in FP64 (plain
 // form) or FP32 (mixed form: there the Hessian already carries TF32/BF16
 // input rounding, so the factor only has to be a good preconditioner; the
@@ -196,10 +198,13 @@ __global__ void __launch_bounds__(256) k_chol_coop(T* __restrict__ L, T* __restr
         }
         panel_sweep<T>(Dk, Ta, true, &spd);
         if (c == 0) {
+          // L_kk itself is not stored: the other panel items of this step
+          // read the diagonal tile of L concurrently (it must keep the
+          // updated Hessian tile until the next barrier), and the solve
+          // only needs D_k = L_kk^{-1}.
           if (!spd && tid == 0) set_status(status, DEV_NOT_SPD);
           for (int e = tid; e < 1024; e += blockDim.x) {
             const int r = e >> 5, q = e & 31;
-            L[(int64_t)(k0 + r) * dp + k0 + q] = (q <= r) ? Dk[r][q] : T(0);
             Dinv[(int64_t)k * 1024 + e] = (q <= r) ? Ta[q][r] : T(0);  // (L_kk^{-T})^T
           }
         } else {

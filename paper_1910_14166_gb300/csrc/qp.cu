@@ -27,6 +27,16 @@
 constexpr int kQpThreads = 1024;
 constexpr int kQpMaxD = 1024;
 constexpr int kFaceEvery = 25;
+static_assert(kQpMaxD <= kQpThreads, "the QP epilogue gives each thread one entry");
+// Faces with at most kFaceSm<TF> indices are factored and solved in shared
+// memory (row stride kFaceSm + 1, odd, so column walks hit distinct banks);
+// larger faces use the global-memory path.
+template <typename TF>
+struct FaceSm {
+  static constexpr int n = sizeof(TF) == 4 ? 160 : 128;
+  static constexpr int ld = n + 1;
+  static constexpr size_t bytes = (size_t)n * ld * sizeof(TF) + (size_t)2 * n * sizeof(double);
+};
 
 size_t qp_work_bytes(int d) {
   const size_t dp = (size_t)chol_padded(d);
@@ -161,23 +171,97 @@ __device__ void chol_small_solve(const TF* L, int k, int ld, double* v) {
   }
 }
 
+// Shared-memory variant: M (k x k, row stride ld) in place, right-looking
+// with one barrier per column.  Step j applies the rank-1 update of pivot
+// column j (still unscaled, so the update uses M_rj M_cj / p_j) to the
+// trailing triangle and, in the same phase, scales column j-1 by its square
+// root pivot -- the two touch disjoint entries.
+template <typename TF>
+__device__ bool chol_sm(TF* M, int k, int ld) {
+  __shared__ TF dg[kQpMaxD];
+  __shared__ int bad;
+  if (threadIdx.x == 0) bad = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (int)(blockDim.x >> 5);
+  for (int j = 0; j <= k; ++j) {
+    if (j >= 1) {
+      const TF dj = dg[j - 1];
+      for (int r = j + threadIdx.x; r < k; r += blockDim.x) M[r * ld + (j - 1)] /= dj;
+      if (threadIdx.x == 0) M[(j - 1) * ld + (j - 1)] = dj;
+    }
+    if (j < k) {
+      TF p = M[j * ld + j];
+      if (!(p > TF(0))) {
+        if (threadIdx.x == 0) bad = 1;
+        p = TF(1);
+      }
+      if (threadIdx.x == 0) dg[j] = sqrt(p);
+      const TF ip = TF(1) / p;
+      for (int r = j + 1 + w; r < k; r += nw) {
+        const TF a = M[r * ld + j] * ip;
+        for (int c = j + 1 + lane; c <= r; c += 32) M[r * ld + c] -= a * M[c * ld + j];
+      }
+    }
+    __syncthreads();
+  }
+  return bad == 0;
+}
+
+// v <- M^{-1} v with M = L L^T from chol_sm, by warp 0 alone (forward then
+// backward substitution, column by column, each lane owning every 32nd entry);
+// the arithmetic is in TF like chol_small_solve.  All threads must call it.
+template <typename TF>
+__device__ void chol_sm_solve(const TF* L, int k, int ld, double* v) {
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    for (int j = 0; j < k; ++j) {
+      const TF yj = (TF)v[j] / L[j * ld + j];
+      for (int i = j + 1 + lane; i < k; i += 32) v[i] = (double)((TF)v[i] - L[i * ld + j] * yj);
+      __syncwarp();
+      if (lane == 0) v[j] = (double)yj;
+      __syncwarp();
+    }
+    for (int j = k - 1; j >= 0; --j) {
+      const TF zj = (TF)v[j] / L[j * ld + j];
+      for (int i = lane; i < j; i += 32) v[i] = (double)((TF)v[i] - L[j * ld + i] * zj);
+      __syncwarp();
+      if (lane == 0) v[j] = (double)zj;
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+}
+
 // Face solve for support sh.S[0..k) with signs sign(sig_src): fills sh.z
 // (dS, mu at [k]); returns false if the face matrix is not positive definite.
 template <typename TF>
+__device__ void face_apply(bool small, const TF* Ls, int k, int ld, double* v) {
+  if (small) chol_sm_solve<TF>(Ls, k, ld, v);
+  else chol_small_solve<TF>(Ls, k, ld, v);
+}
+
+// Ms: shared-memory face area (FaceSm<TF>::bytes) used when k <= FaceSm<TF>::n;
+// otherwise the factor lives in Lg (global, stride ldg) and the two vectors in wg.
+template <typename TF>
 __device__ bool face_solve(const double* __restrict__ H, int d, double R, const float* sig_src,
-                           TF* Ls, int ld, double* wv, QpShared& sh) {
+                           TF* Lg, int ldg, double* wg, TF* Ms, QpShared& sh) {
   const int k = sh.k;
+  const bool small = k <= FaceSm<TF>::n;
+  TF* Ls = small ? Ms : Lg;
+  const int ld = small ? FaceSm<TF>::ld : ldg;
+  double* wv = small ? reinterpret_cast<double*>(Ms + (size_t)FaceSm<TF>::n * FaceSm<TF>::ld) : wg;
+  double* res = small ? wv + FaceSm<TF>::n : wg + d;
   // gather M = H_SS
   for (int64_t e = threadIdx.x; e < (int64_t)k * k; e += blockDim.x) {
     const int a = (int)(e / k), b = (int)(e - (int64_t)a * k);
     Ls[(int64_t)a * ld + b] = (TF)H[(int64_t)sh.S[a] * d + sh.S[b]];
   }
   __syncthreads();
-  if (!chol_small<TF>(Ls, k, ld, sh)) return false;
+  if (small ? !chol_sm<TF>(Ls, k, ld) : !chol_small<TF>(Ls, k, ld, sh)) return false;
   // w = M^{-1} sigma
   for (int a = threadIdx.x; a < k; a += blockDim.x) wv[a] = sig_src[sh.S[a]] > 0.f ? 1.0 : -1.0;
   __syncthreads();
-  chol_small_solve<TF>(Ls, k, ld, wv);
+  face_apply<TF>(small, Ls, k, ld, wv);
   double sw = 0.0;
   for (int a = threadIdx.x; a < k; a += blockDim.x)
     sw += (sig_src[sh.S[a]] > 0.f ? 1.0 : -1.0) * wv[a];
@@ -207,8 +291,7 @@ __device__ bool face_solve(const double* __restrict__ H, int d, double R, const 
   __syncthreads();
   const int rounds = sizeof(TF) == 4 ? 4 : 2;
   for (int it = 0; it < rounds; ++it) {
-    // residual r = rhs - K z  (FP64), r_a in sh.ra? keep rhs: use wv2 = ra - (M z + mu sigma)
-    double* res = wv + d;  // scratch (wv holds 2d doubles)
+    // residual res = rhs - K z in FP64: ra - (H_SS z + mu sigma), beta - sigma^T z
     for (int a = wi; a < k; a += (int)(blockDim.x >> 5)) {
       const double* row = H + (int64_t)sh.S[a] * d;
       double s = 0.0;
@@ -222,7 +305,7 @@ __device__ bool face_solve(const double* __restrict__ H, int d, double R, const 
       sz += (sig_src[sh.S[a]] > 0.f ? 1.0 : -1.0) * sh.z[a];
     const double rb = beta - block_sum(sz, sh.redd);
     // correction: u = M^{-1} res; dmu = (sigma^T u - rb) / sigma^T w; dz = u - dmu w
-    chol_small_solve<TF>(Ls, k, ld, res);
+    face_apply<TF>(small, Ls, k, ld, res);
     double su = 0.0;
     for (int a = threadIdx.x; a < k; a += blockDim.x)
       su += (sig_src[sh.S[a]] > 0.f ? 1.0 : -1.0) * res[a];
@@ -297,9 +380,11 @@ __global__ void __launch_bounds__(kQpThreads, 1) k_l1_step(
     const double* __restrict__ H, const float* __restrict__ Hf, int d,
     const double* __restrict__ g, const double* __restrict__ du, double R, int max_iter,
     double tol, double* __restrict__ x, double* __restrict__ step_norm, int* __restrict__ support,
-    int* __restrict__ iters, double* __restrict__ wv, TF* __restrict__ Ls, int ld, int* status) {
-  extern __shared__ unsigned char qp_smem[];
+    int* __restrict__ iters, double* __restrict__ wv, TF* __restrict__ Ls, int ld,
+    float* __restrict__ evec, int* status) {
+  extern __shared__ __align__(16) unsigned char qp_smem[];
   QpShared& sh = *reinterpret_cast<QpShared*>(qp_smem);
+  TF* Ms = reinterpret_cast<TF*>(qp_smem + (sizeof(QpShared) + 15) / 16 * 16);
   for (int j = threadIdx.x; j < d; j += blockDim.x) {
     sh.xt[j] = x[j];
     sh.gd[j] = g[j];
@@ -336,7 +421,7 @@ __global__ void __launch_bounds__(kQpThreads, 1) k_l1_step(
       if (!zero_sign) {
         for (int j = threadIdx.x; j < d; j += blockDim.x) sh.fx[j] = sh.xt[j] > 0.0 ? 1.f : -1.f;
         __syncthreads();
-        if (face_solve<TF>(H, d, R, sh.fx, Ls, ld, wv, sh) &&
+        if (face_solve<TF>(H, d, R, sh.fx, Ls, ld, wv, Ms, sh) &&
             face_accept<TF>(Hf, d, sh.fx, tol, x, sh))
           done = true;
       }
@@ -345,11 +430,23 @@ __global__ void __launch_bounds__(kQpThreads, 1) k_l1_step(
   }
   // 3. FISTA + periodic face solves
   if (!done) {
-    // Lipschitz constant by power iteration on Hf
-    for (int j = threadIdx.x; j < d; j += blockDim.x) sh.fv[j] = 1.0f + 0.01f * (float)(j % 7);
+    // Lipschitz constant by power iteration on Hf.  It starts from the top
+    // eigenvector estimate left by the previous step when there is one: the
+    // Hessians of successive steps are sketches of the same A^T A and share
+    // their dominant direction up to the sketch's distortion.
+    float e2 = 0.f;
+    for (int j = threadIdx.x; j < d; j += blockDim.x) {
+      const float u = evec[j];
+      sh.fv[j] = u;
+      e2 += u * u;
+    }
+    const bool warm = block_sum(e2, sh.redf) > 0.f;
+    if (!warm)
+      for (int j = threadIdx.x; j < d; j += blockDim.x) sh.fv[j] = 1.0f + 0.01f * (float)(j % 7);
     __syncthreads();
     float lam = 1.f;
-    for (int it = 0; it < 40; ++it) {
+    const int npow = warm ? 12 : 40;
+    for (int it = 0; it < npow; ++it) {
       matvec_f(Hf, d, sh.fv, sh.fy);
       __syncthreads();
       float a = 0.f;
@@ -361,6 +458,7 @@ __global__ void __launch_bounds__(kQpThreads, 1) k_l1_step(
       for (int j = threadIdx.x; j < d; j += blockDim.x) sh.fv[j] = sh.fy[j] / fmaxf(nrm, 1e-30f);
       __syncthreads();
     }
+    for (int j = threadIdx.x; j < d; j += blockDim.x) evec[j] = sh.fv[j];
     const float Lip = 1.1f * fmaxf(lam, 1e-30f);
     const float Rf = (float)R;
     for (int j = threadIdx.x; j < d; j += blockDim.x) sh.fx[j] = sh.fxt[j];
@@ -401,7 +499,7 @@ __global__ void __launch_bounds__(kQpThreads, 1) k_l1_step(
           sh.k = k;
         }
         __syncthreads();
-        if (sh.k > 0 && face_solve<TF>(H, d, R, sh.fx, Ls, ld, wv, sh) &&
+        if (sh.k > 0 && face_solve<TF>(H, d, R, sh.fx, Ls, ld, wv, Ms, sh) &&
             face_accept<TF>(Hf, d, sh.fx, tol, x, sh))
           done = true;
         __syncthreads();
@@ -416,24 +514,35 @@ __global__ void __launch_bounds__(kQpThreads, 1) k_l1_step(
     }
   }
   __syncthreads();
-  // record the support of the new x and the step size
-  double mx = 0.0;
-  for (int j = threadIdx.x; j < d; j += blockDim.x) mx = fmax(mx, fabs(x[j] - sh.xt[j]));
+  // record the support of the new x (in index order; empty unless x lies on
+  // the sphere) and the step size; d <= blockDim.x, one entry per thread
+  const int j0 = threadIdx.x;
+  const double xj = j0 < d ? x[j0] : 0.0;
+  const double l1 = block_sum(fabs(xj), sh.redd);
+  double mx = j0 < d ? fabs(xj - sh.xt[j0]) : 0.0;
   for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-  if ((threadIdx.x & 31) == 0) sh.redd[threadIdx.x >> 5] = mx;
+  __shared__ int wcnt[33];
+  const bool nz = (l1 >= R * (1.0 - 1e-12)) && j0 < d && xj != 0.0;
+  const unsigned bal = __ballot_sync(0xffffffffu, nz);
+  if ((threadIdx.x & 31) == 0) {
+    sh.redd[threadIdx.x >> 5] = mx;
+    wcnt[threadIdx.x >> 5] = __popc(bal);
+  }
   __syncthreads();
   if (threadIdx.x == 0) {
     double m = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmax(m, sh.redd[w]);
+    int acc = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      m = fmax(m, sh.redd[w]);
+      const int c = wcnt[w];
+      wcnt[w] = acc;
+      acc += c;
+    }
     *step_norm = m;
-    int k = 0;
-    double l1 = 0.0;
-    for (int j = 0; j < d; ++j) l1 += fabs(x[j]);
-    if (l1 >= R * (1.0 - 1e-12))
-      for (int j = 0; j < d; ++j)
-        if (x[j] != 0.0) support[k++] = j;
-    support[d] = k;
+    support[d] = acc;
   }
+  __syncthreads();
+  if (nz) support[wcnt[threadIdx.x >> 5] + __popc(bal & lanemask_lt())] = j0;
 }
 
 __global__ void k_to_float(const double* __restrict__ a, int64_t n, float* __restrict__ b) {
@@ -455,7 +564,8 @@ cudaError_t launch_l1_step(const double* H, const void* Lbuf, const void* Dinv, 
   double* wv = w.dbuf + d;          // 2d doubles of face-solve scratch
   e = launch_chol_apply(Lbuf, Dinv, d, f32, g, du, st);
   if (e != cudaSuccess) return e;
-  const size_t smem = sizeof(QpShared);
+  const size_t base = (sizeof(QpShared) + 15) / 16 * 16;
+  const size_t smem = base + (f32 ? FaceSm<float>::bytes : FaceSm<double>::bytes);
   const int ld = chol_padded(d);
   const double tl = tol > 0 ? tol : 1e-12;
   if (f32) {
@@ -468,7 +578,7 @@ cudaError_t launch_l1_step(const double* H, const void* Lbuf, const void* Dinv, 
     }
     { k_l1_step<float><<<1, kQpThreads, smem, st>>>(H, w.Hf, d, g, du, R, max_iter, tl, x,
                                                   step_norm, w.support, w.iters, wv,
-                                                  (float*)w.Ls, ld, status); note_launches(1); }
+                                                  (float*)w.Ls, ld, w.evec, status); note_launches(1); }
   } else {
     static bool attr = false;
     if (!attr) {
@@ -479,7 +589,7 @@ cudaError_t launch_l1_step(const double* H, const void* Lbuf, const void* Dinv, 
     }
     { k_l1_step<double><<<1, kQpThreads, smem, st>>>(H, w.Hf, d, g, du, R, max_iter, tl, x,
                                                    step_norm, w.support, w.iters, wv,
-                                                   (double*)w.Ls, ld, status); note_launches(1); }
+                                                   (double*)w.Ls, ld, w.evec, status); note_launches(1); }
   }
   return cudaGetLastError();
 }

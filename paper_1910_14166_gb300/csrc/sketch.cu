@@ -315,27 +315,43 @@ __global__ void __launch_bounds__(256) k_sketch_csc(
   __syncwarp();
   const int64_t e0 = item_begin[it], e1 = item_end[it];
   const unsigned lt = lanemask_lt();
-  for (int64_t base = e0; base < e1; base += 32) {
-    const int64_t e = base + lane;
-    const bool valid = e < e1;
-    int key = -1 - lane;
-    Tacc v = Tacc(0);
-    if (valid) {
-      int row, neg;
-      sketch_draw(K, k, (uint64_t)(uint32_t)__ldg(rowidx + e), row, neg);
-      key = row - k * mb;
-      Tacc x = (Tacc)__ldg(val + e);
-      v = neg ? -x : x;
-    }
-    const unsigned peers = __match_any_sync(0xffffffffu, key);
-    const int rank = __popc(peers & lt);
-    // max multiplicity in this batch
-    int rounds = __popc(peers);
+  // four batches of 32 entries per pass: all eight loads are issued before
+  // the first hash, so each warp keeps several L2 round trips in flight.
+  // Batches are still accumulated in entry order, and colliding lanes of a
+  // batch in lane order.
+  constexpr int kU = 4;
+  for (int64_t base = e0; base < e1; base += 32 * kU) {
+    uint32_t rq[kU];
+    Tin xq[kU];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) rounds = max(rounds, __shfl_xor_sync(0xffffffffu, rounds, o));
-    for (int r = 0; r < rounds; ++r) {
-      if (valid && rank == r) acc[key] += v;
-      __syncwarp();
+    for (int q = 0; q < kU; ++q) {
+      const int64_t e = base + q * 32 + lane;
+      rq[q] = 0u;
+      xq[q] = Tin(0);
+      if (e < e1) {
+        rq[q] = (uint32_t)__ldg(rowidx + e);
+        xq[q] = __ldg(val + e);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < kU; ++q) {
+      const bool valid = base + q * 32 + lane < e1;
+      int key = -1 - lane;
+      Tacc v = Tacc(0);
+      if (valid) {
+        int row, neg;
+        sketch_draw(K, k, (uint64_t)rq[q], row, neg);
+        key = row - k * mb;
+        v = neg ? -(Tacc)xq[q] : (Tacc)xq[q];
+      }
+      const unsigned peers = __match_any_sync(0xffffffffu, key);
+      const int rank = __popc(peers & lt);
+      // max multiplicity in this batch
+      const int rounds = (int)__reduce_max_sync(0xffffffffu, (unsigned)__popc(peers));
+      for (int r = 0; r < rounds; ++r) {
+        if (valid && rank == r) acc[key] += v;
+        __syncwarp();
+      }
     }
   }
   // write block k's rows of column item_col[it]
