@@ -306,6 +306,9 @@ __global__ void __launch_bounds__(256) k_sketch_csc(
   const int nw = blockDim.x >> 5;
   const int mb = K.mb;
   Tacc* acc = reinterpret_cast<Tacc*>(smem_raw) + (size_t)wib * mb;
+  // one byte per bucket to detect colliding lanes (after the nw accumulators)
+  uint8_t* tag = reinterpret_cast<uint8_t*>(reinterpret_cast<Tacc*>(smem_raw) + (size_t)nw * mb) +
+                 (size_t)wib * mb;
   // work unit = (item, block k)
   const int64_t unit = (int64_t)blockIdx.x * nw + wib;
   if (unit >= (int64_t)nitems * K.s) return;
@@ -344,14 +347,28 @@ __global__ void __launch_bounds__(256) k_sketch_csc(
         key = row - k * mb;
         v = neg ? -(Tacc)xq[q] : (Tacc)xq[q];
       }
-      const unsigned peers = __match_any_sync(0xffffffffu, key);
-      const int rank = __popc(peers & lt);
-      // max multiplicity in this batch
-      const int rounds = (int)__reduce_max_sync(0xffffffffu, (unsigned)__popc(peers));
-      for (int r = 0; r < rounds; ++r) {
-        if (valid && rank == r) acc[key] += v;
-        __syncwarp();
+      // Collision test: every lane writes its index at its bucket; a lane
+      // that reads back another index shares its bucket.  Whichever lane's
+      // write survives, the test is exact, and without a collision the
+      // adds below touch distinct buckets.  (Matching keys across the warp
+      // occupies a narrow pipe, so it is kept for batches that collide,
+      // about one in three at 1250 buckets.)
+      if (valid) tag[key] = (uint8_t)lane;
+      __syncwarp();
+      const bool clash = valid && tag[key] != (uint8_t)lane;
+      if (!__any_sync(0xffffffffu, clash)) {
+        if (valid) acc[key] += v;
+      } else {
+        const unsigned peers = __match_any_sync(0xffffffffu, key);
+        const int rank = __popc(peers & lt);
+        // max multiplicity in this batch
+        const int rounds = (int)__reduce_max_sync(0xffffffffu, (unsigned)__popc(peers));
+        for (int r = 0; r < rounds; ++r) {
+          if (valid && rank == r) acc[key] += v;
+          __syncwarp();
+        }
       }
+      __syncwarp();
     }
   }
   // write block k's rows of column item_col[it]
@@ -385,7 +402,7 @@ __global__ void k_sketch_csc_merge(const int32_t* __restrict__ col_first_item,
 template <typename Tin, typename Tacc>
 static cudaError_t run_csc(const CscA& A, const SketchKeys& K, int64_t m, void* SA, void* partial,
                            cudaStream_t st) {
-  const size_t per_warp = (size_t)K.mb * sizeof(Tacc);
+  const size_t per_warp = (size_t)K.mb * (sizeof(Tacc) + 1);
   int nw = (int)std::min<size_t>(8, (200 * 1024) / per_warp);
   if (nw < 1) return cudaErrorInvalidValue;
   const size_t smem = per_warp * nw;
