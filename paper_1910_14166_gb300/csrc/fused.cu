@@ -23,24 +23,54 @@
 
 namespace {
 
+// Packed FP32 pairs (the sm_100 family's two-wide FP32 instructions, through
+// the __fadd2_rn / __fmul2_rn / __ffma2_rn intrinsics): each applies the
+// scalar round-to-nearest operation to both halves, so the results are
+// those of the scalar code, with half the instructions issued.
+typedef float2 f2t;
+__device__ __forceinline__ f2t f2_pack(float lo, float hi) { return make_float2(lo, hi); }
+__device__ __forceinline__ void f2_unpack(f2t v, float& lo, float& hi) {
+  lo = v.x;
+  hi = v.y;
+}
+__device__ __forceinline__ f2t f2_neg(f2t a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ f2t f2_add(f2t a, f2t b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ f2t f2_sub(f2t a, f2t b) { return __fadd2_rn(a, f2_neg(b)); }
+__device__ __forceinline__ f2t f2_mul(f2t a, f2t b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ f2t f2_fma(f2t a, f2t b, f2t c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ f2t f2_zero() { return make_float2(0.f, 0.f); }
+// (hi, lo) += a * (yh + yl) on both halves, given nyh = -yh: the same steps
+// as dd_fma_acc (exact product a*yh by FMA, TwoSum into hi, low parts and
+// a*yl into lo).  p = a*yh is carried as np = -p, which changes no rounding.
+__device__ __forceinline__ void dd2_fma_acc(f2t& hi, f2t& lo, f2t a, f2t yh, f2t nyh, f2t yl) {
+  const f2t np = f2_mul(a, nyh);
+  const f2t pe = f2_fma(a, yh, np);
+  const f2t s = f2_sub(hi, np);
+  const f2t bb = f2_sub(s, hi);
+  const f2t e = f2_sub(f2_sub(hi, f2_sub(s, bb)), f2_add(np, bb));
+  hi = s;
+  lo = f2_fma(a, yl, f2_add(lo, f2_add(e, pe)));
+}
+
 constexpr int kFuThreads = 256;
 constexpr int kFuWarps = kFuThreads / 32;
 
 template <int NV>
-__global__ void __launch_bounds__(kFuThreads) k_sketch_grad_fused(
+__global__ void __launch_bounds__(kFuThreads, 2) k_sketch_grad_fused(
     const float* __restrict__ A, int64_t lda, int d, const uint32_t* __restrict__ perm,
     const int32_t* __restrict__ seg_start, const int32_t* __restrict__ chunk_first, int m,
     int64_t P, int64_t CH, int nchunks, const float2* __restrict__ bs,
     const double* __restrict__ x, float* __restrict__ SA, float* __restrict__ partial,
     double* __restrict__ gcta) {
   constexpr int DP = NV * 128;
-  __shared__ float xh[DP], xl[DP];
+  __shared__ __align__(16) float xh[DP], xl[DP], nxh[DP];
   __shared__ float2 red[kFuWarps][DP];
   for (int c = threadIdx.x; c < DP; c += blockDim.x) {
     float h = 0.f, l = 0.f;
     if (c < d) split_double(x[c], h, l);
     xh[c] = h;
     xl[c] = l;
+    nxh[c] = -h;
   }
   __syncthreads();
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -52,11 +82,11 @@ __global__ void __launch_bounds__(kFuThreads) k_sketch_grad_fused(
     colq[q] = (q * 32 + lane) * 4;
     ok[q] = colq[q] < d;
   }
-  float gh[NV][4], gl[NV][4];
+  f2t gh[NV][2], gl[NV][2];  // pairs of columns (0,1) and (2,3) of each float4
 #pragma unroll
   for (int q = 0; q < NV; ++q)
 #pragma unroll
-    for (int t = 0; t < 4; ++t) gh[q][t] = gl[q][t] = 0.f;
+    for (int t = 0; t < 2; ++t) gh[q][t] = gl[q][t] = f2_zero();
 
   if (w < nchunks) {
     const int64_t c0 = (int64_t)w * CH;
@@ -66,11 +96,9 @@ __global__ void __launch_bounds__(kFuThreads) k_sketch_grad_fused(
       if (sb >= c1) break;
       const int64_t lo = max(sb, c0), hi = min(eb, c1);
       if (lo >= hi) continue;
-      float acc[NV][4];
+      f2t acc[NV][2];
 #pragma unroll
-      for (int q = 0; q < NV; ++q)
-#pragma unroll
-        for (int t = 0; t < 4; ++t) acc[q][t] = 0.f;
+      for (int q = 0; q < NV; ++q) acc[q][0] = acc[q][1] = f2_zero();
       for (int64_t base = lo; base < hi; base += 32) {
         const int cnt = (int)min((int64_t)32, hi - base);
         const uint32_t my = (lane < cnt) ? __ldg(perm + base + lane) : 0u;
@@ -85,51 +113,53 @@ __global__ void __launch_bounds__(kFuThreads) k_sketch_grad_fused(
           const uint32_t e1 = __shfl_sync(0xffffffffu, my, two ? j + 1 : j);
           const float* row0 = A + (int64_t)(e0 & 0x7fffffffu) * lda;
           const float* row1 = A + (int64_t)(e1 & 0x7fffffffu) * lda;
-          float a0[NV][4], a1[NV][4];
+          f2t a0[NV][2], a1[NV][2];
 #pragma unroll
           for (int q = 0; q < NV; ++q) {
+            a0[q][0] = a0[q][1] = a1[q][0] = a1[q][1] = f2_zero();
             if (ok[q]) {
               const float4 v0 = __ldcs(reinterpret_cast<const float4*>(row0 + colq[q]));
-              a0[q][0] = v0.x; a0[q][1] = v0.y; a0[q][2] = v0.z; a0[q][3] = v0.w;
+              a0[q][0] = f2_pack(v0.x, v0.y);
+              a0[q][1] = f2_pack(v0.z, v0.w);
               if (two) {
                 const float4 v1 = __ldcs(reinterpret_cast<const float4*>(row1 + colq[q]));
-                a1[q][0] = v1.x; a1[q][1] = v1.y; a1[q][2] = v1.z; a1[q][3] = v1.w;
-              } else {
-                a1[q][0] = a1[q][1] = a1[q][2] = a1[q][3] = 0.f;
+                a1[q][0] = f2_pack(v1.x, v1.y);
+                a1[q][1] = f2_pack(v1.z, v1.w);
               }
-            } else {
-#pragma unroll
-              for (int t = 0; t < 4; ++t) a0[q][t] = a1[q][t] = 0.f;
             }
           }
           // sketch: SA[h(i)] += sign(i) A_i, rows in order
           const float sg0 = (e0 >> 31) ? -1.f : 1.f, sg1 = (e1 >> 31) ? -1.f : 1.f;
+          const f2t s0 = f2_pack(sg0, sg0), s1 = f2_pack(sg1, sg1);
 #pragma unroll
           for (int q = 0; q < NV; ++q)
 #pragma unroll
-            for (int t = 0; t < 4; ++t) acc[q][t] = __fmaf_rn(sg0, a0[q][t], acc[q][t]);
+            for (int t = 0; t < 2; ++t) acc[q][t] = f2_fma(s0, a0[q][t], acc[q][t]);
           if (two) {
 #pragma unroll
             for (int q = 0; q < NV; ++q)
 #pragma unroll
-              for (int t = 0; t < 4; ++t) acc[q][t] = __fmaf_rn(sg1, a1[q][t], acc[q][t]);
+              for (int t = 0; t < 2; ++t) acc[q][t] = f2_fma(s1, a1[q][t], acc[q][t]);
           }
-          // residual partials: two float-pair chains per row
-          float p0h = 0.f, p0l = 0.f, q0h = 0.f, q0l = 0.f;
-          float p1h = 0.f, p1l = 0.f, q1h = 0.f, q1l = 0.f;
+          // residual partials: two float-pair chains per row, (p, q) packed:
+          // p takes columns 0 and 2 of each float4, q columns 1 and 3
+          f2t c0h = f2_zero(), c0l = f2_zero(), c1h = f2_zero(), c1l = f2_zero();
 #pragma unroll
           for (int q = 0; q < NV; ++q) {
-            const float4 vh = *reinterpret_cast<const float4*>(xh + colq[q]);
-            const float4 vl = *reinterpret_cast<const float4*>(xl + colq[q]);
-            dd_fma_acc(p0h, p0l, a0[q][0], vh.x, vl.x);
-            dd_fma_acc(q0h, q0l, a0[q][1], vh.y, vl.y);
-            dd_fma_acc(p0h, p0l, a0[q][2], vh.z, vl.z);
-            dd_fma_acc(q0h, q0l, a0[q][3], vh.w, vl.w);
-            dd_fma_acc(p1h, p1l, a1[q][0], vh.x, vl.x);
-            dd_fma_acc(q1h, q1l, a1[q][1], vh.y, vl.y);
-            dd_fma_acc(p1h, p1l, a1[q][2], vh.z, vl.z);
-            dd_fma_acc(q1h, q1l, a1[q][3], vh.w, vl.w);
+            const f2t* vh = reinterpret_cast<const f2t*>(xh + colq[q]);
+            const f2t* vn = reinterpret_cast<const f2t*>(nxh + colq[q]);
+            const f2t* vl = reinterpret_cast<const f2t*>(xl + colq[q]);
+#pragma unroll
+            for (int t = 0; t < 2; ++t) {
+              dd2_fma_acc(c0h, c0l, a0[q][t], vh[t], vn[t], vl[t]);
+              dd2_fma_acc(c1h, c1l, a1[q][t], vh[t], vn[t], vl[t]);
+            }
           }
+          float p0h, q0h, p0l, q0l, p1h, q1h, p1l, q1l;
+          f2_unpack(c0h, p0h, q0h);
+          f2_unpack(c0l, p0l, q0l);
+          f2_unpack(c1h, p1h, q1h);
+          f2_unpack(c1l, p1l, q1l);
           dd_add(p0h, p0l, q0h, q0l);
           dd_add(p1h, p1l, q1h, q1l);
           // level 16: keep my half's row, send the other row's partial
@@ -153,12 +183,14 @@ __global__ void __launch_bounds__(kFuThreads) k_sketch_grad_fused(
           dd_add(r1h, r1l, -d1h, -d1l);
           if (!two) r1h = r1l = 0.f;
           // gradient
+          const f2t r0h2 = f2_pack(r0h, r0h), r0n2 = f2_pack(-r0h, -r0h), r0l2 = f2_pack(r0l, r0l);
+          const f2t r1h2 = f2_pack(r1h, r1h), r1n2 = f2_pack(-r1h, -r1h), r1l2 = f2_pack(r1l, r1l);
 #pragma unroll
           for (int q = 0; q < NV; ++q)
 #pragma unroll
-            for (int t = 0; t < 4; ++t) {
-              dd_fma_acc(gh[q][t], gl[q][t], a0[q][t], r0h, r0l);
-              dd_fma_acc(gh[q][t], gl[q][t], a1[q][t], r1h, r1l);
+            for (int t = 0; t < 2; ++t) {
+              dd2_fma_acc(gh[q][t], gl[q][t], a0[q][t], r0h2, r0n2, r0l2);
+              dd2_fma_acc(gh[q][t], gl[q][t], a1[q][t], r1h2, r1n2, r1l2);
             }
         }
       }
@@ -172,15 +204,25 @@ __global__ void __launch_bounds__(kFuThreads) k_sketch_grad_fused(
       }
 #pragma unroll
       for (int q = 0; q < NV; ++q)
-        if (ok[q]) *reinterpret_cast<float4*>(dst + colq[q]) =
-            make_float4(acc[q][0], acc[q][1], acc[q][2], acc[q][3]);
+        if (ok[q]) {
+          float4 o;
+          f2_unpack(acc[q][0], o.x, o.y);
+          f2_unpack(acc[q][1], o.z, o.w);
+          *reinterpret_cast<float4*>(dst + colq[q]) = o;
+        }
     }
   }
   // CTA reduction of the gradient partials in a fixed warp order (float pairs)
 #pragma unroll
   for (int q = 0; q < NV; ++q)
 #pragma unroll
-    for (int t = 0; t < 4; ++t) red[wib][colq[q] + t] = make_float2(gh[q][t], gl[q][t]);
+    for (int t = 0; t < 2; ++t) {
+      float h0, h1, l0, l1;
+      f2_unpack(gh[q][t], h0, h1);
+      f2_unpack(gl[q][t], l0, l1);
+      red[wib][colq[q] + 2 * t] = make_float2(h0, l0);
+      red[wib][colq[q] + 2 * t + 1] = make_float2(h1, l1);
+    }
   __syncthreads();
   for (int c = threadIdx.x; c < d; c += blockDim.x) {
     float h = red[0][c].x, l = red[0][c].y;
