@@ -101,10 +101,16 @@ typedef struct {
  * two separate passes over A even where the single fused pass applies (dense
  * FP32 data, mixed precision, CountSketch, d <= 512); results agree to
  * rounding, the fused pass reads A once instead of twice. */
-enum { IHS_FLAG_NO_FUSE = 1, IHS_FLAG_SERIAL = 2 };
+enum { IHS_FLAG_NO_FUSE = 1, IHS_FLAG_SERIAL = 2, IHS_FLAG_CLUSTER = 4 };
 /* IHS_FLAG_SERIAL: issue the sketch chain (draw, sort, SA, Gram, factor) on
  * the caller's stream too, instead of overlapping it with the gradient and
- * step on an internal stream.  Same results; useful for timing stages. */
+ * step on an internal stream.  Same results; useful for timing stages.
+ * IHS_FLAG_CLUSTER: factor the sketched Hessian with the 16-CTA cluster
+ * kernel (the whole factor resident in the cluster's shared memory, hardware
+ * cluster barriers between steps) where it fits (FP32 up to d = 1024, FP64
+ * up to d = 768), instead of the cooperative grid kernel.  The two give
+ * identical factors; the grid kernel, spread over every SM, is the faster
+ * one at the sizes measured so far. */
 
 typedef struct {
   int iters;            /* iterations taken                                */

@@ -164,10 +164,12 @@ class IHS:
     (rowptr int32/int64, col int32, val float32/float64) with shape=(n, d).
     b: CUDA float64 vector.  The tensors are borrowed and must outlive the
     object.  kind: 'ols', 'l1' (param = radius) or 'ridge' (param = lambda).
-    precision: 'fp64' (plain), 'tf32' or 'bf16' (mixed)."""
+    precision: 'fp64' (plain), 'tf32' or 'bf16' (mixed).  fuse=False,
+    serial=True and cluster=True set IHS_FLAG_NO_FUSE, IHS_FLAG_SERIAL and
+    IHS_FLAG_CLUSTER."""
 
     def __init__(self, A, b, kind="ols", param=0.0, m=None, s=1, seed=0, precision="fp64",
-                 shape=None, qp_max_iter=0, qp_tol=0.0, fuse=True, serial=False):
+                 shape=None, qp_max_iter=0, qp_tol=0.0, fuse=True, serial=False, cluster=False):
         self._keep = [A, b]
         _need_cuda(b, "b")
         if b.dtype != torch.float64:
@@ -202,7 +204,7 @@ class IHS:
         self.precision = precision
         C = _Constraint(KIND[kind], float(param))
         O = _Options(self.m, self.s, seed & 0xFFFFFFFFFFFFFFFF, PREC[precision], int(qp_max_iter),
-                     float(qp_tol), (0 if fuse else 1) | (2 if serial else 0))
+                     float(qp_tol), (0 if fuse else 1) | (2 if serial else 0) | (4 if cluster else 0))
         h = ctypes.c_void_p()
         _check(_lib.ihs_create(ctypes.byref(h), ctypes.byref(M), _ptr(b), ctypes.byref(C),
                                ctypes.byref(O), _stream()), "ihs_create")

@@ -537,7 +537,7 @@ ihs_status sketch_chain(ihs_ctx* c, int64_t t, int bf) {
   CK(cudaEventRecord(c->ev_gram[t & 1], s2));
   stage_begin(c, IHS_ST_FACTOR, s2);
   CK(launch_cholesky(c->H[bf], (int)c->d, c->f32fac, c->L[bf], c->Dinv[bf], c->bar, c->status,
-                     s2));
+                     s2, (c->opt.flags & IHS_FLAG_CLUSTER) != 0));
   stage_end(c);
   CK(cudaEventRecord(c->ev_fac[bf], s2));
   return IHS_OK;
@@ -634,7 +634,7 @@ ihs_status fused_gram_factor(ihs_ctx* c, int64_t u, int bf, bool after_pass) {
   CK(cudaEventRecord(c->ev_gram[u & 1], s2));
   stage_begin(c, IHS_ST_FACTOR, s2);
   CK(launch_cholesky(c->H[bf], (int)c->d, c->f32fac, c->L[bf], c->Dinv[bf], c->bar, c->status,
-                     s2));
+                     s2, (c->opt.flags & IHS_FLAG_CLUSTER) != 0));
   stage_end(c);
   CK(cudaEventRecord(c->ev_fac[bf], s2));
   return IHS_OK;

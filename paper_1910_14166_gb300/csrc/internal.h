@@ -125,8 +125,11 @@ int chol_padded(int d);  // d rounded up to the 32-tile
 // Lbuf: dp x dp (lower: L, upper: L^T tiles); Dinv: dp/32 tiles of 32 x 32;
 // bar: 4 unsigned of barrier state (zeroed by the launcher).
 size_t chol_dinv_bytes(int d, int f32);
+// Factor with the 16-CTA cluster kernel when allow_cluster and the matrix
+// fits in the cluster's shared memory, else with the cooperative grid kernel
+// (the two give identical factors).
 cudaError_t launch_cholesky(const double* H, int d, int f32, void* Lbuf, void* Dinv, unsigned* bar,
-                            int* status, cudaStream_t st);
+                            int* status, cudaStream_t st, int allow_cluster);
 // x += (L L^T)^{-1} g ; step_norm (device double) gets max |delta|.
 cudaError_t launch_chol_step(const void* Lbuf, const void* Dinv, int d, int f32, const double* g,
                              double* x, double* step_norm, cudaStream_t st);

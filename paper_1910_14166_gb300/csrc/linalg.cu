@@ -29,6 +29,8 @@
 // Backward: the same on the stored transpose, z_k = D_k^T t_k.
 #include <cuda_runtime.h>
 
+#include <cooperative_groups.h>
+
 #include <algorithm>
 
 #include "internal.h"
@@ -247,10 +249,192 @@ __global__ void __launch_bounds__(256) k_chol_coop(T* __restrict__ L, T* __restr
   }
 }
 
+// ----------------------------------------------------------------------------
+// Cluster variant: the same blocked factor and look-ahead schedule, with the
+// whole matrix resident in the shared memory of one 16-CTA thread-block
+// cluster, so a step ends with a hardware cluster barrier instead of a
+// grid barrier through global memory.  Lower tile (i, j), j <= i, number
+// q = i(i+1)/2 + j, lives in slot q / 16 of CTA q % 16; tiles of other CTAs
+// are copied into local scratch through distributed shared memory before
+// use.  Each step's items are the same as k_chol_coop's (panel(k) items
+// first applying update k-1 to their own tiles and refactoring the diagonal
+// tile, update(k-1) items for the remaining trailing tiles), each done by
+// the CTA that owns the tile it writes, in the same arithmetic order, so L
+// and D are identical to k_chol_coop's.  The input is read straight from H
+// (identity padding), and the results go to the same L / Dinv layout.
+// ----------------------------------------------------------------------------
+constexpr int kClusterCtas = 16;
+constexpr int kTileElems = 32 * 33;
+
+template <typename T>
+size_t chol_cluster_smem(int Tt) {
+  const int ntiles = Tt * (Tt + 1) / 2;
+  const int slots = (ntiles + kClusterCtas - 1) / kClusterCtas;
+  return (size_t)(slots + 4) * kTileElems * sizeof(T);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_chol_cluster(const double* __restrict__ H, int d, int dp,
+                                                      int Tt, T* __restrict__ L,
+                                                      T* __restrict__ Dinv, int* status) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cl = cg::this_cluster();
+  extern __shared__ __align__(16) unsigned char cl_smem[];
+  T* base = reinterpret_cast<T*>(cl_smem);
+  const int ntiles = Tt * (Tt + 1) / 2;
+  const int slots = (ntiles + kClusterCtas - 1) / kClusterCtas;
+  typedef T Tile[33];
+  Tile* Dk = reinterpret_cast<Tile*>(base + (size_t)(slots + 0) * kTileElems);
+  Tile* Ta = reinterpret_cast<Tile*>(base + (size_t)(slots + 1) * kTileElems);
+  Tile* Tb = reinterpret_cast<Tile*>(base + (size_t)(slots + 2) * kTileElems);
+  Tile* Tc = reinterpret_cast<Tile*>(base + (size_t)(slots + 3) * kTileElems);
+  __shared__ int spd;
+  const int tid = threadIdx.x;
+  const int me = (int)cl.block_rank();
+  auto tnum = [](int i, int j) { return i * (i + 1) / 2 + j; };
+  auto local_tile = [&](int q) { return reinterpret_cast<Tile*>(base + (size_t)(q / kClusterCtas) * kTileElems); };
+  // copy tile q (any CTA) into local scratch dst
+  auto fetch = [&](Tile* dst, int q) {
+    const T* src = cl.map_shared_rank(base + (size_t)(q / kClusterCtas) * kTileElems, q % kClusterCtas);
+    for (int e = tid; e < 1024; e += blockDim.x) {
+      const int r = e >> 5, c = e & 31;
+      dst[r][c] = src[r * 33 + c];
+    }
+  };
+  // load the owned tiles of H (identity beyond d)
+  for (int q = me; q < ntiles; q += kClusterCtas) {
+    int i = (int)((sqrtf(8.0f * q + 1.0f) - 1.0f) * 0.5f);
+    while (tnum(i + 1, 0) <= q) ++i;
+    while (tnum(i, 0) > q) --i;
+    const int j = q - tnum(i, 0);
+    Tile* t = local_tile(q);
+    for (int e = tid; e < 1024; e += blockDim.x) {
+      const int r = e >> 5, c = e & 31;
+      const int gi = i * 32 + r, gj = j * 32 + c;
+      T v;
+      if (gi < d && gj < d) v = (T)H[(int64_t)gi * d + gj];
+      else v = (gi == gj) ? T(1) : T(0);
+      t[r][c] = v;
+    }
+  }
+  cl.sync();
+  for (int k = 0; k < Tt; ++k) {
+    const int k0 = k * 32;
+    // panel(k): tile rows k..Tt-1 of column k
+    for (int i = k; i < Tt; ++i) {
+      const int qi = tnum(i, k);
+      if (qi % kClusterCtas != me) continue;
+      const int c = i - k, i0 = i * 32;
+      fetch(Dk, tnum(k, k));
+      if (k >= 1) fetch(Tb, tnum(k, k - 1));
+      if (c > 0 && k >= 1) fetch(Tc, tnum(i, k - 1));
+      __syncthreads();
+      Tile* own = local_tile(qi);
+      if (k >= 1) {
+        tile_sub_pqt(Dk, Tb, Tb);
+        if (c > 0) tile_sub_pqt(own, Tc, Tb);
+      }
+      Tile* pan = own;
+      if (c == 0) {
+        for (int e = tid; e < 1024; e += blockDim.x) Ta[e >> 5][e & 31] = ((e >> 5) == (e & 31)) ? T(1) : T(0);
+        __syncthreads();
+        pan = Ta;
+      }
+      panel_sweep<T>(Dk, pan, true, &spd);
+      if (c == 0) {
+        if (!spd && tid == 0) set_status(status, DEV_NOT_SPD);
+        for (int e = tid; e < 1024; e += blockDim.x) {
+          const int r = e >> 5, q = e & 31;
+          Dinv[(int64_t)k * 1024 + e] = (q <= r) ? Ta[q][r] : T(0);  // (L_kk^{-T})^T
+        }
+      } else {
+        for (int e = tid; e < 1024; e += blockDim.x) {
+          const int a = e >> 5, b = e & 31;
+          L[(int64_t)(i0 + a) * dp + k0 + b] = own[a][b];
+          L[(int64_t)(k0 + a) * dp + i0 + b] = own[b][a];  // transpose into tile (k, i)
+        }
+      }
+      __syncthreads();
+    }
+    // update(k-1) of tile (i, j), k < j <= i
+    if (k >= 1) {
+      for (int i = k + 1; i < Tt; ++i)
+        for (int j = k + 1; j <= i; ++j) {
+          const int q = tnum(i, j);
+          if (q % kClusterCtas != me) continue;
+          fetch(Ta, tnum(i, k - 1));
+          fetch(Tb, tnum(j, k - 1));
+          __syncthreads();
+          tile_sub_pqt(local_tile(q), Ta, Tb);
+        }
+    }
+    cl.sync();
+  }
+}
+
+template <typename T>
+static cudaError_t chol_cluster_launch(const double* H, int d, T* L, T* Dinv, int* status,
+                                       cudaStream_t st, bool* used) {
+  *used = false;
+  const int dp = chol_padded(d), Tt = dp / 32;
+  const size_t smem = chol_cluster_smem<T>(Tt);
+  if (smem > 200 * 1024) return cudaSuccess;
+  static int ok = -1;  // per process: can a 16-CTA cluster with this much smem run?
+  static size_t ok_smem = 0;
+  if (ok < 0 || ok_smem < smem) {
+    cudaError_t e = cudaFuncSetAttribute(k_chol_cluster<T>,
+                                         cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_chol_cluster<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               200 * 1024);
+    int nclusters = 0;
+    if (e == cudaSuccess) {
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(kClusterCtas);
+      cfg.blockDim = dim3(256);
+      cfg.dynamicSmemBytes = 200 * 1024;
+      cudaLaunchAttribute at[1];
+      at[0].id = cudaLaunchAttributeClusterDimension;
+      at[0].val.clusterDim.x = kClusterCtas;
+      at[0].val.clusterDim.y = 1;
+      at[0].val.clusterDim.z = 1;
+      cfg.attrs = at;
+      cfg.numAttrs = 1;
+      e = cudaOccupancyMaxActiveClusters(&nclusters, k_chol_cluster<T>, &cfg);
+    }
+    if (e != cudaSuccess) cudaGetLastError();
+    ok = (e == cudaSuccess && nclusters >= 1) ? 1 : 0;
+    ok_smem = 200 * 1024;
+  }
+  if (!ok) return cudaSuccess;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(kClusterCtas);
+  cfg.blockDim = dim3(256);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = kClusterCtas;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  cudaError_t e = cudaLaunchKernelEx(&cfg, k_chol_cluster<T>, H, d, dp, Tt, L, Dinv, status);
+  note_launches(1);
+  if (e != cudaSuccess) return e;
+  *used = true;
+  return cudaGetLastError();
+}
+
 template <typename T>
 static cudaError_t chol_impl(const double* H, int d, T* L, T* Dinv, unsigned* bar, int* status,
-                             cudaStream_t st) {
+                             cudaStream_t st, bool allow_cluster) {
   int dp = chol_padded(d), Tt = dp / 32;
+  if (allow_cluster) {
+    bool used = false;
+    cudaError_t e = chol_cluster_launch<T>(H, d, L, Dinv, status, st, &used);
+    if (e != cudaSuccess || used) return e;
+  }
   const int blocks = (int)std::min<int64_t>(((int64_t)dp * dp + 255) / 256, 2048);
   { k_chol_init<T><<<blocks, 256, 0, st>>>(H, d, dp, L); note_launches(1); }
   cudaError_t e = cudaMemsetAsync(bar, 0, 4 * sizeof(unsigned), st);
@@ -274,9 +458,10 @@ static cudaError_t chol_impl(const double* H, int d, T* L, T* Dinv, unsigned* ba
 }
 
 cudaError_t launch_cholesky(const double* H, int d, int f32, void* Lbuf, void* Dinv, unsigned* bar,
-                            int* status, cudaStream_t st) {
-  return f32 ? chol_impl<float>(H, d, (float*)Lbuf, (float*)Dinv, bar, status, st)
-             : chol_impl<double>(H, d, (double*)Lbuf, (double*)Dinv, bar, status, st);
+                            int* status, cudaStream_t st, int allow_cluster) {
+  return f32 ? chol_impl<float>(H, d, (float*)Lbuf, (float*)Dinv, bar, status, st, allow_cluster != 0)
+             : chol_impl<double>(H, d, (double*)Lbuf, (double*)Dinv, bar, status, st,
+                                 allow_cluster != 0);
 }
 
 // ----------------------------------------------------------------------------

@@ -375,6 +375,42 @@ __device__ bool face_accept(const float* __restrict__ Hf, int d, const float* si
   return true;
 }
 
+// Support of v (indices in increasing order) into sh.S / sh.k, and an
+// order-free signature of (support, signs) returned to every thread.
+// d <= blockDim.x: one entry per thread.
+__device__ unsigned long long support_of(const float* v, int d, QpShared& sh) {
+  __shared__ int wc[33];
+  __shared__ unsigned long long ws[32];
+  const int j = threadIdx.x, lane = j & 31, w = j >> 5;
+  const bool nz = j < d && v[j] != 0.f;
+  const unsigned bal = __ballot_sync(0xffffffffu, nz);
+  unsigned long long h =
+      nz ? sm64_finalise(2ull * (unsigned long long)j + (v[j] < 0.f ? 2ull : 1ull)) : 0ull;
+  for (int o = 16; o > 0; o >>= 1) h += __shfl_xor_sync(0xffffffffu, h, o);
+  if (lane == 0) {
+    wc[w] = __popc(bal);
+    ws[w] = h;
+  }
+  __syncthreads();
+  if (j == 0) {
+    int acc = 0;
+    unsigned long long sig = 0ull;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) {
+      const int c = wc[q];
+      wc[q] = acc;
+      acc += c;
+      sig += ws[q];
+    }
+    sh.k = acc;
+    ws[0] = sig;
+  }
+  __syncthreads();
+  if (nz) sh.S[wc[w] + __popc(bal & lanemask_lt())] = j;
+  const unsigned long long sig = ws[0];
+  __syncthreads();
+  return sig;
+}
+
 template <typename TF>
 __global__ void __launch_bounds__(kQpThreads, 1) k_l1_step(
     const double* __restrict__ H, const float* __restrict__ Hf, int d,
@@ -467,6 +503,7 @@ __global__ void __launch_bounds__(kQpThreads, 1) k_l1_step(
     for (int j = threadIdx.x; j < d; j += blockDim.x) sh.fy[j] = sh.fx[j];
     __syncthreads();
     float tk = 1.f;
+    unsigned long long prev_sig = 0ull, failed_sig = 0ull;
     const int cap = max_iter > 0 ? max_iter : 20000;
     int it = 0;
     for (; it < cap && !done; ++it) {
@@ -491,17 +528,20 @@ __global__ void __launch_bounds__(kQpThreads, 1) k_l1_step(
       tk = tn;
       __syncthreads();
       if ((it + 1) % kFaceEvery == 0) {
-        // support of the FISTA iterate
-        if (threadIdx.x == 0) {
-          int k = 0;
-          for (int j = 0; j < d; ++j)
-            if (sh.fx[j] != 0.f) sh.S[k++] = j;
-          sh.k = k;
+        // Face of the FISTA iterate.  A (support, signs) pair whose face
+        // already failed is not tried again (the face point depends on
+        // nothing else), and a support too large for the shared-memory
+        // factor is tried only once it has held over a whole interval.
+        const unsigned long long sig = support_of(sh.fx, d, sh);
+        const bool stable = sig == prev_sig;
+        prev_sig = sig;
+        if (sh.k > 0 && sig != failed_sig && (sh.k <= FaceSm<TF>::n || stable)) {
+          if (face_solve<TF>(H, d, R, sh.fx, Ls, ld, wv, Ms, sh) &&
+              face_accept<TF>(Hf, d, sh.fx, tol, x, sh))
+            done = true;
+          else
+            failed_sig = sig;
         }
-        __syncthreads();
-        if (sh.k > 0 && face_solve<TF>(H, d, R, sh.fx, Ls, ld, wv, Ms, sh) &&
-            face_accept<TF>(Hf, d, sh.fx, tol, x, sh))
-          done = true;
         __syncthreads();
       }
     }

@@ -312,3 +312,36 @@ def test_fused_pass_agrees_with_two_passes(cuda_lib):
     x1, _ = fu.solve(x1, t0=3, iters=30)
     x2, _ = tw.solve(x2, t0=3, iters=30)
     assert O.err_A(x1.cpu().numpy(), xo, G) < 1e-10 and O.err_A(x2.cpu().numpy(), xo, G) < 1e-10
+
+
+@pytest.mark.parametrize("kind", ["dense_fp64", "dense_tf32", "csr_fp64", "dense_fp64_d700", "ridge_bf16"])
+def test_cluster_factor_matches_grid_factor(cuda_lib, kind):
+    """The 16-CTA cluster factor and the cooperative grid factor carry out the
+    same tile operations in the same order: the iterates they produce are
+    identical bit for bit (FP64 and FP32 factors, d from 50 to 700)."""
+    if kind == "csr_fp64":
+        w = synth.make("lasso_csr_fp64", n=60000, d=200, m=2000)
+        args = ((dev(w["rowptr"]), dev(w["col"]), dev(w["val"])), dev(w["b"]))
+        kw = dict(kind="l1", param=w["param"], m=2000, s=4, precision="fp64", shape=(w["n"], w["d"]))
+    elif kind == "dense_fp64":
+        w = synth.make("ols_dense_fp64")
+        args = (dev(w["A"]), dev(w["b"]))
+        kw = dict(m=500, precision="fp64")
+    elif kind == "dense_fp64_d700":
+        w = synth.make("ols_dense_fp64", n=9000, d=700, m=7000)
+        args = (dev(w["A"]), dev(w["b"]))
+        kw = dict(m=7000, precision="fp64")
+    elif kind == "ridge_bf16":
+        w = synth.make("ridge_dense", n=40000, d=256, m=2560)
+        args = (dev(w["A"]), dev(w["b"]))
+        kw = dict(kind="ridge", param=w["param"], m=2560, precision="bf16")
+    else:
+        w = synth.make("ols_dense_ar1", n=60000, d=500, m=5000)
+        args = (dev(w["A"]), dev(w["b"]))
+        kw = dict(m=5000, precision="tf32")
+    a = cuda_lib.IHS(*args, seed=3, cluster=True, **kw)
+    b = cuda_lib.IHS(*args, seed=3, cluster=False, **kw)
+    xa, ra = a.solve(iters=4)
+    xb, rb = b.solve(iters=4)
+    assert ra.status == 0 and rb.status == 0
+    assert torch.equal(xa, xb)
