@@ -149,11 +149,8 @@ ihs_status ihs_step(ihs_ctx* ctx, double* x);
 /* ihs_solve -- iterations t = t0 .. t0+iters-1 of ihs_sketch + ihs_step from
  * the x given (DEVICE, d doubles; in: x^{t0}, out: x^{t0+iters}).  The run
  * is a pure function of (A, b, C, options, x, t0), so stopping after k
- * iterations and resuming with t0 + k reproduces it exactly.  In the fused
- * form (see IHS_FLAG_NO_FUSE) the pass of iteration t reads A once for the
- * gradient at x^t and the SA of iteration t+1, so a call forms one SA-only
- * pass first unless the previous call (or ihs_sketch) already formed SA(t0).
- * rep: HOST, nullable.  Synchronises and returns the device status. */
+ * iterations and resuming with t0 + k reproduces it exactly.  rep: HOST,
+ * nullable.  Synchronises and returns the device status. */
 ihs_status ihs_solve(ihs_ctx* ctx, double* x, int64_t t0, int iters,
                      ihs_report* rep);
 
@@ -187,12 +184,10 @@ ihs_status ihs_adjoint(ihs_ctx* ctx, const double* x, const double* dLdx,
  * stage of every iteration while enabled) and a count of the library's
  * kernel launches.  Stages, in order: IHS_ST_SORT (sketch draw and bucket
  * sort), IHS_ST_SKETCH (the SA kernel; in the fused form the one pass that
- * forms SA of the next iteration and the gradient), IHS_ST_SKETCH_FIX
- * (straddling and empty buckets), IHS_ST_GRAM, IHS_ST_FACTOR, IHS_ST_GRAD,
- * IHS_ST_STEP, IHS_ST_FIRST_SKETCH (the fused form's SA-only pass for the
- * first iteration of an ihs_solve call, when no earlier pass formed it). */
+ * forms SA and the gradient), IHS_ST_SKETCH_FIX (straddling and empty
+ * buckets), IHS_ST_GRAM, IHS_ST_FACTOR, IHS_ST_GRAD, IHS_ST_STEP. */
 enum { IHS_ST_SORT = 0, IHS_ST_SKETCH, IHS_ST_SKETCH_FIX, IHS_ST_GRAM, IHS_ST_FACTOR,
-       IHS_ST_GRAD, IHS_ST_STEP, IHS_ST_FIRST_SKETCH, IHS_NSTAGES };
+       IHS_ST_GRAD, IHS_ST_STEP, IHS_NSTAGES };
 
 /* ihs_profile -- enable (1) or disable (0) stage timing; enabling clears
  * the totals and the launch count. */

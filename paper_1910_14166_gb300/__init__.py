@@ -93,7 +93,7 @@ def _load():
 
 _lib = _load()
 LIB_PATH = _build.LIB
-STAGES = ["sort", "sketch", "sketch_fix", "gram", "factor", "grad", "step", "first_sketch"]
+STAGES = ["sort", "sketch", "sketch_fix", "gram", "factor", "grad", "step"]
 EXPORTS = ["ihs_create", "ihs_sketch", "ihs_gradient", "ihs_step", "ihs_solve", "ihs_sync",
            "ihs_get_sketch", "ihs_adjoint", "ihs_destroy", "ihs_status_str", "ihs_hash",
            "ihs_sketch_adjoint", "ihs_profile", "ihs_profile_read", "ihs_gradient_noalloc"]

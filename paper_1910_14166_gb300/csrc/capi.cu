@@ -69,16 +69,8 @@ struct ihs_ctx {
   void* rbuf = nullptr;
   double* item_part = nullptr;
   // sketch / Hessian (H, L, Dinv double-buffered: the next iteration's sketch
-  // chain runs while the current step still reads its factor).  The SA of
-  // sketch counter u lives in SAb[u & 1]; the two alias one buffer except in
-  // the fused pipeline, where the pass of iteration t writes SA(t+1) while
-  // the Gram of t may still read SA(t).
-  void* SAb[2] = {};
-  int64_t sa_t[2] = {-1, -1};      // counter whose SA each buffer holds (-1: none)
-  int64_t cur_t = -1;              // counter of the sketch behind H[cur]
-  cudaEvent_t ev_sa = nullptr;     // fused pass done: SA of the next counter written
-  cudaEvent_t ev_gram[2] = {};     // Gram done reading SAb[b]
-  cudaEvent_t ev_first = nullptr;  // first sketch of a fused solve done
+  // chain runs while the current step still reads its factor)
+  void* SA = nullptr;
   GramPlan gp{};
   void* gop = nullptr;
   float* gpart_f = nullptr;
@@ -352,10 +344,7 @@ void ihs_destroy(ihs_ctx* c) {
     if (c->ev_use[k]) cudaEventDestroy(c->ev_use[k]);
   }
   if (c->ev_join) cudaEventDestroy(c->ev_join);
-  if (c->ev_sa) cudaEventDestroy(c->ev_sa);
-  if (c->ev_first) cudaEventDestroy(c->ev_first);
   for (int k = 0; k < 2; ++k) {
-    if (c->ev_gram[k]) cudaEventDestroy(c->ev_gram[k]);
     if (c->ev_sort[k]) cudaEventDestroy(c->ev_sort[k]);
     if (c->ev_read[k]) cudaEventDestroy(c->ev_read[k]);
   }
@@ -420,19 +409,14 @@ ihs_status ihs_create(ihs_ctx** out, const ihs_matrix* A, const double* b,
         cudaEventCreateWithFlags(&c->ev_use[k], cudaEventDisableTiming) != cudaSuccess)
       return fail(IHS_ERR_CUDA);
   }
-  if (cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&c->ev_sa, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&c->ev_first, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&c->ev_gram[0], cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&c->ev_gram[1], cudaEventDisableTiming) != cudaSuccess)
+  if (cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess)
     return fail(IHS_ERR_CUDA);
   for (int k = 0; k < 2; ++k) {
     if (cudaEventCreateWithFlags(&c->ev_sort[k], cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->ev_read[k], cudaEventDisableTiming) != cudaSuccess)
       return fail(IHS_ERR_CUDA);
   }
-  AL2(c->SAb[0], (size_t)c->m * c->d * acc_el);
-  c->SAb[1] = c->SAb[0];
+  AL2(c->SA, (size_t)c->m * c->d * acc_el);
   const int dp = chol_padded((int)c->d);
   for (int k = 0; k < 2; ++k) {
     AL2(c->H[k], (size_t)c->d * c->d * sizeof(double));
@@ -473,7 +457,6 @@ ihs_status ihs_create(ihs_ctx** out, const ihs_matrix* A, const double* b,
       AL2(c->seg2, (c->m + 1) * sizeof(int32_t));
       AL2(c->chunk_first2, c->sp.nchunks * sizeof(int32_t));
       AL2(c->gcta, (size_t)fused_ctas(c->sp) * c->d * sizeof(double));
-      AL2(c->SAb[1], (size_t)c->m * c->d * acc_el);
     }
   } else {
     if ((size_t)(c->m / c->s) * acc_el > 200 * 1024) return fail(IHS_ERR_UNSUPPORTED);
@@ -511,30 +494,24 @@ ihs_status sketch_chain(ihs_ctx* c, int64_t t, int bf) {
   cudaStream_t s2 = (c->opt.flags & IHS_FLAG_SERIAL) ? c->st : c->st2;
   CK(cudaStreamWaitEvent(s2, c->ev_use[bf], 0));
   const SketchKeys K = make_keys(c->opt.seed, t, c->s, c->m);
-  void* SA = c->SAb[t & 1];
-  // the buffer may still be read by the Gram of t - 2 (same stream) or be
-  // written by a fused pass (caller's stream, joined before every chain)
-  c->sa_t[t & 1] = t;
-  if (c->SAb[0] == c->SAb[1]) c->sa_t[(t & 1) ^ 1] = -1;
   if (c->dense) {
     stage_begin(c, IHS_ST_SORT, s2);
     CK(launch_sort_sketch(c->sp, K, c->n, c->sort_ws, c->perm, c->seg, c->chunk_first, s2));
     stage_end(c);
     stage_begin(c, IHS_ST_SKETCH, s2);
-    CK(launch_sketch_dense(c->DA, c->sp, c->perm, c->seg, c->chunk_first, c->acc64, SA,
+    CK(launch_sketch_dense(c->DA, c->sp, c->perm, c->seg, c->chunk_first, c->acc64, c->SA,
                            c->sk_partial, c->counter, c->sms, s2, c->prof ? c : nullptr));
     stage_end(c);
   } else {
     stage_begin(c, IHS_ST_SKETCH, s2);
-    CK(launch_sketch_csc(c->CA, K, c->m, c->acc64, SA, c->csc_partial, s2));
+    CK(launch_sketch_csc(c->CA, K, c->m, c->acc64, c->SA, c->csc_partial, s2));
     stage_end(c);
   }
   const double shift = (c->C.kind == IHS_RIDGE) ? c->C.param : 0.0;
   stage_begin(c, IHS_ST_GRAM, s2);
-  CK(launch_gram(c->gp, SA, c->gop, c->gpart_f, c->gpart_d, 1.0 / c->s, shift, c->H[bf],
+  CK(launch_gram(c->gp, c->SA, c->gop, c->gpart_f, c->gpart_d, 1.0 / c->s, shift, c->H[bf],
                  c->status, s2));
   stage_end(c);
-  CK(cudaEventRecord(c->ev_gram[t & 1], s2));
   stage_begin(c, IHS_ST_FACTOR, s2);
   CK(launch_cholesky(c->H[bf], (int)c->d, c->f32fac, c->L[bf], c->Dinv[bf], c->bar, c->status,
                      s2, (c->opt.flags & IHS_FLAG_CLUSTER) != 0));
@@ -582,19 +559,12 @@ ihs_status step_with(ihs_ctx* c, double* x, int bf) {
   return IHS_OK;
 }
 
-// Fused pipeline.  The pass of iteration t reads A once and forms both the
-// gradient g(x^t) for the step of t and SA(t+1) for the next iteration, so
-// the Gram and factor of t+1 (internal stream) overlap the step of t and the
-// pass of t+1 (caller's stream).  Sort buffer u & 1 holds the sorted pairs of
-// counter u; SA(u) lives in SAb[u & 1].
-
-// Draw and sort the pairs of counter u on the internal stream, after the
-// pass that last read that sort buffer.
-ihs_status fused_sort(ihs_ctx* c, int64_t u) {
+// Fused pipeline, sort half: draw and sort the pairs of counter t into sort
+// buffer pb on the internal stream, after the fused pass that last read it.
+ihs_status fused_sort(ihs_ctx* c, int64_t t, int pb) {
   cudaStream_t s2 = (c->opt.flags & IHS_FLAG_SERIAL) ? c->st : c->st2;
-  const int pb = (int)(u & 1);
   CK(cudaStreamWaitEvent(s2, c->ev_read[pb], 0));
-  const SketchKeys K = make_keys(c->opt.seed, u, c->s, c->m);
+  const SketchKeys K = make_keys(c->opt.seed, t, c->s, c->m);
   stage_begin(c, IHS_ST_SORT, s2);
   CK(launch_sort_sketch(c->sp, K, c->n, c->sort_ws, pb ? c->perm2 : c->perm, pb ? c->seg2 : c->seg,
                         pb ? c->chunk_first2 : c->chunk_first, s2));
@@ -603,62 +573,30 @@ ihs_status fused_sort(ihs_ctx* c, int64_t u) {
   return IHS_OK;
 }
 
-// SA(u) alone (no gradient), to start a fused solve whose first sketch no
-// earlier pass has formed; internal stream, after fused_sort(u).
-ihs_status fused_first_sketch(ihs_ctx* c, int64_t u) {
-  cudaStream_t s2 = (c->opt.flags & IHS_FLAG_SERIAL) ? c->st : c->st2;
-  const int pb = (int)(u & 1);
-  stage_begin(c, IHS_ST_FIRST_SKETCH, s2);
-  CK(launch_sketch_dense(c->DA, c->sp, pb ? c->perm2 : c->perm, pb ? c->seg2 : c->seg,
-                         pb ? c->chunk_first2 : c->chunk_first, c->acc64, c->SAb[pb],
-                         c->sk_partial, c->counter, c->sms, s2, c->prof ? c : nullptr));
-  stage_end(c);
-  CK(cudaEventRecord(c->ev_read[pb], s2));
-  CK(cudaEventRecord(c->ev_first, s2));
-  c->sa_t[pb] = u;
-  return IHS_OK;
-}
-
-// Gram and factor of counter u into H/L/Dinv buffer bf on the internal
-// stream, once SA(u) is written (ev_sa, when a pass formed it) and the step
-// that last read buffer bf is done.
-ihs_status fused_gram_factor(ihs_ctx* c, int64_t u, int bf, bool after_pass) {
-  cudaStream_t s2 = (c->opt.flags & IHS_FLAG_SERIAL) ? c->st : c->st2;
-  if (after_pass) CK(cudaStreamWaitEvent(s2, c->ev_sa, 0));
-  CK(cudaStreamWaitEvent(s2, c->ev_use[bf], 0));
-  const double lam = (c->C.kind == IHS_RIDGE) ? c->C.param : 0.0;
-  stage_begin(c, IHS_ST_GRAM, s2);
-  CK(launch_gram(c->gp, c->SAb[u & 1], c->gop, c->gpart_f, c->gpart_d, 1.0 / c->s, lam, c->H[bf],
-                 c->status, s2));
-  stage_end(c);
-  CK(cudaEventRecord(c->ev_gram[u & 1], s2));
-  stage_begin(c, IHS_ST_FACTOR, s2);
-  CK(launch_cholesky(c->H[bf], (int)c->d, c->f32fac, c->L[bf], c->Dinv[bf], c->bar, c->status,
-                     s2, (c->opt.flags & IHS_FLAG_CLUSTER) != 0));
-  stage_end(c);
-  CK(cudaEventRecord(c->ev_fac[bf], s2));
-  return IHS_OK;
-}
-
-// The pass of iteration t on the caller's stream: g(x^t) into c->g and
-// SA(t+1) into SAb[(t+1) & 1], whose last reader was the Gram of t - 1.
-ihs_status fused_pass(ihs_ctx* c, const double* x, int64_t t) {
+// Fused pipeline, main half (caller's stream): one pass over A forming SA(t)
+// and g(x), then Gram, factor and step into x.
+ihs_status fused_iteration(ihs_ctx* c, double* x, int pb, int bf) {
   cudaStream_t s1 = c->st;
-  const int pb = (int)((t + 1) & 1);
   CK(cudaStreamWaitEvent(s1, c->ev_sort[pb], 0));
-  CK(cudaStreamWaitEvent(s1, c->ev_gram[pb], 0));
   const double lam = (c->C.kind == IHS_RIDGE) ? c->C.param : 0.0;
   stage_begin(c, IHS_ST_SKETCH, s1);
   cudaError_t e = launch_sketch_grad_fused(
       c->DA, c->sp, pb ? c->perm2 : c->perm, pb ? c->seg2 : c->seg,
-      pb ? c->chunk_first2 : c->chunk_first, c->bsplit, x, (float*)c->SAb[pb],
-      (float*)c->sk_partial, c->gcta, c->g, lam, s1, c->prof ? c : nullptr);
+      pb ? c->chunk_first2 : c->chunk_first, c->bsplit, x, (float*)c->SA, (float*)c->sk_partial,
+      c->gcta, c->g, lam, s1, c->prof ? c : nullptr);
   stage_end(c);
   CK(e);
   CK(cudaEventRecord(c->ev_read[pb], s1));
-  CK(cudaEventRecord(c->ev_sa, s1));
-  c->sa_t[pb] = t + 1;
-  return IHS_OK;
+  stage_begin(c, IHS_ST_GRAM, s1);
+  CK(launch_gram(c->gp, c->SA, c->gop, c->gpart_f, c->gpart_d, 1.0 / c->s, lam, c->H[bf],
+                 c->status, s1));
+  stage_end(c);
+  stage_begin(c, IHS_ST_FACTOR, s1);
+  CK(launch_cholesky(c->H[bf], (int)c->d, c->f32fac, c->L[bf], c->Dinv[bf], c->bar, c->status,
+                     s1, (c->opt.flags & IHS_FLAG_CLUSTER) != 0));
+  stage_end(c);
+  CK(cudaEventRecord(c->ev_fac[bf], s1));
+  return step_with(c, x, bf);
 }
 
 }  // namespace
@@ -672,7 +610,6 @@ ihs_status ihs_sketch(ihs_ctx* c, int64_t t) {
   const int bf = c->cur ^ 1;
   if ((s = sketch_chain(c, t, bf)) != IHS_OK) return s;
   c->cur = bf;
-  c->cur_t = t;
   c->have_sketch = true;
   return IHS_OK;
 }
@@ -711,25 +648,13 @@ ihs_status ihs_solve(ihs_ctx* c, double* x, int64_t t0, int iters, ihs_report* r
   ihs_status s = IHS_OK;
   if (iters > 0 && c->fused) {
     if ((s = join_caller(c)) != IHS_OK) return s;
-    int bf = c->cur ^ 1;  // H/L/Dinv buffer of counter t0
-    // SA(t0): left by the last pass or sketch chain, else formed here
-    const bool first = c->sa_t[t0 & 1] != t0;
-    if (first) {
-      if ((s = fused_sort(c, t0)) != IHS_OK) return s;
-      if ((s = fused_first_sketch(c, t0)) != IHS_OK) return s;
-    }
-    if ((s = fused_sort(c, t0 + 1)) != IHS_OK) return s;
-    if ((s = fused_gram_factor(c, t0, bf, false)) != IHS_OK) return s;
-    // the first pass shares the chunk partials with the first sketch
-    if (first) CK(cudaStreamWaitEvent(c->st, c->ev_first, 0));
+    if ((s = fused_sort(c, t0, 0)) != IHS_OK) return s;
+    int bf = c->cur ^ 1;
     for (int k = 0; k < iters; ++k) {
-      const int64_t t = t0 + k;
-      if ((s = fused_pass(c, x, t)) != IHS_OK) return s;
-      if (k + 2 <= iters && (s = fused_sort(c, t + 2)) != IHS_OK) return s;
-      if ((s = step_with(c, x, bf)) != IHS_OK) return s;
+      const int pb = k & 1;
+      if (k + 1 < iters && (s = fused_sort(c, t0 + k + 1, pb ^ 1)) != IHS_OK) return s;
+      if ((s = fused_iteration(c, x, pb, bf)) != IHS_OK) return s;
       c->cur = bf;
-      c->cur_t = t;
-      if (k + 1 < iters && (s = fused_gram_factor(c, t + 1, bf ^ 1, true)) != IHS_OK) return s;
       bf ^= 1;
     }
     c->have_sketch = true;
@@ -745,7 +670,6 @@ ihs_status ihs_solve(ihs_ctx* c, double* x, int64_t t0, int iters, ihs_report* r
       if (k + 1 < iters && (s = sketch_chain(c, t0 + k + 1, bf ^ 1)) != IHS_OK) return s;
       if ((s = step_with(c, x, bf)) != IHS_OK) return s;
       c->cur = bf;
-      c->cur_t = t0 + k;
       bf ^= 1;
     }
     c->have_sketch = true;
@@ -772,8 +696,7 @@ ihs_status ihs_get_sketch(ihs_ctx* c, void* SA_out, int* SA_dtype, double* H_out
   const size_t el = c->acc64 ? 8 : 4;
   CK(cudaStreamWaitEvent(c->st, c->ev_fac[c->cur], 0));
   if (SA_out)
-    CK(cudaMemcpyAsync(SA_out, c->SAb[c->cur_t & 1], (size_t)c->m * c->d * el,
-                       cudaMemcpyDeviceToDevice, c->st));
+    CK(cudaMemcpyAsync(SA_out, c->SA, (size_t)c->m * c->d * el, cudaMemcpyDeviceToDevice, c->st));
   if (H_out)
     CK(cudaMemcpyAsync(H_out, c->H[c->cur], (size_t)c->d * c->d * sizeof(double),
                        cudaMemcpyDeviceToDevice, c->st));
