@@ -402,13 +402,20 @@ def run_iters_only(args):
     import torch
     import paper_1910_14166_gb300 as ihs
     w = synth.make(args.workload, n=args.n, seed=0)
-    A = torch.from_numpy(w["A"]).cuda()
+    prec = args.precision if args.precision_given else w["precision"]
     b = torch.from_numpy(w["b"]).cuda()
-    sv = ihs.IHS(A, b, kind="ols", m=w["m"], s=w["s"], seed=0, precision=args.precision)
+    if "A" in w:
+        A, shape = torch.from_numpy(w["A"]).cuda(), None
+    else:
+        A = tuple(torch.from_numpy(w[k]).cuda() for k in ("rowptr", "col", "val"))
+        shape = (w["n"], w["d"])
+    kind = {"ols": "ols", "l1": "l1", "ridge": "ridge"}[w["kind"]]
+    sv = ihs.IHS(A, b, kind=kind, param=w["param"], m=w["m"], s=w["s"], seed=0, precision=prec,
+                 shape=shape)
     x, rep = sv.solve(iters=args.ncu_iters)
     torch.cuda.synchronize()
-    print("iters_only ok: n=%d d=%d m=%d precision=%s iters=%d status=%d"
-          % (w["n"], w["d"], w["m"], args.precision, args.ncu_iters, rep.status))
+    print("iters_only ok: %s n=%d d=%d m=%d s=%d precision=%s iters=%d status=%d"
+          % (args.workload, w["n"], w["d"], w["m"], w["s"], prec, args.ncu_iters, rep.status))
 
 
 def main():
@@ -427,6 +434,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-two-pass", action="store_true")
     args = ap.parse_args()
+    args.precision_given = any(a == "--precision" or a.startswith("--precision=") for a in sys.argv[1:])
     if args.ncu_iters:
         run_iters_only(args)
         return

@@ -30,6 +30,7 @@ struct ihs_ctx {
   cudaEvent_t ev_fac[2] = {};  // factor of buffer b ready
   cudaEvent_t ev_use[2] = {};  // last step reading buffer b done
   cudaEvent_t ev_join = nullptr;
+  cudaEvent_t ev_grad = nullptr;  // gradient pass of the current iteration done
   bool prof = false;
   StageEvents pe;
   double prof_ms[IHS_NSTAGES] = {};
@@ -344,6 +345,7 @@ void ihs_destroy(ihs_ctx* c) {
     if (c->ev_use[k]) cudaEventDestroy(c->ev_use[k]);
   }
   if (c->ev_join) cudaEventDestroy(c->ev_join);
+  if (c->ev_grad) cudaEventDestroy(c->ev_grad);
   for (int k = 0; k < 2; ++k) {
     if (c->ev_sort[k]) cudaEventDestroy(c->ev_sort[k]);
     if (c->ev_read[k]) cudaEventDestroy(c->ev_read[k]);
@@ -409,7 +411,8 @@ ihs_status ihs_create(ihs_ctx** out, const ihs_matrix* A, const double* b,
         cudaEventCreateWithFlags(&c->ev_use[k], cudaEventDisableTiming) != cudaSuccess)
       return fail(IHS_ERR_CUDA);
   }
-  if (cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess)
+  if (cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_grad, cudaEventDisableTiming) != cudaSuccess)
     return fail(IHS_ERR_CUDA);
   for (int k = 0; k < 2; ++k) {
     if (cudaEventCreateWithFlags(&c->ev_sort[k], cudaEventDisableTiming) != cudaSuccess ||
@@ -662,13 +665,21 @@ ihs_status ihs_solve(ihs_ctx* c, double* x, int64_t t0, int iters, ihs_report* r
     if ((s = join_caller(c)) != IHS_OK) return s;
     int bf = c->cur ^ 1;
     if ((s = sketch_chain(c, t0, bf)) != IHS_OK) return s;
+    // The chain of t+1 starts once the gradient pass of t is done, and is
+    // issued after the step of t: a gradient pass sharing the GPU with a
+    // full-width sketch kernel runs several times slower, and the one-CTA
+    // l1 step needs a whole SM, which it gets only if launched first.
     for (int k = 0; k < iters; ++k) {
       stage_begin(c, IHS_ST_GRAD, c->st);
       s = gradient_on(c, x, c->g, nullptr, true);
       stage_end(c);
       if (s != IHS_OK) return s;
-      if (k + 1 < iters && (s = sketch_chain(c, t0 + k + 1, bf ^ 1)) != IHS_OK) return s;
+      CK(cudaEventRecord(c->ev_grad, c->st));
       if ((s = step_with(c, x, bf)) != IHS_OK) return s;
+      if (k + 1 < iters) {
+        CK(cudaStreamWaitEvent(c->st2, c->ev_grad, 0));
+        if ((s = sketch_chain(c, t0 + k + 1, bf ^ 1)) != IHS_OK) return s;
+      }
       c->cur = bf;
       bf ^= 1;
     }
