@@ -418,6 +418,62 @@ def run_iters_only(args):
           % (args.workload, w["n"], w["d"], w["m"], w["s"], prec, args.ncu_iters, rep.status))
 
 
+def run_sketch_quality(args):
+    """The sketch-quality experiment of App. B on a synthetic stand-in: for
+    m in {5d, 10d, 20d, 40d} and s in {1, 4, 8}, the mean and spread over
+    `trials` independent sketches of ||A^T S^T S A - A^T A||_F / ||A^T A||_F,
+    and the time to form one sketched Hessian (sort, SA, fix-up, Gram; CUDA
+    events).  A^T A, every sketch, every Gram and the error reduction run in
+    the library's kernels.  One JSON line per (m, s)."""
+    import torch
+    import paper_1910_14166_gb300 as ihs
+    w = synth.make(args.workload, n=args.n, seed=0)
+    prec = args.precision if args.precision_given else "fp64"
+    n, d = w["n"], w["d"]
+    b = torch.from_numpy(w["b"]).cuda()
+    if "A" in w:
+        A, shape = torch.from_numpy(w["A"]).cuda(), None
+    else:
+        A = tuple(torch.from_numpy(w[k]).cuda() for k in ("rowptr", "col", "val"))
+        shape = (n, d)
+    G = None
+    for s in (1, 4, 8):
+        for k in (5, 10, 20, 40):
+            m = k * d
+            if m % s or m > n:
+                continue
+            try:
+                sv = ihs.IHS(A, b, m=m, s=s, seed=args.seed, precision=prec, shape=shape)
+            except ihs.IHSError as e:
+                print(json.dumps({"experiment": "sketch_quality", "workload": args.workload, "m": m,
+                                  "s": s, "skipped": str(e)}), flush=True)
+                continue
+            if G is None:
+                G = sv.exact_gram()
+                torch.cuda.synchronize()
+                # closed form of E err^2 (dense A): (||A||_F^4 + ||A^T A||_F^2
+                # - 2 sum_i ||a_i||^4) / (m ||A^T A||_F^2), CountSketch and SJLT
+                c_num = None
+                if shape is None:
+                    row2 = (A.double() ** 2).sum(dim=1)
+                    g2 = float((G * G).sum())
+                    c_num = (float(row2.sum()) ** 2 + g2 - 2.0 * float((row2 * row2).sum())) / g2
+            sv.sketch_error(0, G)  # warm-up
+            sv.profile(True)
+            errs = [sv.sketch_error(t, G) for t in range(args.trials)]
+            ms, cnt, _ = sv.profile_read()
+            per = (ms["sort"] + ms["sketch"] + ms["sketch_fix"] + ms["gram"]) / args.trials
+            print(json.dumps({
+                "experiment": "sketch_quality", "workload": args.workload, "n": n, "d": d,
+                "m": m, "m_over_d": k, "s": s, "precision": prec, "trials": args.trials,
+                "err_mean": statistics.fmean(errs), "err_std": statistics.stdev(errs),
+                "sketch_ms": per,
+                "err_rms_expected": (c_num / m) ** 0.5 if c_num is not None else None,
+                "err_rms": statistics.fmean([e * e for e in errs]) ** 0.5,
+                "error": "||A^T S^T S A - A^T A||_F / ||A^T A||_F (App. B)"}), flush=True)
+            del sv
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -433,10 +489,17 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-two-pass", action="store_true")
+    ap.add_argument("--experiment", default=None, choices=["sketch-quality"],
+                    help="run an experiment instead of the benchmark (one JSON line per point)")
+    ap.add_argument("--trials", type=int, default=10)
+    ap.add_argument("--seed", type=int, default=0)
     args = ap.parse_args()
     args.precision_given = any(a == "--precision" or a.startswith("--precision=") for a in sys.argv[1:])
     if args.ncu_iters:
         run_iters_only(args)
+        return
+    if args.experiment == "sketch-quality":
+        run_sketch_quality(args)
         return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -168,6 +168,22 @@ ihs_status ihs_sync(ihs_ctx* ctx);
 ihs_status ihs_get_sketch(ihs_ctx* ctx, void* SA_out, int* SA_dtype, double* H_out,
                           double* scale);
 
+/* ihs_exact_gram -- G = A^T A in FP64 (DEVICE, d x d doubles, row-major,
+ * both triangles), the reference of the sketch-quality experiment (App. B:
+ * the empirical error ||A^T S^T S A - A^T A||_F / ||A^T A||_F).  Dense A: an
+ * FP64 Gram over the n rows (FP32 entries promoted exactly), deterministic.
+ * CSR A: each row's outer product added with FP64 atomics, so the rounding
+ * order varies from run to run.  Stream-ordered on the context's stream
+ * (does not synchronise); the dense form allocates its split partials on
+ * first use.  Errors: IHS_ERR_ARG (null), IHS_ERR_OOM, IHS_ERR_CUDA. */
+ihs_status ihs_exact_gram(ihs_ctx* ctx, double* G);
+
+/* ihs_sketch_error -- form the sketch of counter t as ihs_sketch does, then
+ * err (HOST) = ||H_t - G||_F / ||G||_F with H_t = (1/s) (S_t A)^T (S_t A)
+ * (+ lambda I for ridge) and G (DEVICE, d x d) normally from
+ * ihs_exact_gram.  Synchronises; returns the device status. */
+ihs_status ihs_sketch_error(ihs_ctx* ctx, int64_t t, const double* G, double* err);
+
 /* ihs_adjoint -- reverse-mode derivative of a loss L(x) of the ridge / OLS
  * solution x = (A^T A + lambda I)^{-1} A^T b (not in the paper).
  * v = (A^T A + lambda I)^{-1} dLdx is solved by conjugate gradients

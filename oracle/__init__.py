@@ -441,3 +441,33 @@ def ridge_adjoint(A, b, lam, dLdx):
     r = b - A @ x
     Av = A @ v
     return x, Av, np.outer(r, v) - np.outer(Av, x)
+
+
+def sketch_error(A, m: int, s: int, seed: int, t: int):
+    """Empirical sketch error of the experiments (App. B):
+    ||A^T S^T S A - A^T A||_F / ||A^T A||_F for the sketch of counter t, with
+    S^T S normalised as in Sec. 2 (Gram scale 1/s)."""
+    n = A.n if isinstance(A, CSR) else np.asarray(A).shape[0]
+    bucket, sign = hash_draw(seed, t, s, m, n)
+    H = gram(sketch(A, m, s, bucket, sign), 1.0 / s)
+    G = ata(A)
+    return float(np.linalg.norm(H - G) / np.linalg.norm(G))
+
+
+def sketch_error_expected_sq(A, m: int):
+    """E ||A^T S^T S A - A^T A||_F^2 / ||A^T A||_F^2 over the draw, for a
+    CountSketch with m rows and for the SJLT of Sec. 2 with m rows in total
+    (s blocks of m/s, scale 1/s): (||A||_F^4 + ||A^T A||_F^2 - 2 sum_i ||a_i||^4)
+    / (m ||A^T A||_F^2).  Derivation: A^T S^T S A - A^T A = sum_{i != j}
+    sigma_i sigma_j [h(i) = h(j)] a_i a_j^T, whose terms are uncorrelated except
+    (i, j) with (j, i); P[h(i) = h(j)] = 1/m, and the s independent blocks of
+    the SJLT each contribute (s/m)(...) scaled by 1/s^2."""
+    A = as_f64(A)
+    if isinstance(A, CSR):
+        raise TypeError("dense A only")
+    A = np.asarray(A)
+    G = A.T @ A
+    row2 = np.einsum("ij,ij->i", A, A)
+    fro2 = float(row2.sum())
+    num = fro2 * fro2 + float(np.sum(G * G)) - 2.0 * float(np.sum(row2 * row2))
+    return num / (m * float(np.sum(G * G)))

@@ -79,6 +79,8 @@ def _load():
         "ihs_profile": [vp, i32],
         "ihs_profile_read": [vp, ctypes.POINTER(f64), ctypes.POINTER(i32), ctypes.POINTER(i64)],
         "ihs_gradient_noalloc": [ctypes.POINTER(_Matrix), vp, vp, f64, vp, vp],
+        "ihs_exact_gram": [vp, vp],
+        "ihs_sketch_error": [vp, i64, vp, ctypes.POINTER(f64)],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -258,6 +260,20 @@ class IHS:
         _check(_lib.ihs_get_sketch(self._h, _ptr(SA), ctypes.byref(dt), _ptr(H),
                                    ctypes.byref(scale)), "ihs_get_sketch")
         return SA, H, scale.value
+
+    def exact_gram(self):
+        """A^T A in FP64 (d x d CUDA tensor), computed by the library."""
+        G = torch.empty((self.d, self.d), dtype=torch.float64, device=self.device)
+        _check(_lib.ihs_exact_gram(self._h, _ptr(G)), "ihs_exact_gram")
+        return G
+
+    def sketch_error(self, t, G):
+        """||(1/s)(S_t A)^T (S_t A) - G||_F / ||G||_F for the sketch of counter t."""
+        _need_cuda(G, "G")
+        err = ctypes.c_double()
+        _check(_lib.ihs_sketch_error(self._h, int(t), _ptr(G), ctypes.byref(err)),
+               "ihs_sketch_error")
+        return err.value
 
     def profile(self, enable=True):
         """Enable stage timing (CUDA events on the context's stream) and reset totals."""

@@ -87,6 +87,10 @@ struct ihs_ctx {
   int* counter = nullptr;
   // adjoint workspace (allocated on first use): v, r, z, p, q (d each), scal[4]
   double* cg = nullptr;
+  // exact-Gram partials and the error scalar (allocated on first use)
+  double* xg_part = nullptr;
+  size_t xg_bytes = 0;
+  double* errbuf = nullptr;
   // l1 QP
   QpWork qw{};
   bool have_sketch = false;
@@ -712,6 +716,41 @@ ihs_status ihs_get_sketch(ihs_ctx* c, void* SA_out, int* SA_dtype, double* H_out
     CK(cudaMemcpyAsync(H_out, c->H[c->cur], (size_t)c->d * c->d * sizeof(double),
                        cudaMemcpyDeviceToDevice, c->st));
   return IHS_OK;
+}
+
+ihs_status ihs_exact_gram(ihs_ctx* c, double* G) {
+  if (!c || !G) return IHS_ERR_ARG;
+  const int d = (int)c->d;
+  if (c->dense) {
+    const GramPlan g = make_gram_plan((int)std::min<int64_t>(c->n, 0x7fffffff), d, IHS_PREC_FP64,
+                                      c->sms);
+    const size_t need = gram_partial_bytes(g);
+    if (c->xg_bytes < need) {
+      ihs_status s = dalloc(c, &c->xg_part, need);
+      if (s != IHS_OK) return s;
+      c->xg_bytes = need;
+    }
+    CK(launch_exact_gram_dense(c->A.val, c->A.dtype == IHS_F32, c->n, d, c->A.ld, c->sms,
+                               c->xg_part, c->xg_bytes, G, c->status, c->st));
+  } else {
+    CK(launch_exact_gram_csr(c->n, d, c->A.rowptr, c->A.rowptr_i64, c->A.col, c->A.val,
+                             c->A.dtype == IHS_F32, G, c->st));
+  }
+  return IHS_OK;
+}
+
+ihs_status ihs_sketch_error(ihs_ctx* c, int64_t t, const double* G, double* err) {
+  if (!c || !G || !err || t < 0) return IHS_ERR_ARG;
+  if (!c->errbuf) {
+    ihs_status s = dalloc(c, &c->errbuf, sizeof(double));
+    if (s != IHS_OK) return s;
+  }
+  ihs_status s = ihs_sketch(c, t);
+  if (s != IHS_OK) return s;
+  CK(cudaStreamWaitEvent(c->st, c->ev_fac[c->cur], 0));
+  CK(launch_fro_ratio(c->H[c->cur], G, c->d * c->d, c->errbuf, c->st));
+  CK(cudaMemcpyAsync(err, c->errbuf, sizeof(double), cudaMemcpyDeviceToHost, c->st));
+  return ihs_sync(c);
 }
 
 ihs_status ihs_adjoint(ihs_ctx* c, const double* x, const double* dLdx, double* dLdb, void* dLdA,

@@ -70,8 +70,9 @@ IHS_DEV void tri_index(int q, int& ti, int& tj) {
 // ----------------------------------------------------------------------------
 // FP64 SIMT
 // ----------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_gram_f64(const double* __restrict__ SA, int m, int d,
-                                                  int tiles, int64_t kchunk,
+template <typename Tin>
+__global__ void __launch_bounds__(256) k_gram_f64(const Tin* __restrict__ SA, int64_t lda, int64_t m,
+                                                  int d, int tiles, int64_t kchunk,
                                                   double* __restrict__ partial) {
   __shared__ double As[16][64 + 1];
   __shared__ double Bs[16][64 + 1];
@@ -86,8 +87,8 @@ __global__ void __launch_bounds__(256) k_gram_f64(const double* __restrict__ SA,
       int rr = e >> 6, c = e & 63;
       int64_t r = rb + rr;
       int ca = ti * 64 + c, cb = tj * 64 + c;
-      As[rr][c] = (r < r1 && ca < d) ? SA[r * d + ca] : 0.0;
-      Bs[rr][c] = (r < r1 && cb < d) ? SA[r * d + cb] : 0.0;
+      As[rr][c] = (r < r1 && ca < d) ? (double)SA[r * lda + ca] : 0.0;
+      Bs[rr][c] = (r < r1 && cb < d) ? (double)SA[r * lda + cb] : 0.0;
     }
     __syncthreads();
 #pragma unroll
@@ -424,7 +425,8 @@ cudaError_t launch_gram(const GramPlan& g, const void* SA, void* operand, float*
   if (g.prec == IHS_PREC_FP64) {
     const int64_t kchunk = ((g.m + g.splits - 1) / g.splits + 15) / 16 * 16;
     dim3 grid(g.tiles, g.splits);
-    { k_gram_f64<<<grid, 256, 0, st>>>((const double*)SA, g.m, g.d, g.tiles, kchunk, partial_d); note_launches(1); }
+    { k_gram_f64<double><<<grid, 256, 0, st>>>((const double*)SA, (int64_t)g.d, (int64_t)g.m, g.d,
+                                                g.tiles, kchunk, partial_d); note_launches(1); }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     { k_gram_reduce<double><<<red_blocks, 256, 0, st>>>(partial_d, g.d, g.tdim, g.tiles, g.splits,
                                                       scale, shift, H, status); note_launches(1); }
@@ -475,5 +477,112 @@ cudaError_t launch_gram(const GramPlan& g, const void* SA, void* operand, float*
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   { k_gram_reduce<float><<<red_blocks, 256, 0, st>>>(partial_f, g.d, g.tdim, g.tiles, g.splits,
                                                    scale, shift, H, status); note_launches(1); }
+  return cudaGetLastError();
+}
+
+// ----------------------------------------------------------------------------
+// Exact Gram A^T A in FP64 (the reference of the sketch-quality experiment,
+// App. B).  Dense: the FP64 SIMT Gram over the n rows of A (FP32 entries are
+// promoted exactly), split-K partials reduced in split order.  CSR: each row
+// adds its outer product a_i a_i^T to the lower triangle with FP64 atomics
+// (rounding depends on the order of the atomics), then the upper triangle is
+// mirrored.
+// ----------------------------------------------------------------------------
+__global__ void k_gram_csr_rows(int64_t n, const void* __restrict__ rowptr, int rowptr_i64,
+                                const int32_t* __restrict__ col, const void* __restrict__ val,
+                                int f32, int d, double* __restrict__ G) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t a = rowptr_i64 ? ((const int64_t*)rowptr)[i] : ((const int32_t*)rowptr)[i];
+    const int64_t b = rowptr_i64 ? ((const int64_t*)rowptr)[i + 1] : ((const int32_t*)rowptr)[i + 1];
+    for (int64_t p = a; p < b; ++p) {
+      const int cp = col[p];
+      const double vp = f32 ? (double)((const float*)val)[p] : ((const double*)val)[p];
+      for (int64_t q = a; q < b; ++q) {
+        const int cq = col[q];
+        if (cq > cp) continue;
+        const double vq = f32 ? (double)((const float*)val)[q] : ((const double*)val)[q];
+        atomicAdd(G + (int64_t)cp * d + cq, vp * vq);
+      }
+    }
+  }
+}
+
+__global__ void k_mirror_lower(double* __restrict__ G, int d) {
+  const int64_t total = (int64_t)d * d;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e / d), j = (int)(e - (int64_t)i * d);
+    if (j > i) G[e] = G[(int64_t)j * d + i];
+  }
+}
+
+cudaError_t launch_exact_gram_dense(const void* A, int f32, int64_t n, int d, int64_t lda,
+                                    int num_sms, double* partial, size_t partial_bytes, double* G,
+                                    int* status, cudaStream_t st) {
+  GramPlan g = make_gram_plan((int)std::min<int64_t>(n, 0x7fffffff), d, IHS_PREC_FP64, num_sms);
+  // keep the partials within the buffer given
+  while (g.splits > 1 && gram_partial_bytes(g) > partial_bytes) --g.splits;
+  if (gram_partial_bytes(g) > partial_bytes) return cudaErrorInvalidValue;
+  const int64_t kchunk = ((n + g.splits - 1) / g.splits + 15) / 16 * 16;
+  dim3 grid(g.tiles, g.splits);
+  if (f32)
+    { k_gram_f64<float><<<grid, 256, 0, st>>>((const float*)A, lda, n, d, g.tiles, kchunk, partial); note_launches(1); }
+  else
+    { k_gram_f64<double><<<grid, 256, 0, st>>>((const double*)A, lda, n, d, g.tiles, kchunk, partial); note_launches(1); }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const int red_blocks = (int)std::min<int64_t>(((int64_t)d * d + 255) / 256, 4096);
+  { k_gram_reduce<double><<<red_blocks, 256, 0, st>>>(partial, d, g.tdim, g.tiles, g.splits, 1.0,
+                                                    0.0, G, status); note_launches(1); }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_exact_gram_csr(int64_t n, int d, const void* rowptr, int rowptr_i64,
+                                  const int32_t* col, const void* val, int f32, double* G,
+                                  cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(G, 0, (size_t)d * d * sizeof(double), st);
+  if (e != cudaSuccess) return e;
+  if (n > 0)
+    { k_gram_csr_rows<<<(unsigned)std::min<int64_t>((n + 255) / 256, 8192), 256, 0, st>>>(
+        n, rowptr, rowptr_i64, col, val, f32, d, G); note_launches(1); }
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  { k_mirror_lower<<<(unsigned)std::min<int64_t>(((int64_t)d * d + 255) / 256, 4096), 256, 0, st>>>(
+      G, d); note_launches(1); }
+  return cudaGetLastError();
+}
+
+// err = ||H - G||_F / ||G||_F, one CTA, sums in a fixed order (FP64).
+__global__ void __launch_bounds__(1024) k_fro_ratio(const double* __restrict__ H,
+                                                    const double* __restrict__ G, int64_t count,
+                                                    double* __restrict__ out) {
+  __shared__ double r1[32], r2[32];
+  double a = 0.0, b = 0.0;
+  for (int64_t e = threadIdx.x; e < count; e += blockDim.x) {
+    const double dh = H[e] - G[e];
+    a = fma(dh, dh, a);
+    b = fma(G[e], G[e], b);
+  }
+  a = warp_sum(a);
+  b = warp_sum(b);
+  if ((threadIdx.x & 31) == 0) {
+    r1[threadIdx.x >> 5] = a;
+    r2[threadIdx.x >> 5] = b;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double sa = 0.0, sb = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      sa += r1[w];
+      sb += r2[w];
+    }
+    out[0] = sb > 0.0 ? sqrt(sa / sb) : 0.0;
+  }
+}
+
+cudaError_t launch_fro_ratio(const double* H, const double* G, int64_t count, double* out,
+                             cudaStream_t st) {
+  k_fro_ratio<<<1, 1024, 0, st>>>(H, G, count, out);
+  note_launches(1);
   return cudaGetLastError();
 }

@@ -116,6 +116,16 @@ GramPlan make_gram_plan(int m, int d, int prec, int num_sms);
 size_t gram_partial_bytes(const GramPlan& g);
 size_t gram_operand_bytes(const GramPlan& g);
 // SA (m x d, double for FP64, float otherwise) -> H (d x d double, full)
+// Exact FP64 Gram A^T A (dense: deterministic split-K; CSR: FP64 atomics) and
+// the ratio ||H - G||_F / ||G||_F into out[0] (device).
+cudaError_t launch_exact_gram_dense(const void* A, int f32, int64_t n, int d, int64_t lda,
+                                    int num_sms, double* partial, size_t partial_bytes, double* G,
+                                    int* status, cudaStream_t st);
+cudaError_t launch_exact_gram_csr(int64_t n, int d, const void* rowptr, int rowptr_i64,
+                                  const int32_t* col, const void* val, int f32, double* G,
+                                  cudaStream_t st);
+cudaError_t launch_fro_ratio(const double* H, const double* G, int64_t count, double* out,
+                             cudaStream_t st);
 cudaError_t launch_gram(const GramPlan& g, const void* SA, void* operand, float* partial_f,
                         double* partial_d, double scale, double shift, double* H, int* status,
                         cudaStream_t st);

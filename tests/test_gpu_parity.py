@@ -345,3 +345,30 @@ def test_cluster_factor_matches_grid_factor(cuda_lib, kind):
     xb, rb = b.solve(iters=4)
     assert ra.status == 0 and rb.status == 0
     assert torch.equal(xa, xb)
+
+
+@pytest.mark.parametrize("kind,s", [("dense64", 1), ("dense32", 4), ("csr64", 4), ("csr32", 8)])
+def test_sketch_error_matches_oracle(cuda_lib, kind, s):
+    """Sketch-quality experiment (App. B): the exact Gram A^T A and the
+    empirical error ||A^T S^T S A - A^T A||_F / ||A^T A||_F of the sketches of
+    counters t = 0..3 agree with the oracle's (FP64 sketch and Gram)."""
+    if kind.startswith("dense"):
+        w = synth.make("ols_dense_fp64", n=6000, d=40, m=400)
+        Ah = w["A"] if kind == "dense64" else w["A"].astype(np.float32)
+        args = (dev(Ah), dev(w["b"]))
+        Ao = Ah.astype(np.float64)
+        kw = dict(m=400, s=s, precision="fp64")
+    else:
+        w = synth.make("lasso_csr_fp64", n=30000, d=60, m=600)
+        val = w["val"] if kind == "csr64" else w["val"].astype(np.float32)
+        args = ((dev(w["rowptr"]), dev(w["col"]), dev(val)), dev(w["b"]))
+        Ao = O.CSR(w["n"], w["d"], w["rowptr"], w["col"], val.astype(np.float64))
+        kw = dict(m=600, s=s, precision="fp64", shape=(w["n"], w["d"]))
+    sv = cuda_lib.IHS(*args, seed=9, **kw)
+    G = sv.exact_gram()
+    Go = O.ata(Ao)
+    assert np.abs(G.cpu().numpy() - Go).max() <= 1e-12 * np.abs(Go).max()
+    for t in range(4):
+        e = sv.sketch_error(t, G)
+        eo = O.sketch_error(Ao, kw["m"], s, 9, t)
+        assert abs(e - eo) <= 1e-10 * eo, (t, e, eo)

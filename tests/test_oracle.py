@@ -403,3 +403,39 @@ def test_synth_recipes():
     # the hottest column holds roughly p_1 of the draws (rejection of repeats lowers it a little)
     p1 = synth.zipf_probs(1000, 1.1)[0]
     assert 0.6 * p1 < freq.max() < 1.05 * p1
+
+
+@pytest.mark.parametrize("s", [1, 4])
+def test_sketch_error_mean_matches_closed_form(s):
+    """The mean of the squared empirical sketch error over independent draws
+    matches E||A^T S^T S A - A^T A||_F^2 / ||A^T A||_F^2 = (||A||_F^4 +
+    ||A^T A||_F^2 - 2 sum ||a_i||^4) / (m ||A^T A||_F^2) (derived from
+    P[h(i) = h(j)] = 1/m and independent signs), within 5 standard errors."""
+    rng = np.random.default_rng(11)
+    A = rng.standard_normal((80, 5)) * rng.uniform(0.2, 3.0, size=(80, 1))
+    m = 24
+    e2 = np.array([O.sketch_error(A, m, s, 7, t) ** 2 for t in range(3000)])
+    want = O.sketch_error_expected_sq(A, m)
+    se = e2.std(ddof=1) / np.sqrt(e2.size)
+    assert abs(e2.mean() - want) <= 5 * se, (e2.mean(), want, se)
+    # and a wrong normalisation (scale 1 instead of 1/s for s > 1) would miss
+    if s > 1:
+        assert abs(e2.mean() * s - want) > 5 * se
+
+
+def test_sketch_error_zero_for_injective_hash_and_decreasing_in_m():
+    """With m >= n and a draw in which no two rows share a bucket, S^T S = I
+    and the error is 0 up to rounding; the mean error falls as m grows."""
+    rng = np.random.default_rng(12)
+    A = rng.standard_normal((6, 3))
+    found = False
+    for t in range(200):
+        b, _ = O.hash_draw(5, t, 1, 4096, 6)
+        if len(set(b[0].tolist())) == 6:
+            assert O.sketch_error(A, 4096, 1, 5, t) < 1e-14
+            found = True
+            break
+    assert found
+    B = rng.standard_normal((400, 6))
+    means = [np.mean([O.sketch_error(B, m, 1, 3, t) for t in range(60)]) for m in (30, 120, 480)]
+    assert means[0] > means[1] > means[2]
