@@ -17,6 +17,9 @@ What is pinned, and by what (see tests/test_oracle.py):
   * residual / gradient: finite differences of f(x) = 1/2 ||Ax - b||^2 (Eq. 1).
   * OLS step: identity sketch gives x_OPT (numpy lstsq) in one step (Eq. 2).
   * l1-ball QP: brute force over all faces of the ball for d <= 6; KKT.
+  * penalised-l1 QP: brute force over all supports and signs for d <= 6; the
+    soft-threshold closed form for diagonal H; KKT.
+  * sketch error (App. B): the closed form of its mean square over draws.
   * x_OPT: Householder QR vs refined normal equations vs lstsq.
   * IHS: geometric convergence at a rate below 1/2 (Thm. 2.2).
   * ridge adjoint: central finite differences in FP64.
@@ -346,10 +349,99 @@ def l1_ball_qp_bruteforce(H, g, xt, R):
     return best
 
 
+def soft_threshold(v, tau):
+    """Proximal map of tau ||.||_1: sign(v) max(|v| - tau, 0)."""
+    return np.sign(v) * np.maximum(np.abs(v) - tau, 0.0)
+
+
+def _pen_face_solve(H, c, lam, S, sgn):
+    """Stationary point of 1/2 x^T H x - c^T x + lam sgn^T x_S on {x_{S^c} = 0}:
+    H_SS x_S = c_S - lam sgn."""
+    return np.linalg.solve(H[np.ix_(S, S)], c[S] - lam * sgn)
+
+
+def l1_penalty_objective(H, g, xt, lam, x):
+    """1/2 (x - xt)^T H (x - xt) - g^T (x - xt) + lam ||x||_1."""
+    e = np.asarray(x) - xt
+    return float(0.5 * e @ H @ e - g @ e + lam * np.abs(x).sum())
+
+
+def l1_penalty_kkt_residual(H, g, xt, lam, x):
+    """Relative violation of 0 in H (x - xt) - g + lam d||x||_1 (0 at the optimum)."""
+    c = H @ xt + g
+    grad = H @ x - c
+    scale = max(np.abs(c).max(), lam, 1e-300)
+    S = x != 0
+    on = np.abs(grad[S] + lam * np.sign(x[S])).max() if S.any() else 0.0
+    off = max(0.0, (np.abs(grad[~S]) - lam).max()) if (~S).any() else 0.0
+    return max(on, off) / scale
+
+
+def l1_penalty_qp(H, g, xt, lam, tol=1e-13, max_rounds=200, inner=200):
+    """Exact minimiser of the penalised-LASSO subproblem (the experiments' form,
+    Sec. 5: 1/2 ||Ax - b||^2 + lam ||x||_1, each subproblem solved exactly):
+        argmin_x 1/2 (x - xt)^T H (x - xt) - g^T (x - xt) + lam ||x||_1.
+    Proximal FISTA (Beck & Teboulle 2009; soft thresholding) locates the
+    support and signs; the stationarity system H_SS x_S = c_S - lam sgn on that
+    support (c = H xt + g) gives the exact point, accepted only when its signs
+    match and |(H x - c)_j| <= lam off the support."""
+    c = H @ xt + g
+    if np.abs(c).max() <= lam:
+        return np.zeros_like(c)
+    Lip = np.linalg.eigvalsh(H)[-1]
+    x = np.array(xt, dtype=np.float64)
+    y = x.copy()
+    tk = 1.0
+    for _ in range(max_rounds):
+        for _ in range(inner):
+            xn = soft_threshold(y - (H @ y - c) / Lip, lam / Lip)
+            tn = 0.5 * (1.0 + np.sqrt(1.0 + 4.0 * tk * tk))
+            y = xn + ((tk - 1.0) / tn) * (xn - x)
+            x, tk = xn, tn
+        S = np.nonzero(x)[0]
+        if S.size == 0:
+            continue
+        sgn = np.sign(x[S])
+        z = _pen_face_solve(H, c, lam, S, sgn)
+        if np.any(z * sgn <= 0):
+            continue
+        xf = np.zeros_like(x)
+        xf[S] = z
+        grad = H @ xf - c
+        mask = np.ones(x.size, bool)
+        mask[S] = False
+        if (not mask.any()) or np.all(np.abs(grad[mask]) <= lam * (1.0 + 1e-9) + tol * np.abs(c).max()):
+            return xf
+    raise RuntimeError("penalised l1 QP did not reach an exact KKT point")
+
+
+def l1_penalty_qp_bruteforce(H, g, xt, lam):
+    """Brute force for tiny d: the best stationary point over every support and
+    sign pattern in {-1,0,1}^d (x = 0 included)."""
+    import itertools
+    d = H.shape[0]
+    best, bq = np.zeros(d), l1_penalty_objective(H, g, xt, lam, np.zeros(d))
+    c = H @ xt + g
+    for pat in itertools.product((-1, 0, 1), repeat=d):
+        pat = np.array(pat)
+        S = np.nonzero(pat)[0]
+        if S.size == 0:
+            continue
+        z = _pen_face_solve(H, c, lam, S, pat[S].astype(float))
+        if np.any(z * pat[S] <= 0):
+            continue
+        x = np.zeros(d)
+        x[S] = z
+        q = l1_penalty_objective(H, g, xt, lam, x)
+        if q < bq:
+            best, bq = x, q
+    return best
+
+
 # --------------------------------------------------------------------------
 # IHS (Eq. 2) and its fixed point.
 # --------------------------------------------------------------------------
-OLS, L1_BALL, RIDGE = 0, 1, 2
+OLS, L1_BALL, RIDGE, L1_PENALTY = 0, 1, 2, 3
 
 
 def ihs(A, b, kind: int, param: float, m: int, s: int, seed: int, iters: int, x0=None,
@@ -375,6 +467,8 @@ def ihs(A, b, kind: int, param: float, m: int, s: int, seed: int, iters: int, x0
             g = g - param * x
         if kind == L1_BALL:
             x = l1_ball_qp(H, g, x, param)
+        elif kind == L1_PENALTY:
+            x = l1_penalty_qp(H, g, x, param)
         else:
             x = x + chol_solve(H, g)
         xs.append(x.copy())
@@ -421,6 +515,13 @@ def x_opt_l1(A, b, R):
     A = as_f64(A)
     G = ata(A)
     return l1_ball_qp(G, atb(A, b), np.zeros(A.shape[1]), R)
+
+
+def x_opt_l1_penalty(A, b, lam):
+    """x_OPT of the penalised LASSO 1/2 ||Ax - b||^2 + lam ||x||_1: the
+    subproblem above with H = A^T A, x^t = 0, g = A^T b."""
+    A = as_f64(A)
+    return l1_penalty_qp(ata(A), atb(A, b), np.zeros(A.shape[1]), lam)
 
 
 def err_A(x, xopt, G):

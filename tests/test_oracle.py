@@ -382,6 +382,19 @@ def test_pins_catch_planted_mistakes(monkeypatch):
     x1 = x - O.chol_solve(H, O.resid_grad(A, b, x))
     xo = np.linalg.lstsq(A, b, rcond=None)[0]
     assert O.err_A(x1, xo, A.T @ A) > O.err_A(x, xo, A.T @ A)
+    # penalised QP with the sign of the penalty term flipped in the face system
+    # is caught by the brute-force pin
+    G = A.T @ A
+    gg = A.T @ b
+    lam = 0.2 * np.abs(gg).max()
+    good = O.l1_penalty_qp_bruteforce(G, gg, np.zeros(d), lam)
+    monkeypatch.setattr(O, "_pen_face_solve",
+                        lambda H_, c_, l_, S_, s_: np.linalg.solve(H_[np.ix_(S_, S_)], c_[S_] + l_ * s_))
+    try:
+        bad = O.l1_penalty_qp(G, gg, np.zeros(d), lam, max_rounds=3, inner=50)
+    except RuntimeError:
+        bad = None  # no face passed the acceptance test: caught
+    assert bad is None or not np.allclose(bad, good)
 
 
 # --------------------------------------------------------------- synth ----
@@ -439,3 +452,51 @@ def test_sketch_error_zero_for_injective_hash_and_decreasing_in_m():
     B = rng.standard_normal((400, 6))
     means = [np.mean([O.sketch_error(B, m, 1, 3, t) for t in range(60)]) for m in (30, 120, 480)]
     assert means[0] > means[1] > means[2]
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_l1_penalty_qp_against_bruteforce(seed):
+    """Penalised subproblem (the experiments' LASSO form): the exact solver
+    equals brute force over all supports and signs (d = 5), and its KKT
+    residual vanishes; lam spans the cases x = 0, sparse and dense."""
+    rng = np.random.default_rng(100 + seed)
+    d = 5
+    M = rng.standard_normal((3 * d, d))
+    H = M.T @ M + 0.1 * np.eye(d)
+    xt = rng.standard_normal(d)
+    g = rng.standard_normal(d) * 3
+    c = H @ xt + g
+    for lam in (0.05, 0.3 * np.abs(c).max(), 0.8 * np.abs(c).max(), 1.5 * np.abs(c).max()):
+        x = O.l1_penalty_qp(H, g, xt, lam)
+        xb = O.l1_penalty_qp_bruteforce(H, g, xt, lam)
+        assert np.allclose(x, xb, rtol=1e-10, atol=1e-12), (lam, x, xb)
+        assert O.l1_penalty_kkt_residual(H, g, xt, lam, x) < 1e-12
+
+
+def test_l1_penalty_qp_diagonal_closed_form():
+    """Diagonal H: the minimiser is soft(c, lam) / h with c = H x^t + g."""
+    rng = np.random.default_rng(7)
+    d = 40
+    h = rng.uniform(0.5, 4.0, d)
+    H = np.diag(h)
+    xt = rng.standard_normal(d)
+    g = rng.standard_normal(d)
+    lam = 0.7
+    c = H @ xt + g
+    want = np.sign(c) * np.maximum(np.abs(c) - lam, 0.0) / h
+    assert np.allclose(O.l1_penalty_qp(H, g, xt, lam), want, rtol=1e-12, atol=1e-14)
+
+
+def test_ihs_l1_penalty_converges_to_xopt():
+    """IHS on the penalised LASSO (lam = 5, the experiments' value) reaches the
+    directly computed x_OPT, geometrically."""
+    w = synth.make("lasso_csr_fp64", n=40000, d=40, m=400)
+    C = O.CSR(w["n"], w["d"], w["rowptr"], w["col"], w["val"])
+    lam = 5.0
+    xo = O.x_opt_l1_penalty(C, w["b"], lam)
+    G = C.gram()
+    assert O.l1_penalty_kkt_residual(G, C.rmatvec(w["b"]), np.zeros(w["d"]), lam, xo) < 1e-12
+    xs = O.ihs(C, w["b"], O.L1_PENALTY, lam, 400, 4, 0, 30)
+    errs = [O.err_A(x, xo, G) for x in xs]
+    assert errs[-1] < 1e-10
+    assert errs[10] < errs[5] < errs[1]
