@@ -67,12 +67,16 @@ typedef struct {
 } ihs_matrix;
 
 /* Constraint set C of Eq. 1 (Sec. 1 lists OLS and the p-norm balls).
- *   IHS_OLS      C = R^d                                  param unused
- *   IHS_L1_BALL  C = {x : ||x||_1 <= param}  (LASSO)       param = radius > 0
- *   IHS_RIDGE    f(x) + (param/2) ||x||^2, C = R^d         param = lambda >= 0
+ *   IHS_OLS        C = R^d                                param unused
+ *   IHS_L1_BALL    C = {x : ||x||_1 <= param}  (LASSO)     param = radius > 0
+ *   IHS_RIDGE      f(x) + (param/2) ||x||^2, C = R^d       param = lambda >= 0
+ *   IHS_L1_PENALTY f(x) + param ||x||_1, C = R^d            param = lambda > 0
  * Ridge is not in the paper; it is the squared-l2 penalty beside the p = 2
- * ball, with the penalty kept exact (not sketched). */
-enum { IHS_OLS = 0, IHS_L1_BALL = 1, IHS_RIDGE = 2 };
+ * ball, with the penalty kept exact (not sketched).  IHS_L1_PENALTY is the
+ * penalised LASSO of the experiments (Sec. 5, lambda = 5): each step solves
+ * argmin_x 1/2 ||S A (x - x^t)||^2 - <A^T (b - A x^t), x - x^t> + lambda ||x||_1
+ * exactly, the penalty unsketched. */
+enum { IHS_OLS = 0, IHS_L1_BALL = 1, IHS_RIDGE = 2, IHS_L1_PENALTY = 3 };
 
 typedef struct {
   int kind;

@@ -371,8 +371,10 @@ ihs_status ihs_create(ihs_ctx** out, const ihs_matrix* A, const double* b,
   if (opt->s < 1 || opt->s > kMaxBlocks || opt->m < 1 || opt->m % opt->s != 0) return IHS_ERR_ARG;
   if (opt->m < A->d) return IHS_ERR_ARG;
   if (opt->precision < IHS_PREC_FP64 || opt->precision > IHS_PREC_BF16) return IHS_ERR_ARG;
-  if (C->kind != IHS_OLS && C->kind != IHS_L1_BALL && C->kind != IHS_RIDGE) return IHS_ERR_ARG;
-  if (C->kind == IHS_L1_BALL && !(C->param > 0)) return IHS_ERR_ARG;
+  if (C->kind != IHS_OLS && C->kind != IHS_L1_BALL && C->kind != IHS_RIDGE &&
+      C->kind != IHS_L1_PENALTY)
+    return IHS_ERR_ARG;
+  if ((C->kind == IHS_L1_BALL || C->kind == IHS_L1_PENALTY) && !(C->param > 0)) return IHS_ERR_ARG;
   if (C->kind == IHS_RIDGE && !(C->param >= 0)) return IHS_ERR_ARG;
   if (A->kind == IHS_DENSE && A->ld < A->d) return IHS_ERR_ARG;
   if (A->kind == IHS_CSR && (A->col == nullptr || A->rowptr == nullptr || A->nnz < 0))
@@ -469,7 +471,7 @@ ihs_status ihs_create(ihs_ctx** out, const ihs_matrix* A, const double* b,
     if ((size_t)(c->m / c->s) * acc_el > 200 * 1024) return fail(IHS_ERR_UNSUPPORTED);
     if ((s = build_csc(c)) != IHS_OK) return fail(s);
   }
-  if (C->kind == IHS_L1_BALL) {
+  if (C->kind == IHS_L1_BALL || C->kind == IHS_L1_PENALTY) {
     size_t qb = qp_work_bytes((int)c->d);
     uint8_t* q;
     AL2(q, qb);
@@ -553,10 +555,10 @@ ihs_status step_with(ihs_ctx* c, double* x, int bf) {
   CK(cudaStreamWaitEvent(c->st, c->ev_fac[bf], 0));
   stage_begin(c, IHS_ST_STEP, c->st);
   cudaError_t e;
-  if (c->C.kind == IHS_L1_BALL)
+  if (c->C.kind == IHS_L1_BALL || c->C.kind == IHS_L1_PENALTY)
     e = launch_l1_step(c->H[bf], c->L[bf], c->Dinv[bf], c->f32fac, (int)c->d, c->g, c->C.param,
-                       c->opt.qp_max_iter, c->opt.qp_tol, c->qw, x, c->step_norm, c->status,
-                       c->st);
+                       c->C.kind == IHS_L1_PENALTY, c->opt.qp_max_iter, c->opt.qp_tol, c->qw, x,
+                       c->step_norm, c->status, c->st);
   else
     e = launch_chol_step(c->L[bf], c->Dinv[bf], (int)c->d, c->f32fac, c->g, x, c->step_norm,
                          c->st);
@@ -651,7 +653,7 @@ ihs_status ihs_sync(ihs_ctx* c) {
 // the step; double buffering keeps the step's factor intact.
 ihs_status ihs_solve(ihs_ctx* c, double* x, int64_t t0, int iters, ihs_report* rep) {
   if (!c || !x || iters < 0 || t0 < 0) return IHS_ERR_ARG;
-  if (c->C.kind == IHS_L1_BALL) CK(cudaMemsetAsync(c->qw.iters, 0, sizeof(int), c->st));
+  if (c->qw.iters) CK(cudaMemsetAsync(c->qw.iters, 0, sizeof(int), c->st));
   ihs_status s = IHS_OK;
   if (iters > 0 && c->fused) {
     if ((s = join_caller(c)) != IHS_OK) return s;
@@ -696,7 +698,7 @@ ihs_status ihs_solve(ihs_ctx* c, double* x, int64_t t0, int iters, ihs_report* r
     rep->step_norm = 0.0;
     rep->qp_fista_iters = 0;
     if (iters > 0) cudaMemcpy(&rep->step_norm, c->step_norm, sizeof(double), cudaMemcpyDeviceToHost);
-    if (c->C.kind == IHS_L1_BALL)
+    if (c->qw.iters)
       cudaMemcpy(&rep->qp_fista_iters, c->qw.iters, sizeof(int), cudaMemcpyDeviceToHost);
   }
   return st;
@@ -756,7 +758,7 @@ ihs_status ihs_sketch_error(ihs_ctx* c, int64_t t, const double* G, double* err)
 ihs_status ihs_adjoint(ihs_ctx* c, const double* x, const double* dLdx, double* dLdb, void* dLdA,
                        ihs_report* rep) {
   if (!c || !x || !dLdx) return IHS_ERR_ARG;
-  if (c->C.kind == IHS_L1_BALL) return IHS_ERR_UNSUPPORTED;
+  if (c->C.kind == IHS_L1_BALL || c->C.kind == IHS_L1_PENALTY) return IHS_ERR_UNSUPPORTED;
   if (!c->have_sketch) return IHS_ERR_ARG;
   if (dLdA && !c->dense) return IHS_ERR_UNSUPPORTED;
   const int d = (int)c->d;

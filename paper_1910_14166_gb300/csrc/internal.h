@@ -158,10 +158,11 @@ struct QpWork {
   int* iters;      // FISTA iterations (device counter)
 };
 size_t qp_work_bytes(int d);
+// The l1 step of Eq. 2: over the ball ||x||_1 <= param (pen = 0) or with the
+// penalty param ||x||_1 (pen = 1).
 cudaError_t launch_l1_step(const double* H, const void* Lbuf, const void* Dinv, int f32, int d,
-                           const double* g,
-                           double R, int max_iter, double tol, QpWork w, double* x,
-                           double* step_norm, int* status, cudaStream_t st);
+                           const double* g, double param, int pen, int max_iter, double tol,
+                           QpWork w, double* x, double* step_norm, int* status, cudaStream_t st);
 
 // ---- adjoint (ridge / OLS) -----------------------------------------------------
 cudaError_t launch_cg_init(const double* rhs, int d, double* v, double* r, double* scal,

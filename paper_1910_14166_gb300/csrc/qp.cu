@@ -17,6 +17,13 @@
 // the mixed form) and refined with FP64 residuals, so dS and mu are FP64
 // accurate.  Failure to certify within the iteration cap records
 // DEV_NOT_CONVERGED and leaves the last feasible FISTA point.
+//
+// The penalised form (the experiments' LASSO, Sec. 5: + lambda ||x||_1
+// instead of the ball) takes the same path without the Newton point: the
+// previous face (x = 0 included), then proximal FISTA (soft threshold at
+// lambda / L) with periodic faces, whose system has no border,
+//     H_SS dS = g_S + H_{S,S^c} x^t_{S^c} - lambda sigma,
+// and whose off-support test is |(H (x - x^t) - g)_j| <= lambda.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -242,9 +249,13 @@ __device__ void face_apply(bool small, const TF* Ls, int k, int ld, double* v) {
 
 // Ms: shared-memory face area (FaceSm<TF>::bytes) used when k <= FaceSm<TF>::n;
 // otherwise the factor lives in Lg (global, stride ldg) and the two vectors in wg.
+// pen: the penalised form, where the face system has no border: H_SS dS =
+// g_S + H_{S,S^c} x^t_{S^c} - lambda sigma (R = lambda), and the multiplier
+// slot sh.z[k] holds lambda for the off-support test.
 template <typename TF>
-__device__ bool face_solve(const double* __restrict__ H, int d, double R, const float* sig_src,
-                           TF* Lg, int ldg, double* wg, TF* Ms, QpShared& sh) {
+__device__ bool face_solve(const double* __restrict__ H, int d, double R, bool pen,
+                           const float* sig_src, TF* Lg, int ldg, double* wg, TF* Ms,
+                           QpShared& sh) {
   const int k = sh.k;
   const bool small = k <= FaceSm<TF>::n;
   TF* Ls = small ? Ms : Lg;
@@ -258,14 +269,17 @@ __device__ bool face_solve(const double* __restrict__ H, int d, double R, const 
   }
   __syncthreads();
   if (small ? !chol_sm<TF>(Ls, k, ld) : !chol_small<TF>(Ls, k, ld, sh)) return false;
-  // w = M^{-1} sigma
-  for (int a = threadIdx.x; a < k; a += blockDim.x) wv[a] = sig_src[sh.S[a]] > 0.f ? 1.0 : -1.0;
-  __syncthreads();
-  face_apply<TF>(small, Ls, k, ld, wv);
-  double sw = 0.0;
-  for (int a = threadIdx.x; a < k; a += blockDim.x)
-    sw += (sig_src[sh.S[a]] > 0.f ? 1.0 : -1.0) * wv[a];
-  const double sTw = block_sum(sw, sh.redd);
+  // w = M^{-1} sigma (the border's direction; not needed in the penalised form)
+  double sTw = 1.0;
+  if (!pen) {
+    for (int a = threadIdx.x; a < k; a += blockDim.x) wv[a] = sig_src[sh.S[a]] > 0.f ? 1.0 : -1.0;
+    __syncthreads();
+    face_apply<TF>(small, Ls, k, ld, wv);
+    double sw = 0.0;
+    for (int a = threadIdx.x; a < k; a += blockDim.x)
+      sw += (sig_src[sh.S[a]] > 0.f ? 1.0 : -1.0) * wv[a];
+    sTw = block_sum(sw, sh.redd);
+  }
   // right-hand side: ra = g_S + H_{S,S^c} x^t_{S^c},  beta = R - sigma^T x^t_S
   // (S^c part: x^t_l for l not in S)
   __shared__ unsigned char inS[kQpMaxD];
@@ -286,8 +300,9 @@ __device__ bool face_solve(const double* __restrict__ H, int d, double R, const 
   for (int a = threadIdx.x; a < k; a += blockDim.x)
     bl += (sig_src[sh.S[a]] > 0.f ? 1.0 : -1.0) * sh.xt[sh.S[a]];
   const double beta = R - block_sum(bl, sh.redd);
-  // solve + FP64 refinement: z = 0, then residual steps
-  for (int a = threadIdx.x; a <= k; a += blockDim.x) sh.z[a] = 0.0;
+  // solve + FP64 refinement: z = 0 (mu = lambda, fixed, when penalised), then
+  // residual steps
+  for (int a = threadIdx.x; a <= k; a += blockDim.x) sh.z[a] = (pen && a == k) ? R : 0.0;
   __syncthreads();
   const int rounds = sizeof(TF) == 4 ? 4 : 2;
   for (int it = 0; it < rounds; ++it) {
@@ -310,7 +325,7 @@ __device__ bool face_solve(const double* __restrict__ H, int d, double R, const 
     for (int a = threadIdx.x; a < k; a += blockDim.x)
       su += (sig_src[sh.S[a]] > 0.f ? 1.0 : -1.0) * res[a];
     const double sTu = block_sum(su, sh.redd);
-    const double dmu = (sTu - rb) / sTw;
+    const double dmu = pen ? 0.0 : (sTu - rb) / sTw;
     for (int a = threadIdx.x; a < k; a += blockDim.x) sh.z[a] += res[a] - dmu * wv[a];
     if (threadIdx.x == 0) sh.z[k] += dmu;
     __syncthreads();
@@ -414,7 +429,7 @@ __device__ unsigned long long support_of(const float* v, int d, QpShared& sh) {
 template <typename TF>
 __global__ void __launch_bounds__(kQpThreads, 1) k_l1_step(
     const double* __restrict__ H, const float* __restrict__ Hf, int d,
-    const double* __restrict__ g, const double* __restrict__ du, double R, int max_iter,
+    const double* __restrict__ g, const double* __restrict__ du, double R, int pen, int max_iter,
     double tol, double* __restrict__ x, double* __restrict__ step_norm, int* __restrict__ support,
     int* __restrict__ iters, double* __restrict__ wv, TF* __restrict__ Ls, int ld,
     float* __restrict__ evec, int* status) {
@@ -428,8 +443,8 @@ __global__ void __launch_bounds__(kQpThreads, 1) k_l1_step(
   }
   __syncthreads();
   bool done = false;
-  // 1. Newton point
-  {
+  // 1. Newton point (the ball form only; du is not formed for the penalty)
+  if (!pen) {
     double a = 0.0;
     for (int j = threadIdx.x; j < d; j += blockDim.x) a += fabs(sh.xt[j] + du[j]);
     const double l1 = block_sum(a, sh.redd);
@@ -439,11 +454,12 @@ __global__ void __launch_bounds__(kQpThreads, 1) k_l1_step(
       done = true;
     }
   }
-  // 2. previous face (signs of x^t on the stored support)
+  // 2. previous face (signs of x^t on the stored support; in the penalised
+  //    form an empty support is the face x = 0, tried too)
   if (!done) {
     if (threadIdx.x == 0) sh.k = support[d];
     __syncthreads();
-    if (sh.k > 0) {
+    if (sh.k > 0 || pen) {
       for (int a = threadIdx.x; a < sh.k; a += blockDim.x) sh.S[a] = support[a];
       for (int j = threadIdx.x; j < d; j += blockDim.x) sh.fv[j] = sh.fxt[j];
       __syncthreads();
@@ -457,7 +473,7 @@ __global__ void __launch_bounds__(kQpThreads, 1) k_l1_step(
       if (!zero_sign) {
         for (int j = threadIdx.x; j < d; j += blockDim.x) sh.fx[j] = sh.xt[j] > 0.0 ? 1.f : -1.f;
         __syncthreads();
-        if (face_solve<TF>(H, d, R, sh.fx, Ls, ld, wv, Ms, sh) &&
+        if (face_solve<TF>(H, d, R, pen, sh.fx, Ls, ld, wv, Ms, sh) &&
             face_accept<TF>(Hf, d, sh.fx, tol, x, sh))
           done = true;
       }
@@ -499,7 +515,7 @@ __global__ void __launch_bounds__(kQpThreads, 1) k_l1_step(
     const float Rf = (float)R;
     for (int j = threadIdx.x; j < d; j += blockDim.x) sh.fx[j] = sh.fxt[j];
     __syncthreads();
-    project_l1(sh.fx, d, Rf, sh);
+    if (!pen) project_l1(sh.fx, d, Rf, sh);
     for (int j = threadIdx.x; j < d; j += blockDim.x) sh.fy[j] = sh.fx[j];
     __syncthreads();
     float tk = 1.f;
@@ -517,7 +533,17 @@ __global__ void __launch_bounds__(kQpThreads, 1) k_l1_step(
       for (int j = threadIdx.x; j < d; j += blockDim.x)
         sh.fv[j] = sh.fy[j] - (hv[j] - (float)sh.gd[j]) / Lip;
       __syncthreads();
-      project_l1(sh.fv, d, Rf, sh);
+      if (pen) {
+        // proximal step of lambda ||.||_1: soft threshold at lambda / L
+        const float tau = Rf / Lip;
+        for (int j = threadIdx.x; j < d; j += blockDim.x) {
+          const float u = fabsf(sh.fv[j]) - tau;
+          sh.fv[j] = u > 0.f ? copysignf(u, sh.fv[j]) : 0.f;
+        }
+        __syncthreads();
+      } else {
+        project_l1(sh.fv, d, Rf, sh);
+      }
       const float tn = 0.5f * (1.f + sqrtf(1.f + 4.f * tk * tk));
       const float mom = (tk - 1.f) / tn;
       for (int j = threadIdx.x; j < d; j += blockDim.x) {
@@ -535,8 +561,8 @@ __global__ void __launch_bounds__(kQpThreads, 1) k_l1_step(
         const unsigned long long sig = support_of(sh.fx, d, sh);
         const bool stable = sig == prev_sig;
         prev_sig = sig;
-        if (sh.k > 0 && sig != failed_sig && (sh.k <= FaceSm<TF>::n || stable)) {
-          if (face_solve<TF>(H, d, R, sh.fx, Ls, ld, wv, Ms, sh) &&
+        if ((sh.k > 0 || pen) && sig != failed_sig && (sh.k <= FaceSm<TF>::n || stable)) {
+          if (face_solve<TF>(H, d, R, pen, sh.fx, Ls, ld, wv, Ms, sh) &&
               face_accept<TF>(Hf, d, sh.fx, tol, x, sh))
             done = true;
           else
@@ -562,7 +588,7 @@ __global__ void __launch_bounds__(kQpThreads, 1) k_l1_step(
   double mx = j0 < d ? fabs(xj - sh.xt[j0]) : 0.0;
   for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
   __shared__ int wcnt[33];
-  const bool nz = (l1 >= R * (1.0 - 1e-12)) && j0 < d && xj != 0.0;
+  const bool nz = (pen || l1 >= R * (1.0 - 1e-12)) && j0 < d && xj != 0.0;
   const unsigned bal = __ballot_sync(0xffffffffu, nz);
   if ((threadIdx.x & 31) == 0) {
     sh.redd[threadIdx.x >> 5] = mx;
@@ -593,7 +619,7 @@ __global__ void k_to_float(const double* __restrict__ a, int64_t n, float* __res
 
 cudaError_t launch_l1_step(const double* H, const void* Lbuf, const void* Dinv, int f32, int d,
                            const double* g,
-                           double R, int max_iter, double tol, QpWork w, double* x,
+                           double R, int pen, int max_iter, double tol, QpWork w, double* x,
                            double* step_norm, int* status, cudaStream_t st) {
   if (d > kQpMaxD) return cudaErrorInvalidValue;
   const int64_t dd = (int64_t)d * d;
@@ -602,8 +628,10 @@ cudaError_t launch_l1_step(const double* H, const void* Lbuf, const void* Dinv, 
   if (e != cudaSuccess) return e;
   double* du = w.dbuf;              // d
   double* wv = w.dbuf + d;          // 2d doubles of face-solve scratch
-  e = launch_chol_apply(Lbuf, Dinv, d, f32, g, du, st);
-  if (e != cudaSuccess) return e;
+  if (!pen) {
+    e = launch_chol_apply(Lbuf, Dinv, d, f32, g, du, st);
+    if (e != cudaSuccess) return e;
+  }
   const size_t base = (sizeof(QpShared) + 15) / 16 * 16;
   const size_t smem = base + (f32 ? FaceSm<float>::bytes : FaceSm<double>::bytes);
   const int ld = chol_padded(d);
@@ -616,7 +644,7 @@ cudaError_t launch_l1_step(const double* H, const void* Lbuf, const void* Dinv, 
       if (e != cudaSuccess) return e;
       attr = true;
     }
-    { k_l1_step<float><<<1, kQpThreads, smem, st>>>(H, w.Hf, d, g, du, R, max_iter, tl, x,
+    { k_l1_step<float><<<1, kQpThreads, smem, st>>>(H, w.Hf, d, g, du, R, pen, max_iter, tl, x,
                                                   step_norm, w.support, w.iters, wv,
                                                   (float*)w.Ls, ld, w.evec, status); note_launches(1); }
   } else {
@@ -627,7 +655,7 @@ cudaError_t launch_l1_step(const double* H, const void* Lbuf, const void* Dinv, 
       if (e != cudaSuccess) return e;
       attr = true;
     }
-    { k_l1_step<double><<<1, kQpThreads, smem, st>>>(H, w.Hf, d, g, du, R, max_iter, tl, x,
+    { k_l1_step<double><<<1, kQpThreads, smem, st>>>(H, w.Hf, d, g, du, R, pen, max_iter, tl, x,
                                                    step_norm, w.support, w.iters, wv,
                                                    (double*)w.Ls, ld, w.evec, status); note_launches(1); }
   }

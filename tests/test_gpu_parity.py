@@ -372,3 +372,81 @@ def test_sketch_error_matches_oracle(cuda_lib, kind, s):
         e = sv.sketch_error(t, G)
         eo = O.sketch_error(Ao, kw["m"], s, 9, t)
         assert abs(e - eo) <= 1e-10 * eo, (t, e, eo)
+
+
+def _pen_lambda(C, b, frac):
+    return frac * float(np.abs(C.rmatvec(b)).max())
+
+
+def test_l1_penalty_step_matches_oracle_qp(cuda_lib):
+    """One penalised-LASSO step (argmin 1/2 ||S A (x - x^t)||^2 - g^T (x - x^t)
+    + lambda ||x||_1) on the GPU equals the oracle's exact solution on the same
+    H and g; the solution is unique."""
+    w, C = _csr_problem("lasso_csr_fp64", 40000, 60, 600)
+    lam = _pen_lambda(C, w["b"], 0.05)
+    solver = cuda_lib.IHS((dev(w["rowptr"]), dev(w["col"]), dev(w["val"])), dev(w["b"]),
+                          kind="l1pen", param=lam, m=600, s=4, seed=0, precision="fp64",
+                          shape=(w["n"], w["d"]))
+    x = torch.zeros(w["d"], dtype=torch.float64, device="cuda")
+    xo = np.zeros(w["d"])
+    for t in range(4):
+        solver.sketch(t)
+        SA, H, _ = solver.get_sketch()
+        g = solver.gradient(x).cpu().numpy()
+        solver.step(x)
+        solver.sync()
+        xq = O.l1_penalty_qp(H.cpu().numpy(), g, xo.copy(), lam)
+        assert 0 < np.count_nonzero(xq) < w["d"]
+        xo = xq
+        assert rel(x.cpu().numpy(), xq) < 1e-11, t
+        x.copy_(dev(xq))
+
+
+def test_ihs_lasso_penalty_plain_matches_oracle_every_iteration(cuda_lib):
+    """Penalised LASSO, CSR FP64 data, SJLT s = 4: every GPU iterate within
+    1e-11 of the oracle's (A-seminorm, relative to x_OPT), and 1e-10 of x_OPT
+    after 25 iterations."""
+    w, C = _csr_problem("lasso_csr_fp64", 100000, 200, 2000)
+    lam = _pen_lambda(C, w["b"], 0.02)
+    G = C.gram()
+    xo = O.x_opt_l1_penalty(C, w["b"], lam)
+    assert 0 < np.count_nonzero(xo) < w["d"]
+    xs = O.ihs(C, w["b"], O.L1_PENALTY, lam, 2000, 4, 0, 25)
+    solver = cuda_lib.IHS((dev(w["rowptr"]), dev(w["col"]), dev(w["val"])), dev(w["b"]),
+                          kind="l1pen", param=lam, m=2000, s=4, seed=0, precision="fp64",
+                          shape=(w["n"], w["d"]))
+    x = torch.zeros(w["d"], dtype=torch.float64, device="cuda")
+    nrm = np.sqrt(xo @ G @ xo)
+    for t in range(25):
+        solver.sketch(t)
+        solver.step(x)
+        e = x.cpu().numpy() - xs[t + 1]
+        assert np.sqrt(max(e @ G @ e, 0)) / nrm <= 1e-11, t
+    solver.sync()
+    assert O.err_A(x.cpu().numpy(), xo, G) < 1e-10
+
+
+def test_ihs_lasso_penalty_mixed_lambda5(cuda_lib):
+    """The experiments' setting, lambda = 5, mixed form on Zipf-column CSR FP32
+    data (SJLT s = 8): 1e-10 of x_OPT."""
+    w, C = _csr_problem("lasso_csr_zipf", 200000, 100, 1000)
+    G = C.gram()
+    xo = O.x_opt_l1_penalty(C, w["b"], 5.0)
+    solver = cuda_lib.IHS((dev(w["rowptr"]), dev(w["col"]), dev(w["val"])), dev(w["b"]),
+                          kind="l1pen", param=5.0, m=1000, s=8, seed=0, precision="tf32",
+                          shape=(w["n"], w["d"]))
+    x, rep = solver.solve(iters=30)
+    assert rep.status == 0
+    assert O.err_A(x.cpu().numpy(), xo, G) < 1e-10
+
+
+def test_l1_penalty_zero_solution(cuda_lib):
+    """lambda >= ||A^T b||_inf: x_OPT = 0, reached exactly in one step."""
+    w, C = _csr_problem("lasso_csr_fp64", 20000, 30, 300)
+    lam = _pen_lambda(C, w["b"], 1.01)
+    solver = cuda_lib.IHS((dev(w["rowptr"]), dev(w["col"]), dev(w["val"])), dev(w["b"]),
+                          kind="l1pen", param=lam, m=300, s=1, seed=0, precision="fp64",
+                          shape=(w["n"], w["d"]))
+    x, rep = solver.solve(iters=2)
+    assert rep.status == 0
+    assert torch.count_nonzero(x).item() == 0
