@@ -474,6 +474,65 @@ def run_sketch_quality(args):
             del sv
 
 
+def run_workloads(args):
+    """Time every workload of the suite (and the penalised-LASSO form on the
+    two sparse ones, lambda = 5) through ihs_solve: CUDA events around the
+    call, median of `--steps` runs after one warm-up, plus the library's stage
+    times (one serial-mode run: every stage on one stream) and launch count.
+    The dense 1,048,576 x 500 OLS line is the main benchmark's step.  One JSON
+    line per case."""
+    import torch
+    import paper_1910_14166_gb300 as ihs
+    cases = [("ols_dense_fp64", None, None), ("lasso_csr_fp64", None, None),
+             ("ols_dense_ar1", None, None), ("ridge_dense", None, None),
+             ("lasso_csr_zipf", None, None), ("lasso_csr_fp64", "l1pen", 5.0),
+             ("lasso_csr_zipf", "l1pen", 5.0)]
+    for name, kind_o, param_o in cases:
+        if args.only and name not in args.only.split(","):
+            continue
+        w = synth.make(name, seed=0)
+        b = torch.from_numpy(w["b"]).cuda()
+        if "A" in w:
+            A, shape = torch.from_numpy(w["A"]).cuda(), None
+        else:
+            A = tuple(torch.from_numpy(w[k]).cuda() for k in ("rowptr", "col", "val"))
+            shape = (w["n"], w["d"])
+        kind = kind_o or {"ols": "ols", "l1": "l1", "ridge": "ridge"}[w["kind"]]
+        param = w["param"] if param_o is None else param_o
+        iters = w["iters"] or 25
+        times = []
+        for serial in (False, True):
+            sv = ihs.IHS(A, b, kind=kind, param=param, m=w["m"], s=w["s"], seed=0,
+                         precision=w["precision"], shape=shape, serial=serial)
+            x0 = torch.zeros(w["d"], dtype=torch.float64, device="cuda")
+            sv.solve(x0.clone(), iters=iters)  # warm-up
+            if serial:
+                sv.profile(True)
+                sv.solve(x0.clone(), iters=iters)
+                ms, cnt, launches = sv.profile_read()
+                stages = {k: round(v / iters, 4) for k, v in ms.items()}
+            else:
+                for _ in range(max(1, args.steps)):
+                    x = x0.clone()
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    torch.cuda.synchronize()
+                    e0.record()
+                    _, rep = sv.solve(x, iters=iters)
+                    e1.record()
+                    torch.cuda.synchronize()
+                    times.append(e0.elapsed_time(e1))
+                    status = rep.status
+                    fista = rep.qp_fista_iters
+            del sv
+        print(json.dumps({
+            "experiment": "workloads", "workload": name, "kind": kind, "param": param,
+            "n": w["n"], "d": w["d"], "m": w["m"], "s": w["s"], "precision": w["precision"],
+            "iters": iters, "solve_ms_median": statistics.median(times), "solve_ms_all": times,
+            "status": status, "qp_fista_iters": fista, "stage_ms_per_iter_serial": stages,
+            "launches_per_solve": launches}), flush=True)
+        del A, b
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -489,7 +548,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-two-pass", action="store_true")
-    ap.add_argument("--experiment", default=None, choices=["sketch-quality"],
+    ap.add_argument("--only", default=None, help="workloads experiment: comma-separated names")
+    ap.add_argument("--experiment", default=None, choices=["sketch-quality", "workloads"],
                     help="run an experiment instead of the benchmark (one JSON line per point)")
     ap.add_argument("--trials", type=int, default=10)
     ap.add_argument("--seed", type=int, default=0)
@@ -500,6 +560,9 @@ def main():
         return
     if args.experiment == "sketch-quality":
         run_sketch_quality(args)
+        return
+    if args.experiment == "workloads":
+        run_workloads(args)
         return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -482,7 +482,9 @@ ihs_status ihs_create(ihs_ctx** out, const ihs_matrix* A, const double* b,
     c->qw.dbuf = (double*)(q + dd * dd * 4 + (size_t)dp * dp * 8) + dd;
     c->qw.support = (int*)(c->qw.dbuf + 8 * dd);
     c->qw.iters = c->qw.support + dd + 1;
-    if (cudaMemsetAsync(c->qw.support, 0, (dd + 2) * sizeof(int), c->st) != cudaSuccess ||
+    c->qw.need = c->qw.iters + 1;
+    if (C->kind == IHS_L1_PENALTY) AL2(c->qw.Hinv, (size_t)dd * dd * (c->f32fac ? 4 : 8));
+    if (cudaMemsetAsync(c->qw.support, 0, (dd + 3) * sizeof(int), c->st) != cudaSuccess ||
         cudaMemsetAsync(c->qw.evec, 0, dd * sizeof(float), c->st) != cudaSuccess)
       return fail(IHS_ERR_CUDA);
   }

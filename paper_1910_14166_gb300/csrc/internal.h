@@ -144,6 +144,11 @@ cudaError_t launch_cholesky(const double* H, int d, int f32, void* Lbuf, void* D
 cudaError_t launch_chol_step(const void* Lbuf, const void* Dinv, int d, int f32, const double* g,
                              double* x, double* step_norm, cudaStream_t st);
 // delta = (L L^T)^{-1} v (no update), for preconditioning.
+// H^{-1} (d x d, factor precision) from the factor, skipped when need && !*need;
+// the shared memory it needs (must be <= 220 KB: FP32 any d <= 1024, FP64 d <= 832).
+size_t chol_inverse_smem_bytes(int d, int f32);
+cudaError_t launch_chol_inverse(const void* Lbuf, const void* Dinv, int d, int f32, void* Hinv,
+                                const int* need, cudaStream_t st);
 cudaError_t launch_chol_apply(const void* Lbuf, const void* Dinv, int d, int f32, const double* v,
                               double* out, cudaStream_t st);
 
@@ -156,6 +161,8 @@ struct QpWork {
   int* support;    // d ints, previous face (count in support[d])
   double* dbuf;    // 8 * d doubles of scratch
   int* iters;      // FISTA iterations (device counter)
+  int* need;       // penalised form: the step is still open after the previous pass
+  void* Hinv;      // penalised form: H^{-1} (d x d, factor precision), or null
 };
 size_t qp_work_bytes(int d);
 // The l1 step of Eq. 2: over the ball ||x||_1 <= param (pen = 0) or with the

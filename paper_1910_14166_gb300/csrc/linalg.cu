@@ -570,3 +570,135 @@ cudaError_t launch_chol_apply(const void* Lbuf, const void* Dinv, int d, int f32
              : solve_impl<double>((const double*)Lbuf, (const double*)Dinv, d, v, out, nullptr, 1,
                                   st);
 }
+
+// ----------------------------------------------------------------------------
+// H^{-1} = L^{-T} L^{-1} from the factor, one CTA per 32-column block c of the
+// identity (used by the penalised l1 step's active-set pass, which needs
+// arbitrary columns of the inverse):
+//   forward   Y_k = D_k (E_kc - sum_{c <= j < k} L_kj Y_j)   for k >= c
+//             (Y_k = 0 for k < c: L is lower triangular),
+//   backward  X_k = D_k^T (Y_k - sum_{j > k} (L^T)_kj X_j)   for k = Tt-1..0,
+// with the Y / X tiles in shared memory and each thread reading its row of
+// every L tile straight from global memory (eight threads share a row, so
+// L1 serves most of it).  Skipped entirely when *need == 0.
+// ----------------------------------------------------------------------------
+template <typename T>
+size_t chol_inverse_smem(int Tt) { return (size_t)(Tt + 1) * 32 * 33 * sizeof(T); }
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_chol_inverse(const T* __restrict__ L,
+                                                      const T* __restrict__ Dinv, int d, int dp,
+                                                      T* __restrict__ Hinv,
+                                                      const int* __restrict__ need) {
+  if (need && *need == 0) return;
+  extern __shared__ __align__(16) unsigned char inv_smem[];
+  typedef T Row[33];
+  Row* Ys = reinterpret_cast<Row*>(inv_smem);  // Tt tiles of 32 rows: rows k*32.., this column block
+  Row* Tmp = Ys + dp;                          // one tile: staging for the D_k products
+  const int Tt = dp / 32, c = blockIdx.x, tid = threadIdx.x;
+  const int a = tid >> 3, b0 = (tid & 7) * 4;
+  for (int k = 0; k < c; ++k)
+    for (int e = tid; e < 1024; e += blockDim.x) Ys[k * 32 + (e >> 5)][e & 31] = T(0);
+  // forward
+  for (int k = c; k < Tt; ++k) {
+    T acc[4];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) acc[v] = (k == c && a == b0 + v) ? T(1) : T(0);
+    const T* Lrow = L + (int64_t)(k * 32 + a) * dp;
+    for (int j = c; j < k; ++j) {
+      const T* lr = Lrow + j * 32;
+#pragma unroll 8
+      for (int q = 0; q < 32; ++q) {
+        const T l = __ldg(lr + q);
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[v] -= l * Ys[(j) * 32 + q][b0 + v];
+      }
+    }
+#pragma unroll
+    for (int v = 0; v < 4; ++v) Tmp[a][b0 + v] = acc[v];
+    __syncthreads();
+    const T* Dr = Dinv + (int64_t)k * 1024 + a * 32;  // row a of D_k
+    T out[4] = {T(0), T(0), T(0), T(0)};
+#pragma unroll 8
+    for (int q = 0; q < 32; ++q) {
+      const T dq = __ldg(Dr + q);
+#pragma unroll
+      for (int v = 0; v < 4; ++v) out[v] += dq * Tmp[q][b0 + v];
+    }
+#pragma unroll
+    for (int v = 0; v < 4; ++v) Ys[(k) * 32 + a][b0 + v] = out[v];
+    __syncthreads();
+  }
+  // backward (X_k overwrites Y_k)
+  for (int k = Tt - 1; k >= 0; --k) {
+    T acc[4];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) acc[v] = Ys[(k) * 32 + a][b0 + v];
+    const T* Urow = L + (int64_t)(k * 32 + a) * dp;  // row of the stored L^T tiles (k, j)
+    for (int j = k + 1; j < Tt; ++j) {
+      const T* ur = Urow + j * 32;
+#pragma unroll 8
+      for (int q = 0; q < 32; ++q) {
+        const T u = __ldg(ur + q);
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[v] -= u * Ys[(j) * 32 + q][b0 + v];
+      }
+    }
+#pragma unroll
+    for (int v = 0; v < 4; ++v) Tmp[a][b0 + v] = acc[v];
+    __syncthreads();
+    const T* Dc = Dinv + (int64_t)k * 1024 + a;  // column a of D_k
+    T out[4] = {T(0), T(0), T(0), T(0)};
+#pragma unroll 8
+    for (int q = 0; q < 32; ++q) {
+      const T dq = __ldg(Dc + q * 32);
+#pragma unroll
+      for (int v = 0; v < 4; ++v) out[v] += dq * Tmp[q][b0 + v];
+    }
+#pragma unroll
+    for (int v = 0; v < 4; ++v) Ys[(k) * 32 + a][b0 + v] = out[v];
+    __syncthreads();
+  }
+  for (int e = tid; e < dp * 32; e += blockDim.x) {
+    const int r = e >> 5, cc = e & 31, col = c * 32 + cc;
+    if (r < d && col < d) Hinv[(int64_t)r * d + col] = Ys[r][cc];
+  }
+}
+
+size_t chol_inverse_smem_bytes(int d, int f32) {
+  const int Tt = chol_padded(d) / 32;
+  return f32 ? chol_inverse_smem<float>(Tt) : chol_inverse_smem<double>(Tt);
+}
+
+cudaError_t launch_chol_inverse(const void* Lbuf, const void* Dinv, int d, int f32, void* Hinv,
+                                const int* need, cudaStream_t st) {
+  const int dp = chol_padded(d), Tt = dp / 32;
+  const size_t smem = chol_inverse_smem_bytes(d, f32);
+  if (smem > 220 * 1024) return cudaErrorInvalidValue;
+  cudaError_t e;
+  if (f32) {
+    static bool attr = false;
+    if (!attr) {
+      if ((e = cudaFuncSetAttribute(k_chol_inverse<float>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024)) !=
+          cudaSuccess)
+        return e;
+      attr = true;
+    }
+    k_chol_inverse<float><<<Tt, 256, smem, st>>>((const float*)Lbuf, (const float*)Dinv, d, dp,
+                                                 (float*)Hinv, need);
+  } else {
+    static bool attr = false;
+    if (!attr) {
+      if ((e = cudaFuncSetAttribute(k_chol_inverse<double>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024)) !=
+          cudaSuccess)
+        return e;
+      attr = true;
+    }
+    k_chol_inverse<double><<<Tt, 256, smem, st>>>((const double*)Lbuf, (const double*)Dinv, d,
+                                                  dp, (double*)Hinv, need);
+  }
+  note_launches(1);
+  return cudaGetLastError();
+}

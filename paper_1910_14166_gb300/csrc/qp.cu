@@ -19,9 +19,11 @@
 // DEV_NOT_CONVERGED and leaves the last feasible FISTA point.
 //
 // The penalised form (the experiments' LASSO, Sec. 5: + lambda ||x||_1
-// instead of the ball) takes the same path without the Newton point: the
-// previous face (x = 0 included), then proximal FISTA (soft threshold at
-// lambda / L) with periodic faces, whose system has no border,
+// instead of the ball) takes the same path: the full face first (every index
+// in the support, signs from x^t, else from H^{-1} g: one more solve with the
+// sketched factor, the answer when no sign changes), the previous face (x = 0
+// included), then proximal FISTA (soft threshold at lambda / L) with periodic
+// faces, whose system has no border,
 //     H_SS dS = g_S + H_{S,S^c} x^t_{S^c} - lambda sigma,
 // and whose off-support test is |(H (x - x^t) - g)_j| <= lambda.
 #include <cuda_runtime.h>
@@ -47,7 +49,7 @@ struct FaceSm {
 
 size_t qp_work_bytes(int d) {
   const size_t dp = (size_t)chol_padded(d);
-  return (size_t)d * d * 4 + dp * dp * 8 + (size_t)9 * d * 8 + (size_t)(d + 2) * 4 + 256;
+  return (size_t)d * d * 4 + dp * dp * 8 + (size_t)9 * d * 8 + (size_t)(d + 3) * 4 + 256;
 }
 
 // ---- block reductions (1024 threads) --------------------------------------
@@ -390,6 +392,56 @@ __device__ bool face_accept(const float* __restrict__ Hf, int d, const float* si
   return true;
 }
 
+// Sign used for index j by the penalised full face: that of x^t_j, else that
+// of u_j = (H^{-1} g)_j, else 0 (no sign: the full face is not tried).
+__host__ __device__ __forceinline__ double pen_sign(double xt, double u) {
+  if (xt != 0.0) return xt > 0.0 ? 1.0 : -1.0;
+  return u > 0.0 ? 1.0 : (u < 0.0 ? -1.0 : 0.0);
+}
+
+// rhs_j = g_j - lambda pen_sign(x^t_j, u_j)
+__global__ void k_pen_rhs(const double* __restrict__ xt, const double* __restrict__ g,
+                          const double* __restrict__ u, double lam, int d,
+                          double* __restrict__ rhs) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < d; j += gridDim.x * blockDim.x)
+    rhs[j] = g[j] - lam * pen_sign(xt[j], u[j]);
+}
+
+// After a step: record the support of the new x (indices in increasing
+// order; for the ball only when x lies on the sphere) for the next step's
+// first face, and the step size max |x - x^t|.  d <= blockDim.x.
+__device__ void qp_epilogue(const double* x, const double* xt, int d, double R, bool pen,
+                            double* step_norm, int* support, double* redd) {
+  __syncthreads();
+  const int j0 = threadIdx.x;
+  const double xj = j0 < d ? x[j0] : 0.0;
+  const double l1 = block_sum(fabs(xj), redd);
+  double mx = j0 < d ? fabs(xj - xt[j0]) : 0.0;
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  __shared__ int wcnt[33];
+  const bool nz = (pen || l1 >= R * (1.0 - 1e-12)) && j0 < d && xj != 0.0;
+  const unsigned bal = __ballot_sync(0xffffffffu, nz);
+  if ((threadIdx.x & 31) == 0) {
+    redd[threadIdx.x >> 5] = mx;
+    wcnt[threadIdx.x >> 5] = __popc(bal);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double m = 0.0;
+    int acc = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      m = fmax(m, redd[w]);
+      const int c = wcnt[w];
+      wcnt[w] = acc;
+      acc += c;
+    }
+    *step_norm = m;
+    support[d] = acc;
+  }
+  __syncthreads();
+  if (nz) support[wcnt[threadIdx.x >> 5] + __popc(bal & lanemask_lt())] = j0;
+}
+
 // Support of v (indices in increasing order) into sh.S / sh.k, and an
 // order-free signature of (support, signs) returned to every thread.
 // d <= blockDim.x: one entry per thread.
@@ -429,21 +481,28 @@ __device__ unsigned long long support_of(const float* v, int d, QpShared& sh) {
 template <typename TF>
 __global__ void __launch_bounds__(kQpThreads, 1) k_l1_step(
     const double* __restrict__ H, const float* __restrict__ Hf, int d,
-    const double* __restrict__ g, const double* __restrict__ du, double R, int pen, int max_iter,
+    const double* __restrict__ g, const double* __restrict__ du, const double* __restrict__ uvec,
+    double R, int pen, int phase, int* __restrict__ need, int max_iter,
     double tol, double* __restrict__ x, double* __restrict__ step_norm, int* __restrict__ support,
     int* __restrict__ iters, double* __restrict__ wv, TF* __restrict__ Ls, int ld,
     float* __restrict__ evec, int* status) {
   extern __shared__ __align__(16) unsigned char qp_smem[];
   QpShared& sh = *reinterpret_cast<QpShared*>(qp_smem);
   TF* Ms = reinterpret_cast<TF*>(qp_smem + (sizeof(QpShared) + 15) / 16 * 16);
+  // phase 1 (penalised form): only if the earlier passes left the step open
+  if (phase == 1 && *need == 0) return;
   for (int j = threadIdx.x; j < d; j += blockDim.x) {
     sh.xt[j] = x[j];
     sh.gd[j] = g[j];
     sh.fxt[j] = (float)x[j];
   }
   __syncthreads();
-  bool done = false;
-  // 1. Newton point (the ball form only; du is not formed for the penalty)
+  bool done = phase == 1;
+  // 1. Newton point.  Ball: du = H^{-1} g; x^t + du is the answer if it lies
+  //    in the ball.  Penalty: du = H^{-1} (g - lambda sigma) with sigma the
+  //    signs of x^t (of H^{-1} g where x^t is 0), the stationary point of the
+  //    face with every index in the support; it is the answer if no sign
+  //    changes and no entry is zero.
   if (!pen) {
     double a = 0.0;
     for (int j = threadIdx.x; j < d; j += blockDim.x) a += fabs(sh.xt[j] + du[j]);
@@ -453,13 +512,30 @@ __global__ void __launch_bounds__(kQpThreads, 1) k_l1_step(
       if (threadIdx.x == 0) support[d] = 0;
       done = true;
     }
+  } else if (!done) {
+    __shared__ int flips;
+    if (threadIdx.x == 0) flips = 0;
+    __syncthreads();
+    for (int j = threadIdx.x; j < d; j += blockDim.x) {
+      const double sj = pen_sign(sh.xt[j], uvec[j]);
+      const double xn = sh.xt[j] + du[j];
+      if (!(sj * xn > 0.0)) flips = 1;
+    }
+    __syncthreads();
+    if (!flips) {
+      for (int j = threadIdx.x; j < d; j += blockDim.x) x[j] = sh.xt[j] + du[j];
+      done = true;
+    }
+    __syncthreads();
   }
   // 2. previous face (signs of x^t on the stored support; in the penalised
   //    form an empty support is the face x = 0, tried too)
   if (!done) {
     if (threadIdx.x == 0) sh.k = support[d];
     __syncthreads();
-    if (sh.k > 0 || pen) {
+    // (penalised form: a face too large for shared memory is left to the
+    // active-set pass, which works on its small zero set instead)
+    if ((sh.k > 0 || pen) && !(pen && sh.k > FaceSm<TF>::n)) {
       for (int a = threadIdx.x; a < sh.k; a += blockDim.x) sh.S[a] = support[a];
       for (int j = threadIdx.x; j < d; j += blockDim.x) sh.fv[j] = sh.fxt[j];
       __syncthreads();
@@ -479,6 +555,12 @@ __global__ void __launch_bounds__(kQpThreads, 1) k_l1_step(
       }
     }
     __syncthreads();
+  }
+  if (phase == 1) done = false;
+  // penalised form, phase 0: leave the rest to the active-set pass and phase 1
+  if (pen && phase == 0 && !done) {
+    if (threadIdx.x == 0) *need = 1;
+    return;
   }
   // 3. FISTA + periodic face solves
   if (!done) {
@@ -580,35 +662,199 @@ __global__ void __launch_bounds__(kQpThreads, 1) k_l1_step(
     }
   }
   __syncthreads();
-  // record the support of the new x (in index order; empty unless x lies on
-  // the sphere) and the step size; d <= blockDim.x, one entry per thread
-  const int j0 = threadIdx.x;
-  const double xj = j0 < d ? x[j0] : 0.0;
-  const double l1 = block_sum(fabs(xj), sh.redd);
-  double mx = j0 < d ? fabs(xj - sh.xt[j0]) : 0.0;
-  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-  __shared__ int wcnt[33];
-  const bool nz = (pen || l1 >= R * (1.0 - 1e-12)) && j0 < d && xj != 0.0;
-  const unsigned bal = __ballot_sync(0xffffffffu, nz);
-  if ((threadIdx.x & 31) == 0) {
-    sh.redd[threadIdx.x >> 5] = mx;
-    wcnt[threadIdx.x >> 5] = __popc(bal);
+  qp_epilogue(x, sh.xt, d, R, pen, step_norm, support, sh.redd);
+  if (threadIdx.x == 0 && need) *need = 0;
+}
+
+// ----------------------------------------------------------------------------
+// Penalised form, active-set pass (a primal-dual active-set method, i.e. a
+// semismooth Newton method on the optimality conditions; Hintermueller, Ito &
+// Kunisch 2002).  Faces whose zero set Z is small -- the common case for
+// lambda small against A^T b, where the support covers most indices -- are
+// solved with H^{-1} at hand (from the sketched factor): the face with zero
+// set Z and signs sigma elsewhere is the KKT system
+//     H dl + E_Z nu = g - lambda sigma~,   E_Z^T (x^t + dl) = 0
+// (sigma~ = sigma off Z, 0 on Z): p = H^{-1}(g - lambda sigma~),
+// nu = ((H^{-1})_ZZ)^{-1} (p_Z + x^t_Z), dl = p - (H^{-1})_{:,Z} nu, refined
+// with FP64 residuals of that system.  The point is the answer when every
+// index off Z keeps its sign and |nu_j| <= lambda on Z (nu_j = -(H dl - g)_j
+// there).  Each round takes the signs and zeros from the current point x and
+// its dual y = g - H (x - x^t) by the diagonally scaled proximal rule
+// sigma_j = sign(z_j) if |z_j| > lambda else 0, z_j = H_jj x_j + y_j,
+// starting from x = x^t, y = g; at most kActiveRounds rounds,
+// |Z| <= FaceSm<TF>::n, and a repeated pattern ends the pass.
+constexpr int kActiveRounds = 32;
+
+struct PenShared {
+  double xt[kQpMaxD], gd[kQpMaxD], dl[kQpMaxD], p[kQpMaxD], v[kQpMaxD], r1[kQpMaxD];
+  int Z[kQpMaxD];
+  int pos[kQpMaxD];  // index in Z, or -1
+  signed char sg[kQpMaxD];
+  int zc;
+  int flag, best;
+  double bestv;
+  double redd[33];
+};
+
+// out_j = sum_i M[j, i] v_i (FP64 accumulation), M d x d row-major in TM
+template <typename TM>
+__device__ void matvec_d(const TM* __restrict__ M, int d, const double* v, double* out) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int j = w; j < d; j += (int)(blockDim.x >> 5)) {
+    const TM* row = M + (int64_t)j * d;
+    double s = 0.0;
+    for (int i = lane; i < d; i += 32) s = fma((double)row[i], v[i], s);
+    s = warp_sum(s);
+    if (lane == 0) out[j] = s;
   }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double m = 0.0;
-    int acc = 0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-      m = fmax(m, sh.redd[w]);
-      const int c = wcnt[w];
-      wcnt[w] = acc;
-      acc += c;
+}
+
+// out_j = base_j - sum_a Hinv[j, Z_a] nu_a
+template <typename TF>
+__device__ void sub_cols(const TF* __restrict__ Hinv, int d, const int* Z, int zc, const double* nu,
+                         const double* base, double* out) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int j = w; j < d; j += (int)(blockDim.x >> 5)) {
+    const TF* row = Hinv + (int64_t)j * d;
+    double s = 0.0;
+    for (int a = lane; a < zc; a += 32) s = fma((double)row[Z[a]], nu[a], s);
+    s = warp_sum(s);
+    if (lane == 0) out[j] = base[j] - s;
+  }
+}
+
+template <typename TF>
+__global__ void __launch_bounds__(kQpThreads, 1) k_pen_active(
+    const double* __restrict__ H, const TF* __restrict__ Hinv, int d,
+    const double* __restrict__ g, const double* __restrict__ du, const double* __restrict__ uvec,
+    double lam, double* __restrict__ x, double* __restrict__ step_norm,
+    int* __restrict__ support, int* __restrict__ need) {
+  if (*need == 0) return;
+  extern __shared__ __align__(16) unsigned char pa_smem[];
+  PenShared& P = *reinterpret_cast<PenShared*>(pa_smem);
+  TF* M = reinterpret_cast<TF*>(pa_smem + (sizeof(PenShared) + 15) / 16 * 16);
+  constexpr int zmax = FaceSm<TF>::n, ld = FaceSm<TF>::ld;
+  double* nu = reinterpret_cast<double*>(M + (size_t)zmax * ld);
+  double* nu2 = nu + zmax;
+  const int tid = threadIdx.x;
+  for (int j = tid; j < d; j += blockDim.x) {
+    P.xt[j] = x[j];
+    P.gd[j] = g[j];
+    P.dl[j] = 0.0;       // x - x^t
+    P.r1[j] = g[j];      // y = g - H (x - x^t)
+  }
+  __shared__ int changed;
+  bool accepted = false;
+  for (int round = 0; round < kActiveRounds; ++round) {
+    __syncthreads();
+    // signs and zeros from the current point and its dual
+    if (tid == 0) changed = (round == 0);
+    __syncthreads();
+    for (int j = tid; j < d; j += blockDim.x) {
+      const double xj = (round == 0) ? P.xt[j] : (P.sg[j] == 0 ? 0.0 : P.xt[j] + P.dl[j]);
+      const double z = H[(int64_t)j * d + j] * xj + P.r1[j];
+      const signed char sj = fabs(z) > lam ? (z > 0.0 ? 1 : -1) : 0;
+      if (round > 0 && sj != P.sg[j]) changed = 1;
+      P.sg[j] = sj;
     }
-    *step_norm = m;
-    support[d] = acc;
+    __syncthreads();
+    if (!changed) break;  // the same pattern again: no progress
+    // Z list in index order
+    if (tid == 0) {
+      int c = 0;
+      for (int j = 0; j < d; ++j) {
+        P.pos[j] = -1;
+        if (P.sg[j] == 0) {
+          if (c < kQpMaxD) P.Z[c] = j;
+          P.pos[j] = c;
+          ++c;
+        }
+      }
+      P.zc = c;
+    }
+    __syncthreads();
+    const int zc = P.zc;
+    if (zc > zmax) break;
+    for (int j = tid; j < d; j += blockDim.x) P.v[j] = P.gd[j] - lam * (double)P.sg[j];
+    __syncthreads();
+    matvec_d<TF>(Hinv, d, P.v, P.p);
+    __syncthreads();
+    // M = (H^{-1})_ZZ, factored in TF
+    for (int e = tid; e < zc * zc; e += blockDim.x) {
+      const int a = e / zc, b = e - a * zc;
+      M[a * ld + b] = Hinv[(int64_t)P.Z[a] * d + P.Z[b]];
+    }
+    __syncthreads();
+    if (!chol_sm<TF>(M, zc, ld)) break;
+    for (int a = tid; a < zc; a += blockDim.x) nu[a] = P.p[P.Z[a]] + P.xt[P.Z[a]];
+    __syncthreads();
+    chol_sm_solve<TF>(M, zc, ld, nu);
+    sub_cols<TF>(Hinv, d, P.Z, zc, nu, P.p, P.dl);
+    __syncthreads();
+    // FP64 refinement of the bordered system
+    const int nref = sizeof(TF) == 4 ? 2 : 1;
+    for (int it = 0; it < nref; ++it) {
+      matvec_d<double>(H, d, P.dl, P.r1);  // r1 = H dl
+      __syncthreads();
+      for (int j = tid; j < d; j += blockDim.x) {
+        const int a = P.pos[j];
+        P.r1[j] = P.v[j] - P.r1[j] - (a >= 0 ? nu[a] : 0.0);
+      }
+      __syncthreads();
+      matvec_d<TF>(Hinv, d, P.r1, P.p);  // p = H^{-1} r1
+      __syncthreads();
+      for (int a = tid; a < zc; a += blockDim.x)
+        nu2[a] = P.p[P.Z[a]] - (-P.xt[P.Z[a]] - P.dl[P.Z[a]]);
+      __syncthreads();
+      chol_sm_solve<TF>(M, zc, ld, nu2);
+      sub_cols<TF>(Hinv, d, P.Z, zc, nu2, P.p, P.r1);  // r1 <- correction
+      __syncthreads();
+      for (int j = tid; j < d; j += blockDim.x) P.dl[j] += P.r1[j];
+      for (int a = tid; a < zc; a += blockDim.x) nu[a] += nu2[a];
+      __syncthreads();
+    }
+    // optimality: signs off Z, |nu| <= lambda on Z
+    if (tid == 0) {
+      P.flag = 0;
+      P.best = -1;
+      P.bestv = 0.0;
+    }
+    __syncthreads();
+    for (int j = tid; j < d; j += blockDim.x) {
+      if (P.sg[j] != 0 && !((double)P.sg[j] * (P.xt[j] + P.dl[j]) > 0.0)) atomicOr(&P.flag, 1);
+    }
+    __syncthreads();
+    const double lim = lam * (1.0 + 1e-9);
+    if (tid == 0) {
+      for (int a = 0; a < zc; ++a) {
+        const double over = fabs(nu[a]) - lim;
+        if (over > P.bestv) {
+          P.bestv = over;
+          P.best = a;
+        }
+      }
+    }
+    __syncthreads();
+    if (P.flag == 0 && P.best < 0) {
+      for (int j = tid; j < d; j += blockDim.x) x[j] = P.sg[j] == 0 ? 0.0 : P.xt[j] + P.dl[j];
+      accepted = true;
+      break;
+    }
+    // dual at the new point: y = g - H dl (x - x^t = dl, with dl_Z = -x^t_Z)
+    matvec_d<double>(H, d, P.dl, P.r1);
+    __syncthreads();
+    for (int j = tid; j < d; j += blockDim.x) P.r1[j] = P.gd[j] - P.r1[j];
   }
   __syncthreads();
-  if (nz) support[wcnt[threadIdx.x >> 5] + __popc(bal & lanemask_lt())] = j0;
+  if (accepted) {
+    qp_epilogue(x, P.xt, d, lam, true, step_norm, support, P.redd);
+    if (tid == 0) *need = 0;
+  }
+}
+
+size_t pen_active_smem(int f32) {
+  const size_t base = (sizeof(PenShared) + 15) / 16 * 16;
+  return base + (f32 ? FaceSm<float>::bytes : FaceSm<double>::bytes);
 }
 
 __global__ void k_to_float(const double* __restrict__ a, int64_t n, float* __restrict__ b) {
@@ -628,36 +874,84 @@ cudaError_t launch_l1_step(const double* H, const void* Lbuf, const void* Dinv, 
   if (e != cudaSuccess) return e;
   double* du = w.dbuf;              // d
   double* wv = w.dbuf + d;          // 2d doubles of face-solve scratch
+  double* uvec = w.dbuf + 3 * d;    // penalty: H^{-1} g
+  double* rhs = w.dbuf + 4 * d;     // penalty: g - lambda sigma
   if (!pen) {
     e = launch_chol_apply(Lbuf, Dinv, d, f32, g, du, st);
+    if (e != cudaSuccess) return e;
+  } else {
+    e = launch_chol_apply(Lbuf, Dinv, d, f32, g, uvec, st);
+    if (e != cudaSuccess) return e;
+    { k_pen_rhs<<<(d + 255) / 256, 256, 0, st>>>(x, g, uvec, R, d, rhs); note_launches(1); }
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    e = launch_chol_apply(Lbuf, Dinv, d, f32, rhs, du, st);
     if (e != cudaSuccess) return e;
   }
   const size_t base = (sizeof(QpShared) + 15) / 16 * 16;
   const size_t smem = base + (f32 ? FaceSm<float>::bytes : FaceSm<double>::bytes);
   const int ld = chol_padded(d);
   const double tl = tol > 0 ? tol : 1e-12;
-  if (f32) {
-    static bool attr = false;
-    if (!attr) {
-      e = cudaFuncSetAttribute(k_l1_step<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)smem);
-      if (e != cudaSuccess) return e;
-      attr = true;
+  int* need = pen ? w.need : nullptr;
+  // the penalised form runs phase 0, the inverse and the active-set pass, then
+  // phase 1 (FISTA) -- each of the later ones exits at once if the step is done
+  const bool active = pen && w.Hinv && chol_inverse_smem_bytes(d, f32) <= 220 * 1024;
+  auto l1 = [&](int phase) -> cudaError_t {
+    cudaError_t e2;
+    if (f32) {
+      static bool attr = false;
+      if (!attr) {
+        e2 = cudaFuncSetAttribute(k_l1_step<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem);
+        if (e2 != cudaSuccess) return e2;
+        attr = true;
+      }
+      k_l1_step<float><<<1, kQpThreads, smem, st>>>(H, w.Hf, d, g, du, uvec, R, pen, phase, need,
+                                                    max_iter, tl, x, step_norm, w.support, w.iters,
+                                                    wv, (float*)w.Ls, ld, w.evec, status);
+    } else {
+      static bool attr = false;
+      if (!attr) {
+        e2 = cudaFuncSetAttribute(k_l1_step<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem);
+        if (e2 != cudaSuccess) return e2;
+        attr = true;
+      }
+      k_l1_step<double><<<1, kQpThreads, smem, st>>>(H, w.Hf, d, g, du, uvec, R, pen, phase, need,
+                                                     max_iter, tl, x, step_norm, w.support,
+                                                     w.iters, wv, (double*)w.Ls, ld, w.evec,
+                                                     status);
     }
-    { k_l1_step<float><<<1, kQpThreads, smem, st>>>(H, w.Hf, d, g, du, R, pen, max_iter, tl, x,
-                                                  step_norm, w.support, w.iters, wv,
-                                                  (float*)w.Ls, ld, w.evec, status); note_launches(1); }
-  } else {
-    static bool attr = false;
-    if (!attr) {
-      e = cudaFuncSetAttribute(k_l1_step<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)smem);
-      if (e != cudaSuccess) return e;
-      attr = true;
+    note_launches(1);
+    return cudaGetLastError();
+  };
+  if ((e = l1(0)) != cudaSuccess) return e;
+  if (!pen) return cudaSuccess;
+  if (active) {
+    if ((e = launch_chol_inverse(Lbuf, Dinv, d, f32, w.Hinv, need, st)) != cudaSuccess) return e;
+    const size_t ps = pen_active_smem(f32);
+    if (f32) {
+      static bool attr = false;
+      if (!attr) {
+        e = cudaFuncSetAttribute(k_pen_active<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)ps);
+        if (e != cudaSuccess) return e;
+        attr = true;
+      }
+      k_pen_active<float><<<1, kQpThreads, ps, st>>>(H, (const float*)w.Hinv, d, g, du, uvec, R,
+                                                     x, step_norm, w.support, need);
+    } else {
+      static bool attr = false;
+      if (!attr) {
+        e = cudaFuncSetAttribute(k_pen_active<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)ps);
+        if (e != cudaSuccess) return e;
+        attr = true;
+      }
+      k_pen_active<double><<<1, kQpThreads, ps, st>>>(H, (const double*)w.Hinv, d, g, du, uvec,
+                                                      R, x, step_norm, w.support, need);
     }
-    { k_l1_step<double><<<1, kQpThreads, smem, st>>>(H, w.Hf, d, g, du, R, pen, max_iter, tl, x,
-                                                   step_norm, w.support, w.iters, wv,
-                                                   (double*)w.Ls, ld, w.evec, status); note_launches(1); }
+    note_launches(1);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
-  return cudaGetLastError();
+  return l1(1);
 }
