@@ -118,9 +118,10 @@ enum { IHS_FLAG_NO_FUSE = 1, IHS_FLAG_SERIAL = 2, IHS_FLAG_CLUSTER = 4 };
 
 typedef struct {
   int iters;            /* iterations taken                                */
-  int qp_fista_iters;   /* l1 ball: FISTA iterations spent, summed          */
+  int qp_fista_iters;   /* l1 steps: FISTA iterations spent, summed         */
   int status;           /* ihs_status of the device status word             */
   double step_norm;     /* ||x^{t+1} - x^t||_inf of the last step            */
+  int qp_active_rounds; /* penalised l1: active-set rounds spent, summed     */
 } ihs_report;
 
 /* ihs_create -- validate (A, b, C, options) and allocate every workspace.

@@ -56,7 +56,8 @@ class _Options(ctypes.Structure):
 
 class _Report(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("qp_fista_iters", ctypes.c_int),
-                ("status", ctypes.c_int), ("step_norm", ctypes.c_double)]
+                ("status", ctypes.c_int), ("step_norm", ctypes.c_double),
+                ("qp_active_rounds", ctypes.c_int)]
 
 
 def _load():

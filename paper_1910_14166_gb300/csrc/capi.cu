@@ -484,7 +484,7 @@ ihs_status ihs_create(ihs_ctx** out, const ihs_matrix* A, const double* b,
     c->qw.iters = c->qw.support + dd + 1;
     c->qw.need = c->qw.iters + 1;
     if (C->kind == IHS_L1_PENALTY) AL2(c->qw.Hinv, (size_t)dd * dd * (c->f32fac ? 4 : 8));
-    if (cudaMemsetAsync(c->qw.support, 0, (dd + 3) * sizeof(int), c->st) != cudaSuccess ||
+    if (cudaMemsetAsync(c->qw.support, 0, (dd + 4) * sizeof(int), c->st) != cudaSuccess ||
         cudaMemsetAsync(c->qw.evec, 0, dd * sizeof(float), c->st) != cudaSuccess)
       return fail(IHS_ERR_CUDA);
   }
@@ -655,7 +655,10 @@ ihs_status ihs_sync(ihs_ctx* c) {
 // the step; double buffering keeps the step's factor intact.
 ihs_status ihs_solve(ihs_ctx* c, double* x, int64_t t0, int iters, ihs_report* rep) {
   if (!c || !x || iters < 0 || t0 < 0) return IHS_ERR_ARG;
-  if (c->qw.iters) CK(cudaMemsetAsync(c->qw.iters, 0, sizeof(int), c->st));
+  if (c->qw.iters) {
+    CK(cudaMemsetAsync(c->qw.iters, 0, sizeof(int), c->st));
+    CK(cudaMemsetAsync(c->qw.need + 1, 0, sizeof(int), c->st));
+  }
   ihs_status s = IHS_OK;
   if (iters > 0 && c->fused) {
     if ((s = join_caller(c)) != IHS_OK) return s;
@@ -699,9 +702,12 @@ ihs_status ihs_solve(ihs_ctx* c, double* x, int64_t t0, int iters, ihs_report* r
     rep->status = st;
     rep->step_norm = 0.0;
     rep->qp_fista_iters = 0;
+    rep->qp_active_rounds = 0;
     if (iters > 0) cudaMemcpy(&rep->step_norm, c->step_norm, sizeof(double), cudaMemcpyDeviceToHost);
-    if (c->qw.iters)
+    if (c->qw.iters) {
       cudaMemcpy(&rep->qp_fista_iters, c->qw.iters, sizeof(int), cudaMemcpyDeviceToHost);
+      cudaMemcpy(&rep->qp_active_rounds, c->qw.need + 1, sizeof(int), cudaMemcpyDeviceToHost);
+    }
   }
   return st;
 }
@@ -806,6 +812,7 @@ ihs_status ihs_adjoint(ihs_ctx* c, const double* x, const double* dLdx, double* 
     rep->iters = it;
     rep->status = st;
     rep->qp_fista_iters = 0;
+    rep->qp_active_rounds = 0;
     rep->step_norm = 0.0;
   }
   if (st != IHS_OK) return st;

@@ -161,7 +161,8 @@ struct QpWork {
   int* support;    // d ints, previous face (count in support[d])
   double* dbuf;    // 8 * d doubles of scratch
   int* iters;      // FISTA iterations (device counter)
-  int* need;       // penalised form: the step is still open after the previous pass
+  int* need;       // penalised form: the step is still open after the previous pass;
+                   // need[1]: active-set rounds spent (device counter)
   void* Hinv;      // penalised form: H^{-1} (d x d, factor precision), or null
 };
 size_t qp_work_bytes(int d);

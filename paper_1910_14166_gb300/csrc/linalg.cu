@@ -582,6 +582,22 @@ cudaError_t launch_chol_apply(const void* Lbuf, const void* Dinv, int d, int f32
 // every L tile straight from global memory (eight threads share a row, so
 // L1 serves most of it).  Skipped entirely when *need == 0.
 // ----------------------------------------------------------------------------
+// 32 consecutive values (16-byte aligned) into registers with vector loads.
+IHS_DEV void load32(const float* __restrict__ p, float (&r)[32]) {
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const float4 v = __ldg(reinterpret_cast<const float4*>(p) + i);
+    r[4 * i] = v.x; r[4 * i + 1] = v.y; r[4 * i + 2] = v.z; r[4 * i + 3] = v.w;
+  }
+}
+IHS_DEV void load32(const double* __restrict__ p, double (&r)[32]) {
+#pragma unroll
+  for (int i = 0; i < 16; ++i) {
+    const double2 v = __ldg(reinterpret_cast<const double2*>(p) + i);
+    r[2 * i] = v.x; r[2 * i + 1] = v.y;
+  }
+}
+
 template <typename T>
 size_t chol_inverse_smem(int Tt) { return (size_t)(Tt + 1) * 32 * 33 * sizeof(T); }
 
@@ -605,14 +621,17 @@ __global__ void __launch_bounds__(256) k_chol_inverse(const T* __restrict__ L,
 #pragma unroll
     for (int v = 0; v < 4; ++v) acc[v] = (k == c && a == b0 + v) ? T(1) : T(0);
     const T* Lrow = L + (int64_t)(k * 32 + a) * dp;
+    T lr[32];
+    if (c < k) load32(Lrow + c * 32, lr);
     for (int j = c; j < k; ++j) {
-      const T* lr = Lrow + j * 32;
-#pragma unroll 8
-      for (int q = 0; q < 32; ++q) {
-        const T l = __ldg(lr + q);
+      T cur[32];
 #pragma unroll
-        for (int v = 0; v < 4; ++v) acc[v] -= l * Ys[(j) * 32 + q][b0 + v];
-      }
+      for (int q = 0; q < 32; ++q) cur[q] = lr[q];
+      if (j + 1 < k) load32(Lrow + (j + 1) * 32, lr);  // next tile's row in flight
+#pragma unroll
+      for (int q = 0; q < 32; ++q)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[v] -= cur[q] * Ys[j * 32 + q][b0 + v];
     }
 #pragma unroll
     for (int v = 0; v < 4; ++v) Tmp[a][b0 + v] = acc[v];
@@ -635,14 +654,17 @@ __global__ void __launch_bounds__(256) k_chol_inverse(const T* __restrict__ L,
 #pragma unroll
     for (int v = 0; v < 4; ++v) acc[v] = Ys[(k) * 32 + a][b0 + v];
     const T* Urow = L + (int64_t)(k * 32 + a) * dp;  // row of the stored L^T tiles (k, j)
+    T ur[32];
+    if (k + 1 < Tt) load32(Urow + (k + 1) * 32, ur);
     for (int j = k + 1; j < Tt; ++j) {
-      const T* ur = Urow + j * 32;
-#pragma unroll 8
-      for (int q = 0; q < 32; ++q) {
-        const T u = __ldg(ur + q);
+      T cur[32];
 #pragma unroll
-        for (int v = 0; v < 4; ++v) acc[v] -= u * Ys[(j) * 32 + q][b0 + v];
-      }
+      for (int q = 0; q < 32; ++q) cur[q] = ur[q];
+      if (j + 1 < Tt) load32(Urow + (j + 1) * 32, ur);
+#pragma unroll
+      for (int q = 0; q < 32; ++q)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[v] -= cur[q] * Ys[j * 32 + q][b0 + v];
     }
 #pragma unroll
     for (int v = 0; v < 4; ++v) Tmp[a][b0 + v] = acc[v];

@@ -49,7 +49,7 @@ struct FaceSm {
 
 size_t qp_work_bytes(int d) {
   const size_t dp = (size_t)chol_padded(d);
-  return (size_t)d * d * 4 + dp * dp * 8 + (size_t)9 * d * 8 + (size_t)(d + 3) * 4 + 256;
+  return (size_t)d * d * 4 + dp * dp * 8 + (size_t)9 * d * 8 + (size_t)(d + 4) * 4 + 256;
 }
 
 // ---- block reductions (1024 threads) --------------------------------------
@@ -674,9 +674,12 @@ __global__ void __launch_bounds__(kQpThreads, 1) k_l1_step(
 // solved with H^{-1} at hand (from the sketched factor): the face with zero
 // set Z and signs sigma elsewhere is the KKT system
 //     H dl + E_Z nu = g - lambda sigma~,   E_Z^T (x^t + dl) = 0
-// (sigma~ = sigma off Z, 0 on Z): p = H^{-1}(g - lambda sigma~),
-// nu = ((H^{-1})_ZZ)^{-1} (p_Z + x^t_Z), dl = p - (H^{-1})_{:,Z} nu, refined
-// with FP64 residuals of that system.  The point is the answer when every
+// (sigma~ = sigma off Z, 0 on Z), solved for nu' = nu - g_Z (which, like
+// dl, vanishes at the optimum): p = H^{-1} v with v = g - lambda sigma off Z
+// and 0 on Z, nu' = ((H^{-1})_ZZ)^{-1} (p_Z + x^t_Z), dl = p - (H^{-1})_{:,Z} nu' (in the
+// plain form refined once with FP64 residuals of that system; the mixed form
+// keeps the factor-precision point, as its OLS step does, and runs its
+// products in FP32).  The point is the answer when every
 // index off Z keeps its sign and |nu_j| <= lambda on Z (nu_j = -(H dl - g)_j
 // there).  Each round takes the signs and zeros from the current point x and
 // its dual y = g - H (x - x^t) by the diagonally scaled proximal rule
@@ -687,6 +690,7 @@ constexpr int kActiveRounds = 32;
 
 struct PenShared {
   double xt[kQpMaxD], gd[kQpMaxD], dl[kQpMaxD], p[kQpMaxD], v[kQpMaxD], r1[kQpMaxD];
+  double vt[kQpMaxD];  // a matvec operand in the kernel's arithmetic type (float or double)
   int Z[kQpMaxD];
   int pos[kQpMaxD];  // index in Z, or -1
   signed char sg[kQpMaxD];
@@ -696,39 +700,40 @@ struct PenShared {
   double redd[33];
 };
 
-// out_j = sum_i M[j, i] v_i (FP64 accumulation), M d x d row-major in TM
+// out_j = sum_i M[j, i] v_i, M d x d row-major in TM, accumulated in TM
+// (FP32 in the mixed form: GB300's FP64 rate is 1/64 of FP32 and a d = 1000
+// matrix-vector product in FP64 costs a quarter millisecond on one SM).
 template <typename TM>
-__device__ void matvec_d(const TM* __restrict__ M, int d, const double* v, double* out) {
+__device__ void matvec_d(const TM* __restrict__ M, int d, const TM* v, double* out) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   for (int j = w; j < d; j += (int)(blockDim.x >> 5)) {
     const TM* row = M + (int64_t)j * d;
-    double s = 0.0;
-    for (int i = lane; i < d; i += 32) s = fma((double)row[i], v[i], s);
+    TM s = TM(0);
+    for (int i = lane; i < d; i += 32) s += row[i] * v[i];
     s = warp_sum(s);
-    if (lane == 0) out[j] = s;
+    if (lane == 0) out[j] = (double)s;
   }
 }
 
-// out_j = base_j - sum_a Hinv[j, Z_a] nu_a
+// out_j = base_j - sum_a Hinv[j, Z_a] nu_a (accumulated in TF)
 template <typename TF>
 __device__ void sub_cols(const TF* __restrict__ Hinv, int d, const int* Z, int zc, const double* nu,
                          const double* base, double* out) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   for (int j = w; j < d; j += (int)(blockDim.x >> 5)) {
     const TF* row = Hinv + (int64_t)j * d;
-    double s = 0.0;
-    for (int a = lane; a < zc; a += 32) s = fma((double)row[Z[a]], nu[a], s);
+    TF s = TF(0);
+    for (int a = lane; a < zc; a += 32) s += row[Z[a]] * (TF)nu[a];
     s = warp_sum(s);
-    if (lane == 0) out[j] = base[j] - s;
+    if (lane == 0) out[j] = base[j] - (double)s;
   }
 }
 
 template <typename TF>
 __global__ void __launch_bounds__(kQpThreads, 1) k_pen_active(
-    const double* __restrict__ H, const TF* __restrict__ Hinv, int d,
-    const double* __restrict__ g, const double* __restrict__ du, const double* __restrict__ uvec,
-    double lam, double* __restrict__ x, double* __restrict__ step_norm,
-    int* __restrict__ support, int* __restrict__ need) {
+    const double* __restrict__ H, const float* __restrict__ Hf, const TF* __restrict__ Hinv, int d,
+    const double* __restrict__ g, double lam, double* __restrict__ x,
+    double* __restrict__ step_norm, int* __restrict__ support, int* __restrict__ need) {
   if (*need == 0) return;
   extern __shared__ __align__(16) unsigned char pa_smem[];
   PenShared& P = *reinterpret_cast<PenShared*>(pa_smem);
@@ -737,6 +742,9 @@ __global__ void __launch_bounds__(kQpThreads, 1) k_pen_active(
   double* nu = reinterpret_cast<double*>(M + (size_t)zmax * ld);
   double* nu2 = nu + zmax;
   const int tid = threadIdx.x;
+  TF* vt = reinterpret_cast<TF*>(P.vt);
+  // H in the arithmetic type: FP64 H (plain form) or its FP32 copy (mixed)
+  const TF* Ht = sizeof(TF) == 8 ? reinterpret_cast<const TF*>(H) : reinterpret_cast<const TF*>(Hf);
   for (int j = tid; j < d; j += blockDim.x) {
     P.xt[j] = x[j];
     P.gd[j] = g[j];
@@ -745,8 +753,10 @@ __global__ void __launch_bounds__(kQpThreads, 1) k_pen_active(
   }
   __shared__ int changed;
   bool accepted = false;
+  int rounds_used = 0;
   for (int round = 0; round < kActiveRounds; ++round) {
     __syncthreads();
+    rounds_used = round + 1;
     // signs and zeros from the current point and its dual
     if (tid == 0) changed = (round == 0);
     __syncthreads();
@@ -775,9 +785,15 @@ __global__ void __launch_bounds__(kQpThreads, 1) k_pen_active(
     __syncthreads();
     const int zc = P.zc;
     if (zc > zmax) break;
-    for (int j = tid; j < d; j += blockDim.x) P.v[j] = P.gd[j] - lam * (double)P.sg[j];
+    // right-hand side in the shifted form nu = g_Z + nu': g_j - lambda sigma_j
+    // off Z and 0 on Z, so p, nu' and dl all vanish at the optimum and the
+    // factor-precision products carry no O(lambda) cancellation
+    for (int j = tid; j < d; j += blockDim.x) {
+      P.v[j] = P.sg[j] != 0 ? P.gd[j] - lam * (double)P.sg[j] : 0.0;
+      vt[j] = (TF)P.v[j];
+    }
     __syncthreads();
-    matvec_d<TF>(Hinv, d, P.v, P.p);
+    matvec_d<TF>(Hinv, d, vt, P.p);
     __syncthreads();
     // M = (H^{-1})_ZZ, factored in TF
     for (int e = tid; e < zc * zc; e += blockDim.x) {
@@ -791,17 +807,22 @@ __global__ void __launch_bounds__(kQpThreads, 1) k_pen_active(
     chol_sm_solve<TF>(M, zc, ld, nu);
     sub_cols<TF>(Hinv, d, P.Z, zc, nu, P.p, P.dl);
     __syncthreads();
-    // FP64 refinement of the bordered system
-    const int nref = sizeof(TF) == 4 ? 2 : 1;
+    // refinement of the bordered system (plain form; the mixed form keeps the
+    // factor-precision point, as its OLS step does)
+    const int nref = sizeof(TF) == 4 ? 0 : 1;
     for (int it = 0; it < nref; ++it) {
-      matvec_d<double>(H, d, P.dl, P.r1);  // r1 = H dl
+      for (int j = tid; j < d; j += blockDim.x) vt[j] = (TF)P.dl[j];
+      __syncthreads();
+      matvec_d<TF>(Ht, d, vt, P.r1);  // r1 = H dl
       __syncthreads();
       for (int j = tid; j < d; j += blockDim.x) {
         const int a = P.pos[j];
         P.r1[j] = P.v[j] - P.r1[j] - (a >= 0 ? nu[a] : 0.0);
       }
       __syncthreads();
-      matvec_d<TF>(Hinv, d, P.r1, P.p);  // p = H^{-1} r1
+      for (int j = tid; j < d; j += blockDim.x) vt[j] = (TF)P.r1[j];
+      __syncthreads();
+      matvec_d<TF>(Hinv, d, vt, P.p);  // p = H^{-1} r1
       __syncthreads();
       for (int a = tid; a < zc; a += blockDim.x)
         nu2[a] = P.p[P.Z[a]] - (-P.xt[P.Z[a]] - P.dl[P.Z[a]]);
@@ -827,7 +848,7 @@ __global__ void __launch_bounds__(kQpThreads, 1) k_pen_active(
     const double lim = lam * (1.0 + 1e-9);
     if (tid == 0) {
       for (int a = 0; a < zc; ++a) {
-        const double over = fabs(nu[a]) - lim;
+        const double over = fabs(P.gd[P.Z[a]] + nu[a]) - lim;
         if (over > P.bestv) {
           P.bestv = over;
           P.best = a;
@@ -841,11 +862,14 @@ __global__ void __launch_bounds__(kQpThreads, 1) k_pen_active(
       break;
     }
     // dual at the new point: y = g - H dl (x - x^t = dl, with dl_Z = -x^t_Z)
-    matvec_d<double>(H, d, P.dl, P.r1);
+    for (int j = tid; j < d; j += blockDim.x) vt[j] = (TF)P.dl[j];
+    __syncthreads();
+    matvec_d<TF>(Ht, d, vt, P.r1);
     __syncthreads();
     for (int j = tid; j < d; j += blockDim.x) P.r1[j] = P.gd[j] - P.r1[j];
   }
   __syncthreads();
+  if (tid == 0) atomicAdd(need + 1, rounds_used);
   if (accepted) {
     qp_epilogue(x, P.xt, d, lam, true, step_norm, support, P.redd);
     if (tid == 0) *need = 0;
@@ -937,8 +961,8 @@ cudaError_t launch_l1_step(const double* H, const void* Lbuf, const void* Dinv, 
         if (e != cudaSuccess) return e;
         attr = true;
       }
-      k_pen_active<float><<<1, kQpThreads, ps, st>>>(H, (const float*)w.Hinv, d, g, du, uvec, R,
-                                                     x, step_norm, w.support, need);
+      k_pen_active<float><<<1, kQpThreads, ps, st>>>(H, w.Hf, (const float*)w.Hinv, d, g, R, x,
+                                                     step_norm, w.support, need);
     } else {
       static bool attr = false;
       if (!attr) {
@@ -947,8 +971,8 @@ cudaError_t launch_l1_step(const double* H, const void* Lbuf, const void* Dinv, 
         if (e != cudaSuccess) return e;
         attr = true;
       }
-      k_pen_active<double><<<1, kQpThreads, ps, st>>>(H, (const double*)w.Hinv, d, g, du, uvec,
-                                                      R, x, step_norm, w.support, need);
+      k_pen_active<double><<<1, kQpThreads, ps, st>>>(H, w.Hf, (const double*)w.Hinv, d, g, R,
+                                                      x, step_norm, w.support, need);
     }
     note_launches(1);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
