@@ -20,6 +20,9 @@ What is pinned, and by what (see tests/test_oracle.py):
   * penalised-l1 QP: brute force over all supports and signs for d <= 6; the
     soft-threshold closed form for diagonal H; KKT.
   * sketch error (App. B): the closed form of its mean square over draws.
+  * SRHT (Sec. 2): P H D A against the materialised product with SciPy's
+    Sylvester Hadamard matrix; the fast transform against the definition;
+    E[S^T S] = I over draws; uniform sampled rows.
   * x_OPT: Householder QR vs refined normal equations vs lstsq.
   * IHS: geometric convergence at a rate below 1/2 (Thm. 2.2).
   * ridge adjoint: central finite differences in FP64.
@@ -77,6 +80,10 @@ def lib():
             L.orc_resid_grad_csr.argtypes = [i64, i64, vp, vp, vp, vp, vp, vp, vp]
             L.orc_sketch_adjoint.restype = None
             L.orc_sketch_adjoint.argtypes = [i64, i64, i64, i32, vp, vp, vp, f64, vp]
+            L.orc_srht_draw.restype = i32
+            L.orc_srht_draw.argtypes = [u64, i64, i64, i64, i64, vp, vp]
+            L.orc_srht_sketch_dense.restype = None
+            L.orc_srht_sketch_dense.argtypes = [i64, i64, vp, i64, i64, vp, vp, vp]
             _lib = L
     return _lib
 
@@ -445,23 +452,30 @@ OLS, L1_BALL, RIDGE, L1_PENALTY = 0, 1, 2, 3
 
 
 def ihs(A, b, kind: int, param: float, m: int, s: int, seed: int, iters: int, x0=None,
-        t0: int = 0, keep_sketch: bool = False):
+        t0: int = 0, keep_sketch: bool = False, sketch_kind: str = "sparse"):
     """Iterates x^0..x^iters of Eq. 2 with a fresh sketch per step.
 
     Iteration t (t = t0, t0+1, ...) draws the sketch with counter t, builds
     H = (1/s) (SA)^T SA (+ lam I for ridge) and g = A^T (b - A x^t) (- lam x^t
     for ridge), then takes the QP step: Cholesky for OLS / ridge, the exact
-    l1-ball QP for LASSO.  x^0 = 0 unless x0 is given."""
+    l1-ball QP for LASSO, the exact penalised QP for L1_PENALTY.  x^0 = 0
+    unless x0 is given.  sketch_kind "srht" uses S = m^{-1/2} P H D (Sec. 2)
+    instead of the sparse embedding: H = (1/m) (P H D A)^T (P H D A)."""
     A = as_f64(A)
     n, d = A.shape
     x = np.zeros(d) if x0 is None else np.array(x0, dtype=np.float64)
     xs = [x.copy()]
     sk = []
     for t in range(t0, t0 + iters):
-        bucket, sign = hash_draw(seed, t, s, m, n)
-        SA = sketch(A, m, s, bucket, sign)
         shift = param if kind == RIDGE else 0.0
-        H = gram(SA, 1.0 / s, shift)
+        if sketch_kind == "srht":
+            rows, sgn = srht_draw(seed, t, m, n)
+            SA = srht_sketch_fast(A, m, rows, sgn)
+            H = gram(SA, 1.0 / m, shift)
+        else:
+            bucket, sign = hash_draw(seed, t, s, m, n)
+            SA = sketch(A, m, s, bucket, sign)
+            H = gram(SA, 1.0 / s, shift)
         g = resid_grad(A, b, x)
         if kind == RIDGE:
             g = g - param * x
@@ -542,6 +556,62 @@ def ridge_adjoint(A, b, lam, dLdx):
     r = b - A @ x
     Av = A @ v
     return x, Av, np.outer(r, v) - np.outer(Av, x)
+
+
+def srht_n2(n: int) -> int:
+    """Rows of the Hadamard transform: the least power of two >= n (A is padded with zero rows)."""
+    return 1 << max(0, (int(n) - 1).bit_length())
+
+
+def srht_draw(seed: int, t: int, m: int, n: int):
+    """SRHT of Sec. 2 (S = P H D): sampled rows (int32 [m], in [0, n2)) and signs (int8 [n])."""
+    n2 = srht_n2(n)
+    rows = np.empty(m, dtype=np.int32)
+    sign = np.empty(n, dtype=np.int8)
+    rc = lib().orc_srht_draw(u64(seed & 0xFFFFFFFFFFFFFFFF), i64(t), i64(m), i64(n), i64(n2),
+                             _p(rows), _p(sign))
+    if rc != 0:
+        raise ValueError("invalid SRHT shape")
+    return rows, sign
+
+
+def srht_sketch(A, m: int, rows, sign):
+    """Raw P H D A (m x d, FP64) by the definition (Sec. 2, SRHT), O(m n d)."""
+    A = np.ascontiguousarray(as_f64(A))
+    n, d = A.shape
+    rows = np.ascontiguousarray(rows, dtype=np.int32)
+    sign = np.ascontiguousarray(sign, dtype=np.int8)
+    SA = np.empty((m, d))
+    lib().orc_srht_sketch_dense(n, d, _p(A), d, m, _p(rows), _p(sign), _p(SA))
+    return SA
+
+
+def fwht_rows(X):
+    """Unnormalised Walsh-Hadamard transform along axis 0 (length a power of
+    two), by the recursive definition H_{2k} = [H_k H_k; H_k -H_k]: stage h
+    replaces each pair (u, v) at distance h by (u + v, u - v)."""
+    Y = np.array(X, dtype=np.float64, copy=True)
+    n2 = Y.shape[0]
+    h = 1
+    while h < n2:
+        Y = Y.reshape(n2 // (2 * h), 2, h, *Y.shape[1:])
+        u = Y[:, 0].copy()
+        v = Y[:, 1].copy()
+        Y[:, 0] = u + v
+        Y[:, 1] = u - v
+        Y = Y.reshape(n2, *Y.shape[3:])
+        h *= 2
+    return Y
+
+
+def srht_sketch_fast(A, m: int, rows, sign):
+    """P H D A through the fast transform (the same numbers as srht_sketch up
+    to the order of the additions): pad D A to n2 rows, transform, take rows."""
+    A = as_f64(A)
+    n, d = A.shape
+    X = np.zeros((srht_n2(n), d))
+    X[:n] = np.asarray(sign, dtype=np.float64)[:, None] * A
+    return fwht_rows(X)[np.asarray(rows)]
 
 
 def sketch_error(A, m: int, s: int, seed: int, t: int):

@@ -21,6 +21,8 @@
  *   orc_resid_grad_dense / orc_resid_grad_csr
  *                     r = b - A x,  g = A^T r                               (Eq. 2, linear term)
  *   orc_sketch_adjoint  (S^T G) row by row                                  (adjoint of Sec. 2's map)
+ *   orc_srht_draw     SRHT signs D and sampled rows P                       (Sec. 2, SRHT)
+ *   orc_srht_sketch_dense  P H D A by its definition, entry by entry        (Sec. 2, SRHT)
  *
  * Build: gcc -O2 -std=c11 -shared -fPIC -o libihs_oracle.so ihs_oracle.c
  * (-O2 keeps IEEE semantics: no -ffast-math, no FMA contraction, see below).
@@ -193,6 +195,70 @@ void orc_sketch_adjoint(int64_t n, int64_t d, int64_t m, int s,
       int64_t row = bucket[(int64_t)k * n + i];
       double sg = (double)sign[(int64_t)k * n + i] * entry_scale;
       for (int64_t j = 0; j < d; ++j) out[i * d + j] += sg * G[row * d + j];
+    }
+  }
+}
+
+/*
+ * SRHT draw (Sec. 2: S = P H D, with D diagonal +-1 signs, H the recursively
+ * defined (Sylvester) Hadamard transform and P a uniform row sampler).  The
+ * paper fixes no generator, no padding and no sampling scheme; this
+ * library's reading:
+ *   - A is padded with zero rows to n2 = the least power of two >= n;
+ *   - D_i is the sign of block 0's word of row i, the same word a
+ *     CountSketch with the same (seed, t) uses: sign[i] = -1 iff bit 0 of
+ *     out(key_t0, i) is set;
+ *   - P takes m rows with replacement: sample r uses w = out(key_t1, r) and
+ *     row = floor(hi32(w) * n2 / 2^32), with key_tk as in orc_hash.
+ * Output: rows[r] in [0, n2), sign[i] for i < n.  Returns 0, or -1 if n2 is
+ * not a power of two >= n or exceeds 2^31.
+ */
+int orc_srht_draw(uint64_t seed, int64_t t, int64_t m, int64_t n, int64_t n2, int32_t* rows,
+                  int8_t* sign) {
+  if (n2 < n || n2 < 1 || n2 > 2147483648LL || (n2 & (n2 - 1)) != 0 || m < 1) return -1;
+  uint64_t key_seed = orc_sm64_at(seed, 0);
+  uint64_t key_t = orc_sm64_at(key_seed, (uint64_t)t);
+  uint64_t key_t0 = orc_sm64_at(key_t, 0);
+  uint64_t key_t1 = orc_sm64_at(key_t, 1);
+  for (int64_t i = 0; i < n; ++i) {
+    uint64_t w = orc_sm64_at(key_t0, (uint64_t)i);
+    sign[i] = (w & 1ULL) ? (int8_t)-1 : (int8_t)1;
+  }
+  for (int64_t r = 0; r < m; ++r) {
+    uint64_t w = orc_sm64_at(key_t1, (uint64_t)r);
+    rows[r] = (int32_t)(((w >> 32) * (uint64_t)n2) >> 32);
+  }
+  return 0;
+}
+
+/* Popcount parity: H[r][i] = (-1)^{popcount(r & i)} for the Sylvester
+ * Hadamard matrix H_{2n} = [H_n H_n; H_n -H_n]. */
+static int hadamard_sign(uint64_t r, uint64_t i) {
+  uint64_t v = r & i;
+  int p = 0;
+  while (v) {
+    p ^= 1;
+    v &= v - 1;
+  }
+  return p ? -1 : 1;
+}
+
+/*
+ * SA_raw = P H D A for a dense row-major A (n x d, leading dimension lda):
+ * row k of SA_raw is sum_{i < n} H[rows[k]][i] sign[i] A_i, in ascending i,
+ * in FP64.  The entries of H are the raw +-1; the normalisation (S = m^{-1/2}
+ * P H D, so that E[S^T S] = I) is applied as the Gram scale 1/m.  O(m n d):
+ * the definition, for small cases.
+ */
+void orc_srht_sketch_dense(int64_t n, int64_t d, const double* A, int64_t lda, int64_t m,
+                           const int32_t* rows, const int8_t* sign, double* SA) {
+  for (int64_t k = 0; k < m; ++k) {
+    double* out = SA + k * d;
+    for (int64_t j = 0; j < d; ++j) out[j] = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+      const double c = (double)(hadamard_sign((uint64_t)rows[k], (uint64_t)i) * sign[i]);
+      const double* a = A + i * lda;
+      for (int64_t j = 0; j < d; ++j) out[j] += c * a[j];
     }
   }
 }

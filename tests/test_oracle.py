@@ -500,3 +500,68 @@ def test_ihs_l1_penalty_converges_to_xopt():
     errs = [O.err_A(x, xo, G) for x in xs]
     assert errs[-1] < 1e-10
     assert errs[10] < errs[5] < errs[1]
+
+
+# --------------------------------------------------------------- SRHT ----
+def test_srht_definition_against_materialised_hadamard():
+    """P H D A by the definition equals the product with S materialised from
+    SciPy's Sylvester Hadamard matrix, and the fast transform agrees (n padded
+    to a power of two)."""
+    from scipy.linalg import hadamard
+    rng = np.random.default_rng(21)
+    for n in (1, 7, 64, 100):
+        A = rng.standard_normal((n, 3))
+        m = 12
+        rows, sign = O.srht_draw(3, 5, m, n)
+        n2 = O.srht_n2(n)
+        assert n2 >= n and n2 & (n2 - 1) == 0 and n2 < 2 * max(n, 1) + 1
+        S = hadamard(n2)[rows][:, :n] * sign[None, :].astype(float)
+        want = S @ A
+        got = O.srht_sketch(A, m, rows, sign)
+        assert np.allclose(got, want, rtol=0, atol=1e-12)
+        assert np.allclose(O.srht_sketch_fast(A, m, rows, sign), want, rtol=0, atol=1e-12)
+
+
+def test_fwht_is_hadamard_and_involutive():
+    """The fast transform is multiplication by the Sylvester matrix, and
+    applying it twice gives n2 times the input (H H = n2 I)."""
+    from scipy.linalg import hadamard
+    rng = np.random.default_rng(22)
+    X = rng.standard_normal((256, 4))
+    assert np.allclose(O.fwht_rows(X), hadamard(256) @ X, atol=1e-11)
+    assert np.allclose(O.fwht_rows(O.fwht_rows(X)), 256 * X, atol=1e-9)
+
+
+def test_srht_isotropy_and_uniform_rows():
+    """E[S^T S] = I for S = m^{-1/2} P H D (mean over draws within 5 standard
+    errors entrywise) and the sampled rows are uniform (chi-square)."""
+    from scipy.linalg import hadamard
+    n, m = 12, 6
+    n2 = O.srht_n2(n)
+    Hd = hadamard(n2)[:, :n].astype(float)
+    acc = np.zeros((n, n)); acc2 = np.zeros((n, n)); T = 4000
+    counts = np.zeros(n2)
+    for t in range(T):
+        rows, sign = O.srht_draw(11, t, m, n)
+        S = Hd[rows] * sign[None, :] / np.sqrt(m)
+        P = S.T @ S
+        acc += P; acc2 += P * P
+        np.add.at(counts, rows, 1)
+    mean = acc / T
+    se = np.sqrt(np.maximum(acc2 / T - mean ** 2, 1e-30) / T)
+    assert np.all(np.abs(mean - np.eye(n)) <= 5 * se + 1e-12)
+    from scipy.stats import chisquare
+    assert chisquare(counts).pvalue > 1e-4
+
+
+def test_ihs_srht_converges_to_xopt():
+    """IHS with the SRHT (Sec. 2's comparison sketch) reaches x_OPT on a dense
+    OLS problem at a per-step rate below 1/2."""
+    w = synth.make("ols_dense_fp64", n=3000, d=20, m=200)
+    A, b = w["A"], w["b"]
+    xo = O.x_opt_ols_qr(A, b)
+    G = A.T @ A
+    xs = O.ihs(A, b, O.OLS, 0.0, 200, 1, 0, 25, sketch_kind="srht")
+    errs = [O.err_A(x, xo, G) for x in xs]
+    assert errs[-1] < 1e-10
+    assert np.median([errs[i + 1] / errs[i] for i in range(8)]) < 0.5
