@@ -99,7 +99,20 @@ typedef struct {
   int qp_max_iter;    /* l1 ball: FISTA iteration cap per QP (0 = default)   */
   double qp_tol;      /* l1 ball: KKT acceptance tolerance (0 = default)     */
   int flags;          /* IHS_FLAG_* (0 = default)                           */
+  int sketch;         /* IHS_SKETCH_* (0 = the sparse embedding)             */
 } ihs_options;
+
+/* Sketch family (Sec. 2).
+ *   IHS_SKETCH_SPARSE  CountSketch (s = 1) or SJLT (s > 1): the method's sketch.
+ *   IHS_SKETCH_SRHT    S = m^{-1/2} P H D, the paper's dense comparison: D the
+ *                      +-1 signs of the sparse draw's block 0, H the Sylvester
+ *                      Hadamard transform of order n2 = the least power of two
+ *                      >= n (A padded with zero rows), P m rows sampled
+ *                      uniformly with replacement (block 1's words).  Dense A
+ *                      only (IHS_ERR_UNSUPPORTED for CSR), s must be 1; the
+ *                      context holds an n2 x d work buffer (FP64 in the plain
+ *                      form, FP32 in the mixed form). */
+enum { IHS_SKETCH_SPARSE = 0, IHS_SKETCH_SRHT = 1 };
 
 /* Option flags.  IHS_FLAG_NO_FUSE: in ihs_solve, form SA and the gradient in
  * two separate passes over A even where the single fused pass applies (dense

@@ -72,6 +72,10 @@ struct ihs_ctx {
   // sketch / Hessian (H, L, Dinv double-buffered: the next iteration's sketch
   // chain runs while the current step still reads its factor)
   void* SA = nullptr;
+  // SRHT comparison sketch: n2 x ldt transform buffer and the sampled rows
+  bool srht = false;
+  void* srht_T = nullptr;
+  int32_t* srht_rows = nullptr;
   GramPlan gp{};
   void* gop = nullptr;
   float* gpart_f = nullptr;
@@ -380,6 +384,11 @@ ihs_status ihs_create(ihs_ctx** out, const ihs_matrix* A, const double* b,
   if (A->kind == IHS_CSR && (A->col == nullptr || A->rowptr == nullptr || A->nnz < 0))
     return IHS_ERR_ARG;
   if (A->kind == IHS_DENSE && (int64_t)opt->s * A->n >= (1ll << 31)) return IHS_ERR_UNSUPPORTED;
+  if (opt->sketch != IHS_SKETCH_SPARSE && opt->sketch != IHS_SKETCH_SRHT) return IHS_ERR_ARG;
+  if (opt->sketch == IHS_SKETCH_SRHT) {
+    if (opt->s != 1) return IHS_ERR_ARG;
+    if (A->kind != IHS_DENSE || srht_n2(A->n) > (1ll << 31)) return IHS_ERR_UNSUPPORTED;
+  }
 
   ihs_ctx* c = new (std::nothrow) ihs_ctx();
   if (!c) return IHS_ERR_OOM;
@@ -460,7 +469,13 @@ ihs_status ihs_create(ihs_ctx** out, const ihs_matrix* A, const double* b,
     AL2(c->sk_partial, (size_t)2 * c->sp.nchunks * c->d * acc_el);
     c->rg_warps = rg_dense_warps(c->n);
     AL2(c->gpart, (size_t)c->rg_warps * c->d * sizeof(double));
-    c->fused = !c->acc64 && fused_supported(c->DA, c->s) && !(opt->flags & IHS_FLAG_NO_FUSE);
+    c->srht = opt->sketch == IHS_SKETCH_SRHT;
+    c->fused = !c->acc64 && !c->srht && fused_supported(c->DA, c->s) &&
+               !(opt->flags & IHS_FLAG_NO_FUSE);
+    if (c->srht) {
+      AL2(c->srht_T, (size_t)srht_n2(c->n) * srht_ldt((int)c->d) * acc_el);
+      AL2(c->srht_rows, (size_t)c->m * sizeof(int32_t));
+    }
     if (c->fused) {
       AL2(c->perm2, c->sp.P * sizeof(uint32_t));
       AL2(c->seg2, (c->m + 1) * sizeof(int32_t));
@@ -498,6 +513,10 @@ ihs_status ihs_create(ihs_ctx** out, const ihs_matrix* A, const double* b,
 
 namespace {
 
+// Scale of the Gram of the raw SA: 1/s for the sparse embedding (entries
+// +-1/sqrt(s)), 1/m for the SRHT (S = m^{-1/2} P H D).
+double gram_scale(const ihs_ctx* c) { return c->srht ? 1.0 / (double)c->m : 1.0 / c->s; }
+
 // The sketch chain of counter t into buffer `bf`, on the internal stream:
 // draw S and sort (dense), SA, Gram (+ lambda I), Cholesky factor.  Waits
 // for the last step that read buffer `bf`; records ev_fac[bf].
@@ -505,7 +524,12 @@ ihs_status sketch_chain(ihs_ctx* c, int64_t t, int bf) {
   cudaStream_t s2 = (c->opt.flags & IHS_FLAG_SERIAL) ? c->st : c->st2;
   CK(cudaStreamWaitEvent(s2, c->ev_use[bf], 0));
   const SketchKeys K = make_keys(c->opt.seed, t, c->s, c->m);
-  if (c->dense) {
+  if (c->srht) {
+    stage_begin(c, IHS_ST_SKETCH, s2);
+    CK(launch_srht(c->DA, make_keys(c->opt.seed, t, 2, c->m), c->m, c->acc64, c->srht_T,
+                   c->srht_rows, c->SA, s2));
+    stage_end(c);
+  } else if (c->dense) {
     stage_begin(c, IHS_ST_SORT, s2);
     CK(launch_sort_sketch(c->sp, K, c->n, c->sort_ws, c->perm, c->seg, c->chunk_first, s2));
     stage_end(c);
@@ -520,7 +544,7 @@ ihs_status sketch_chain(ihs_ctx* c, int64_t t, int bf) {
   }
   const double shift = (c->C.kind == IHS_RIDGE) ? c->C.param : 0.0;
   stage_begin(c, IHS_ST_GRAM, s2);
-  CK(launch_gram(c->gp, c->SA, c->gop, c->gpart_f, c->gpart_d, 1.0 / c->s, shift, c->H[bf],
+  CK(launch_gram(c->gp, c->SA, c->gop, c->gpart_f, c->gpart_d, gram_scale(c), shift, c->H[bf],
                  c->status, s2));
   stage_end(c);
   stage_begin(c, IHS_ST_FACTOR, s2);
@@ -599,7 +623,7 @@ ihs_status fused_iteration(ihs_ctx* c, double* x, int pb, int bf) {
   CK(e);
   CK(cudaEventRecord(c->ev_read[pb], s1));
   stage_begin(c, IHS_ST_GRAM, s1);
-  CK(launch_gram(c->gp, c->SA, c->gop, c->gpart_f, c->gpart_d, 1.0 / c->s, lam, c->H[bf],
+  CK(launch_gram(c->gp, c->SA, c->gop, c->gpart_f, c->gpart_d, gram_scale(c), lam, c->H[bf],
                  c->status, s1));
   stage_end(c);
   stage_begin(c, IHS_ST_FACTOR, s1);
@@ -716,7 +740,7 @@ ihs_status ihs_get_sketch(ihs_ctx* c, void* SA_out, int* SA_dtype, double* H_out
                           double* scale) {
   if (!c) return IHS_ERR_ARG;
   if (SA_dtype) *SA_dtype = c->acc64 ? IHS_F64 : IHS_F32;
-  if (scale) *scale = 1.0 / c->s;
+  if (scale) *scale = gram_scale(c);
   if ((SA_out || H_out) && !c->have_sketch) return IHS_ERR_ARG;
   const size_t el = c->acc64 ? 8 : 4;
   CK(cudaStreamWaitEvent(c->st, c->ev_fac[c->cur], 0));

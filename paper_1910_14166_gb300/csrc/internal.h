@@ -172,6 +172,14 @@ cudaError_t launch_l1_step(const double* H, const void* Lbuf, const void* Dinv, 
                            const double* g, double param, int pen, int max_iter, double tol,
                            QpWork w, double* x, double* step_norm, int* status, cudaStream_t st);
 
+// ---- SRHT (Sec. 2's comparison sketch) ------------------------------------------
+// n2 = least power of two >= n; T buffer n2 x srht_ldt(d) (FP64 if acc64 else FP32);
+// rows: m int32.  Writes the raw P H D A into SA (m x d).
+int64_t srht_n2(int64_t n);
+int64_t srht_ldt(int d);
+cudaError_t launch_srht(const DenseA& A, const SketchKeys& K, int64_t m, int acc64, void* Tbuf,
+                        int32_t* rows, void* SA, cudaStream_t st);
+
 // ---- adjoint (ridge / OLS) -----------------------------------------------------
 cudaError_t launch_cg_init(const double* rhs, int d, double* v, double* r, double* scal,
                            cudaStream_t st);

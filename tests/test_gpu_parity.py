@@ -483,3 +483,76 @@ def test_ihs_lasso_penalty_large_support(cuda_lib, precision):
         x, rep = solver.solve(iters=30)
         assert rep.status == 0
     assert O.err_A(x.cpu().numpy(), xo, G) < 1e-10
+
+
+@pytest.mark.parametrize("n,d,m", [(1, 3, 4), (4096, 40, 400), (5000, 33, 300), (100000, 64, 640)])
+def test_srht_sketch_matches_oracle(cuda_lib, n, d, m):
+    """SRHT (Sec. 2, S = m^{-1/2} P H D): the draw and the raw P H D A equal the
+    oracle's -- bit for bit in FP64 (the transform runs the stages in the
+    definition's order), to FP32 accumulation in the mixed form; the Gram
+    scale is 1/m.  Sizes cover n = 1, a power of two, zero padding, several
+    passes of the transform and d not a multiple of 32."""
+    rng = np.random.default_rng(n + d)
+    A = rng.standard_normal((n, d))
+    b = rng.standard_normal(n)
+    rows, sign = O.srht_draw(4, 2, m, n)
+    want = O.srht_sketch_fast(A, m, rows, sign)
+    if n * m * d <= 4e8:
+        assert np.allclose(want, O.srht_sketch(A, m, rows, sign), rtol=0, atol=1e-10 * np.abs(want).max())
+    sv = cuda_lib.IHS(dev(A), dev(b), m=m, seed=4, precision="fp64", sketch="srht")
+    sv.sketch(2)
+    SA, H, scale = sv.get_sketch()
+    assert scale == 1.0 / m
+    assert np.array_equal(SA.cpu().numpy(), want)
+    Hn = H.cpu().numpy()
+    Ho = O.gram(want, 1.0 / m)
+    assert np.abs(Hn - Ho).max() <= 1e-12 * np.abs(Ho).max()
+    A32 = A.astype(np.float32)
+    want32 = O.srht_sketch_fast(A32.astype(np.float64), m, rows, sign)
+    sv32 = cuda_lib.IHS(dev(A32), dev(b), m=m, seed=4, precision="tf32", sketch="srht")
+    sv32.sketch(2)
+    SA32, _, _ = sv32.get_sketch()
+    tol = 1e-6 * np.sqrt(O.srht_n2(n)) * np.abs(A32).max() * 4
+    assert np.abs(SA32.cpu().numpy() - want32).max() <= tol
+
+
+def test_ihs_srht_plain_matches_oracle_every_iteration(cuda_lib):
+    """IHS with the SRHT on the 20000 x 50 FP64 OLS workload (m = 500): every
+    GPU iterate within 1e-12 of the oracle's; 25 iterations reach 1e-10."""
+    w = synth.make("ols_dense_fp64")
+    A, b = w["A"], w["b"]
+    xo = O.x_opt_ols_qr(A, b)
+    G = A.T @ A
+    xs = O.ihs(A, b, O.OLS, 0.0, 500, 1, 0, 25, sketch_kind="srht")
+    sv = cuda_lib.IHS(dev(A), dev(b), m=500, seed=0, precision="fp64", sketch="srht")
+    x = torch.zeros(w["d"], dtype=torch.float64, device="cuda")
+    nrm = np.sqrt(xo @ G @ xo)
+    for t in range(25):
+        sv.solve(x, t0=t, iters=1)
+        e = x.cpu().numpy() - xs[t + 1]
+        assert np.sqrt(max(e @ G @ e, 0.0)) / nrm <= 1e-12, t
+    assert O.err_A(x.cpu().numpy(), xo, G) < 1e-10
+
+
+def test_ihs_srht_mixed_reaches_1e10(cuda_lib):
+    """Mixed form with the SRHT on AR(1) FP32 data reaches 1e-10 of x_OPT."""
+    w = synth.make("ols_dense_ar1", n=100000, d=96, m=960)
+    A64 = w["A"].astype(np.float64)
+    xo = O.x_opt_ols_normal(A64, w["b"])
+    G = A64.T @ A64
+    sv = cuda_lib.IHS(dev(w["A"]), dev(w["b"]), m=960, seed=0, precision="tf32", sketch="srht")
+    x, rep = sv.solve(iters=30)
+    assert rep.status == 0
+    assert O.err_A(x.cpu().numpy(), xo, G) < 1e-10
+
+
+def test_srht_rejects_sparse_and_sjlt(cuda_lib):
+    w = synth.make("lasso_csr_fp64", n=1000, d=10, m=100)
+    with pytest.raises(cuda_lib.IHSError) as e:
+        cuda_lib.IHS((dev(w["rowptr"]), dev(w["col"]), dev(w["val"])), dev(w["b"]), m=100,
+                     shape=(w["n"], w["d"]), sketch="srht")
+    assert e.value.status == 8
+    A = np.random.default_rng(0).standard_normal((100, 5))
+    with pytest.raises(cuda_lib.IHSError) as e:
+        cuda_lib.IHS(dev(A), dev(A[:, 0].copy()), m=40, s=4, sketch="srht")
+    assert e.value.status == 1
