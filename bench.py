@@ -476,18 +476,20 @@ def run_sketch_quality(args):
 
 def run_workloads(args):
     """Time every workload of the suite (and the penalised-LASSO form on the
-    two sparse ones, lambda = 5) through ihs_solve: CUDA events around the
+    two sparse ones, lambda = 5; the SRHT comparison sketch on the two dense
+    OLS ones) through ihs_solve: CUDA events around the
     call, median of `--steps` runs after one warm-up, plus the library's stage
     times (one serial-mode run: every stage on one stream) and launch count.
     The dense 1,048,576 x 500 OLS line is the main benchmark's step.  One JSON
     line per case."""
     import torch
     import paper_1910_14166_gb300 as ihs
-    cases = [("ols_dense_fp64", None, None), ("lasso_csr_fp64", None, None),
-             ("ols_dense_ar1", None, None), ("ridge_dense", None, None),
-             ("lasso_csr_zipf", None, None), ("lasso_csr_fp64", "l1pen", 5.0),
-             ("lasso_csr_zipf", "l1pen", 5.0)]
-    for name, kind_o, param_o in cases:
+    cases = [("ols_dense_fp64", None, None, "sparse"), ("lasso_csr_fp64", None, None, "sparse"),
+             ("ols_dense_ar1", None, None, "sparse"), ("ridge_dense", None, None, "sparse"),
+             ("lasso_csr_zipf", None, None, "sparse"), ("lasso_csr_fp64", "l1pen", 5.0, "sparse"),
+             ("lasso_csr_zipf", "l1pen", 5.0, "sparse"), ("ols_dense_fp64", None, None, "srht"),
+             ("ols_dense_ar1", None, None, "srht")]
+    for name, kind_o, param_o, sketch in cases:
         if args.only and name not in args.only.split(","):
             continue
         w = synth.make(name, seed=0)
@@ -503,7 +505,7 @@ def run_workloads(args):
         times = []
         for serial in (False, True):
             sv = ihs.IHS(A, b, kind=kind, param=param, m=w["m"], s=w["s"], seed=0,
-                         precision=w["precision"], shape=shape, serial=serial)
+                         precision=w["precision"], shape=shape, serial=serial, sketch=sketch)
             x0 = torch.zeros(w["d"], dtype=torch.float64, device="cuda")
             sv.solve(x0.clone(), iters=iters)  # warm-up
             if serial:
@@ -525,7 +527,7 @@ def run_workloads(args):
                     fista = rep.qp_fista_iters
             del sv
         print(json.dumps({
-            "experiment": "workloads", "workload": name, "kind": kind, "param": param,
+            "experiment": "workloads", "workload": name, "kind": kind, "param": param, "sketch": sketch,
             "n": w["n"], "d": w["d"], "m": w["m"], "s": w["s"], "precision": w["precision"],
             "iters": iters, "solve_ms_median": statistics.median(times), "solve_ms_all": times,
             "status": status, "qp_fista_iters": fista, "stage_ms_per_iter_serial": stages,
