@@ -421,7 +421,8 @@ def run_iters_only(args):
 def run_sketch_quality(args):
     """The sketch-quality experiment of App. B on a synthetic stand-in: for
     m in {5d, 10d, 20d, 40d} and s in {1, 4, 8}, the mean and spread over
-    `trials` independent sketches of ||A^T S^T S A - A^T A||_F / ||A^T A||_F,
+    `trials` independent sketches of ||A^T S^T S A - A^T A||_F / ||A^T A||_F
+    (and the SRHT at the same m on dense data, the paper's comparison),
     and the time to form one sketched Hessian (sort, SA, fix-up, Gram; CUDA
     events).  A^T A, every sketch, every Gram and the error reduction run in
     the library's kernels.  One JSON line per (m, s)."""
@@ -437,16 +438,18 @@ def run_sketch_quality(args):
         A = tuple(torch.from_numpy(w[k]).cuda() for k in ("rowptr", "col", "val"))
         shape = (n, d)
     G = None
-    for s in (1, 4, 8):
+    kinds = [("sparse", 1), ("sparse", 4), ("sparse", 8)] + ([("srht", 1)] if shape is None else [])
+    for sketch, s in kinds:
         for k in (5, 10, 20, 40):
             m = k * d
             if m % s or m > n:
                 continue
             try:
-                sv = ihs.IHS(A, b, m=m, s=s, seed=args.seed, precision=prec, shape=shape)
+                sv = ihs.IHS(A, b, m=m, s=s, seed=args.seed, precision=prec, shape=shape,
+                             sketch=sketch)
             except ihs.IHSError as e:
                 print(json.dumps({"experiment": "sketch_quality", "workload": args.workload, "m": m,
-                                  "s": s, "skipped": str(e)}), flush=True)
+                                  "s": s, "sketch": sketch, "skipped": str(e)}), flush=True)
                 continue
             if G is None:
                 G = sv.exact_gram()
@@ -465,10 +468,12 @@ def run_sketch_quality(args):
             per = (ms["sort"] + ms["sketch"] + ms["sketch_fix"] + ms["gram"]) / args.trials
             print(json.dumps({
                 "experiment": "sketch_quality", "workload": args.workload, "n": n, "d": d,
-                "m": m, "m_over_d": k, "s": s, "precision": prec, "trials": args.trials,
+                "m": m, "m_over_d": k, "s": s, "sketch": sketch, "precision": prec,
+                "trials": args.trials,
                 "err_mean": statistics.fmean(errs), "err_std": statistics.stdev(errs),
                 "sketch_ms": per,
-                "err_rms_expected": (c_num / m) ** 0.5 if c_num is not None else None,
+                "err_rms_expected": ((c_num / m) ** 0.5 if c_num is not None and sketch == "sparse"
+                                     else None),
                 "err_rms": statistics.fmean([e * e for e in errs]) ** 0.5,
                 "error": "||A^T S^T S A - A^T A||_F / ||A^T A||_F (App. B)"}), flush=True)
             del sv
