@@ -23,6 +23,8 @@ What is pinned, and by what (see tests/test_oracle.py):
   * SRHT (Sec. 2): P H D A against the materialised product with SciPy's
     Sylvester Hadamard matrix; the fast transform against the definition;
     E[S^T S] = I over draws; uniform sampled rows.
+  * Gaussian sketch (Sec. 2): moments and a Kolmogorov-Smirnov test of the
+    entries against N(0, 1); E[S^T S] = I.
   * x_OPT: Householder QR vs refined normal equations vs lstsq.
   * IHS: geometric convergence at a rate below 1/2 (Thm. 2.2).
   * ridge adjoint: central finite differences in FP64.
@@ -84,6 +86,8 @@ def lib():
             L.orc_srht_draw.argtypes = [u64, i64, i64, i64, i64, vp, vp]
             L.orc_srht_sketch_dense.restype = None
             L.orc_srht_sketch_dense.argtypes = [i64, i64, vp, i64, i64, vp, vp, vp]
+            L.orc_gauss_draw.restype = None
+            L.orc_gauss_draw.argtypes = [u64, i64, i64, i64, vp]
             _lib = L
     return _lib
 
@@ -460,7 +464,8 @@ def ihs(A, b, kind: int, param: float, m: int, s: int, seed: int, iters: int, x0
     for ridge), then takes the QP step: Cholesky for OLS / ridge, the exact
     l1-ball QP for LASSO, the exact penalised QP for L1_PENALTY.  x^0 = 0
     unless x0 is given.  sketch_kind "srht" uses S = m^{-1/2} P H D (Sec. 2)
-    instead of the sparse embedding: H = (1/m) (P H D A)^T (P H D A)."""
+    instead of the sparse embedding: H = (1/m) (P H D A)^T (P H D A);
+    "gaussian" uses S = G / sqrt(m): H = (1/m) (G A)^T (G A)."""
     A = as_f64(A)
     n, d = A.shape
     x = np.zeros(d) if x0 is None else np.array(x0, dtype=np.float64)
@@ -472,6 +477,8 @@ def ihs(A, b, kind: int, param: float, m: int, s: int, seed: int, iters: int, x0
             rows, sgn = srht_draw(seed, t, m, n)
             SA = srht_sketch_fast(A, m, rows, sgn)
             H = gram(SA, 1.0 / m, shift)
+        elif sketch_kind == "gaussian":
+            H = gram(gauss_sketch(A, m, seed, t), 1.0 / m, shift)
         else:
             bucket, sign = hash_draw(seed, t, s, m, n)
             SA = sketch(A, m, s, bucket, sign)
@@ -612,6 +619,19 @@ def srht_sketch_fast(A, m: int, rows, sign):
     X = np.zeros((srht_n2(n), d))
     X[:n] = np.asarray(sign, dtype=np.float64)[:, None] * A
     return fwht_rows(X)[np.asarray(rows)]
+
+
+def gauss_draw(seed: int, t: int, m: int, n: int):
+    """G (m x n, FP64) of the Gaussian sketch S = G / sqrt(m) (Sec. 2)."""
+    G = np.empty((m, n))
+    lib().orc_gauss_draw(u64(seed & 0xFFFFFFFFFFFFFFFF), i64(t), i64(m), i64(n), _p(G))
+    return G
+
+
+def gauss_sketch(A, m: int, seed: int, t: int):
+    """Raw G A (m x d, FP64) for the Gaussian sketch of counter t (Gram scale 1/m)."""
+    A = as_f64(A)
+    return gauss_draw(seed, t, m, A.shape[0]) @ A
 
 
 def sketch_error(A, m: int, s: int, seed: int, t: int):

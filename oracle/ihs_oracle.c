@@ -23,6 +23,7 @@
  *   orc_sketch_adjoint  (S^T G) row by row                                  (adjoint of Sec. 2's map)
  *   orc_srht_draw     SRHT signs D and sampled rows P                       (Sec. 2, SRHT)
  *   orc_srht_sketch_dense  P H D A by its definition, entry by entry        (Sec. 2, SRHT)
+ *   orc_gauss_draw    the entries of the Gaussian sketch's G                (Sec. 2, Gaussian)
  *
  * Build: gcc -O2 -std=c11 -shared -fPIC -o libihs_oracle.so ihs_oracle.c
  * (-O2 keeps IEEE semantics: no -ffast-math, no FMA contraction, see below).
@@ -261,4 +262,27 @@ void orc_srht_sketch_dense(int64_t n, int64_t d, const double* A, int64_t lda, i
       for (int64_t j = 0; j < d; ++j) out[j] += c * a[j];
     }
   }
+}
+
+/*
+ * Gaussian sketch (Sec. 2: S = G / sqrt(m), G_ij iid N(0, 1)).  The paper
+ * names no generator; this library's reading: entry (r, i) of the m x n
+ * matrix G uses the word w = out(key_t2, r * n + i) (key_tk as in orc_hash,
+ * k = 2) and the Box-Muller transform (Box & Muller 1958) of the two 32-bit
+ * halves, u1 = (hi32(w) + 1/2) / 2^32 and u2 = (lo32(w) + 1/2) / 2^32 (both
+ * in (0, 1)): g = sqrt(-2 ln u1) cos(2 pi u2), in double.  G is row-major.
+ */
+#include <math.h>
+void orc_gauss_draw(uint64_t seed, int64_t t, int64_t m, int64_t n, double* G) {
+  uint64_t key_seed = orc_sm64_at(seed, 0);
+  uint64_t key_t = orc_sm64_at(key_seed, (uint64_t)t);
+  uint64_t key_t2 = orc_sm64_at(key_t, 2);
+  const double two_pi = 6.283185307179586476925286766559;
+  for (int64_t r = 0; r < m; ++r)
+    for (int64_t i = 0; i < n; ++i) {
+      uint64_t w = orc_sm64_at(key_t2, (uint64_t)(r * n + i));
+      double u1 = ((double)(w >> 32) + 0.5) / 4294967296.0;
+      double u2 = ((double)(w & 0xFFFFFFFFULL) + 0.5) / 4294967296.0;
+      G[r * n + i] = sqrt(-2.0 * log(u1)) * cos(two_pi * u2);
+    }
 }

@@ -565,3 +565,38 @@ def test_ihs_srht_converges_to_xopt():
     errs = [O.err_A(x, xo, G) for x in xs]
     assert errs[-1] < 1e-10
     assert np.median([errs[i + 1] / errs[i] for i in range(8)]) < 0.5
+
+
+# ------------------------------------------------------------ Gaussian ----
+def test_gauss_draw_is_standard_normal():
+    """The Gaussian sketch's entries (Box-Muller of the counter words) have
+    mean 0, variance 1 and pass a Kolmogorov-Smirnov test against N(0, 1);
+    E[S^T S] = I for S = G / sqrt(m) (5 standard errors entrywise)."""
+    from scipy.stats import kstest
+    G = O.gauss_draw(5, 0, 200, 1000)
+    z = G.ravel()
+    assert abs(z.mean()) < 5 / np.sqrt(z.size)
+    assert abs(z.var() - 1.0) < 5 * np.sqrt(2.0 / z.size)
+    assert kstest(z, "norm").pvalue > 1e-3
+    n, m, T = 6, 4, 3000
+    acc = np.zeros((n, n)); acc2 = np.zeros((n, n))
+    for t in range(T):
+        S = O.gauss_draw(9, t, m, n) / np.sqrt(m)
+        P = S.T @ S
+        acc += P; acc2 += P * P
+    mean = acc / T
+    se = np.sqrt(np.maximum(acc2 / T - mean ** 2, 1e-30) / T)
+    assert np.all(np.abs(mean - np.eye(n)) <= 5 * se)
+
+
+def test_ihs_gaussian_converges_to_xopt():
+    """IHS with the Gaussian sketch reaches x_OPT at a rate near the
+    inverse-Wishart value (0.39 at m = 10d)."""
+    w = synth.make("ols_dense_fp64", n=3000, d=20, m=200)
+    A, b = w["A"], w["b"]
+    xo = O.x_opt_ols_qr(A, b)
+    G = A.T @ A
+    xs = O.ihs(A, b, O.OLS, 0.0, 200, 1, 0, 25, sketch_kind="gaussian")
+    errs = [O.err_A(x, xo, G) for x in xs]
+    assert errs[-1] < 1e-10
+    assert np.median([errs[i + 1] / errs[i] for i in range(10)]) < 0.5
