@@ -111,8 +111,13 @@ typedef struct {
  *                      uniformly with replacement (block 1's words).  Dense A
  *                      only (IHS_ERR_UNSUPPORTED for CSR), s must be 1; the
  *                      context holds an n2 x d work buffer (FP64 in the plain
- *                      form, FP32 in the mixed form). */
-enum { IHS_SKETCH_SPARSE = 0, IHS_SKETCH_SRHT = 1 };
+ *                      form, FP32 in the mixed form).
+ *   IHS_SKETCH_GAUSSIAN S = G / sqrt(m) with G_ij iid N(0, 1) (Box-Muller of
+ *                      the counter words of block 2), the dense comparison
+ *                      whose cost is an O(m n d) product: G is generated in
+ *                      column chunks and multiplied in by cuBLAS (TF32 in the
+ *                      mixed form, FP64 in the plain form).  Dense A only, s = 1. */
+enum { IHS_SKETCH_SPARSE = 0, IHS_SKETCH_SRHT = 1, IHS_SKETCH_GAUSSIAN = 2 };
 
 /* Option flags.  IHS_FLAG_NO_FUSE: in ihs_solve, form SA and the gradient in
  * two separate passes over A even where the single fused pass applies (dense

@@ -56,7 +56,7 @@ def build_oracle(force: bool = False) -> str:
     if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
         tmp = _SO + ".tmp%d" % os.getpid()
         subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math",
-                               "-shared", "-fPIC", "-o", tmp, _SRC])
+                               "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _SO)
     return _SO
 

@@ -76,6 +76,11 @@ struct ihs_ctx {
   bool srht = false;
   void* srht_T = nullptr;
   int32_t* srht_rows = nullptr;
+  // Gaussian comparison sketch: chunk buffers and the BLAS handle
+  bool gauss = false;
+  void* gauss_G = nullptr;
+  void* gauss_A = nullptr;
+  void* blas = nullptr;
   GramPlan gp{};
   void* gop = nullptr;
   float* gpart_f = nullptr;
@@ -359,6 +364,7 @@ void ihs_destroy(ihs_ctx* c) {
     if (c->ev_read[k]) cudaEventDestroy(c->ev_read[k]);
   }
   if (c->st2) cudaStreamDestroy(c->st2);
+  gauss_blas_destroy(c->blas);
   for (void* p : c->allocs) cudaFree(p);
   delete c;
 }
@@ -384,10 +390,13 @@ ihs_status ihs_create(ihs_ctx** out, const ihs_matrix* A, const double* b,
   if (A->kind == IHS_CSR && (A->col == nullptr || A->rowptr == nullptr || A->nnz < 0))
     return IHS_ERR_ARG;
   if (A->kind == IHS_DENSE && (int64_t)opt->s * A->n >= (1ll << 31)) return IHS_ERR_UNSUPPORTED;
-  if (opt->sketch != IHS_SKETCH_SPARSE && opt->sketch != IHS_SKETCH_SRHT) return IHS_ERR_ARG;
-  if (opt->sketch == IHS_SKETCH_SRHT) {
+  if (opt->sketch != IHS_SKETCH_SPARSE && opt->sketch != IHS_SKETCH_SRHT &&
+      opt->sketch != IHS_SKETCH_GAUSSIAN)
+    return IHS_ERR_ARG;
+  if (opt->sketch != IHS_SKETCH_SPARSE) {
     if (opt->s != 1) return IHS_ERR_ARG;
-    if (A->kind != IHS_DENSE || srht_n2(A->n) > (1ll << 31)) return IHS_ERR_UNSUPPORTED;
+    if (A->kind != IHS_DENSE) return IHS_ERR_UNSUPPORTED;
+    if (opt->sketch == IHS_SKETCH_SRHT && srht_n2(A->n) > (1ll << 31)) return IHS_ERR_UNSUPPORTED;
   }
 
   ihs_ctx* c = new (std::nothrow) ihs_ctx();
@@ -470,8 +479,16 @@ ihs_status ihs_create(ihs_ctx** out, const ihs_matrix* A, const double* b,
     c->rg_warps = rg_dense_warps(c->n);
     AL2(c->gpart, (size_t)c->rg_warps * c->d * sizeof(double));
     c->srht = opt->sketch == IHS_SKETCH_SRHT;
-    c->fused = !c->acc64 && !c->srht && fused_supported(c->DA, c->s) &&
+    c->gauss = opt->sketch == IHS_SKETCH_GAUSSIAN;
+    c->fused = !c->acc64 && !c->srht && !c->gauss && fused_supported(c->DA, c->s) &&
                !(opt->flags & IHS_FLAG_NO_FUSE);
+    if (c->gauss) {
+      const int64_t nc = gauss_chunk(c->m, c->n);
+      AL2(c->gauss_G, (size_t)c->m * nc * acc_el);
+      AL2(c->gauss_A, (size_t)nc * c->d * acc_el);
+      c->blas = gauss_blas_create();
+      if (!c->blas) return fail(IHS_ERR_CUDA);
+    }
     if (c->srht) {
       AL2(c->srht_T, (size_t)srht_n2(c->n) * srht_ldt((int)c->d) * acc_el);
       AL2(c->srht_rows, (size_t)c->m * sizeof(int32_t));
@@ -514,8 +531,11 @@ ihs_status ihs_create(ihs_ctx** out, const ihs_matrix* A, const double* b,
 namespace {
 
 // Scale of the Gram of the raw SA: 1/s for the sparse embedding (entries
-// +-1/sqrt(s)), 1/m for the SRHT (S = m^{-1/2} P H D).
-double gram_scale(const ihs_ctx* c) { return c->srht ? 1.0 / (double)c->m : 1.0 / c->s; }
+// +-1/sqrt(s)), 1/m for the SRHT (S = m^{-1/2} P H D) and the Gaussian
+// sketch (S = G / sqrt(m)).
+double gram_scale(const ihs_ctx* c) {
+  return (c->srht || c->gauss) ? 1.0 / (double)c->m : 1.0 / c->s;
+}
 
 // The sketch chain of counter t into buffer `bf`, on the internal stream:
 // draw S and sort (dense), SA, Gram (+ lambda I), Cholesky factor.  Waits
@@ -524,7 +544,12 @@ ihs_status sketch_chain(ihs_ctx* c, int64_t t, int bf) {
   cudaStream_t s2 = (c->opt.flags & IHS_FLAG_SERIAL) ? c->st : c->st2;
   CK(cudaStreamWaitEvent(s2, c->ev_use[bf], 0));
   const SketchKeys K = make_keys(c->opt.seed, t, c->s, c->m);
-  if (c->srht) {
+  if (c->gauss) {
+    stage_begin(c, IHS_ST_SKETCH, s2);
+    CK(launch_gauss(c->blas, c->DA, make_keys(c->opt.seed, t, 3, c->m), c->m, c->acc64,
+                    c->gauss_G, c->gauss_A, c->SA, s2));
+    stage_end(c);
+  } else if (c->srht) {
     stage_begin(c, IHS_ST_SKETCH, s2);
     CK(launch_srht(c->DA, make_keys(c->opt.seed, t, 2, c->m), c->m, c->acc64, c->srht_T,
                    c->srht_rows, c->SA, s2));

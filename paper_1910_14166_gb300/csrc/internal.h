@@ -180,6 +180,16 @@ int64_t srht_ldt(int d);
 cudaError_t launch_srht(const DenseA& A, const SketchKeys& K, int64_t m, int acc64, void* Tbuf,
                         int32_t* rows, void* SA, cudaStream_t st);
 
+// ---- Gaussian sketch (Sec. 2's dense comparison) --------------------------------
+// G generated in chunks of gauss_chunk(m, n) columns into Gbuf (m x nc), A's rows
+// copied into Abuf (nc x d) when their type differs or for the ragged last chunk,
+// SA = G A by cuBLAS (TF32 / FP64).  cublas: a handle from gauss_blas_create().
+int64_t gauss_chunk(int64_t m, int64_t n);
+cudaError_t launch_gauss(void* cublas, const DenseA& A, const SketchKeys& K, int64_t m, int acc64,
+                         void* Gbuf, void* Abuf, void* SA, cudaStream_t st);
+void* gauss_blas_create();
+void gauss_blas_destroy(void* h);
+
 // ---- adjoint (ridge / OLS) -----------------------------------------------------
 cudaError_t launch_cg_init(const double* rhs, int d, double* v, double* r, double* scal,
                            cudaStream_t st);

@@ -556,3 +556,56 @@ def test_srht_rejects_sparse_and_sjlt(cuda_lib):
     with pytest.raises(cuda_lib.IHSError) as e:
         cuda_lib.IHS(dev(A), dev(A[:, 0].copy()), m=40, s=4, sketch="srht")
     assert e.value.status == 1
+
+
+@pytest.mark.parametrize("n,d,m", [(3000, 40, 200), (700000, 8, 200)])
+def test_gauss_sketch_matches_oracle(cuda_lib, n, d, m):
+    """Gaussian sketch (Sec. 2, S = G / sqrt(m)): the raw G A equals the
+    oracle's to FP64 rounding in the plain form and to TF32 input rounding in
+    the mixed form; the Gram scale is 1/m.  The second size spans several
+    generated column chunks of G and a ragged last chunk."""
+    rng = np.random.default_rng(n + d)
+    A = rng.standard_normal((n, d))
+    b = rng.standard_normal(n)
+    want = O.gauss_sketch(A, m, 6, 1)
+    sv = cuda_lib.IHS(dev(A), dev(b), m=m, seed=6, precision="fp64", sketch="gaussian")
+    sv.sketch(1)
+    SA, H, scale = sv.get_sketch()
+    assert scale == 1.0 / m
+    assert np.abs(SA.cpu().numpy() - want).max() <= 1e-12 * np.abs(want).max()
+    A32 = A.astype(np.float32)
+    want32 = O.gauss_sketch(A32.astype(np.float64), m, 6, 1)
+    sv32 = cuda_lib.IHS(dev(A32), dev(b), m=m, seed=6, precision="tf32", sketch="gaussian")
+    sv32.sketch(1)
+    SA32, _, _ = sv32.get_sketch()
+    err = np.linalg.norm(SA32.cpu().numpy() - want32) / np.linalg.norm(want32)
+    assert err < 2e-3
+
+
+def test_ihs_gaussian_plain_matches_oracle_every_iteration(cuda_lib):
+    """IHS with the Gaussian sketch on the 20000 x 50 FP64 OLS workload: every
+    GPU iterate within 1e-12 of the oracle's."""
+    w = synth.make("ols_dense_fp64")
+    A, b = w["A"], w["b"]
+    xo = O.x_opt_ols_qr(A, b)
+    G = A.T @ A
+    xs = O.ihs(A, b, O.OLS, 0.0, 500, 1, 0, 10, sketch_kind="gaussian")
+    sv = cuda_lib.IHS(dev(A), dev(b), m=500, seed=0, precision="fp64", sketch="gaussian")
+    x = torch.zeros(w["d"], dtype=torch.float64, device="cuda")
+    nrm = np.sqrt(xo @ G @ xo)
+    for t in range(10):
+        sv.solve(x, t0=t, iters=1)
+        e = x.cpu().numpy() - xs[t + 1]
+        assert np.sqrt(max(e @ G @ e, 0.0)) / nrm <= 1e-12, t
+
+
+def test_ihs_gaussian_mixed_reaches_1e10(cuda_lib):
+    """Mixed form with the Gaussian sketch (TF32 GEMM) reaches 1e-10."""
+    w = synth.make("ols_dense_ar1", n=100000, d=96, m=960)
+    A64 = w["A"].astype(np.float64)
+    xo = O.x_opt_ols_normal(A64, w["b"])
+    G = A64.T @ A64
+    sv = cuda_lib.IHS(dev(w["A"]), dev(w["b"]), m=960, seed=0, precision="tf32", sketch="gaussian")
+    x, rep = sv.solve(iters=30)
+    assert rep.status == 0
+    assert O.err_A(x.cpu().numpy(), xo, G) < 1e-10
