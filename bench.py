@@ -438,11 +438,17 @@ def run_sketch_quality(args):
         A = tuple(torch.from_numpy(w[k]).cuda() for k in ("rowptr", "col", "val"))
         shape = (n, d)
     G = None
-    kinds = [("sparse", 1), ("sparse", 4), ("sparse", 8)] + ([("srht", 1)] if shape is None else [])
+    kinds = [("sparse", 1), ("sparse", 4), ("sparse", 8)]
+    if shape is None:
+        kinds += [("srht", 1), ("gaussian", 1)]
     for sketch, s in kinds:
         for k in (5, 10, 20, 40):
             m = k * d
             if m % s or m > n:
+                continue
+            # the Gaussian sketch is a dense m x n x d product: keep its FP64
+            # form to problems where one sketch is a fraction of a second
+            if sketch == "gaussian" and prec == "fp64" and 2.0 * m * n * d > 2e11:
                 continue
             try:
                 sv = ihs.IHS(A, b, m=m, s=s, seed=args.seed, precision=prec, shape=shape,
@@ -481,8 +487,8 @@ def run_sketch_quality(args):
 
 def run_workloads(args):
     """Time every workload of the suite (and the penalised-LASSO form on the
-    two sparse ones, lambda = 5; the SRHT comparison sketch on the two dense
-    OLS ones) through ihs_solve: CUDA events around the
+    two sparse ones, lambda = 5; the SRHT and Gaussian comparison sketches on
+    the two dense OLS ones) through ihs_solve: CUDA events around the
     call, median of `--steps` runs after one warm-up, plus the library's stage
     times (one serial-mode run: every stage on one stream) and launch count.
     The dense 1,048,576 x 500 OLS line is the main benchmark's step.  One JSON
@@ -493,7 +499,8 @@ def run_workloads(args):
              ("ols_dense_ar1", None, None, "sparse"), ("ridge_dense", None, None, "sparse"),
              ("lasso_csr_zipf", None, None, "sparse"), ("lasso_csr_fp64", "l1pen", 5.0, "sparse"),
              ("lasso_csr_zipf", "l1pen", 5.0, "sparse"), ("ols_dense_fp64", None, None, "srht"),
-             ("ols_dense_ar1", None, None, "srht")]
+             ("ols_dense_ar1", None, None, "srht"), ("ols_dense_fp64", None, None, "gaussian"),
+             ("ols_dense_ar1", None, None, "gaussian")]
     for name, kind_o, param_o, sketch in cases:
         if args.only and name not in args.only.split(","):
             continue
