@@ -23,6 +23,8 @@ What is pinned, and by what (see tests/test_oracle.py):
   * SRHT (Sec. 2): P H D A against the materialised product with SciPy's
     Sylvester Hadamard matrix; the fast transform against the definition;
     E[S^T S] = I over draws; uniform sampled rows.
+  * p = 2 ball QP: the projection closed form for H = I; brute force over
+    the circle for d = 2; KKT.
   * Gaussian sketch (Sec. 2): moments and a Kolmogorov-Smirnov test of the
     entries against N(0, 1); E[S^T S] = I.
   * x_OPT: Householder QR vs refined normal equations vs lstsq.
@@ -449,10 +451,50 @@ def l1_penalty_qp_bruteforce(H, g, xt, lam):
     return best
 
 
+def l2_ball_qp(H, g, xt, R, iters: int = 400):
+    """Exact minimiser of the p = 2 ball subproblem (Sec. 1's C = {x : ||x||_2 <= R}):
+        argmin_{||x||_2 <= R} 1/2 (x - xt)^T H (x - xt) - g^T (x - xt).
+    With c = H xt + g: the Newton point H^{-1} c if it lies in the ball; else
+    x(mu) = (H + mu I)^{-1} c on the sphere, mu > 0 the root of
+    ||x(mu)|| = R, found on the eigenbasis of H (numpy.linalg.eigh) by
+    bisection on [0, ||c|| / R] to the last bit (||x(mu)|| falls with mu)."""
+    c = H @ xt + g
+    xn = chol_solve(H, c)
+    if np.linalg.norm(xn) <= R:
+        return xn
+    lam, Q = np.linalg.eigh(H)
+    bq = Q.T @ c
+    norm = lambda mu: np.sqrt(np.sum((bq / (lam + mu)) ** 2))
+    lo, hi = 0.0, np.linalg.norm(c) / R
+    for _ in range(iters):
+        mid = 0.5 * (lo + hi)
+        if mid <= lo or mid >= hi:
+            break
+        if norm(mid) > R:
+            lo = mid
+        else:
+            hi = mid
+    mu = 0.5 * (lo + hi)
+    return Q @ (bq / (lam + mu))
+
+
+def l2_ball_kkt_residual(H, g, xt, R, x):
+    """Relative KKT violation of x for the p = 2 ball subproblem: stationarity
+    H (x - xt) - g + mu x = 0 with mu >= 0, and mu (||x|| - R) = 0."""
+    c = H @ xt + g
+    grad = H @ x - c
+    scale = max(np.abs(c).max(), 1e-300)
+    nx = np.linalg.norm(x)
+    if nx < R * (1 - 1e-12):
+        return np.abs(grad).max() / scale
+    mu = -float(grad @ x) / (nx * nx)
+    return max(np.abs(grad + mu * x).max(), max(0.0, -mu) * nx, abs(nx - R) / R * scale) / scale
+
+
 # --------------------------------------------------------------------------
 # IHS (Eq. 2) and its fixed point.
 # --------------------------------------------------------------------------
-OLS, L1_BALL, RIDGE, L1_PENALTY = 0, 1, 2, 3
+OLS, L1_BALL, RIDGE, L1_PENALTY, L2_BALL = 0, 1, 2, 3, 4
 
 
 def ihs(A, b, kind: int, param: float, m: int, s: int, seed: int, iters: int, x0=None,
@@ -490,6 +532,8 @@ def ihs(A, b, kind: int, param: float, m: int, s: int, seed: int, iters: int, x0
             x = l1_ball_qp(H, g, x, param)
         elif kind == L1_PENALTY:
             x = l1_penalty_qp(H, g, x, param)
+        elif kind == L2_BALL:
+            x = l2_ball_qp(H, g, x, param)
         else:
             x = x + chol_solve(H, g)
         xs.append(x.copy())
@@ -543,6 +587,12 @@ def x_opt_l1_penalty(A, b, lam):
     subproblem above with H = A^T A, x^t = 0, g = A^T b."""
     A = as_f64(A)
     return l1_penalty_qp(ata(A), atb(A, b), np.zeros(A.shape[1]), lam)
+
+
+def x_opt_l2(A, b, R):
+    """x_OPT of Eq. 1 over the p = 2 ball: the subproblem with H = A^T A, x^t = 0, g = A^T b."""
+    A = as_f64(A)
+    return l2_ball_qp(ata(A), atb(A, b), np.zeros(A.shape[1]), R)
 
 
 def err_A(x, xopt, G):

@@ -600,3 +600,59 @@ def test_ihs_gaussian_converges_to_xopt():
     errs = [O.err_A(x, xo, G) for x in xs]
     assert errs[-1] < 1e-10
     assert np.median([errs[i + 1] / errs[i] for i in range(10)]) < 0.5
+
+
+# ------------------------------------------------------------ p = 2 ball ----
+def test_l2_ball_qp_identity_is_projection():
+    """H = I: the minimiser is the Euclidean projection of x^t + g onto the ball."""
+    rng = np.random.default_rng(31)
+    d = 9
+    xt = rng.standard_normal(d)
+    g = 3 * rng.standard_normal(d)
+    v = xt + g
+    for R in (0.3 * np.linalg.norm(v), 2 * np.linalg.norm(v)):
+        want = v * min(1.0, R / np.linalg.norm(v))
+        assert np.allclose(O.l2_ball_qp(np.eye(d), g, xt, R), want, rtol=1e-13, atol=1e-14)
+
+
+def test_l2_ball_qp_against_circle_bruteforce():
+    """d = 2: the exact solver matches a brute-force minimum over 2e5 points of
+    the circle (refined by golden section) and has a vanishing KKT residual."""
+    rng = np.random.default_rng(32)
+    for trial in range(5):
+        M = rng.standard_normal((4, 2))
+        H = M.T @ M + 0.1 * np.eye(2)
+        xt = rng.standard_normal(2)
+        g = 4 * rng.standard_normal(2)
+        c = H @ xt + g
+        R = 0.5 * np.linalg.norm(np.linalg.solve(H, c))
+        q = lambda x: 0.5 * (x - xt) @ H @ (x - xt) - g @ (x - xt)
+        th = np.linspace(0, 2 * np.pi, 200001)
+        pts = R * np.stack([np.cos(th), np.sin(th)], 1)
+        vals = 0.5 * np.einsum("ij,jk,ik->i", pts - xt, H, pts - xt) - (pts - xt) @ g
+        t0 = th[np.argmin(vals)]
+        a, b = t0 - 1e-4, t0 + 1e-4
+        f = lambda t: q(R * np.array([np.cos(t), np.sin(t)]))
+        gr = (np.sqrt(5) - 1) / 2
+        for _ in range(200):
+            c1, c2 = b - gr * (b - a), a + gr * (b - a)
+            if f(c1) < f(c2):
+                b = c2
+            else:
+                a = c1
+        xb = R * np.array([np.cos(0.5 * (a + b)), np.sin(0.5 * (a + b))])
+        x = O.l2_ball_qp(H, g, xt, R)
+        assert np.allclose(x, xb, atol=1e-8), (x, xb)
+        assert O.l2_ball_kkt_residual(H, g, xt, R, x) < 1e-12
+
+
+def test_ihs_l2_ball_converges_to_xopt():
+    """IHS over the p = 2 ball (radius half of ||x_OLS||) reaches x_OPT."""
+    w = synth.make("ols_dense_fp64", n=3000, d=20, m=200)
+    A, b = w["A"], w["b"]
+    R = 0.5 * np.linalg.norm(O.x_opt_ols_qr(A, b))
+    xo = O.x_opt_l2(A, b, R)
+    G = A.T @ A
+    assert O.l2_ball_kkt_residual(G, A.T @ b, np.zeros(20), R, xo) < 1e-12
+    xs = O.ihs(A, b, O.L2_BALL, R, 200, 1, 0, 30)
+    assert O.err_A(xs[-1], xo, G) < 1e-10
