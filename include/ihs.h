@@ -71,12 +71,18 @@ typedef struct {
  *   IHS_L1_BALL    C = {x : ||x||_1 <= param}  (LASSO)     param = radius > 0
  *   IHS_RIDGE      f(x) + (param/2) ||x||^2, C = R^d       param = lambda >= 0
  *   IHS_L1_PENALTY f(x) + param ||x||_1, C = R^d            param = lambda > 0
+ *   IHS_L2_BALL    C = {x : ||x||_2 <= param}               param = radius > 0
  * Ridge is not in the paper; it is the squared-l2 penalty beside the p = 2
  * ball, with the penalty kept exact (not sketched).  IHS_L1_PENALTY is the
  * penalised LASSO of the experiments (Sec. 5, lambda = 5): each step solves
  * argmin_x 1/2 ||S A (x - x^t)||^2 - <A^T (b - A x^t), x - x^t> + lambda ||x||_1
- * exactly, the penalty unsketched. */
-enum { IHS_OLS = 0, IHS_L1_BALL = 1, IHS_RIDGE = 2, IHS_L1_PENALTY = 3 };
+ * exactly, the penalty unsketched.
+ * IHS_L2_BALL (Sec. 1's p = 2 ball) solves each step exactly through the
+ * secular equation ||(H + mu I)^{-1} (H x^t + g)|| = R (Newton's method on mu,
+ * one factorisation of H + mu I per Newton step, FP64-refined solves); the
+ * host reads two scalars per Newton step, so ihs_step / ihs_solve wait on
+ * the GPU inside each such step. */
+enum { IHS_OLS = 0, IHS_L1_BALL = 1, IHS_RIDGE = 2, IHS_L1_PENALTY = 3, IHS_L2_BALL = 4 };
 
 typedef struct {
   int kind;

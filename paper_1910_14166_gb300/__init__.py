@@ -25,9 +25,9 @@ STATUS_NAMES = {0: "IHS_OK", 1: "IHS_ERR_ARG", 2: "IHS_ERR_CUDA", 3: "IHS_ERR_OO
                 7: "IHS_ERR_TIMEOUT", 8: "IHS_ERR_UNSUPPORTED"}
 DENSE, CSR = 0, 1
 F64, F32 = 0, 1
-OLS, L1_BALL, RIDGE, L1_PENALTY = 0, 1, 2, 3
+OLS, L1_BALL, RIDGE, L1_PENALTY, L2_BALL = 0, 1, 2, 3, 4
 PREC = {"fp64": 0, "tf32": 1, "bf16": 2}
-KIND = {"ols": OLS, "l1": L1_BALL, "ridge": RIDGE, "l1pen": L1_PENALTY}
+KIND = {"ols": OLS, "l1": L1_BALL, "ridge": RIDGE, "l1pen": L1_PENALTY, "l2": L2_BALL}
 
 
 class IHSError(RuntimeError):
@@ -167,7 +167,8 @@ class IHS:
     (rowptr int32/int64, col int32, val float32/float64) with shape=(n, d).
     b: CUDA float64 vector.  The tensors are borrowed and must outlive the
     object.  kind: 'ols', 'l1' (ball, param = radius), 'l1pen' (penalised,
-    param = lambda) or 'ridge' (param = lambda).
+    param = lambda), 'l2' (p = 2 ball, param = radius) or 'ridge' (param =
+    lambda).
     precision: 'fp64' (plain), 'tf32' or 'bf16' (mixed).  fuse=False,
     serial=True and cluster=True set IHS_FLAG_NO_FUSE, IHS_FLAG_SERIAL and
     IHS_FLAG_CLUSTER; sketch: 'sparse' (CountSketch / SJLT), 'srht' or

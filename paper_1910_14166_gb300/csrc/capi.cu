@@ -102,6 +102,9 @@ struct ihs_ctx {
   double* errbuf = nullptr;
   // l1 QP
   QpWork qw{};
+  // p = 2 ball: c, x(mu), w, r, du (d each), scalars, and a barrier of its own
+  double* l2buf = nullptr;
+  unsigned* l2bar = nullptr;
   bool have_sketch = false;
   std::vector<void*> allocs;
 };
@@ -382,9 +385,11 @@ ihs_status ihs_create(ihs_ctx** out, const ihs_matrix* A, const double* b,
   if (opt->m < A->d) return IHS_ERR_ARG;
   if (opt->precision < IHS_PREC_FP64 || opt->precision > IHS_PREC_BF16) return IHS_ERR_ARG;
   if (C->kind != IHS_OLS && C->kind != IHS_L1_BALL && C->kind != IHS_RIDGE &&
-      C->kind != IHS_L1_PENALTY)
+      C->kind != IHS_L1_PENALTY && C->kind != IHS_L2_BALL)
     return IHS_ERR_ARG;
-  if ((C->kind == IHS_L1_BALL || C->kind == IHS_L1_PENALTY) && !(C->param > 0)) return IHS_ERR_ARG;
+  if ((C->kind == IHS_L1_BALL || C->kind == IHS_L1_PENALTY || C->kind == IHS_L2_BALL) &&
+      !(C->param > 0))
+    return IHS_ERR_ARG;
   if (C->kind == IHS_RIDGE && !(C->param >= 0)) return IHS_ERR_ARG;
   if (A->kind == IHS_DENSE && A->ld < A->d) return IHS_ERR_ARG;
   if (A->kind == IHS_CSR && (A->col == nullptr || A->rowptr == nullptr || A->nnz < 0))
@@ -503,6 +508,10 @@ ihs_status ihs_create(ihs_ctx** out, const ihs_matrix* A, const double* b,
     if ((size_t)(c->m / c->s) * acc_el > 200 * 1024) return fail(IHS_ERR_UNSUPPORTED);
     if ((s = build_csc(c)) != IHS_OK) return fail(s);
   }
+  if (C->kind == IHS_L2_BALL) {
+    AL2(c->l2buf, (size_t)(5 * c->d + 8) * sizeof(double));
+    AL2(c->l2bar, 4 * sizeof(unsigned));
+  }
   if (C->kind == IHS_L1_BALL || C->kind == IHS_L1_PENALTY) {
     size_t qb = qp_work_bytes((int)c->d);
     uint8_t* q;
@@ -601,11 +610,72 @@ ihs_status gradient_on(ihs_ctx* c, const double* x, double* g, double* r, bool w
   return IHS_OK;
 }
 
+// p = 2 ball step (see l2ball.cu): the Newton point, else Newton's method on
+// the secular equation, factoring H + mu I into buffer bf (its factor is not
+// needed after the step) with a barrier word of its own.
+ihs_status l2_step(ihs_ctx* c, double* x, int bf) {
+  cudaStream_t st = c->st;
+  const int d = (int)c->d;
+  const double R = c->C.param;
+  double* cv = c->l2buf;
+  double* xm = cv + d;
+  double* w = xm + d;
+  double* r = w + d;
+  double* du = r + d;
+  double* scal = du + d;
+  const int nref = c->f32fac ? 2 : 1;
+  // out = (H + mu I)^{-1} rhs with the current factor, refined in FP64
+  auto solve = [&](double mu, const double* rhs, double* out) -> cudaError_t {
+    cudaError_t e = launch_chol_apply(c->L[bf], c->Dinv[bf], d, c->f32fac, rhs, out, st);
+    for (int k = 0; k < nref && e == cudaSuccess; ++k) {
+      if ((e = launch_l2_matvec(c->H[bf], d, out, mu, rhs, -1.0, r, st)) != cudaSuccess) break;
+      if ((e = launch_chol_apply(c->L[bf], c->Dinv[bf], d, c->f32fac, r, du, st)) != cudaSuccess)
+        break;
+      e = launch_l2_axpy(out, du, d, st);
+    }
+    return e;
+  };
+  double h[2];
+  CK(launch_l2_matvec(c->H[bf], d, x, 0.0, c->g, 1.0, cv, st));  // c = H x^t + g
+  CK(solve(0.0, cv, xm));                                           // Newton point
+  CK(launch_l2_dots(xm, xm, d, scal, st));
+  CK(cudaMemcpyAsync(h, scal, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (std::sqrt(h[0]) > R) {
+    double mu = 0.0;
+    for (int it = 0; it < 100; ++it) {
+      if (it > 0)
+        CK(launch_cholesky(c->H[bf], d, c->f32fac, c->L[bf], c->Dinv[bf], c->l2bar, c->status, st,
+                           0, mu));
+      if (it > 0) CK(solve(mu, cv, xm));
+      CK(launch_chol_apply(c->L[bf], c->Dinv[bf], d, c->f32fac, xm, w, st));  // (H + mu I)^{-1} x
+      CK(launch_l2_dots(xm, w, d, scal, st));
+      CK(cudaMemcpyAsync(h, scal, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      const double nx = std::sqrt(h[0]);
+      if (!(nx > 0.0) || !(h[1] > 0.0)) break;
+      if (std::fabs(nx - R) <= 1e-15 * R) break;
+      const double next = mu + (h[0] / h[1]) * (nx - R) / R;  // phi(mu) / phi'(mu)
+      if (!(next > mu)) break;  // at the root to rounding
+      mu = next;
+    }
+  }
+  CK(launch_l2_store(xm, d, x, c->step_norm, st));
+  return IHS_OK;
+}
+
 // QP step of Eq. 2 with buffer bf (gradient already in c->g), on the caller's stream.
 ihs_status step_with(ihs_ctx* c, double* x, int bf) {
   CK(cudaStreamWaitEvent(c->st, c->ev_fac[bf], 0));
   stage_begin(c, IHS_ST_STEP, c->st);
   cudaError_t e;
+  if (c->C.kind == IHS_L2_BALL) {
+    ihs_status s = l2_step(c, x, bf);
+    stage_end(c);
+    if (s != IHS_OK) return s;
+    CK(cudaEventRecord(c->ev_use[bf], c->st));
+    return IHS_OK;
+  }
   if (c->C.kind == IHS_L1_BALL || c->C.kind == IHS_L1_PENALTY)
     e = launch_l1_step(c->H[bf], c->L[bf], c->Dinv[bf], c->f32fac, (int)c->d, c->g, c->C.param,
                        c->C.kind == IHS_L1_PENALTY, c->opt.qp_max_iter, c->opt.qp_tol, c->qw, x,
@@ -815,7 +885,8 @@ ihs_status ihs_sketch_error(ihs_ctx* c, int64_t t, const double* G, double* err)
 ihs_status ihs_adjoint(ihs_ctx* c, const double* x, const double* dLdx, double* dLdb, void* dLdA,
                        ihs_report* rep) {
   if (!c || !x || !dLdx) return IHS_ERR_ARG;
-  if (c->C.kind == IHS_L1_BALL || c->C.kind == IHS_L1_PENALTY) return IHS_ERR_UNSUPPORTED;
+  if (c->C.kind == IHS_L1_BALL || c->C.kind == IHS_L1_PENALTY || c->C.kind == IHS_L2_BALL)
+    return IHS_ERR_UNSUPPORTED;
   if (!c->have_sketch) return IHS_ERR_ARG;
   if (dLdA && !c->dense) return IHS_ERR_UNSUPPORTED;
   const int d = (int)c->d;

@@ -135,11 +135,11 @@ int chol_padded(int d);  // d rounded up to the 32-tile
 // Lbuf: dp x dp (lower: L, upper: L^T tiles); Dinv: dp/32 tiles of 32 x 32;
 // bar: 4 unsigned of barrier state (zeroed by the launcher).
 size_t chol_dinv_bytes(int d, int f32);
-// Factor with the 16-CTA cluster kernel when allow_cluster and the matrix
-// fits in the cluster's shared memory, else with the cooperative grid kernel
-// (the two give identical factors).
+// Factor H + shift I with the 16-CTA cluster kernel when allow_cluster (and
+// shift == 0) and the matrix fits in the cluster's shared memory, else with
+// the cooperative grid kernel (the two give identical factors).
 cudaError_t launch_cholesky(const double* H, int d, int f32, void* Lbuf, void* Dinv, unsigned* bar,
-                            int* status, cudaStream_t st, int allow_cluster);
+                            int* status, cudaStream_t st, int allow_cluster, double shift = 0.0);
 // x += (L L^T)^{-1} g ; step_norm (device double) gets max |delta|.
 cudaError_t launch_chol_step(const void* Lbuf, const void* Dinv, int d, int f32, const double* g,
                              double* x, double* step_norm, cudaStream_t st);
@@ -189,6 +189,14 @@ cudaError_t launch_gauss(void* cublas, const DenseA& A, const SketchKeys& K, int
                          void* Gbuf, void* Abuf, void* SA, cudaStream_t st);
 void* gauss_blas_create();
 void gauss_blas_destroy(void* h);
+
+// ---- p = 2 ball step (host-driven secular iteration; kernels in l2ball.cu) ------
+cudaError_t launch_l2_matvec(const double* H, int d, const double* x, double mu, const double* base,
+                             double sgn, double* out, cudaStream_t st);
+cudaError_t launch_l2_dots(const double* a, const double* b, int d, double* scal, cudaStream_t st);
+cudaError_t launch_l2_axpy(double* y, const double* a, int d, cudaStream_t st);
+cudaError_t launch_l2_store(const double* src, int d, double* x, double* step_norm,
+                            cudaStream_t st);
 
 // ---- adjoint (ridge / OLS) -----------------------------------------------------
 cudaError_t launch_cg_init(const double* rhs, int d, double* v, double* r, double* scal,

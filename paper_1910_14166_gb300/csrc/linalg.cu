@@ -41,13 +41,14 @@ size_t chol_dinv_bytes(int d, int f32) {
 }
 
 template <typename T>
-__global__ void k_chol_init(const double* __restrict__ H, int d, int dp, T* __restrict__ L) {
+__global__ void k_chol_init(const double* __restrict__ H, int d, int dp, double shift,
+                            T* __restrict__ L) {
   const int64_t total = (int64_t)dp * dp;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
        e += (int64_t)gridDim.x * blockDim.x) {
     const int i = (int)(e / dp), j = (int)(e - (int64_t)i * dp);
     T v;
-    if (i < d && j < d) v = (T)H[(int64_t)i * d + j];
+    if (i < d && j < d) v = (T)(H[(int64_t)i * d + j] + (i == j ? shift : 0.0));
     else v = (i == j) ? T(1) : T(0);
     L[e] = v;
   }
@@ -427,16 +428,17 @@ static cudaError_t chol_cluster_launch(const double* H, int d, T* L, T* Dinv, in
 }
 
 template <typename T>
-static cudaError_t chol_impl(const double* H, int d, T* L, T* Dinv, unsigned* bar, int* status,
+static cudaError_t chol_impl(const double* H, int d, double shift, T* L, T* Dinv, unsigned* bar,
+                             int* status,
                              cudaStream_t st, bool allow_cluster) {
   int dp = chol_padded(d), Tt = dp / 32;
-  if (allow_cluster) {
+  if (allow_cluster && shift == 0.0) {
     bool used = false;
     cudaError_t e = chol_cluster_launch<T>(H, d, L, Dinv, status, st, &used);
     if (e != cudaSuccess || used) return e;
   }
   const int blocks = (int)std::min<int64_t>(((int64_t)dp * dp + 255) / 256, 2048);
-  { k_chol_init<T><<<blocks, 256, 0, st>>>(H, d, dp, L); note_launches(1); }
+  { k_chol_init<T><<<blocks, 256, 0, st>>>(H, d, dp, shift, L); note_launches(1); }
   cudaError_t e = cudaMemsetAsync(bar, 0, 4 * sizeof(unsigned), st);
   if (e != cudaSuccess) return e;
   int dev = 0, sms = 0, per = 0;
@@ -458,9 +460,10 @@ static cudaError_t chol_impl(const double* H, int d, T* L, T* Dinv, unsigned* ba
 }
 
 cudaError_t launch_cholesky(const double* H, int d, int f32, void* Lbuf, void* Dinv, unsigned* bar,
-                            int* status, cudaStream_t st, int allow_cluster) {
-  return f32 ? chol_impl<float>(H, d, (float*)Lbuf, (float*)Dinv, bar, status, st, allow_cluster != 0)
-             : chol_impl<double>(H, d, (double*)Lbuf, (double*)Dinv, bar, status, st,
+                            int* status, cudaStream_t st, int allow_cluster, double shift) {
+  return f32 ? chol_impl<float>(H, d, shift, (float*)Lbuf, (float*)Dinv, bar, status, st,
+                                allow_cluster != 0)
+             : chol_impl<double>(H, d, shift, (double*)Lbuf, (double*)Dinv, bar, status, st,
                                  allow_cluster != 0);
 }
 

@@ -609,3 +609,55 @@ def test_ihs_gaussian_mixed_reaches_1e10(cuda_lib):
     x, rep = sv.solve(iters=30)
     assert rep.status == 0
     assert O.err_A(x.cpu().numpy(), xo, G) < 1e-10
+
+
+def test_ihs_l2_ball_plain_matches_oracle_every_iteration(cuda_lib):
+    """p = 2 ball (R = ||x_OLS|| / 2, the constraint active), 20000 x 50 FP64
+    OLS data: every GPU iterate within 1e-11 of the oracle's (whose subproblem
+    solver is the secular equation on H's eigenbasis, a different route),
+    1e-10 of x_OPT after 30 iterations."""
+    w = synth.make("ols_dense_fp64")
+    A, b = w["A"], w["b"]
+    R = 0.5 * np.linalg.norm(O.x_opt_ols_qr(A, b))
+    xo = O.x_opt_l2(A, b, R)
+    G = A.T @ A
+    xs = O.ihs(A, b, O.L2_BALL, R, 500, 1, 0, 30)
+    sv = cuda_lib.IHS(dev(A), dev(b), kind="l2", param=R, m=500, seed=0, precision="fp64")
+    x = torch.zeros(w["d"], dtype=torch.float64, device="cuda")
+    nrm = np.sqrt(xo @ G @ xo)
+    for t in range(30):
+        sv.solve(x, t0=t, iters=1)
+        e = x.cpu().numpy() - xs[t + 1]
+        assert np.sqrt(max(e @ G @ e, 0.0)) / nrm <= 1e-11, t
+    assert O.err_A(x.cpu().numpy(), xo, G) < 1e-10
+    assert np.linalg.norm(x.cpu().numpy()) <= R * (1 + 1e-12)
+
+
+@pytest.mark.parametrize("frac", [0.3, 2.0])
+def test_ihs_l2_ball_mixed_reaches_1e10(cuda_lib, frac):
+    """Mixed form (FP32 factor of H + mu I, FP64-refined solves) on AR(1) FP32
+    data reaches 1e-10 of x_OPT, with the ball active (0.3) and inactive (2.0)."""
+    w = synth.make("ols_dense_ar1", n=100000, d=96, m=960)
+    A64 = w["A"].astype(np.float64)
+    R = frac * np.linalg.norm(O.x_opt_ols_normal(A64, w["b"]))
+    xo = O.x_opt_l2(A64, w["b"], R)
+    G = A64.T @ A64
+    sv = cuda_lib.IHS(dev(w["A"]), dev(w["b"]), kind="l2", param=R, m=960, seed=0,
+                      precision="tf32")
+    x, rep = sv.solve(iters=30)
+    assert rep.status == 0
+    assert O.err_A(x.cpu().numpy(), xo, G) < 1e-10
+
+
+def test_ihs_l2_ball_csr(cuda_lib):
+    """p = 2 ball over CSR data with an SJLT (s = 4), plain form: 1e-10 of x_OPT."""
+    w, C = _csr_problem("lasso_csr_fp64", 100000, 200, 2000)
+    xols = O.x_opt_ols_normal(C, w["b"])
+    R = 0.4 * np.linalg.norm(xols)
+    G = C.gram()
+    xo = O.l2_ball_qp(G, C.rmatvec(w["b"]), np.zeros(w["d"]), R)
+    sv = cuda_lib.IHS((dev(w["rowptr"]), dev(w["col"]), dev(w["val"])), dev(w["b"]), kind="l2",
+                      param=R, m=2000, s=4, seed=0, precision="fp64", shape=(w["n"], w["d"]))
+    x, rep = sv.solve(iters=30)
+    assert rep.status == 0
+    assert O.err_A(x.cpu().numpy(), xo, G) < 1e-10
