@@ -487,8 +487,9 @@ def run_sketch_quality(args):
 
 def run_workloads(args):
     """Time every workload of the suite (and the penalised-LASSO form on the
-    two sparse ones, lambda = 5; the SRHT and Gaussian comparison sketches on
-    the two dense OLS ones) through ihs_solve: CUDA events around the
+    two sparse ones, lambda = 5; the SRHT and Gaussian comparison sketches and
+    the p = 2 ball of radius ||x*|| / 2 on the two dense OLS ones) through
+    ihs_solve: CUDA events around the
     call, median of `--steps` runs after one warm-up, plus the library's stage
     times (one serial-mode run: every stage on one stream) and launch count.
     The dense 1,048,576 x 500 OLS line is the main benchmark's step.  One JSON
@@ -500,7 +501,8 @@ def run_workloads(args):
              ("lasso_csr_zipf", None, None, "sparse"), ("lasso_csr_fp64", "l1pen", 5.0, "sparse"),
              ("lasso_csr_zipf", "l1pen", 5.0, "sparse"), ("ols_dense_fp64", None, None, "srht"),
              ("ols_dense_ar1", None, None, "srht"), ("ols_dense_fp64", None, None, "gaussian"),
-             ("ols_dense_ar1", None, None, "gaussian")]
+             ("ols_dense_ar1", None, None, "gaussian"), ("ols_dense_fp64", "l2", "half", "sparse"),
+             ("ols_dense_ar1", "l2", "half", "sparse")]
     for name, kind_o, param_o, sketch in cases:
         if args.only and name not in args.only.split(","):
             continue
@@ -513,6 +515,8 @@ def run_workloads(args):
             shape = (w["n"], w["d"])
         kind = kind_o or {"ols": "ols", "l1": "l1", "ridge": "ridge"}[w["kind"]]
         param = w["param"] if param_o is None else param_o
+        if param_o == "half":  # p = 2 ball of radius ||x*|| / 2 (the constraint active)
+            param = 0.5 * float(np.linalg.norm(w["x_star"]))
         iters = w["iters"] or 25
         times = []
         for serial in (False, True):
