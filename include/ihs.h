@@ -153,6 +153,8 @@ typedef struct {
  * b: DEVICE, n doubles, borrowed.  C, opt: HOST structs, copied.
  * stream: a cudaStream_t (NULL = legacy default stream).  For CSR input a
  * column-major (CSC) copy of A is built once here and owned by the context.
+ * Workspaces come from a library-owned device memory pool (see
+ * ihs_trim_memory).
  * Synchronises.  Errors: IHS_ERR_ARG for shapes (m % s != 0, m < d, d > 1024,
  * n >= 2^31, bad kind/dtype), IHS_ERR_OOM, IHS_ERR_CUDA. */
 ihs_status ihs_create(ihs_ctx** out, const ihs_matrix* A, const double* b,
@@ -196,6 +198,14 @@ ihs_status ihs_sync(ihs_ctx* ctx);
  * IHS_ERR_ARG if no sketch has been formed yet. */
 ihs_status ihs_get_sketch(ihs_ctx* ctx, void* SA_out, int* SA_dtype, double* H_out,
                           double* scale);
+
+/* ihs_trim_memory -- contexts take their device workspaces from a
+ * library-owned memory pool per device that keeps what ihs_destroy frees, so
+ * that creating the next context does not map new device memory.  This call
+ * returns every pool's unused memory to the device.  Call it with no context
+ * operation in flight (it does not synchronise streams).  Errors:
+ * IHS_ERR_CUDA. */
+ihs_status ihs_trim_memory(void);
 
 /* ihs_exact_gram -- G = A^T A in FP64 (DEVICE, d x d doubles, row-major,
  * both triangles), the reference of the sketch-quality experiment (App. B:

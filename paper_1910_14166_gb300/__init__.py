@@ -81,6 +81,7 @@ def _load():
         "ihs_profile_read": [vp, ctypes.POINTER(f64), ctypes.POINTER(i32), ctypes.POINTER(i64)],
         "ihs_gradient_noalloc": [ctypes.POINTER(_Matrix), vp, vp, f64, vp, vp],
         "ihs_exact_gram": [vp, vp],
+        "ihs_trim_memory": [],
         "ihs_sketch_error": [vp, i64, vp, ctypes.POINTER(f64)],
     }
     for name, args in sig.items():
@@ -158,6 +159,12 @@ def ihs_gradient_noalloc(A, b, x, lam=0.0):
     _check(_lib.ihs_gradient_noalloc(ctypes.byref(M), _ptr(b), _ptr(x), float(lam), _ptr(g),
                                      _stream()), "ihs_gradient_noalloc")
     return g
+
+
+def trim_memory():
+    """Return the library's cached device workspace memory to the device
+    (contexts keep reusing it otherwise; see ihs_trim_memory)."""
+    _check(_lib.ihs_trim_memory(), "ihs_trim_memory")
 
 
 class IHS:

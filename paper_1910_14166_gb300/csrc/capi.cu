@@ -8,6 +8,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -179,11 +180,47 @@ ihs_status cuda_status(cudaError_t e) {
     if (e_ != cudaSuccess) return cuda_status(e_);  \
   } while (0)
 
+// Library-owned stream-ordered memory pool, one per device, whose release
+// threshold is the maximum: what ihs_destroy frees stays in the pool, and the
+// next ihs_create on the device takes it back without new device mappings
+// (a create with ~25 separate cudaMalloc calls cost milliseconds).
+// ihs_trim_memory returns the pool's unused memory to the device.
+constexpr int kMaxDevices = 64;
+std::mutex g_pool_mu;
+cudaMemPool_t g_pool[kMaxDevices] = {};
+
+cudaError_t library_pool(cudaMemPool_t* out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lk(g_pool_mu);
+  if (!g_pool[dev]) {
+    cudaMemPoolProps props = {};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    if ((e = cudaMemPoolCreate(&g_pool[dev], &props)) != cudaSuccess) return e;
+    uint64_t keep = UINT64_MAX;
+    if ((e = cudaMemPoolSetAttribute(g_pool[dev], cudaMemPoolAttrReleaseThreshold, &keep)) !=
+        cudaSuccess)
+      return e;
+  }
+  *out = g_pool[dev];
+  return cudaSuccess;
+}
+
 template <typename T>
 ihs_status dalloc(ihs_ctx* c, T** p, size_t bytes) {
   void* q = nullptr;
   if (bytes == 0) bytes = 16;
-  cudaError_t e = cudaMalloc(&q, bytes);
+  cudaMemPool_t pool;
+  cudaError_t e = library_pool(&pool);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return IHS_ERR_CUDA;
+  }
+  e = cudaMallocFromPoolAsync(&q, bytes, pool, c->st);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return IHS_ERR_OOM;
@@ -368,7 +405,8 @@ void ihs_destroy(ihs_ctx* c) {
   }
   if (c->st2) cudaStreamDestroy(c->st2);
   gauss_blas_destroy(c->blas);
-  for (void* p : c->allocs) cudaFree(p);
+  for (void* p : c->allocs) cudaFreeAsync(p, c->st);
+  cudaStreamSynchronize(c->st);
   delete c;
 }
 
@@ -844,6 +882,13 @@ ihs_status ihs_get_sketch(ihs_ctx* c, void* SA_out, int* SA_dtype, double* H_out
   if (H_out)
     CK(cudaMemcpyAsync(H_out, c->H[c->cur], (size_t)c->d * c->d * sizeof(double),
                        cudaMemcpyDeviceToDevice, c->st));
+  return IHS_OK;
+}
+
+ihs_status ihs_trim_memory(void) {
+  std::lock_guard<std::mutex> lk(g_pool_mu);
+  for (int k = 0; k < kMaxDevices; ++k)
+    if (g_pool[k]) CK(cudaMemPoolTrimTo(g_pool[k], 0));
   return IHS_OK;
 }
 

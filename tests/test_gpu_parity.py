@@ -661,3 +661,22 @@ def test_ihs_l2_ball_csr(cuda_lib):
     x, rep = sv.solve(iters=30)
     assert rep.status == 0
     assert O.err_A(x.cpu().numpy(), xo, G) < 1e-10
+
+
+def test_contexts_reuse_pool_memory_and_trim(cuda_lib):
+    """Workspaces come from the library's pool: creating and destroying
+    contexts in a loop gives the same results each time, and trimming the
+    pool between them changes nothing but the cached memory."""
+    w = synth.make("ols_dense_fp64", n=5000, d=30, m=300)
+    A, b = dev(w["A"]), dev(w["b"])
+    xs = []
+    for k in range(4):
+        sv = cuda_lib.IHS(A, b, m=300, seed=2, precision="fp64")
+        x, rep = sv.solve(iters=5)
+        assert rep.status == 0
+        xs.append(x.cpu().numpy())
+        sv.close()
+        if k == 1:
+            cuda_lib.trim_memory()
+    for x in xs[1:]:
+        assert np.array_equal(x, xs[0])
