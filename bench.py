@@ -409,13 +409,15 @@ def run_iters_only(args):
     else:
         A = tuple(torch.from_numpy(w[k]).cuda() for k in ("rowptr", "col", "val"))
         shape = (w["n"], w["d"])
-    kind = {"ols": "ols", "l1": "l1", "ridge": "ridge"}[w["kind"]]
-    sv = ihs.IHS(A, b, kind=kind, param=w["param"], m=w["m"], s=w["s"], seed=0, precision=prec,
-                 shape=shape)
+    kind = args.kind or {"ols": "ols", "l1": "l1", "ridge": "ridge"}[w["kind"]]
+    param = w["param"] if args.param is None else args.param
+    sv = ihs.IHS(A, b, kind=kind, param=param, m=w["m"], s=w["s"], seed=0, precision=prec,
+                 shape=shape, sketch=args.sketch)
     x, rep = sv.solve(iters=args.ncu_iters)
     torch.cuda.synchronize()
-    print("iters_only ok: %s n=%d d=%d m=%d s=%d precision=%s iters=%d status=%d"
-          % (args.workload, w["n"], w["d"], w["m"], w["s"], prec, args.ncu_iters, rep.status))
+    print("iters_only ok: %s n=%d d=%d m=%d s=%d precision=%s kind=%s sketch=%s iters=%d status=%d"
+          % (args.workload, w["n"], w["d"], w["m"], w["s"], prec, kind, args.sketch, args.ncu_iters,
+             rep.status))
 
 
 def run_sketch_quality(args):
@@ -570,6 +572,12 @@ def main():
     ap.add_argument("--experiment", default=None, choices=["sketch-quality", "workloads"],
                     help="run an experiment instead of the benchmark (one JSON line per point)")
     ap.add_argument("--trials", type=int, default=10)
+    ap.add_argument("--sketch", default="sparse", choices=["sparse", "srht", "gaussian"],
+                    help="profiling driver: sketch family")
+    ap.add_argument("--kind", default=None, choices=["ols", "l1", "l1pen", "l2", "ridge"],
+                    help="profiling driver: constraint (default: the workload's)")
+    ap.add_argument("--param", type=float, default=None,
+                    help="profiling driver: constraint parameter (default: the workload's)")
     ap.add_argument("--seed", type=int, default=0)
     args = ap.parse_args()
     args.precision_given = any(a == "--precision" or a.startswith("--precision=") for a in sys.argv[1:])
