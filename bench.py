@@ -267,10 +267,17 @@ def run_ours(args, rank, world):
     ms_stage, cnt, launches = prof
     a_bytes = n * d * 4
     fused = cnt["grad"] == 0 and cnt["sketch"] > 0
+    lookahead = 0 < cnt["sketch"] < cnt["grad"]
     if fused:
         # one pass: A, the sorted pair list (4 B/row), b as a float pair (8 B/row), SA out
         alg = {"sketch": a_bytes + m * d * 4 + n * 12}
         names = {"sketch": "k_sketch_grad_fused"}
+    elif lookahead:
+        # look-ahead pipeline: per solve one sketch-only pass, then T fused passes
+        # (gradient + SA of the next iteration; the last one without SA)
+        alg = {"grad": a_bytes + n * 12 + m * d * 4 * (T_mixed - 1) / T_mixed,
+               "sketch": a_bytes + m * d * 4}
+        names = {"grad": "k_sketch_grad_fused", "sketch": "k_sketch_dense"}
     else:
         alg = {"sketch": a_bytes + m * d * 4, "grad": a_bytes + n * 8}
         names = {"sketch": "k_sketch_dense", "grad": "k_rg_dense_f32"}
@@ -289,7 +296,7 @@ def run_ours(args, rank, world):
 
     # the mixed form with SA and the gradient in two separate passes, for comparison
     ms_two = None
-    if fused and not args.no_two_pass:
+    if (fused or lookahead) and not args.no_two_pass:
         two = ihs.IHS(A, b, kind="ols", m=m, s=s, seed=0, precision=args.precision, fuse=False)
         ms_two, _, _ = timed(two, T_mixed, max(1, args.steps // 2), 1)
         del two

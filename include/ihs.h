@@ -129,7 +129,7 @@ enum { IHS_SKETCH_SPARSE = 0, IHS_SKETCH_SRHT = 1, IHS_SKETCH_GAUSSIAN = 2 };
  * two separate passes over A even where the single fused pass applies (dense
  * FP32 data, mixed precision, CountSketch, d <= 512); results agree to
  * rounding, the fused pass reads A once instead of twice. */
-enum { IHS_FLAG_NO_FUSE = 1, IHS_FLAG_SERIAL = 2, IHS_FLAG_CLUSTER = 4 };
+enum { IHS_FLAG_NO_FUSE = 1, IHS_FLAG_SERIAL = 2, IHS_FLAG_CLUSTER = 4, IHS_FLAG_NO_LOOKAHEAD = 8 };
 /* IHS_FLAG_SERIAL: issue the sketch chain (draw, sort, SA, Gram, factor) on
  * the caller's stream too, instead of overlapping it with the gradient and
  * step on an internal stream.  Same results; useful for timing stages.
@@ -138,7 +138,14 @@ enum { IHS_FLAG_NO_FUSE = 1, IHS_FLAG_SERIAL = 2, IHS_FLAG_CLUSTER = 4 };
  * cluster barriers between steps) where it fits (FP32 up to d = 1024, FP64
  * up to d = 768), instead of the cooperative grid kernel.  The two give
  * identical factors; the grid kernel, spread over every SM, is the faster
- * one at the sizes measured so far. */
+ * one at the sizes measured so far.
+ * IHS_FLAG_NO_LOOKAHEAD: with the fused pass, form SA of iteration t and the
+ * gradient of iteration t in the same pass and factor before the step.  By
+ * default the pass of iteration t forms the gradient of t and SA of t + 1,
+ * so the Gram and factor of t + 1 (on a 16-CTA share of the GPU) run beside
+ * the step of t and the pass of t + 1 instead of between them; SA of the
+ * first iteration then takes one sketch-only pass.  Same sketches, same
+ * iterates to rounding. */
 
 typedef struct {
   int iters;            /* iterations taken                                */

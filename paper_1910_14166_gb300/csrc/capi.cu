@@ -14,6 +14,11 @@
 
 #include "internal.h"
 
+// CTAs of the factor that runs beside the look-ahead fused pass (the pass
+// leaves these slots free: at d <= 512 the factor on 16 SMs still ends well
+// within one pass).
+constexpr int kLookaheadFactorCtas = 16;
+
 static int64_t g_launches = 0;  // kernel launches issued by the library
 void note_launches(int k) { __atomic_add_fetch(&g_launches, (int64_t)k, __ATOMIC_RELAXED); }
 int64_t launches_total() { return __atomic_load_n(&g_launches, __ATOMIC_RELAXED); }
@@ -32,6 +37,8 @@ struct ihs_ctx {
   cudaEvent_t ev_use[2] = {};  // last step reading buffer b done
   cudaEvent_t ev_join = nullptr;
   cudaEvent_t ev_grad = nullptr;  // gradient pass of the current iteration done
+  cudaEvent_t ev_sa = nullptr;    // look-ahead: SA of the next counter formed
+  cudaEvent_t ev_gram = nullptr;  // look-ahead: the Gram has read SA (SA free)
   bool prof = false;
   StageEvents pe;
   double prof_ms[IHS_NSTAGES] = {};
@@ -58,6 +65,7 @@ struct ihs_ctx {
   int32_t* seg2 = nullptr;
   int32_t* chunk_first2 = nullptr;
   bool fused = false;              // ihs_solve uses the single fused pass
+  bool lookahead = false;          // ... forming SA one iteration ahead
   double* gcta = nullptr;          // per-CTA gradient partials of the fused pass
   cudaEvent_t ev_sort[2] = {};
   cudaEvent_t ev_read[2] = {};
@@ -399,6 +407,8 @@ void ihs_destroy(ihs_ctx* c) {
   }
   if (c->ev_join) cudaEventDestroy(c->ev_join);
   if (c->ev_grad) cudaEventDestroy(c->ev_grad);
+  if (c->ev_sa) cudaEventDestroy(c->ev_sa);
+  if (c->ev_gram) cudaEventDestroy(c->ev_gram);
   for (int k = 0; k < 2; ++k) {
     if (c->ev_sort[k]) cudaEventDestroy(c->ev_sort[k]);
     if (c->ev_read[k]) cudaEventDestroy(c->ev_read[k]);
@@ -479,7 +489,9 @@ ihs_status ihs_create(ihs_ctx** out, const ihs_matrix* A, const double* b,
       return fail(IHS_ERR_CUDA);
   }
   if (cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&c->ev_grad, cudaEventDisableTiming) != cudaSuccess)
+      cudaEventCreateWithFlags(&c->ev_grad, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_sa, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_gram, cudaEventDisableTiming) != cudaSuccess)
     return fail(IHS_ERR_CUDA);
   for (int k = 0; k < 2; ++k) {
     if (cudaEventCreateWithFlags(&c->ev_sort[k], cudaEventDisableTiming) != cudaSuccess ||
@@ -512,7 +524,15 @@ ihs_status ihs_create(ihs_ctx** out, const ihs_matrix* A, const double* b,
   }
   if (c->dense) {
     c->DA = DenseA{A->val, A->n, A->d, A->ld, A->dtype == IHS_F32};
-    c->sp = make_sort_plan((int64_t)c->s * c->n, (int)c->m, c->sms * 16);
+    c->srht = opt->sketch == IHS_SKETCH_SRHT;
+    c->gauss = opt->sketch == IHS_SKETCH_GAUSSIAN;
+    c->fused = !c->acc64 && !c->srht && !c->gauss && fused_supported(c->DA, c->s) &&
+               !(opt->flags & IHS_FLAG_NO_FUSE);
+    c->lookahead = c->fused && !(opt->flags & IHS_FLAG_NO_LOOKAHEAD);
+    // one warp per chunk; the fused pass runs two CTAs of eight warps per SM,
+    // less the SMs' share left to the factor that runs beside it
+    const int warps = c->lookahead ? (2 * c->sms - kLookaheadFactorCtas) * 8 : c->sms * 16;
+    c->sp = make_sort_plan((int64_t)c->s * c->n, (int)c->m, warps);
     if ((size_t)c->m * sizeof(int32_t) > 200 * 1024) return fail(IHS_ERR_UNSUPPORTED);
     AL2(c->sort_ws, sort_workspace_bytes(c->sp));
     AL2(c->perm, c->sp.P * sizeof(uint32_t));
@@ -521,10 +541,6 @@ ihs_status ihs_create(ihs_ctx** out, const ihs_matrix* A, const double* b,
     AL2(c->sk_partial, (size_t)2 * c->sp.nchunks * c->d * acc_el);
     c->rg_warps = rg_dense_warps(c->n);
     AL2(c->gpart, (size_t)c->rg_warps * c->d * sizeof(double));
-    c->srht = opt->sketch == IHS_SKETCH_SRHT;
-    c->gauss = opt->sketch == IHS_SKETCH_GAUSSIAN;
-    c->fused = !c->acc64 && !c->srht && !c->gauss && fused_supported(c->DA, c->s) &&
-               !(opt->flags & IHS_FLAG_NO_FUSE);
     if (c->gauss) {
       const int64_t nc = gauss_chunk(c->m, c->n);
       AL2(c->gauss_G, (size_t)c->m * nc * acc_el);
@@ -586,8 +602,11 @@ double gram_scale(const ihs_ctx* c) {
 
 // The sketch chain of counter t into buffer `bf`, on the internal stream:
 // draw S and sort (dense), SA, Gram (+ lambda I), Cholesky factor.  Waits
-// for the last step that read buffer `bf`; records ev_fac[bf].
-ihs_status sketch_chain(ihs_ctx* c, int64_t t, int bf) {
+// for the last step that read buffer `bf`; records ev_fac[bf] (and
+// after_gram, if given, once the Gram has read SA).  fac_ctas > 0 caps the
+// factor's grid.
+ihs_status sketch_chain(ihs_ctx* c, int64_t t, int bf, int fac_ctas = 0,
+                        cudaEvent_t after_gram = nullptr) {
   cudaStream_t s2 = (c->opt.flags & IHS_FLAG_SERIAL) ? c->st : c->st2;
   CK(cudaStreamWaitEvent(s2, c->ev_use[bf], 0));
   const SketchKeys K = make_keys(c->opt.seed, t, c->s, c->m);
@@ -619,9 +638,10 @@ ihs_status sketch_chain(ihs_ctx* c, int64_t t, int bf) {
   CK(launch_gram(c->gp, c->SA, c->gop, c->gpart_f, c->gpart_d, gram_scale(c), shift, c->H[bf],
                  c->status, s2));
   stage_end(c);
+  if (after_gram) CK(cudaEventRecord(after_gram, s2));
   stage_begin(c, IHS_ST_FACTOR, s2);
   CK(launch_cholesky(c->H[bf], (int)c->d, c->f32fac, c->L[bf], c->Dinv[bf], c->bar, c->status,
-                     s2, (c->opt.flags & IHS_FLAG_CLUSTER) != 0));
+                     s2, (c->opt.flags & IHS_FLAG_CLUSTER) != 0, 0.0, fac_ctas));
   stage_end(c);
   CK(cudaEventRecord(c->ev_fac[bf], s2));
   return IHS_OK;
@@ -767,6 +787,65 @@ ihs_status fused_iteration(ihs_ctx* c, double* x, int pb, int bf) {
   return step_with(c, x, bf);
 }
 
+// Look-ahead fused pipeline.  Pass k (caller's stream) reads A once for the
+// gradient at x^k and SA of counter t0+k+1; the Gram and factor of t0+k+1
+// then run on the internal stream beside the step of k and the pass of k+1
+// (the factor on kLookaheadFactorCtas CTAs, the slots the pass leaves free),
+// and the sort of counter t0+k+3 follows them there.  Counter t0's SA comes
+// from a sketch-only pass first; the last pass forms the gradient only (in
+// the row order of the last sort), so SA, H and the factor left behind are
+// those of the last iteration, as in the other loops.  Sort buffer u&1 holds
+// counter t0+u; factor buffers alternate as in the other loops.
+ihs_status fused_lookahead(ihs_ctx* c, double* x, int64_t t0, int iters) {
+  const bool serial = (c->opt.flags & IHS_FLAG_SERIAL) != 0;
+  cudaStream_t s1 = c->st, s2 = serial ? c->st : c->st2;
+  const int fac_ctas = serial ? 0 : kLookaheadFactorCtas;
+  const double lam = (c->C.kind == IHS_RIDGE) ? c->C.param : 0.0;
+  ihs_status s;
+  int bf = c->cur ^ 1;  // factor buffer of counter t0
+  if ((s = sketch_chain(c, t0, bf, fac_ctas, c->ev_gram)) != IHS_OK) return s;
+  CK(cudaEventRecord(c->ev_read[0], s2));  // the sketch-only pass read sort buffer 0
+  if (iters > 1 && (s = fused_sort(c, t0 + 1, 1)) != IHS_OK) return s;
+  if (iters > 2 && (s = fused_sort(c, t0 + 2, 0)) != IHS_OK) return s;
+  for (int k = 0; k < iters; ++k) {
+    const bool ahead = k + 1 < iters;
+    const int pb = ahead ? (k + 1) & 1 : k & 1;
+    const int nb = bf ^ 1;  // factor buffer of counter t0+k+1
+    if (k > 0 || ahead) CK(cudaStreamWaitEvent(s1, c->ev_sort[pb], 0));
+    else CK(cudaStreamWaitEvent(s1, c->ev_read[0], 0));  // one pass: counter t0's sort
+    CK(cudaStreamWaitEvent(s1, c->ev_gram, 0));  // SA no longer needed by the last Gram
+    // timed as the gradient stage: the sketch stage is the sketch-only pass
+    stage_begin(c, IHS_ST_GRAD, s1);
+    cudaError_t e = launch_sketch_grad_fused(
+        c->DA, c->sp, pb ? c->perm2 : c->perm, pb ? c->seg2 : c->seg,
+        pb ? c->chunk_first2 : c->chunk_first, c->bsplit, x, (float*)c->SA,
+        (float*)c->sk_partial, c->gcta, c->g, lam, s1, c->prof ? c : nullptr, ahead);
+    stage_end(c);
+    CK(e);
+    CK(cudaEventRecord(c->ev_read[pb], s1));
+    if (ahead) {
+      CK(cudaEventRecord(c->ev_sa, s1));
+      CK(cudaStreamWaitEvent(s2, c->ev_sa, 0));
+      CK(cudaStreamWaitEvent(s2, c->ev_use[nb], 0));  // step k-1 read factor buffer nb
+      stage_begin(c, IHS_ST_GRAM, s2);
+      CK(launch_gram(c->gp, c->SA, c->gop, c->gpart_f, c->gpart_d, gram_scale(c), lam,
+                     c->H[nb], c->status, s2));
+      stage_end(c);
+      CK(cudaEventRecord(c->ev_gram, s2));
+      stage_begin(c, IHS_ST_FACTOR, s2);
+      CK(launch_cholesky(c->H[nb], (int)c->d, c->f32fac, c->L[nb], c->Dinv[nb], c->bar,
+                         c->status, s2, (c->opt.flags & IHS_FLAG_CLUSTER) != 0, 0.0, fac_ctas));
+      stage_end(c);
+      CK(cudaEventRecord(c->ev_fac[nb], s2));
+      if (k + 3 < iters && (s = fused_sort(c, t0 + k + 3, pb)) != IHS_OK) return s;
+    }
+    if ((s = step_with(c, x, bf)) != IHS_OK) return s;
+    c->cur = bf;
+    bf = nb;
+  }
+  return IHS_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -817,7 +896,11 @@ ihs_status ihs_solve(ihs_ctx* c, double* x, int64_t t0, int iters, ihs_report* r
     CK(cudaMemsetAsync(c->qw.need + 1, 0, sizeof(int), c->st));
   }
   ihs_status s = IHS_OK;
-  if (iters > 0 && c->fused) {
+  if (iters > 0 && c->lookahead) {
+    if ((s = join_caller(c)) != IHS_OK) return s;
+    if ((s = fused_lookahead(c, x, t0, iters)) != IHS_OK) return s;
+    c->have_sketch = true;
+  } else if (iters > 0 && c->fused) {
     if ((s = join_caller(c)) != IHS_OK) return s;
     if ((s = fused_sort(c, t0, 0)) != IHS_OK) return s;
     int bf = c->cur ^ 1;

@@ -14,7 +14,8 @@
 // in a fixed warp order, then over CTAs in a fixed order.
 //
 // Used for CountSketch (s = 1) with d <= 512; other shapes take the two
-// separate passes.
+// separate passes.  With form_sa = 0 the pass forms the gradient only (the
+// rows still walked in the given bucket order).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -61,7 +62,7 @@ __global__ void __launch_bounds__(kFuThreads, 2) k_sketch_grad_fused(
     const int32_t* __restrict__ seg_start, const int32_t* __restrict__ chunk_first, int m,
     int64_t P, int64_t CH, int nchunks, const float2* __restrict__ bs,
     const double* __restrict__ x, float* __restrict__ SA, float* __restrict__ partial,
-    double* __restrict__ gcta) {
+    double* __restrict__ gcta, int form_sa) {
   constexpr int DP = NV * 128;
   __shared__ __align__(16) float xh[DP], xl[DP], nxh[DP];
   __shared__ float2 red[kFuWarps][DP];
@@ -194,6 +195,7 @@ __global__ void __launch_bounds__(kFuThreads, 2) k_sketch_grad_fused(
             }
         }
       }
+      if (!form_sa) continue;
       const bool split = (sb / CH) != ((eb - 1) / CH);
       float* dst;
       if (!split) {
@@ -243,13 +245,15 @@ int fused_ctas(const SortPlan& p) { return (p.nchunks + kFuWarps - 1) / kFuWarps
 cudaError_t launch_sketch_grad_fused(const DenseA& A, const SortPlan& p, const uint32_t* perm,
                                      const int32_t* seg, const int32_t* cf, const float2* bsplit,
                                      const double* x, float* SA, float* partial, double* gcta,
-                                     double* g, double lam, cudaStream_t st, void* prof) {
+                                     double* g, double lam, cudaStream_t st, void* prof,
+                                     bool form_sa) {
   const int blocks = fused_ctas(p);
   const int nv = (int)((A.d + 127) / 128);
 #define FU(NV)                                                                              \
   k_sketch_grad_fused<NV><<<blocks, kFuThreads, 0, st>>>((const float*)A.val, A.ld, (int)A.d, \
                                                          perm, seg, cf, p.m, p.P, p.chunk,     \
-                                                         p.nchunks, bsplit, x, SA, partial, gcta)
+                                                         p.nchunks, bsplit, x, SA, partial, gcta, \
+                                                         form_sa ? 1 : 0)
   switch (nv) {
     case 1: FU(1); break;
     case 2: FU(2); break;
@@ -261,9 +265,11 @@ cudaError_t launch_sketch_grad_fused(const DenseA& A, const SortPlan& p, const u
   note_launches(1);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  prof_stage_end(prof);
-  prof_stage_begin(prof, IHS_ST_SKETCH_FIX);
-  e = launch_sketch_fixup_f32(p, seg, (int)A.d, partial, SA, st);
-  if (e != cudaSuccess) return e;
+  if (form_sa) {
+    prof_stage_end(prof);
+    prof_stage_begin(prof, IHS_ST_SKETCH_FIX);
+    e = launch_sketch_fixup_f32(p, seg, (int)A.d, partial, SA, st);
+    if (e != cudaSuccess) return e;
+  }
   return launch_reduce_partials(gcta, blocks, (int)A.d, x, lam, g, st);
 }

@@ -79,7 +79,8 @@ int fused_ctas(const SortPlan& p);
 cudaError_t launch_sketch_grad_fused(const DenseA& A, const SortPlan& p, const uint32_t* perm,
                                      const int32_t* seg, const int32_t* cf, const float2* bsplit,
                                      const double* x, float* SA, float* partial, double* gcta,
-                                     double* g, double lam, cudaStream_t st, void* prof);
+                                     double* g, double lam, cudaStream_t st, void* prof,
+                                     bool form_sa = true);
 
 // S^T G gather (G m x d double, out n x d double).
 cudaError_t launch_sketch_adjoint(const SketchKeys& K, int64_t n, int64_t d, const double* G,
@@ -137,9 +138,12 @@ int chol_padded(int d);  // d rounded up to the 32-tile
 size_t chol_dinv_bytes(int d, int f32);
 // Factor H + shift I with the 16-CTA cluster kernel when allow_cluster (and
 // shift == 0) and the matrix fits in the cluster's shared memory, else with
-// the cooperative grid kernel (the two give identical factors).
+// the cooperative grid kernel (the two give identical factors).  max_ctas > 0
+// caps the grid kernel's CTAs (the factor then leaves the other SMs to a
+// kernel running beside it).
 cudaError_t launch_cholesky(const double* H, int d, int f32, void* Lbuf, void* Dinv, unsigned* bar,
-                            int* status, cudaStream_t st, int allow_cluster, double shift = 0.0);
+                            int* status, cudaStream_t st, int allow_cluster, double shift = 0.0,
+                            int max_ctas = 0);
 // x += (L L^T)^{-1} g ; step_norm (device double) gets max |delta|.
 cudaError_t launch_chol_step(const void* Lbuf, const void* Dinv, int d, int f32, const double* g,
                              double* x, double* step_norm, cudaStream_t st);

@@ -159,9 +159,12 @@ __device__ void tile_sub_pqt(T (*C)[33], T (*P)[33], T (*Q)[33]) {
 //                   rank-32 update of step k-1 to its own tiles, and
 //   update(k-1)     every trailing tile (i, j) with k < j <= i,
 // so a step costs one grid barrier.  The diagonal factor and the panel tile's
-// solve x L_kk^T = a share one register sweep (panel_sweep).
+// solve x L_kk^T = a share one register sweep (panel_sweep).  The FP32 kernel
+// is held to 128 registers a thread, so one of its CTAs fits on an SM beside
+// a CTA of the fused pass (256 threads x 128 registers): the look-ahead
+// pipeline runs the two together.
 template <typename T>
-__global__ void __launch_bounds__(256) k_chol_coop(T* __restrict__ L, T* __restrict__ Dinv, int dp,
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_chol_coop(T* __restrict__ L, T* __restrict__ Dinv, int dp,
                                                    int Tt, unsigned* bar, int* status) {
   __shared__ T Dk[32][33];
   __shared__ T Ta[32][33];
@@ -429,8 +432,7 @@ static cudaError_t chol_cluster_launch(const double* H, int d, T* L, T* Dinv, in
 
 template <typename T>
 static cudaError_t chol_impl(const double* H, int d, double shift, T* L, T* Dinv, unsigned* bar,
-                             int* status,
-                             cudaStream_t st, bool allow_cluster) {
+                             int* status, cudaStream_t st, bool allow_cluster, int max_ctas) {
   int dp = chol_padded(d), Tt = dp / 32;
   if (allow_cluster && shift == 0.0) {
     bool used = false;
@@ -451,6 +453,7 @@ static cudaError_t chol_impl(const double* H, int d, double shift, T* L, T* Dinv
   if (per < 1) return cudaErrorCooperativeLaunchTooLarge;
   // one CTA per SM at most; no more CTAs than the largest phase has items
   int grid = std::min(sms, std::max(Tt, Tt + (Tt - 2) * (Tt - 1) / 2));
+  if (max_ctas > 0) grid = std::min(grid, max_ctas);
   grid = std::max(grid, 1);
   void* args[] = {(void*)&L, (void*)&Dinv, (void*)&dp, (void*)&Tt, (void*)&bar, (void*)&status};
   e = cudaLaunchCooperativeKernel((const void*)k_chol_coop<T>, dim3(grid), dim3(256), args, 0, st);
@@ -460,11 +463,12 @@ static cudaError_t chol_impl(const double* H, int d, double shift, T* L, T* Dinv
 }
 
 cudaError_t launch_cholesky(const double* H, int d, int f32, void* Lbuf, void* Dinv, unsigned* bar,
-                            int* status, cudaStream_t st, int allow_cluster, double shift) {
+                            int* status, cudaStream_t st, int allow_cluster, double shift,
+                            int max_ctas) {
   return f32 ? chol_impl<float>(H, d, shift, (float*)Lbuf, (float*)Dinv, bar, status, st,
-                                allow_cluster != 0)
+                                allow_cluster != 0, max_ctas)
              : chol_impl<double>(H, d, shift, (double*)Lbuf, (double*)Dinv, bar, status, st,
-                                 allow_cluster != 0);
+                                 allow_cluster != 0, max_ctas);
 }
 
 // ----------------------------------------------------------------------------

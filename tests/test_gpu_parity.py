@@ -314,6 +314,48 @@ def test_fused_pass_agrees_with_two_passes(cuda_lib):
     assert O.err_A(x1.cpu().numpy(), xo, G) < 1e-10 and O.err_A(x2.cpu().numpy(), xo, G) < 1e-10
 
 
+@pytest.mark.parametrize("kind,iters,serial", [
+    ("ols", 1, False), ("ols", 2, False), ("ols", 3, False), ("ols", 7, False), ("ols", 4, True),
+    ("ridge", 5, False), ("l1", 5, False), ("l2", 4, False)])
+def test_lookahead_matches_in_order_fused(cuda_lib, kind, iters, serial):
+    """The look-ahead fused pipeline (SA of iteration t+1 formed in the pass of
+    iteration t, its factor beside the next pass) takes the same sketches as
+    the in-order fused pipeline: the iterates agree to rounding, for 1 to 7
+    iterations (every branch of the sort schedule), serial or overlapped,
+    and a second solve continues to 1e-10.  At this size (fewer than 32 rows
+    per warp slot) both pipelines split the rows into the same chunks, so the
+    sketch and Hessian left behind (the last iteration's) are identical bit
+    for bit and the iterates differ only by the gradient's summation order."""
+    w = synth.make("ols_dense_ar1", n=70001, d=120, m=1200)
+    A64 = w["A"].astype(np.float64)
+    A, b = dev(w["A"]), dev(w["b"])
+    xo = O.x_opt_ols_normal(A64, w["b"])
+    G = A64.T @ A64
+    kw = dict(m=1200, precision="tf32", seed=11, serial=serial)
+    if kind == "ridge":
+        kw.update(kind="ridge", param=3.0)
+    elif kind == "l1":
+        kw.update(kind="l1", param=0.5 * float(np.abs(xo).sum()))
+    elif kind == "l2":
+        kw.update(kind="l2", param=0.5 * float(np.linalg.norm(xo)))
+    la = cuda_lib.IHS(A, b, lookahead=True, **kw)
+    io = cuda_lib.IHS(A, b, lookahead=False, **kw)
+    x1, r1 = la.solve(iters=iters)
+    x2, r2 = io.solve(iters=iters)
+    assert r1.status == 0 and r2.status == 0
+    S1, H1, _ = la.get_sketch()
+    S2, H2, _ = io.get_sketch()
+    assert torch.equal(S1, S2) and torch.equal(H1, H2)
+    e = (x1 - x2).cpu().numpy()
+    scale = np.sqrt(max(xo @ G @ xo, 1e-300))
+    assert np.sqrt(e @ G @ e) / scale < 1e-11
+    if kind == "ols" and not serial:
+        x1, _ = la.solve(x1, t0=iters, iters=30)
+        x2, _ = io.solve(x2, t0=iters, iters=30)
+        assert O.err_A(x1.cpu().numpy(), xo, G) < 1e-10
+        assert O.err_A(x2.cpu().numpy(), xo, G) < 1e-10
+
+
 @pytest.mark.parametrize("kind", ["dense_fp64", "dense_tf32", "csr_fp64", "dense_fp64_d700", "ridge_bf16"])
 def test_cluster_factor_matches_grid_factor(cuda_lib, kind):
     """The 16-CTA cluster factor and the cooperative grid factor carry out the
