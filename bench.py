@@ -300,6 +300,14 @@ def run_ours(args, rank, world):
         two = ihs.IHS(A, b, kind="ols", m=m, s=s, seed=0, precision=args.precision, fuse=False)
         ms_two, _, _ = timed(two, T_mixed, max(1, args.steps // 2), 1)
         del two
+    # the mixed form with the sketched Hessian factored in FP64 instead of FP32
+    ms_f64fac, T_f64fac = None, None
+    if not args.no_two_pass:
+        f64f = ihs.IHS(A, b, kind="ols", m=m, s=s, seed=0, precision=args.precision,
+                       fp64_factor=True)
+        T_f64fac, _ = iterations_to(f64f, xo, G, 1e-10)
+        ms_f64fac, _, _ = timed(f64f, T_f64fac, max(1, args.steps // 2), 1)
+        del f64f
 
     # end to end through the public API with host buffers
     e2e = None
@@ -353,11 +361,12 @@ def run_ours(args, rank, world):
                    % (args.workload, n, d, m, s),
                    "precision": args.precision, "l2": "inputs larger than L2 (A = %.2f GB)" % (a_bytes / 1e9),
                    "parallelism": "replicas" if world > 1 else "single GPU"},
-        "iters_to_1e-10": {"mixed": T_mixed, "fp64": T_plain},
+        "iters_to_1e-10": {"mixed": T_mixed, "fp64": T_plain, "mixed_fp64_factor": T_f64fac},
         "final_err": {"mixed": err_final, "fp64": err_final_plain},
         "fp64_time_to_1e-10_ms": round(ms_plain, 3),
         "mixed_speedup_vs_fp64": round(ms_plain / ms_mixed, 3),
         "mixed_two_pass_ms": round(ms_two, 3) if ms_two else None,
+        "mixed_fp64_factor_ms": round(ms_f64fac, 3) if ms_f64fac else None,
         "sketch_GB_s": sk["GB_s"],
         "sketch_frac_of_hbm": sk["frac"],
         "kernels": kernels,

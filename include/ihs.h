@@ -129,7 +129,13 @@ enum { IHS_SKETCH_SPARSE = 0, IHS_SKETCH_SRHT = 1, IHS_SKETCH_GAUSSIAN = 2 };
  * two separate passes over A even where the single fused pass applies (dense
  * FP32 data, mixed precision, CountSketch, d <= 512); results agree to
  * rounding, the fused pass reads A once instead of twice. */
-enum { IHS_FLAG_NO_FUSE = 1, IHS_FLAG_SERIAL = 2, IHS_FLAG_CLUSTER = 4, IHS_FLAG_NO_LOOKAHEAD = 8 };
+enum {
+  IHS_FLAG_NO_FUSE = 1,
+  IHS_FLAG_SERIAL = 2,
+  IHS_FLAG_CLUSTER = 4,
+  IHS_FLAG_NO_LOOKAHEAD = 8,
+  IHS_FLAG_FP64_FACTOR = 16
+};
 /* IHS_FLAG_SERIAL: issue the sketch chain (draw, sort, SA, Gram, factor) on
  * the caller's stream too, instead of overlapping it with the gradient and
  * step on an internal stream.  Same results; useful for timing stages.
@@ -145,7 +151,14 @@ enum { IHS_FLAG_NO_FUSE = 1, IHS_FLAG_SERIAL = 2, IHS_FLAG_CLUSTER = 4, IHS_FLAG
  * so the Gram and factor of t + 1 (on a 16-CTA share of the GPU) run beside
  * the step of t and the pass of t + 1 instead of between them; SA of the
  * first iteration then takes one sketch-only pass.  Same sketches, same
- * iterates to rounding. */
+ * iterates to rounding.
+ * IHS_FLAG_FP64_FACTOR: in the mixed forms, factor the (TF32/BF16) sketched
+ * Hessian and apply the factor in FP64, as the plain form does, instead of
+ * in FP32.  The factor only preconditions the step (the residual, gradient
+ * and update that set the attainable accuracy are FP64-class either way), so
+ * both reach the same accuracy in the same iterations; the FP64 factor costs
+ * more on this GPU's FP64 units and implies IHS_FLAG_NO_LOOKAHEAD (its kernel
+ * needs a whole SM's registers, so it cannot run beside the fused pass). */
 
 typedef struct {
   int iters;            /* iterations taken                                */

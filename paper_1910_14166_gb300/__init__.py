@@ -177,14 +177,15 @@ class IHS:
     param = lambda), 'l2' (p = 2 ball, param = radius) or 'ridge' (param =
     lambda).
     precision: 'fp64' (plain), 'tf32' or 'bf16' (mixed).  fuse=False,
-    serial=True, cluster=True and lookahead=False set IHS_FLAG_NO_FUSE,
-    IHS_FLAG_SERIAL, IHS_FLAG_CLUSTER and IHS_FLAG_NO_LOOKAHEAD; sketch:
+    serial=True, cluster=True, lookahead=False and fp64_factor=True set
+    IHS_FLAG_NO_FUSE, IHS_FLAG_SERIAL, IHS_FLAG_CLUSTER, IHS_FLAG_NO_LOOKAHEAD
+    and IHS_FLAG_FP64_FACTOR; sketch:
     'sparse' (CountSketch / SJLT), 'srht' or 'gaussian' (the paper's dense
     comparisons)."""
 
     def __init__(self, A, b, kind="ols", param=0.0, m=None, s=1, seed=0, precision="fp64",
                  shape=None, qp_max_iter=0, qp_tol=0.0, fuse=True, serial=False, cluster=False,
-                 sketch="sparse", lookahead=True):
+                 sketch="sparse", lookahead=True, fp64_factor=False):
         self._keep = [A, b]
         _need_cuda(b, "b")
         if b.dtype != torch.float64:
@@ -220,7 +221,7 @@ class IHS:
         C = _Constraint(KIND[kind], float(param))
         O = _Options(self.m, self.s, seed & 0xFFFFFFFFFFFFFFFF, PREC[precision], int(qp_max_iter),
                      float(qp_tol), (0 if fuse else 1) | (2 if serial else 0) | (4 if cluster else 0)
-                     | (0 if lookahead else 8),
+                     | (0 if lookahead else 8) | (16 if fp64_factor else 0),
                      {"sparse": 0, "srht": 1, "gaussian": 2}[sketch])
         h = ctypes.c_void_p()
         _check(_lib.ihs_create(ctypes.byref(h), ctypes.byref(M), _ptr(b), ctypes.byref(C),

@@ -465,7 +465,7 @@ ihs_status ihs_create(ihs_ctx** out, const ihs_matrix* A, const double* b,
   c->s = opt->s;
   c->prec = opt->precision;
   c->acc64 = (c->prec == IHS_PREC_FP64);
-  c->f32fac = (c->prec != IHS_PREC_FP64);
+  c->f32fac = (c->prec != IHS_PREC_FP64) && !(opt->flags & IHS_FLAG_FP64_FACTOR);
   c->dense = (A->kind == IHS_DENSE);
   int dev = 0;
   cudaGetDevice(&dev);
@@ -528,7 +528,7 @@ ihs_status ihs_create(ihs_ctx** out, const ihs_matrix* A, const double* b,
     c->gauss = opt->sketch == IHS_SKETCH_GAUSSIAN;
     c->fused = !c->acc64 && !c->srht && !c->gauss && fused_supported(c->DA, c->s) &&
                !(opt->flags & IHS_FLAG_NO_FUSE);
-    c->lookahead = c->fused && !(opt->flags & IHS_FLAG_NO_LOOKAHEAD);
+    c->lookahead = c->fused && c->f32fac && !(opt->flags & IHS_FLAG_NO_LOOKAHEAD);
     // one warp per chunk; the fused pass runs two CTAs of eight warps per SM,
     // less the SMs' share left to the factor that runs beside it
     const int warps = c->lookahead ? (2 * c->sms - kLookaheadFactorCtas) * 8 : c->sms * 16;

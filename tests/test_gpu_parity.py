@@ -264,6 +264,42 @@ def test_ihs_lasso_mixed_reaches_1e10(cuda_lib):
     assert O.err_A(x.cpu().numpy(), xo, G) < 1e-10
 
 
+@pytest.mark.parametrize("kind", ["ols_dense", "l1_csr"])
+def test_mixed_fp64_factor(cuda_lib, kind):
+    """IHS_FLAG_FP64_FACTOR: the mixed form with the TF32 sketched Hessian
+    factored and applied in FP64 (as in the plain form) reaches 1e-10 in the
+    same iteration budget as with the FP32 factor; after the first step (the
+    same sketch, the same TF32 Hessian) the two iterates agree to FP32
+    accuracy, the only difference being the factor's precision."""
+    if kind == "ols_dense":
+        w = synth.make("ols_dense_ar1", n=65536, d=128, m=1280)
+        A64 = w["A"].astype(np.float64)
+        xo = O.x_opt_ols_normal(A64, w["b"])
+        G = A64.T @ A64
+        args = (dev(w["A"]), dev(w["b"]))
+        kw = dict(m=1280, precision="tf32")
+        iters = 40
+    else:
+        w, C = _csr_problem("lasso_csr_zipf", 200000, 100, 1000)
+        G = C.gram()
+        xo = O.x_opt_l1(C, w["b"], w["param"])
+        args = ((dev(w["rowptr"]), dev(w["col"]), dev(w["val"])), dev(w["b"]))
+        kw = dict(kind="l1", param=w["param"], m=1000, s=8, precision="tf32",
+                  shape=(w["n"], w["d"]))
+        iters = 30
+    f64 = cuda_lib.IHS(*args, fp64_factor=True, **kw)
+    f32 = cuda_lib.IHS(*args, **kw)
+    x1, r1 = f64.solve(iters=1)
+    x2, r2 = f32.solve(iters=1)
+    assert r1.status == 0 and r2.status == 0
+    e = (x1 - x2).cpu().numpy()
+    assert np.sqrt(e @ G @ e) / np.sqrt(xo @ G @ xo) < 1e-5
+    x1, _ = f64.solve(x1, t0=1, iters=iters - 1)
+    x2, _ = f32.solve(x2, t0=1, iters=iters - 1)
+    assert O.err_A(x1.cpu().numpy(), xo, G) < 1e-10
+    assert O.err_A(x2.cpu().numpy(), xo, G) < 1e-10
+
+
 def test_ihs_ridge_plain_and_mixed(cuda_lib):
     w = synth.make("ridge_dense", n=32768, d=64, m=640)
     A64 = w["A"].astype(np.float64)
