@@ -503,6 +503,53 @@ def run_sketch_quality(args):
             del sv
 
 
+def run_adjoint(args):
+    """The differentiation form on the 262144 x 256 ridge workload: solve to
+    1e-10 (mixed), then the adjoint of L = ||x - x_target||^2 through
+    ihs_adjoint: PCG with the sketched factor, dL/db and dL/dA.  CUDA events
+    around the call, median of `--steps` runs after one warm-up, with and
+    without dL/dA (the difference is the dL/dA pass: read A, write dL/dA).
+    One JSON line."""
+    import torch
+    import paper_1910_14166_gb300 as ihs
+    w = synth.make("ridge_dense", n=args.n)
+    n, d, m = w["n"], w["d"], w["m"]
+    A = torch.from_numpy(w["A"]).cuda()
+    b = torch.from_numpy(w["b"]).cuda()
+    xt = torch.from_numpy(w["x_target"]).cuda()
+    sv = ihs.IHS(A, b, kind="ridge", param=w["param"], m=m, s=1, seed=0, precision="tf32")
+    x, _ = sv.solve(iters=40)
+    dLdx = 2.0 * (x - xt)
+    st = torch.cuda.current_stream()
+
+    def timed(want_A):
+        ts, cg = [], 0
+        for it in range(1 + args.steps):
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            _, _, rep = sv.adjoint(x, dLdx, want_A=want_A)
+            e1.record(st)
+            torch.cuda.synchronize()
+            cg = rep.iters
+            if it >= 1:
+                ts.append(e0.elapsed_time(e1))
+        return statistics.median(ts), cg
+
+    ms_full, cg = timed(True)
+    ms_b, _ = timed(False)
+    hbm, hbm_kind = peaks()
+    dA_ms = max(ms_full - ms_b, 1e-6)
+    dA_bytes = 2 * n * d * 4 + n * 8 * 2  # read A, write dL/dA, b and the residual pass's vectors
+    print(json.dumps({
+        "experiment": "adjoint", "workload": "ridge_dense n=%d d=%d m=%d lambda=%g tf32" % (
+            n, d, m, w["param"]),
+        "cg_iters": cg, "adjoint_ms": round(ms_full, 3), "adjoint_no_dLdA_ms": round(ms_b, 3),
+        "dLdA_pass_ms": round(dA_ms, 4), "dLdA_GB_s": round(dA_bytes / (dA_ms * 1e-3) / 1e9, 1),
+        "dLdA_frac_of_hbm": round(dA_bytes / (dA_ms * 1e-3) / 1e9 / hbm, 3), "peak_kind": hbm_kind,
+        "pass_bytes": n * d * 4}), flush=True)
+
+
 def run_workloads(args):
     """Time every workload of the suite (and the penalised-LASSO form on the
     two sparse ones, lambda = 5; the SRHT and Gaussian comparison sketches and
@@ -585,7 +632,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-two-pass", action="store_true")
     ap.add_argument("--only", default=None, help="workloads experiment: comma-separated names")
-    ap.add_argument("--experiment", default=None, choices=["sketch-quality", "workloads"],
+    ap.add_argument("--experiment", default=None, choices=["sketch-quality", "workloads", "adjoint"],
                     help="run an experiment instead of the benchmark (one JSON line per point)")
     ap.add_argument("--trials", type=int, default=10)
     ap.add_argument("--sketch", default="sparse", choices=["sparse", "srht", "gaussian"],
@@ -605,6 +652,9 @@ def main():
         return
     if args.experiment == "workloads":
         run_workloads(args)
+        return
+    if args.experiment == "adjoint":
+        run_adjoint(args)
         return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

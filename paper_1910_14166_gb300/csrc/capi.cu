@@ -23,6 +23,25 @@ static int64_t g_launches = 0;  // kernel launches issued by the library
 void note_launches(int k) { __atomic_add_fetch(&g_launches, (int64_t)k, __ATOMIC_RELAXED); }
 int64_t launches_total() { return __atomic_load_n(&g_launches, __ATOMIC_RELAXED); }
 
+cudaError_t ensure_smem(const void* fn, int bytes) {
+  static std::mutex mu;
+  static std::vector<std::pair<std::pair<const void*, int>, int>> set;  // (kernel, device) -> bytes
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(mu);
+  for (auto& kv : set)
+    if (kv.first.first == fn && kv.first.second == dev) {
+      if (kv.second >= bytes) return cudaSuccess;
+      e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+      if (e == cudaSuccess) kv.second = bytes;
+      return e;
+    }
+  e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess) set.push_back({{fn, dev}, bytes});
+  return e;
+}
+
 struct StageEvents {
   std::vector<cudaEvent_t> ev;     // pool: pairs (start, stop)
   std::vector<int> stage;          // stage of pair k

@@ -458,20 +458,10 @@ cudaError_t launch_gram(const GramPlan& g, const void* SA, void* operand, float*
   const int kblocks = (int)(g.ldt / (128 / el));
   dim3 grid(g.tiles, g.splits);
   if (bf16) {
-    static bool attr = false;
-    if (!attr) {
-      e = cudaFuncSetAttribute(k_gram_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
-      if (e != cudaSuccess) return e;
-      attr = true;
-    }
+    if ((e = ensure_smem((const void*)k_gram_tc<1>, kTcSmem)) != cudaSuccess) return e;
     { k_gram_tc<1><<<grid, 192, kTcSmem, st>>>(map, g.tiles, kblocks, g.splits, partial_f, status); note_launches(1); }
   } else {
-    static bool attr = false;
-    if (!attr) {
-      e = cudaFuncSetAttribute(k_gram_tc<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
-      if (e != cudaSuccess) return e;
-      attr = true;
-    }
+    if ((e = ensure_smem((const void*)k_gram_tc<0>, kTcSmem)) != cudaSuccess) return e;
     { k_gram_tc<0><<<grid, 192, kTcSmem, st>>>(map, g.tiles, kblocks, g.splits, partial_f, status); note_launches(1); }
   }
   if ((e = cudaGetLastError()) != cudaSuccess) return e;

@@ -8,6 +8,10 @@
 
 // Kernel launches issued by the library (for the profiler's launch count).
 void note_launches(int k);
+// Raise a kernel's dynamic shared-memory limit to at least `bytes` on the
+// current device (the attribute is per device; set once per kernel and
+// device, thread-safe).
+cudaError_t ensure_smem(const void* fn, int bytes);
 int64_t launches_total();
 
 // ---- sketch draw ----------------------------------------------------------

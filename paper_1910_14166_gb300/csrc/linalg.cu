@@ -32,6 +32,7 @@
 #include <cooperative_groups.h>
 
 #include <algorithm>
+#include <atomic>
 
 #include "internal.h"
 
@@ -383,14 +384,19 @@ static cudaError_t chol_cluster_launch(const double* H, int d, T* L, T* Dinv, in
   const int dp = chol_padded(d), Tt = dp / 32;
   const size_t smem = chol_cluster_smem<T>(Tt);
   if (smem > 200 * 1024) return cudaSuccess;
-  static int ok = -1;  // per process: can a 16-CTA cluster with this much smem run?
-  static size_t ok_smem = 0;
-  if (ok < 0 || ok_smem < smem) {
+  // per device: can a 16-CTA cluster with 200 KB of shared memory a CTA run?
+  static std::atomic<int> ok_dev[64];  // 0 unknown, 1 yes, 2 no
+  int dev = 0;
+  {
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+  }
+  if (dev >= 64) return cudaSuccess;
+  int ok = ok_dev[dev].load() == 1;
+  if (ok_dev[dev].load() == 0) {
     cudaError_t e = cudaFuncSetAttribute(k_chol_cluster<T>,
                                          cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_chol_cluster<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               200 * 1024);
+    if (e == cudaSuccess) e = ensure_smem((const void*)k_chol_cluster<T>, 200 * 1024);
     int nclusters = 0;
     if (e == cudaSuccess) {
       cudaLaunchConfig_t cfg = {};
@@ -408,7 +414,7 @@ static cudaError_t chol_cluster_launch(const double* H, int d, T* L, T* Dinv, in
     }
     if (e != cudaSuccess) cudaGetLastError();
     ok = (e == cudaSuccess && nclusters >= 1) ? 1 : 0;
-    ok_smem = 200 * 1024;
+    ok_dev[dev].store(ok ? 1 : 2);
   }
   if (!ok) return cudaSuccess;
   cudaLaunchConfig_t cfg = {};
@@ -552,12 +558,9 @@ static cudaError_t solve_impl(const T* L, const T* Dinv, int d, const double* v,
   const size_t dinv = (size_t)(dp / 32) * 1024 * sizeof(T);
   const int in_smem = (base + dinv) <= 200 * 1024;
   const size_t smem = base + (in_smem ? dinv : 0);
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_chol_solve<T>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  {
+    cudaError_t e = ensure_smem((const void*)k_chol_solve<T>, 200 * 1024);
     if (e != cudaSuccess) return e;
-    attr = true;
   }
   k_chol_solve<T><<<1, 1024, smem, st>>>(L, Dinv, d, dp, v, x, step_norm, mode, in_smem);
   note_launches(1);
@@ -706,25 +709,13 @@ cudaError_t launch_chol_inverse(const void* Lbuf, const void* Dinv, int d, int f
   if (smem > 220 * 1024) return cudaErrorInvalidValue;
   cudaError_t e;
   if (f32) {
-    static bool attr = false;
-    if (!attr) {
-      if ((e = cudaFuncSetAttribute(k_chol_inverse<float>,
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024)) !=
-          cudaSuccess)
-        return e;
-      attr = true;
-    }
+    if ((e = ensure_smem((const void*)k_chol_inverse<float>, 220 * 1024)) != cudaSuccess)
+      return e;
     k_chol_inverse<float><<<Tt, 256, smem, st>>>((const float*)Lbuf, (const float*)Dinv, d, dp,
                                                  (float*)Hinv, need);
   } else {
-    static bool attr = false;
-    if (!attr) {
-      if ((e = cudaFuncSetAttribute(k_chol_inverse<double>,
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024)) !=
-          cudaSuccess)
-        return e;
-      attr = true;
-    }
+    if ((e = ensure_smem((const void*)k_chol_inverse<double>, 220 * 1024)) != cudaSuccess)
+      return e;
     k_chol_inverse<double><<<Tt, 256, smem, st>>>((const double*)Lbuf, (const double*)Dinv, d,
                                                   dp, (double*)Hinv, need);
   }

@@ -922,24 +922,13 @@ cudaError_t launch_l1_step(const double* H, const void* Lbuf, const void* Dinv, 
   auto l1 = [&](int phase) -> cudaError_t {
     cudaError_t e2;
     if (f32) {
-      static bool attr = false;
-      if (!attr) {
-        e2 = cudaFuncSetAttribute(k_l1_step<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)smem);
-        if (e2 != cudaSuccess) return e2;
-        attr = true;
-      }
+      if ((e2 = ensure_smem((const void*)k_l1_step<float>, (int)smem)) != cudaSuccess) return e2;
       k_l1_step<float><<<1, kQpThreads, smem, st>>>(H, w.Hf, d, g, du, uvec, R, pen, phase, need,
                                                     max_iter, tl, x, step_norm, w.support, w.iters,
                                                     wv, (float*)w.Ls, ld, w.evec, status);
     } else {
-      static bool attr = false;
-      if (!attr) {
-        e2 = cudaFuncSetAttribute(k_l1_step<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)smem);
-        if (e2 != cudaSuccess) return e2;
-        attr = true;
-      }
+      if ((e2 = ensure_smem((const void*)k_l1_step<double>, (int)smem)) != cudaSuccess)
+        return e2;
       k_l1_step<double><<<1, kQpThreads, smem, st>>>(H, w.Hf, d, g, du, uvec, R, pen, phase, need,
                                                      max_iter, tl, x, step_norm, w.support,
                                                      w.iters, wv, (double*)w.Ls, ld, w.evec,
@@ -954,23 +943,11 @@ cudaError_t launch_l1_step(const double* H, const void* Lbuf, const void* Dinv, 
     if ((e = launch_chol_inverse(Lbuf, Dinv, d, f32, w.Hinv, need, st)) != cudaSuccess) return e;
     const size_t ps = pen_active_smem(f32);
     if (f32) {
-      static bool attr = false;
-      if (!attr) {
-        e = cudaFuncSetAttribute(k_pen_active<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)ps);
-        if (e != cudaSuccess) return e;
-        attr = true;
-      }
+      if ((e = ensure_smem((const void*)k_pen_active<float>, (int)ps)) != cudaSuccess) return e;
       k_pen_active<float><<<1, kQpThreads, ps, st>>>(H, w.Hf, (const float*)w.Hinv, d, g, R, x,
                                                      step_norm, w.support, need);
     } else {
-      static bool attr = false;
-      if (!attr) {
-        e = cudaFuncSetAttribute(k_pen_active<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)ps);
-        if (e != cudaSuccess) return e;
-        attr = true;
-      }
+      if ((e = ensure_smem((const void*)k_pen_active<double>, (int)ps)) != cudaSuccess) return e;
       k_pen_active<double><<<1, kQpThreads, ps, st>>>(H, w.Hf, (const double*)w.Hinv, d, g, R,
                                                       x, step_norm, w.support, need);
     }

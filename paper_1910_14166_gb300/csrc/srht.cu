@@ -178,13 +178,10 @@ cudaError_t srht_impl(const DenseA& A, const SketchKeys& K, int64_t m, int64_t n
   while (s0 < L) {
     const int kp = std::min(maxk, L - s0);
     const size_t smem = (size_t)(1 << kp) * (kCols + 1) * sizeof(T);
-    static bool attr = false;
-    if (!attr) {
-      cudaError_t e = cudaFuncSetAttribute(k_fwht_pass<T, Tin>,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)((1 << maxk) * (kCols + 1) * sizeof(T)));
+    {
+      cudaError_t e = ensure_smem((const void*)k_fwht_pass<T, Tin>,
+                                  (int)((1 << maxk) * (kCols + 1) * sizeof(T)));
       if (e != cudaSuccess) return e;
-      attr = true;
     }
     dim3 grid((unsigned)(n2 >> kp), (unsigned)((d + kCols - 1) / kCols));
     k_fwht_pass<T, Tin><<<grid, block, smem, st>>>((const Tin*)A.val, A.n, A.ld, d, K.key[0], Tbuf,
