@@ -102,28 +102,40 @@ class Clocks:
 
 
 # ------------------------------------------------------------ CPU oracle ---
-def oracle_time_to_tol(w, n_sample, T, seed=0):
-    """The FP64 CPU oracle, timed on a bounded sample of the workload: one IHS
-    iteration (sketch + Gram + gradient + Cholesky step) on the first
-    n_sample rows, with the O(n) passes scaled to the full n and the O(m d^2)
-    Gram kept whole; times T iterations.  Returns (ms, description)."""
+def oracle_time_to_tol(w, n_sample, T, seed=0, iters=3):
+    """The FP64 CPU oracle, timed on a bounded sample of the workload: `iters`
+    IHS iterations (sketch draw, SA, gradient, Gram, Cholesky step) on the
+    first n_sample rows (all n by default), with the O(n) passes scaled to the
+    full n when sampled and the O(m d^2) Gram kept whole; the mean iteration
+    times T.  Returns (ms, description, CPU seconds spent)."""
     import oracle as O
+    n = w["n"]
+    n_sample = min(n_sample or n, w["A"].shape[0])
     A = np.ascontiguousarray(w["A"][:n_sample], dtype=np.float64)
     b = np.ascontiguousarray(w["b"][:n_sample])
-    m, s, n = w["m"], w["s"], w["n"]
+    m, s = w["m"], w["s"]
     x = np.zeros(A.shape[1])
-    t0 = time.perf_counter()
-    bucket, sign = O.hash_draw(seed, 0, s, m, n_sample)
-    SA = O.sketch(A, m, s, bucket, sign)
-    g = O.resid_grad(A, b, x)
-    t1 = time.perf_counter()
-    H = O.gram(SA, 1.0 / s)
-    x = x + O.chol_solve(H, g)
-    t2 = time.perf_counter()
-    per_iter = (t1 - t0) * (n / n_sample) + (t2 - t1)
-    desc = ("one oracle iteration on the first %d of %d rows (O(n) passes scaled by %.1f, "
-            "m x d Gram whole), times %d iterations" % (n_sample, n, n / n_sample, T))
-    return per_iter * T * 1e3, desc, (t2 - t0)
+    t_n = t_g = 0.0
+    for t in range(iters):
+        t0 = time.perf_counter()
+        bucket, sign = O.hash_draw(seed, t, s, m, n_sample)
+        SA = O.sketch(A, m, s, bucket, sign)
+        g = O.resid_grad(A, b, x)
+        t1 = time.perf_counter()
+        H = O.gram(SA, 1.0 / s)
+        x = x + O.chol_solve(H, g)
+        t2 = time.perf_counter()
+        t_n += t1 - t0
+        t_g += t2 - t1
+    per_iter = (t_n * (n / n_sample) + t_g) / iters
+    ran = "one oracle iteration" if iters == 1 else "%d oracle iterations" % iters
+    if n_sample == n:
+        desc = ("%s on the whole %d-row workload, the mean iteration times %d iterations"
+                % (ran, n, T))
+    else:
+        desc = ("%s on the first %d of %d rows (O(n) passes scaled by %.1f, m x d Gram whole), "
+                "the mean iteration times %d iterations" % (ran, n_sample, n, n / n_sample, T))
+    return per_iter * T * 1e3, desc, t_n + t_g
 
 
 def oracle_iterations_proxy():
@@ -394,7 +406,7 @@ def run_reference(args, rank, world):
     vals = []
     spent = 0.0
     for it in range(args.warmup + args.steps):
-        ms, desc, sp = oracle_time_to_tol(w, nrows, T)
+        ms, desc, sp = oracle_time_to_tol(w, nrows, T, iters=1)
         spent += sp
         if it >= args.warmup:
             vals.append(ms)
@@ -627,7 +639,8 @@ def main():
     ap.add_argument("--ncu-iters", type=int, default=0,
                     help="profiling driver: run this many iterations and exit")
     ap.add_argument("--n", type=int, default=None)
-    ap.add_argument("--cpu-rows", type=int, default=131072)
+    ap.add_argument("--cpu-rows", type=int, default=None,
+                    help="rows of the workload the CPU oracle is timed on (default: all)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-two-pass", action="store_true")
