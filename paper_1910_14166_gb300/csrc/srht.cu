@@ -11,12 +11,11 @@
 // (stage h maps the pair (u, v) at rows (i, i + h), bit h of i clear, to
 // (u + v, u - v), for h = 1, 2, 4, ...), so every output is rounded in the
 // same order as the plain stage loop: in FP64 the result is the oracle's
-// bit for bit.  Passes of up to 10 (FP32) / 9 (FP64) stages over blocks of 2^kp rows
-// (at stride 2^s0) x kCols columns: the low five stages of a block in
-// registers (32 values per thread), a transpose through shared memory, the
-// remaining stages in registers again.  Each pass reads and writes the n2 x
-// d_pad buffer T once (the first reads A and applies D); the sampled rows
-// are then gathered into SA.
+// bit for bit.  Passes of five stages: one warp per group of 32 rows (at
+// stride 2^s0) and 32 columns, each lane one column in registers; the first
+// pass reads A and applies D and the zero padding, the others read and write
+// the n2 x d_pad buffer T, and the last transforms only the groups holding a
+// sampled row and writes those rows straight into SA.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -25,113 +24,133 @@
 
 namespace {
 
-constexpr int kCols = 32;       // columns per block
+constexpr int kCols = 32;  // columns per warp slab (T rows padded to a multiple)
 
-// threads per block: 512 (FP32), 256 (FP64: 32 doubles per thread in registers)
-template <typename T>
-__host__ __device__ constexpr int fw_threads() { return sizeof(T) == 4 ? 512 : 256; }
-
-template <typename T>
-__host__ __device__ constexpr int pass_stages() { return sizeof(T) == 4 ? 10 : 9; }
-
-// In-register butterflies over the low `r` bits of the index of v[0..2^r).
-template <typename T, int R>
-IHS_DEV void fwht_regs(T (&v)[32]) {
-#pragma unroll
-  for (int h = 1; h < (1 << R); h <<= 1)
-#pragma unroll
-    for (int i = 0; i < (1 << R); ++i)
-      if (!(i & h)) {
-        const T a = v[i], b = v[i + h];
-        v[i] = a + b;
-        v[i + h] = a - b;
-      }
-}
-
-template <typename T, int R>
-IHS_DEV void fwht_regs_dyn(T (&v)[32], int r) {
-  // r <= R; stages h = 1 .. 2^(r-1)
-#pragma unroll
-  for (int hb = 0; hb < R; ++hb) {
-    if (hb >= r) break;
-    const int h = 1 << hb;
-#pragma unroll
-    for (int i = 0; i < (1 << R); ++i)
-      if (!(i & h) && i + h < (1 << r)) {
-        const T a = v[i], b = v[i + h];
-        v[i] = a + b;
-        v[i + h] = a - b;
-      }
-  }
-}
-
-// One pass: stages s0 .. s0 + kp - 1 (kp <= pass_stages<T>()).
-// first: read A (Tin, n rows, lda) with the signs of D and zero padding;
-// else read T.  Always writes T (n2 x ldt).
-template <typename T, typename Tin>
-__global__ void __launch_bounds__(fw_threads<T>()) k_fwht_pass(const Tin* __restrict__ A, int64_t n,
-                                                        int64_t lda, int d, uint64_t key_sign,
-                                                        T* __restrict__ Tbuf, int64_t ldt,
-                                                        int s0, int kp, int first) {
-  extern __shared__ __align__(16) unsigned char fw_smem[];
-  T (*S)[kCols + 1] = reinterpret_cast<T (*)[kCols + 1]>(fw_smem);
-  const int c = 1 << kp;
+// Register-only pass: stages s0 .. s0 + KP - 1 (KP <= 5).  One warp per
+// (group of 2^KP rows at stride 2^s0, slab of 32 columns): each lane holds
+// one column of the group in registers, so the pass needs no shared memory
+// and no block barrier and a warp keeps 2^KP row loads in flight; many
+// warps per SM overlap their loads and stores.  The stages run in the same
+// order as the recursive definition (h = 2^s0, 2^(s0+1), ...), so every
+// output is rounded exactly as in the plain stage loop.
+template <typename T, typename Tin, bool First, int KP>
+__global__ void __launch_bounds__(256) k_fwht_reg(const Tin* __restrict__ A, int64_t n,
+                                                  int64_t lda, int d, uint64_t key_sign,
+                                                  T* __restrict__ Tbuf, int64_t ldt, int64_t n2,
+                                                  int s0) {
+  constexpr int C = 1 << KP;
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int slabs = (d + 31) / 32;
   const int64_t st = (int64_t)1 << s0;
-  // block -> (low, high, column slab)
-  const int64_t rb = blockIdx.x;
-  const int64_t low = rb % st, high = rb / st;
-  const int64_t row0 = high * st * c + low;
-  const int col0 = blockIdx.y * kCols;
-  const int tid = threadIdx.x, lane = tid & 31, wq = tid >> 5;
-  const int col = col0 + lane;
-  const int r1 = kp < 5 ? kp : 5;
-  const int g1 = 1 << r1;           // rows per thread in phase A
-  const int ngroups = c / g1;       // row groups
-  // phase A: rows j = g * g1 + i, i < g1, stages on the low r1 bits of j
-  for (int g = wq; g < ngroups; g += fw_threads<T>() / 32) {
-    T v[32];
+  const int64_t groups = n2 >> KP;
+  for (int64_t u = warp; u < groups * slabs; u += nwarps) {
+    const int64_t grp = u / slabs;
+    const int col = (int)(u - grp * slabs) * 32 + lane;
+    const int64_t row0 = (grp >> s0) * st * C + (grp & (st - 1));
+    const bool cin = col < d;
+    T v[C];
+    if constexpr (First) {
+      // lane i draws the sign of the group's row i; the warp shares them
+      const int64_t Rl = row0 + (int64_t)lane * st;
+      const bool neg = lane < C && (sm64_out(key_sign, (uint64_t)Rl) & 1ULL);
+      const unsigned sgn = __ballot_sync(0xffffffffu, neg);
+      const Tin* q = A + row0 * lda + col;
+      const int64_t step = st * lda;
 #pragma unroll
-    for (int i = 0; i < 32; ++i) {
-      v[i] = T(0);
-      if (i < g1) {
-        const int64_t R = row0 + (int64_t)(g * g1 + i) * st;
-        if (first) {
-          if (R < n && col < d) {
-            const T a = (T)A[R * lda + col];
-            const uint64_t w = sm64_out(key_sign, (uint64_t)R);
-            v[i] = (w & 1ULL) ? -a : a;
-          }
-        } else if (col < d) {
-          v[i] = Tbuf[R * ldt + col];
+      for (int i = 0; i < C; ++i) {
+        const int64_t R = row0 + (int64_t)i * st;
+        v[i] = T(0);
+        if (R < n && cin) {
+          const T a = (T)q[(int64_t)i * step];
+          v[i] = ((sgn >> i) & 1u) ? -a : a;
         }
       }
-    }
-    if (r1 == 5) fwht_regs<T, 5>(v);
-    else fwht_regs_dyn<T, 5>(v, r1);
-    if (kp == r1) {
-#pragma unroll
-      for (int i = 0; i < 32; ++i)
-        if (i < g1 && col < d) Tbuf[(row0 + (int64_t)(g * g1 + i) * st) * ldt + col] = v[i];
     } else {
+      const T* q = Tbuf + row0 * ldt + col;
+      const int64_t step = st * ldt;
 #pragma unroll
-      for (int i = 0; i < 32; ++i) S[g * g1 + i][lane] = v[i];
+      for (int i = 0; i < C; ++i) v[i] = cin ? q[(int64_t)i * step] : T(0);
+    }
+#pragma unroll
+    for (int h = 1; h < C; h <<= 1)
+#pragma unroll
+      for (int i = 0; i < C; ++i)
+        if (!(i & h)) {
+          const T a = v[i], b = v[i + h];
+          v[i] = a + b;
+          v[i + h] = a - b;
+        }
+    if (cin) {
+      T* q = Tbuf + row0 * ldt + col;
+      const int64_t step = st * ldt;
+#pragma unroll
+      for (int i = 0; i < C; ++i) q[(int64_t)i * step] = v[i];
     }
   }
-  if (kp == r1) return;
-  __syncthreads();
-  // phase B: rows j = lo + i2 * 32, stages on bits 5 .. kp-1 of j
-  const int r2 = kp - 5;
-  const int g2 = 1 << r2;
-  for (int lo = wq; lo < 32; lo += fw_threads<T>() / 32) {
-    T v[32];
+}
+
+// Last pass fused with the row sampling: for sample k (row p = rows[k] of
+// H D A), the pass's group holding p (rows p mod 2^s0 + i 2^s0, i < 2^KP:
+// the last pass spans the top KP bits) is loaded, transformed exactly as
+// k_fwht_reg would, and only the entry of p goes to SA row k.  Only the
+// groups that hold a sampled row are read (about m of n2 / 2^KP), and T is
+// not written back.
+template <typename T, int KP>
+__global__ void __launch_bounds__(256) k_fwht_last_gather(const T* __restrict__ Tbuf, int64_t ldt,
+                                                          int d, int s0,
+                                                          const int32_t* __restrict__ rows,
+                                                          int64_t m, T* __restrict__ SA) {
+  constexpr int C = 1 << KP;
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int slabs = (d + 31) / 32;
+  const int64_t st = (int64_t)1 << s0;
+  for (int64_t u = warp; u < m * slabs; u += nwarps) {
+    const int64_t k = u / slabs;
+    const int col = (int)(u - k * slabs) * 32 + lane;
+    const int64_t p = rows[k];
+    const int64_t low = p & (st - 1);
+    const int ip = (int)(p >> s0);
+    if (col >= d) continue;
+    const T* q = Tbuf + low * ldt + col;
+    const int64_t step = st * ldt;
+    T v[C];
 #pragma unroll
-    for (int i = 0; i < 32; ++i) v[i] = (i < g2) ? S[lo + i * 32][lane] : T(0);
-    if (r2 == 5) fwht_regs<T, 5>(v);
-    else fwht_regs_dyn<T, 5>(v, r2);
+    for (int i = 0; i < C; ++i) v[i] = q[(int64_t)i * step];
 #pragma unroll
-    for (int i = 0; i < 32; ++i)
-      if (i < g2 && col < d) Tbuf[(row0 + (int64_t)(lo + i * 32) * st) * ldt + col] = v[i];
+    for (int h = 1; h < C; h <<= 1)
+#pragma unroll
+      for (int i = 0; i < C; ++i)
+        if (!(i & h)) {
+          const T a = v[i], b = v[i + h];
+          v[i] = a + b;
+          v[i + h] = a - b;
+        }
+    T out = v[0];
+#pragma unroll
+    for (int i = 1; i < C; ++i)
+      if (i == ip) out = v[i];
+    SA[k * d + col] = out;
   }
+}
+
+template <typename T, typename Tin, bool First>
+cudaError_t fwht_reg_pass(const DenseA& A, uint64_t key, T* Tbuf, int64_t ldt, int64_t n2, int s0,
+                          int kp, unsigned blocks, cudaStream_t st) {
+  const Tin* a = (const Tin*)A.val;
+  const int d = (int)A.d;
+  switch (kp) {
+#define FW(K) \
+  case K: k_fwht_reg<T, Tin, First, K><<<blocks, 256, 0, st>>>(a, A.n, A.ld, d, key, Tbuf, ldt, n2, s0); break;
+    FW(0) FW(1) FW(2) FW(3) FW(4) FW(5)
+#undef FW
+    default: return cudaErrorInvalidValue;
+  }
+  note_launches(1);
+  return cudaGetLastError();
 }
 
 // rows[r] = floor(hi32(out(key_rows, r)) * n2 / 2^32)
@@ -163,37 +182,46 @@ cudaError_t srht_impl(const DenseA& A, const SketchKeys& K, int64_t m, int64_t n
   const int64_t ldt = srht_ldt(d);
   int L = 0;
   while (((int64_t)1 << L) < n2) ++L;
-  const int maxk = pass_stages<T>();
-  const dim3 block(fw_threads<T>());
-  int s0 = 0;
-  bool first = true;
-  if (L == 0) {
-    // n2 = 1: H = [1]; T = D A
-    const size_t smem = (size_t)1 * (kCols + 1) * sizeof(T);
-    dim3 grid(1, (unsigned)((d + kCols - 1) / kCols));
-    k_fwht_pass<T, Tin><<<grid, block, smem, st>>>((const Tin*)A.val, A.n, A.ld, d, K.key[0], Tbuf,
-                                                   ldt, 0, 0, 1);
-    note_launches(1);
-  }
-  while (s0 < L) {
-    const int kp = std::min(maxk, L - s0);
-    const size_t smem = (size_t)(1 << kp) * (kCols + 1) * sizeof(T);
-    {
-      cudaError_t e = ensure_smem((const void*)k_fwht_pass<T, Tin>,
-                                  (int)((1 << maxk) * (kCols + 1) * sizeof(T)));
-      if (e != cudaSuccess) return e;
-    }
-    dim3 grid((unsigned)(n2 >> kp), (unsigned)((d + kCols - 1) / kCols));
-    k_fwht_pass<T, Tin><<<grid, block, smem, st>>>((const Tin*)A.val, A.n, A.ld, d, K.key[0], Tbuf,
-                                                   ldt, s0, kp, first ? 1 : 0);
-    note_launches(1);
-    cudaError_t e = cudaGetLastError();
+  // passes of five stages in registers (k_fwht_reg); n2 = 1 is the pass
+  // with no stage (T = D A)
+  int dev = 0, sms = 0;
+  {
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
-    first = false;
-    s0 += kp;
   }
+  const int64_t slabs = (d + 31) / 32;
   { k_srht_rows<<<(unsigned)std::min<int64_t>((m + 255) / 256, 1024), 256, 0, st>>>(
       K.key[1], m, (uint64_t)n2, rows); note_launches(1); }
+  // every pass but the last writes T; the last (when there are two or more)
+  // transforms only the sampled rows' groups, straight into SA
+  const int npass = std::max(1, (L + 4) / 5);
+  int s0 = 0;
+  for (int pass = 0; pass < npass; ++pass) {
+    const int kp = std::min(5, L - s0);
+    if (pass == npass - 1 && pass > 0) {
+      const unsigned blocks = (unsigned)std::max<int64_t>(
+          1, std::min<int64_t>((m * slabs + 7) / 8, (int64_t)sms * 8));
+      switch (kp) {
+#define FL(KK) \
+  case KK: k_fwht_last_gather<T, KK><<<blocks, 256, 0, st>>>(Tbuf, ldt, d, s0, rows, m, SA); break;
+        FL(1) FL(2) FL(3) FL(4) FL(5)
+#undef FL
+        default: return cudaErrorInvalidValue;
+      }
+      note_launches(1);
+      return cudaGetLastError();
+    }
+    const int64_t units = (n2 >> kp) * slabs;
+    const unsigned blocks =
+        (unsigned)std::max<int64_t>(1, std::min<int64_t>((units + 7) / 8, (int64_t)sms * 8));
+    cudaError_t e = pass == 0
+        ? fwht_reg_pass<T, Tin, true>(A, K.key[0], Tbuf, ldt, n2, s0, kp, blocks, st)
+        : fwht_reg_pass<T, Tin, false>(A, K.key[0], Tbuf, ldt, n2, s0, kp, blocks, st);
+    if (e != cudaSuccess) return e;
+    s0 += kp;
+  }
+  // one pass in all (n2 <= 32): T holds H D A; gather the sampled rows
   { k_srht_gather<T><<<(unsigned)std::min<int64_t>((m * d + 255) / 256, 4096), 256, 0, st>>>(
       Tbuf, ldt, rows, m, d, SA); note_launches(1); }
   return cudaGetLastError();
