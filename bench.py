@@ -471,6 +471,8 @@ def run_sketch_quality(args):
     kinds = [("sparse", 1), ("sparse", 4), ("sparse", 8)]
     if shape is None:
         kinds += [("srht", 1), ("gaussian", 1)]
+    if args.families:
+        kinds = [kv for kv in kinds if kv[0] in args.families.split(",")]
     for sketch, s in kinds:
         for k in (5, 10, 20, 40):
             m = k * d
@@ -648,6 +650,8 @@ def main():
     ap.add_argument("--experiment", default=None, choices=["sketch-quality", "workloads", "adjoint"],
                     help="run an experiment instead of the benchmark (one JSON line per point)")
     ap.add_argument("--trials", type=int, default=10)
+    ap.add_argument("--families", default=None,
+                    help="sketch-quality: comma list of sparse, srht, gaussian (default all)")
     ap.add_argument("--sketch", default="sparse", choices=["sparse", "srht", "gaussian"],
                     help="profiling driver: sketch family")
     ap.add_argument("--kind", default=None, choices=["ols", "l1", "l1pen", "l2", "ridge"],
