@@ -255,12 +255,15 @@ ihs_status ihs_sketch_error(ihs_ctx* ctx, int64_t t, const double* G, double* er
 ihs_status ihs_adjoint(ihs_ctx* ctx, const double* x, const double* dLdx,
                        double* dLdb, void* dLdA, ihs_report* rep);
 
-/* Stage timing (CUDA events recorded on the context's stream around each
- * stage of every iteration while enabled) and a count of the library's
- * kernel launches.  Stages, in order: IHS_ST_SORT (sketch draw and bucket
- * sort), IHS_ST_SKETCH (the SA kernel; in the fused form the one pass that
- * forms SA and the gradient), IHS_ST_SKETCH_FIX (straddling and empty
- * buckets), IHS_ST_GRAM, IHS_ST_FACTOR, IHS_ST_GRAD, IHS_ST_STEP. */
+/* Stage timing (CUDA events recorded on the stream that runs each stage,
+ * around each stage of every iteration while enabled) and a count of the
+ * library's kernel launches.  Stages, in order: IHS_ST_SORT (sketch draw and
+ * bucket sort), IHS_ST_SKETCH (the SA kernel; in the in-order fused form the
+ * one pass that forms SA and the gradient; in the look-ahead fused form the
+ * sketch-only pass that starts each ihs_solve), IHS_ST_SKETCH_FIX
+ * (straddling and empty buckets), IHS_ST_GRAM, IHS_ST_FACTOR, IHS_ST_GRAD
+ * (the gradient pass; in the look-ahead fused form the pass that forms the
+ * gradient and the next iteration's SA), IHS_ST_STEP. */
 enum { IHS_ST_SORT = 0, IHS_ST_SKETCH, IHS_ST_SKETCH_FIX, IHS_ST_GRAM, IHS_ST_FACTOR,
        IHS_ST_GRAD, IHS_ST_STEP, IHS_NSTAGES };
 

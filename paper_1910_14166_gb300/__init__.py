@@ -28,6 +28,15 @@ F64, F32 = 0, 1
 OLS, L1_BALL, RIDGE, L1_PENALTY, L2_BALL = 0, 1, 2, 3, 4
 PREC = {"fp64": 0, "tf32": 1, "bf16": 2}
 KIND = {"ols": OLS, "l1": L1_BALL, "ridge": RIDGE, "l1pen": L1_PENALTY, "l2": L2_BALL}
+SKETCH = {"sparse": 0, "srht": 1, "gaussian": 2}
+FLAG_NO_FUSE, FLAG_SERIAL, FLAG_CLUSTER, FLAG_NO_LOOKAHEAD, FLAG_FP64_FACTOR = 1, 2, 4, 8, 16
+
+
+def option_flags(fuse=True, serial=False, cluster=False, lookahead=True, fp64_factor=False):
+    """The IHS_FLAG_* word of ihs_options for IHS()'s keyword options."""
+    return ((0 if fuse else FLAG_NO_FUSE) | (FLAG_SERIAL if serial else 0)
+            | (FLAG_CLUSTER if cluster else 0) | (0 if lookahead else FLAG_NO_LOOKAHEAD)
+            | (FLAG_FP64_FACTOR if fp64_factor else 0))
 
 
 class IHSError(RuntimeError):
@@ -220,9 +229,8 @@ class IHS:
         self.precision = precision
         C = _Constraint(KIND[kind], float(param))
         O = _Options(self.m, self.s, seed & 0xFFFFFFFFFFFFFFFF, PREC[precision], int(qp_max_iter),
-                     float(qp_tol), (0 if fuse else 1) | (2 if serial else 0) | (4 if cluster else 0)
-                     | (0 if lookahead else 8) | (16 if fp64_factor else 0),
-                     {"sparse": 0, "srht": 1, "gaussian": 2}[sketch])
+                     float(qp_tol), option_flags(fuse, serial, cluster, lookahead, fp64_factor),
+                     SKETCH[sketch])
         h = ctypes.c_void_p()
         _check(_lib.ihs_create(ctypes.byref(h), ctypes.byref(M), _ptr(b), ctypes.byref(C),
                                ctypes.byref(O), _stream()), "ihs_create")

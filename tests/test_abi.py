@@ -53,3 +53,55 @@ def test_python_binding_rejects_cpu_tensors():
     import paper_1910_14166_gb300 as ihs
     with pytest.raises(TypeError):
         ihs.IHS(torch.zeros(10, 2), torch.zeros(10, dtype=torch.float64))
+
+
+def header_enums():
+    """Every NAME = value of the header's enums."""
+    src = open(os.path.join(ROOT, "include", "ihs.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    vals = {}
+    for body in re.findall(r"enum\s*\{(.*?)\}", src, flags=re.S):
+        nxt = 0
+        for item in body.split(","):
+            item = item.strip()
+            if not item:
+                continue
+            if "=" in item:
+                name, v = (t.strip() for t in item.split("="))
+                nxt = int(v)
+            else:
+                name = item
+            vals[name] = nxt
+            nxt += 1
+    return vals
+
+
+def test_binding_constants_match_the_header():
+    """The Python binding marshals the same codes the header defines: status
+    codes, storage kinds, constraint kinds, precisions, sketches, option flags
+    and profiling stages."""
+    import paper_1910_14166_gb300 as ihs
+    h = header_enums()
+    for code, name in ihs.STATUS_NAMES.items():
+        assert h[name] == code, name
+    assert (h["IHS_DENSE"], h["IHS_CSR"], h["IHS_F64"], h["IHS_F32"]) == (
+        ihs.DENSE, ihs.CSR, ihs.F64, ihs.F32)
+    kinds = {"ols": "IHS_OLS", "l1": "IHS_L1_BALL", "ridge": "IHS_RIDGE",
+             "l1pen": "IHS_L1_PENALTY", "l2": "IHS_L2_BALL"}
+    for k, name in kinds.items():
+        assert ihs.KIND[k] == h[name], k
+    for p, name in {"fp64": "IHS_PREC_FP64", "tf32": "IHS_PREC_TF32",
+                    "bf16": "IHS_PREC_BF16"}.items():
+        assert ihs.PREC[p] == h[name], p
+    for sk, name in {"sparse": "IHS_SKETCH_SPARSE", "srht": "IHS_SKETCH_SRHT",
+                     "gaussian": "IHS_SKETCH_GAUSSIAN"}.items():
+        assert ihs.SKETCH[sk] == h[name], sk
+    assert ihs.option_flags() == 0
+    assert ihs.option_flags(fuse=False) == h["IHS_FLAG_NO_FUSE"]
+    assert ihs.option_flags(serial=True) == h["IHS_FLAG_SERIAL"]
+    assert ihs.option_flags(cluster=True) == h["IHS_FLAG_CLUSTER"]
+    assert ihs.option_flags(lookahead=False) == h["IHS_FLAG_NO_LOOKAHEAD"]
+    assert ihs.option_flags(fp64_factor=True) == h["IHS_FLAG_FP64_FACTOR"]
+    assert ihs.option_flags(False, True, True, False, True) == 31
+    stages = [n for n in sorted(h, key=h.get) if n.startswith("IHS_ST_") and n != "IHS_ST_COUNT"]
+    assert [s[len("IHS_ST_"):].lower() for s in stages[:len(ihs.STAGES)]] == ihs.STAGES
