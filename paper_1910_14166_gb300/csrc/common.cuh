@@ -84,6 +84,35 @@ IHS_DEV void dd_add(float& ah, float& al, float bh, float bl) {
   e = __fadd_rn(e, __fadd_rn(al, bl));
   fast_two_sum(s, e, ah, al);
 }
+// Packed FP32 pairs (the sm_100 family's two-wide FP32 instructions, through
+// the __fadd2_rn / __fmul2_rn / __ffma2_rn intrinsics): each applies the
+// scalar round-to-nearest operation to both halves, so the results are
+// those of the scalar code, with half the instructions issued.
+typedef float2 f2t;
+__device__ __forceinline__ f2t f2_pack(float lo, float hi) { return make_float2(lo, hi); }
+__device__ __forceinline__ void f2_unpack(f2t v, float& lo, float& hi) {
+  lo = v.x;
+  hi = v.y;
+}
+__device__ __forceinline__ f2t f2_neg(f2t a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ f2t f2_add(f2t a, f2t b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ f2t f2_sub(f2t a, f2t b) { return __fadd2_rn(a, f2_neg(b)); }
+__device__ __forceinline__ f2t f2_mul(f2t a, f2t b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ f2t f2_fma(f2t a, f2t b, f2t c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ f2t f2_zero() { return make_float2(0.f, 0.f); }
+// (hi, lo) += a * (yh + yl) on both halves, given nyh = -yh: the same steps
+// as dd_fma_acc (exact product a*yh by FMA, TwoSum into hi, low parts and
+// a*yl into lo).  p = a*yh is carried as np = -p, which changes no rounding.
+__device__ __forceinline__ void dd2_fma_acc(f2t& hi, f2t& lo, f2t a, f2t yh, f2t nyh, f2t yl) {
+  const f2t np = f2_mul(a, nyh);
+  const f2t pe = f2_fma(a, yh, np);
+  const f2t s = f2_sub(hi, np);
+  const f2t bb = f2_sub(s, hi);
+  const f2t e = f2_sub(f2_sub(hi, f2_sub(s, bb)), f2_add(np, bb));
+  hi = s;
+  lo = f2_fma(a, yl, f2_add(lo, f2_add(e, pe)));
+}
+
 IHS_DEV void split_double(double v, float& h, float& l) {
   h = __double2float_rn(v);
   l = __double2float_rn(v - (double)h);

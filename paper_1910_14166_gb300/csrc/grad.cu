@@ -118,6 +118,128 @@ __global__ void __launch_bounds__(kRgThreads) k_rg_dense_f32(
     }
 }
 
+// The same pass for 16-byte-aligned rows with packed FP32 pair arithmetic
+// and two rows per step (the fused pass's arithmetic without the sketch):
+// both rows' loads are in flight together, one butterfly reduces both dot
+// products (its first level exchanges the rows between half-warps), and the
+// float-pair steps run on pairs of columns.  Rows are taken in order, so
+// each column's gradient is summed in the same row order as above.
+template <int NV>
+__global__ void __launch_bounds__(kRgThreads, 2) k_rg_dense_f32x2(
+    const float* __restrict__ A, int64_t lda, int64_t n, int d, const float2* __restrict__ bs,
+    const double* __restrict__ x, double* __restrict__ r_out, double* __restrict__ gpart,
+    int nwarps) {
+  constexpr int DP = NV * 128;
+  __shared__ __align__(16) float xh[DP], xl[DP], nxh[DP];
+  for (int c = threadIdx.x; c < DP; c += blockDim.x) {
+    float h = 0.f, l = 0.f;
+    if (c < d) split_double(x[c], h, l);
+    xh[c] = h;
+    xl[c] = l;
+    nxh[c] = -h;
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (w >= nwarps) return;
+  const int64_t per = (n + nwarps - 1) / nwarps;
+  const int64_t r0 = (int64_t)w * per, r1 = min(n, r0 + per);
+  int colq[NV];
+  bool ok[NV];
+#pragma unroll
+  for (int q = 0; q < NV; ++q) {
+    colq[q] = (q * 32 + lane) * 4;
+    ok[q] = colq[q] < d;
+  }
+  f2t gh[NV][2], gl[NV][2];
+#pragma unroll
+  for (int q = 0; q < NV; ++q)
+#pragma unroll
+    for (int t = 0; t < 2; ++t) gh[q][t] = gl[q][t] = f2_zero();
+  for (int64_t i = r0; i < r1; i += 2) {
+    const bool two = i + 1 < r1;
+    const float* row0 = A + i * lda;
+    const float* row1 = row0 + lda;
+    f2t a0[NV][2], a1[NV][2];
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+      a0[q][0] = a0[q][1] = a1[q][0] = a1[q][1] = f2_zero();
+      if (ok[q]) {
+        const float4 v0 = __ldcs(reinterpret_cast<const float4*>(row0 + colq[q]));
+        a0[q][0] = f2_pack(v0.x, v0.y);
+        a0[q][1] = f2_pack(v0.z, v0.w);
+        if (two) {
+          const float4 v1 = __ldcs(reinterpret_cast<const float4*>(row1 + colq[q]));
+          a1[q][0] = f2_pack(v1.x, v1.y);
+          a1[q][1] = f2_pack(v1.z, v1.w);
+        }
+      }
+    }
+    const float2 b0 = bs ? __ldg(bs + i) : make_float2(0.f, 0.f);  // no b: r = -A x
+    const float2 b1 = (bs && two) ? __ldg(bs + i + 1) : make_float2(0.f, 0.f);
+    f2t c0h = f2_zero(), c0l = f2_zero(), c1h = f2_zero(), c1l = f2_zero();
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+      const f2t* vh = reinterpret_cast<const f2t*>(xh + colq[q]);
+      const f2t* vn = reinterpret_cast<const f2t*>(nxh + colq[q]);
+      const f2t* vl = reinterpret_cast<const f2t*>(xl + colq[q]);
+#pragma unroll
+      for (int t = 0; t < 2; ++t) {
+        dd2_fma_acc(c0h, c0l, a0[q][t], vh[t], vn[t], vl[t]);
+        dd2_fma_acc(c1h, c1l, a1[q][t], vh[t], vn[t], vl[t]);
+      }
+    }
+    float p0h, q0h, p0l, q0l, p1h, q1h, p1l, q1l;
+    f2_unpack(c0h, p0h, q0h);
+    f2_unpack(c0l, p0l, q0l);
+    f2_unpack(c1h, p1h, q1h);
+    f2_unpack(c1l, p1l, q1l);
+    dd_add(p0h, p0l, q0h, q0l);
+    dd_add(p1h, p1l, q1h, q1l);
+    const bool hi_half = lane >= 16;
+    float kh = hi_half ? p1h : p0h, kl = hi_half ? p1l : p0l;
+    const float sh_ = hi_half ? p0h : p1h, sl_ = hi_half ? p0l : p1l;
+    dd_add(kh, kl, __shfl_xor_sync(0xffffffffu, sh_, 16), __shfl_xor_sync(0xffffffffu, sl_, 16));
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) {
+      const float oh = __shfl_xor_sync(0xffffffffu, kh, o);
+      const float ol = __shfl_xor_sync(0xffffffffu, kl, o);
+      dd_add(kh, kl, oh, ol);
+    }
+    float r0h = b0.x, r0l = b0.y, r1h = b1.x, r1l = b1.y;
+    const float d0h = __shfl_sync(0xffffffffu, kh, 0), d0l = __shfl_sync(0xffffffffu, kl, 0);
+    const float d1h = __shfl_sync(0xffffffffu, kh, 16), d1l = __shfl_sync(0xffffffffu, kl, 16);
+    dd_add(r0h, r0l, -d0h, -d0l);
+    dd_add(r1h, r1l, -d1h, -d1l);
+    if (!two) r1h = r1l = 0.f;
+    if (r_out) {
+      if (lane == 0) r_out[i] = (double)r0h + (double)r0l;
+      if (lane == 1 && two) r_out[i + 1] = (double)r1h + (double)r1l;
+    }
+    const f2t r0h2 = f2_pack(r0h, r0h), r0n2 = f2_pack(-r0h, -r0h), r0l2 = f2_pack(r0l, r0l);
+    const f2t r1h2 = f2_pack(r1h, r1h), r1n2 = f2_pack(-r1h, -r1h), r1l2 = f2_pack(r1l, r1l);
+#pragma unroll
+    for (int q = 0; q < NV; ++q)
+#pragma unroll
+      for (int t = 0; t < 2; ++t) {
+        dd2_fma_acc(gh[q][t], gl[q][t], a0[q][t], r0h2, r0n2, r0l2);
+        dd2_fma_acc(gh[q][t], gl[q][t], a1[q][t], r1h2, r1n2, r1l2);
+      }
+  }
+  double* gp = gpart + (int64_t)w * d;
+#pragma unroll
+  for (int q = 0; q < NV; ++q)
+    if (ok[q])
+#pragma unroll
+      for (int t = 0; t < 2; ++t) {
+        float h0, h1, l0, l1;
+        f2_unpack(gh[q][t], h0, h1);
+        f2_unpack(gl[q][t], l0, l1);
+        gp[colq[q] + 2 * t] = (double)h0 + (double)l0;
+        gp[colq[q] + 2 * t + 1] = (double)h1 + (double)l1;
+      }
+}
+
 // ---------------------------------------------------------------- FP64 data --
 template <int NQ>
 __global__ void __launch_bounds__(kRgThreads) k_rg_dense_f64(
@@ -193,7 +315,17 @@ cudaError_t launch_resid_grad_dense(const DenseA& A, const double* b, const floa
              (const float*)A.val, A.ld, A.n, d, bsplit, x, r, gpart, nwarps), 0)              \
       : (k_rg_dense_f32<NV, false><<<blocks, kRgThreads, smem, st>>>(                        \
              (const float*)A.val, A.ld, A.n, d, bsplit, x, r, gpart, nwarps), 0))
-      switch (nv) {
+#define RGX2(NV)                                                                              \
+  k_rg_dense_f32x2<NV><<<blocks, kRgThreads, 0, st>>>((const float*)A.val, A.ld, A.n, d, bsplit, \
+                                                      x, r, gpart, nwarps)
+      if (v4 && nv <= 4) {
+        switch (nv) {
+          case 1: RGX2(1); break;
+          case 2: RGX2(2); break;
+          case 3: RGX2(3); break;
+          default: RGX2(4); break;
+        }
+      } else switch (nv) {
         case 1: RG32(1); break;
         case 2: RG32(2); break;
         case 3: RG32(3); break;
@@ -205,6 +337,7 @@ cudaError_t launch_resid_grad_dense(const DenseA& A, const double* b, const floa
         default: return cudaErrorInvalidValue;
       }
 #undef RG32
+#undef RGX2
       note_launches(1);
     } else {
       const int nq = (d + 31) / 32;
