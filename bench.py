@@ -177,6 +177,18 @@ def x_opt_gpu(A, b):
     return x, G
 
 
+def max_over_ranks(values, device):
+    """Element-wise maximum of a list of floats over the ranks of the default
+    process group (the job's time is its slowest rank's); unchanged alone."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return list(values)
+    t = torch.tensor(list(values), dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.tolist()
+
+
 def err_A(x, xo, G):
     e = x - xo
     return float(((e @ G @ e).clamp_min(0).sqrt() / (xo @ G @ xo).sqrt()).item())
@@ -268,11 +280,7 @@ def run_ours(args, rank, world):
     err_final_plain = err_A(x_p, xo, G)
 
     # max over ranks
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms_mixed, ms_plain], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_mixed, ms_plain = t.tolist()
+    ms_mixed, ms_plain = max_over_ranks([ms_mixed, ms_plain], "cuda")
 
     # per-kernel roofline from the stage events of the timed region
     hbm, hbm_kind = peaks()
