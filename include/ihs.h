@@ -125,7 +125,8 @@ typedef struct {
  *                      mixed form, FP64 in the plain form).  Dense A only, s = 1. */
 enum { IHS_SKETCH_SPARSE = 0, IHS_SKETCH_SRHT = 1, IHS_SKETCH_GAUSSIAN = 2 };
 
-/* Option flags.  IHS_FLAG_NO_FUSE: in ihs_solve, form SA and the gradient in
+/* Option flags (a bit not listed here makes ihs_create return IHS_ERR_ARG).
+ * IHS_FLAG_NO_FUSE: in ihs_solve, form SA and the gradient in
  * two separate passes over A even where the single fused pass applies (dense
  * FP32 data, mixed precision, CountSketch, d <= 512); results agree to
  * rounding, the fused pass reads A once instead of twice. */

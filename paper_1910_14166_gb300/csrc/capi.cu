@@ -451,6 +451,9 @@ ihs_status ihs_create(ihs_ctx** out, const ihs_matrix* A, const double* b,
   if (opt->s < 1 || opt->s > kMaxBlocks || opt->m < 1 || opt->m % opt->s != 0) return IHS_ERR_ARG;
   if (opt->m < A->d) return IHS_ERR_ARG;
   if (opt->precision < IHS_PREC_FP64 || opt->precision > IHS_PREC_BF16) return IHS_ERR_ARG;
+  const int known = IHS_FLAG_NO_FUSE | IHS_FLAG_SERIAL | IHS_FLAG_CLUSTER | IHS_FLAG_NO_LOOKAHEAD |
+                    IHS_FLAG_FP64_FACTOR;
+  if (opt->flags & ~known) return IHS_ERR_ARG;
   if (C->kind != IHS_OLS && C->kind != IHS_L1_BALL && C->kind != IHS_RIDGE &&
       C->kind != IHS_L1_PENALTY && C->kind != IHS_L2_BALL)
     return IHS_ERR_ARG;

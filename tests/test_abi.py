@@ -105,3 +105,33 @@ def test_binding_constants_match_the_header():
     assert ihs.option_flags(False, True, True, False, True) == 31
     stages = [n for n in sorted(h, key=h.get) if n.startswith("IHS_ST_") and n != "IHS_ST_COUNT"]
     assert [s[len("IHS_ST_"):].lower() for s in stages[:len(ihs.STAGES)]] == ihs.STAGES
+
+
+def test_create_rejects_invalid_options_before_touching_the_device():
+    """ihs_create's argument checks run on the host before any CUDA call:
+    unknown flag bits, an unknown sketch, m not divisible by s, m < d, an
+    unknown constraint kind and a non-positive ball radius each return
+    IHS_ERR_ARG (the device pointers are never dereferenced)."""
+    import paper_1910_14166_gb300 as ihs
+    lib = ihs._lib
+    M = ihs._Matrix()
+    M.kind, M.dtype, M.n, M.d, M.ld = ihs.DENSE, ihs.F32, 1000, 10, 10
+    M.val = 0x1000  # never read: every case fails a host-side check first
+    b = ctypes.c_void_p(0x2000)
+
+    def create(flags=0, sketch=0, m=100, s=1, kind=ihs.OLS, param=0.0):
+        C = ihs._Constraint(kind, param)
+        O = ihs._Options(m, s, 0, 1, 0, 0.0, flags, sketch)
+        h = ctypes.c_void_p()
+        return lib.ihs_create(ctypes.byref(h), ctypes.byref(M), b, ctypes.byref(C),
+                              ctypes.byref(O), None)
+
+    ERR_ARG = 1
+    assert create(flags=32) == ERR_ARG
+    assert create(flags=1 << 30) == ERR_ARG
+    assert create(sketch=3) == ERR_ARG
+    assert create(m=101, s=2) == ERR_ARG
+    assert create(m=5) == ERR_ARG
+    assert create(kind=7) == ERR_ARG
+    assert create(kind=ihs.L1_BALL, param=0.0) == ERR_ARG
+    assert create(sketch=1, s=2, m=100) == ERR_ARG
