@@ -228,6 +228,16 @@ ihs_status ihs_get_sketch(ihs_ctx* ctx, void* SA_out, int* SA_dtype, double* H_o
  * IHS_ERR_CUDA. */
 ihs_status ihs_trim_memory(void);
 
+/* ihs_selftest_wait -- exercises the bounded device wait used by the
+ * library's grid barriers without faulting or hanging the GPU: two CTAs wait
+ * at a barrier that expects three (nothing ever completes it), each gives up
+ * after 4096 polls (well under a millisecond) and records the timeout in a
+ * device status word, which is read back.  Returns IHS_ERR_TIMEOUT when the
+ * wait gave up as designed, IHS_OK if the barrier wrongly passed,
+ * IHS_ERR_CUDA / IHS_ERR_OOM on a runtime failure.  stream: a cudaStream_t
+ * (NULL = legacy default stream); synchronises it. */
+ihs_status ihs_selftest_wait(void* stream);
+
 /* ihs_exact_gram -- G = A^T A in FP64 (DEVICE, d x d doubles, row-major,
  * both triangles), the reference of the sketch-quality experiment (App. B:
  * the empirical error ||A^T S^T S A - A^T A||_F / ||A^T A||_F).  Dense A: an

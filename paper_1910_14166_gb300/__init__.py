@@ -91,6 +91,7 @@ def _load():
         "ihs_gradient_noalloc": [ctypes.POINTER(_Matrix), vp, vp, f64, vp, vp],
         "ihs_exact_gram": [vp, vp],
         "ihs_trim_memory": [],
+        "ihs_selftest_wait": [vp],
         "ihs_sketch_error": [vp, i64, vp, ctypes.POINTER(f64)],
     }
     for name, args in sig.items():
@@ -174,6 +175,12 @@ def trim_memory():
     """Return the library's cached device workspace memory to the device
     (contexts keep reusing it otherwise; see ihs_trim_memory)."""
     _check(_lib.ihs_trim_memory(), "ihs_trim_memory")
+
+
+def selftest_wait():
+    """Run the bounded-wait self-test on the current stream and return its
+    status code (IHS_ERR_TIMEOUT = 7 when the wait gave up as designed)."""
+    return int(_lib.ihs_selftest_wait(_stream()))
 
 
 class IHS:

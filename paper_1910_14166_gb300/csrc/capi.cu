@@ -990,6 +990,21 @@ ihs_status ihs_get_sketch(ihs_ctx* c, void* SA_out, int* SA_dtype, double* H_out
   return IHS_OK;
 }
 
+ihs_status ihs_selftest_wait(void* stream) {
+  cudaStream_t st = (cudaStream_t)stream;
+  unsigned* bar = nullptr;
+  if (cudaMalloc(&bar, 4 * sizeof(unsigned) + sizeof(int)) != cudaSuccess) return IHS_ERR_OOM;
+  int* status = reinterpret_cast<int*>(bar + 4);
+  int h = -1;
+  cudaError_t e = cudaMemsetAsync(bar, 0, 4 * sizeof(unsigned) + sizeof(int), st);
+  if (e == cudaSuccess) e = launch_barrier_selftest(bar, status, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h, status, sizeof(int), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(bar);
+  if (e != cudaSuccess) return IHS_ERR_CUDA;
+  return (ihs_status)h;
+}
+
 ihs_status ihs_trim_memory(void) {
   std::lock_guard<std::mutex> lk(g_pool_mu);
   for (int k = 0; k < kMaxDevices; ++k)

@@ -154,6 +154,9 @@ cudaError_t launch_chol_step(const void* Lbuf, const void* Dinv, int d, int f32,
 // delta = (L L^T)^{-1} v (no update), for preconditioning.
 // H^{-1} (d x d, factor precision) from the factor, skipped when need && !*need;
 // the shared memory it needs (must be <= 220 KB: FP32 any d <= 1024, FP64 d <= 832).
+// Two CTAs wait at a grid barrier that expects three, with a 4096-poll
+// limit: each gives up and records DEV_TIMEOUT in *status (bar: 4 zeroed words).
+cudaError_t launch_barrier_selftest(unsigned* bar, int* status, cudaStream_t st);
 size_t chol_inverse_smem_bytes(int d, int f32);
 cudaError_t launch_chol_inverse(const void* Lbuf, const void* Dinv, int d, int f32, void* Hinv,
                                 const int* need, cudaStream_t st);

@@ -57,7 +57,8 @@ __global__ void k_chol_init(const double* __restrict__ H, int d, int dp, double 
 
 // Grid-wide barrier (generation counter), bounded spin.  bar[0] = arrivals,
 // bar[1] = generation, bar[2] = abort flag; all zero before the launch.
-IHS_DEV bool grid_barrier(unsigned* bar, unsigned nblocks, int* status) {
+IHS_DEV bool grid_barrier(unsigned* bar, unsigned nblocks, int* status,
+                          long long limit = kSpinLimit) {
   __shared__ int ok;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -73,7 +74,7 @@ IHS_DEV bool grid_barrier(unsigned* bar, unsigned nblocks, int* status) {
     } else {
       long long it = 0;
       while (*gen == g) {
-        if (++it > kSpinLimit || *abort_flag) {
+        if (++it > limit || *abort_flag) {
           set_status(status, DEV_TIMEOUT);
           *abort_flag = 1u;
           ok = 0;
@@ -86,6 +87,19 @@ IHS_DEV bool grid_barrier(unsigned* bar, unsigned nblocks, int* status) {
   }
   __syncthreads();
   return ok != 0;
+}
+
+// Self-test of the bounded wait: a barrier that expects one CTA more than
+// are launched can never complete, so every CTA must give up after `limit`
+// polls, record DEV_TIMEOUT and return.
+__global__ void k_barrier_selftest(unsigned* bar, int* status, long long limit) {
+  grid_barrier(bar, gridDim.x + 1, status, limit);
+}
+
+cudaError_t launch_barrier_selftest(unsigned* bar, int* status, cudaStream_t st) {
+  k_barrier_selftest<<<2, 32, 0, st>>>(bar, status, 4096);
+  note_launches(1);
+  return cudaGetLastError();
 }
 
 // Panel sweep with warp 0 over the tall block [Dk; Ta] (Ta optional): lane r

@@ -767,3 +767,18 @@ def test_contexts_reuse_pool_memory_and_trim(cuda_lib):
             cuda_lib.trim_memory()
     for x in xs[1:]:
         assert np.array_equal(x, xs[0])
+
+
+def test_bounded_wait_gives_up_and_the_context_stays_usable(cuda_lib):
+    """Failure detection on the GPU without a fault: a grid barrier that can
+    never complete (two CTAs waiting for three) gives up after its poll limit
+    and reports IHS_ERR_TIMEOUT through the device status word; the GPU stays
+    usable, and a solve afterwards matches the oracle."""
+    assert cuda_lib.selftest_wait() == 7  # IHS_ERR_TIMEOUT
+    assert cuda_lib.selftest_wait() == 7
+    w = synth.make("ols_dense_fp64", n=5000, d=20, m=200)
+    xs = O.ihs(w["A"], w["b"], O.OLS, 0.0, 200, 1, 0, 3)
+    solver = cuda_lib.IHS(dev(w["A"]), dev(w["b"]), m=200, s=1, seed=0, precision="fp64")
+    x, rep = solver.solve(iters=3)
+    assert rep.status == 0
+    assert np.abs(x.cpu().numpy() - xs[-1]).max() <= 1e-12 * np.abs(xs[-1]).max()
