@@ -44,7 +44,6 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "ihs_oracle.c")
 _SO = os.path.join(_HERE, "libihs_oracle.so")
 _lock = threading.Lock()
-_lib = None
 
 u64 = ctypes.c_uint64
 i64 = ctypes.c_int64
@@ -53,45 +52,84 @@ f64 = ctypes.c_double
 vp = ctypes.c_void_p
 
 
+_SO_MT = os.path.join(_HERE, "libihs_oracle_mt.so")
+_libs = {}
+_active = "serial"
+
+
 def build_oracle(force: bool = False) -> str:
-    """Compile ihs_oracle.c with gcc (plain -O2, no fast-math, no FMA contraction)."""
-    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
-        tmp = _SO + ".tmp%d" % os.getpid()
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math",
-                               "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"])
-        os.replace(tmp, _SO)
+    """Compile ihs_oracle.c with gcc (plain -O2, no fast-math, no FMA
+    contraction), and the same file with -fopenmp into the multi-core build
+    (the timed CPU baseline; bit-identical results, see the C file)."""
+    base = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-shared", "-fPIC"]
+    for so, extra in ((_SO, []), (_SO_MT, ["-fopenmp"])):
+        if force or not os.path.exists(so) or os.path.getmtime(so) < os.path.getmtime(_SRC):
+            tmp = so + ".tmp%d" % os.getpid()
+            try:
+                subprocess.check_call(base + extra + ["-o", tmp, _SRC, "-lm"])
+            except subprocess.CalledProcessError:
+                if extra:  # no OpenMP runtime: the multi-core build is simply absent
+                    continue
+                raise
+            os.replace(tmp, so)
     return _SO
 
 
-def lib():
-    global _lib
+def _bind(L):
+    L.orc_set_threads.restype = i32
+    L.orc_set_threads.argtypes = [i32]
+    L.orc_sm64_at.restype = u64
+    L.orc_sm64_at.argtypes = [u64, u64]
+    L.orc_hash.restype = i32
+    L.orc_hash.argtypes = [u64, i64, i32, i64, i64, vp, vp]
+    L.orc_sketch_dense.restype = None
+    L.orc_sketch_dense.argtypes = [i64, i64, vp, i64, i64, i32, vp, vp, vp]
+    L.orc_sketch_csr.restype = None
+    L.orc_sketch_csr.argtypes = [i64, i64, vp, vp, vp, i64, i32, vp, vp, vp]
+    L.orc_gram.restype = None
+    L.orc_gram.argtypes = [i64, i64, vp, f64, f64, vp]
+    L.orc_resid_grad_dense.restype = i32
+    L.orc_resid_grad_dense.argtypes = [i64, i64, vp, i64, vp, vp, vp, vp]
+    L.orc_resid_grad_csr.restype = i32
+    L.orc_resid_grad_csr.argtypes = [i64, i64, vp, vp, vp, vp, vp, vp, vp]
+    L.orc_sketch_adjoint.restype = None
+    L.orc_sketch_adjoint.argtypes = [i64, i64, i64, i32, vp, vp, vp, f64, vp]
+    L.orc_srht_draw.restype = i32
+    L.orc_srht_draw.argtypes = [u64, i64, i64, i64, i64, vp, vp]
+    L.orc_srht_sketch_dense.restype = None
+    L.orc_srht_sketch_dense.argtypes = [i64, i64, vp, i64, i64, vp, vp, vp]
+    L.orc_gauss_draw.restype = None
+    L.orc_gauss_draw.argtypes = [u64, i64, i64, i64, vp]
+    return L
+
+
+def _load(kind):
     with _lock:
-        if _lib is None:
-            L = ctypes.CDLL(build_oracle())
-            L.orc_sm64_at.restype = u64
-            L.orc_sm64_at.argtypes = [u64, u64]
-            L.orc_hash.restype = i32
-            L.orc_hash.argtypes = [u64, i64, i32, i64, i64, vp, vp]
-            L.orc_sketch_dense.restype = None
-            L.orc_sketch_dense.argtypes = [i64, i64, vp, i64, i64, i32, vp, vp, vp]
-            L.orc_sketch_csr.restype = None
-            L.orc_sketch_csr.argtypes = [i64, i64, vp, vp, vp, i64, i32, vp, vp, vp]
-            L.orc_gram.restype = None
-            L.orc_gram.argtypes = [i64, i64, vp, f64, f64, vp]
-            L.orc_resid_grad_dense.restype = None
-            L.orc_resid_grad_dense.argtypes = [i64, i64, vp, i64, vp, vp, vp, vp]
-            L.orc_resid_grad_csr.restype = None
-            L.orc_resid_grad_csr.argtypes = [i64, i64, vp, vp, vp, vp, vp, vp, vp]
-            L.orc_sketch_adjoint.restype = None
-            L.orc_sketch_adjoint.argtypes = [i64, i64, i64, i32, vp, vp, vp, f64, vp]
-            L.orc_srht_draw.restype = i32
-            L.orc_srht_draw.argtypes = [u64, i64, i64, i64, i64, vp, vp]
-            L.orc_srht_sketch_dense.restype = None
-            L.orc_srht_sketch_dense.argtypes = [i64, i64, vp, i64, i64, vp, vp, vp]
-            L.orc_gauss_draw.restype = None
-            L.orc_gauss_draw.argtypes = [u64, i64, i64, i64, vp]
-            _lib = L
-    return _lib
+        if kind not in _libs:
+            build_oracle()
+            path = _SO if kind == "serial" else _SO_MT
+            if not os.path.exists(path):
+                raise RuntimeError("the multi-core oracle build is unavailable (no OpenMP)")
+            _libs[kind] = _bind(ctypes.CDLL(path))
+    return _libs[kind]
+
+
+def lib():
+    """The C library the oracle's data passes run in (serial unless
+    use_threads() selected the multi-core build)."""
+    return _load(_active)
+
+
+def use_threads(n: int) -> int:
+    """Run the C loops on n threads (the multi-core build; n <= 1: the serial
+    build).  Results are bit-identical either way.  Returns the threads used."""
+    global _active
+    if n is None or n <= 1:
+        _active = "serial"
+        return 1
+    L = _load("mt")
+    _active = "mt"
+    return int(L.orc_set_threads(int(n)))
 
 
 def _p(a):
@@ -209,13 +247,15 @@ def resid_grad(A, b, x, want_r: bool = False):
     r = np.empty(n) if want_r else None
     if isinstance(A, CSR):
         g = np.empty(A.d)
-        lib().orc_resid_grad_csr(A.n, A.d, _p(A.rowptr), _p(A.col), _p(A.val), _p(b), _p(x),
-                                 _p(r) if want_r else None, _p(g))
+        rc = lib().orc_resid_grad_csr(A.n, A.d, _p(A.rowptr), _p(A.col), _p(A.val), _p(b),
+                                      _p(x), _p(r) if want_r else None, _p(g))
     else:
         A = as_f64(A)
         g = np.empty(A.shape[1])
-        lib().orc_resid_grad_dense(A.shape[0], A.shape[1], _p(A), A.shape[1], _p(b), _p(x),
-                                   _p(r) if want_r else None, _p(g))
+        rc = lib().orc_resid_grad_dense(A.shape[0], A.shape[1], _p(A), A.shape[1], _p(b), _p(x),
+                                        _p(r) if want_r else None, _p(g))
+    if rc != 0:
+        raise MemoryError("oracle residual buffer")
     return (r, g) if want_r else g
 
 

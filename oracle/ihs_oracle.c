@@ -27,9 +27,46 @@
  *
  * Build: gcc -O2 -std=c11 -shared -fPIC -o libihs_oracle.so ihs_oracle.c
  * (-O2 keeps IEEE semantics: no -ffast-math, no FMA contraction, see below).
+ *
+ * Multi-core build (the timed CPU baseline only): the same file with
+ * -fopenmp.  Each parallel loop gives every thread a disjoint set of outputs
+ * (rows of SA by bucket, rows of r, columns of g, rows of H, entries of the
+ * draws) and each output is still summed over the same terms in the same
+ * ascending order as the serial loop, so the two builds return bit-identical
+ * results (a CPU test checks it).  Without -fopenmp the pragmas are ignored
+ * and every "owned range" below is the whole range.
  */
 #include <stdint.h>
 #include <stddef.h>
+#include <stdlib.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* The part [lo, hi) of [0, count) owned by the calling thread of the current
+ * OpenMP team (all of it outside a team or in the serial build). */
+static void owned_range(int64_t count, int64_t* lo, int64_t* hi) {
+#ifdef _OPENMP
+  const int64_t nt = omp_get_num_threads(), t = omp_get_thread_num();
+  *lo = count * t / nt;
+  *hi = count * (t + 1) / nt;
+#else
+  *lo = 0;
+  *hi = count;
+#endif
+}
+
+/* Threads of the multi-core build (ignored by the serial build); returns the
+ * number the next parallel region will use. */
+int orc_set_threads(int n) {
+#ifdef _OPENMP
+  if (n > 0) omp_set_num_threads(n);
+  return omp_get_max_threads();
+#else
+  (void)n;
+  return 1;
+#endif
+}
 
 /* Keep a*b+c as two roundings so the oracle is plain IEEE double arithmetic. */
 #if defined(__GNUC__)
@@ -81,6 +118,7 @@ int orc_hash(uint64_t seed, int64_t t, int s, int64_t m, int64_t n,
   uint64_t key_t = orc_sm64_at(key_seed, (uint64_t)t);
   for (int k = 0; k < s; ++k) {
     uint64_t key_tk = orc_sm64_at(key_t, (uint64_t)k);
+#pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < n; ++i) {
       uint64_t w = orc_sm64_at(key_tk, (uint64_t)i);
       uint64_t hi = w >> 32;
@@ -104,12 +142,18 @@ int orc_hash(uint64_t seed, int64_t t, int s, int64_t m, int64_t n,
 void orc_sketch_dense(int64_t n, int64_t d, const double* A, int64_t lda,
                       int64_t m, int s, const int32_t* bucket,
                       const int8_t* sign, double* SA) {
-  for (int64_t q = 0; q < m * d; ++q) SA[q] = 0.0;
-  for (int k = 0; k < s; ++k) {
-    for (int64_t i = 0; i < n; ++i) {
-      int64_t row = bucket[(int64_t)k * n + i];
-      double sg = (double)sign[(int64_t)k * n + i];
-      for (int64_t j = 0; j < d; ++j) SA[row * d + j] += sg * A[i * lda + j];
+#pragma omp parallel
+  {
+    int64_t r0, r1; /* the rows of SA (buckets) this thread owns */
+    owned_range(m, &r0, &r1);
+    for (int64_t q = r0 * d; q < r1 * d; ++q) SA[q] = 0.0;
+    for (int k = 0; k < s; ++k) {
+      for (int64_t i = 0; i < n; ++i) {
+        int64_t row = bucket[(int64_t)k * n + i];
+        if (row < r0 || row >= r1) continue;
+        double sg = (double)sign[(int64_t)k * n + i];
+        for (int64_t j = 0; j < d; ++j) SA[row * d + j] += sg * A[i * lda + j];
+      }
     }
   }
 }
@@ -122,13 +166,19 @@ void orc_sketch_dense(int64_t n, int64_t d, const double* A, int64_t lda,
 void orc_sketch_csr(int64_t n, int64_t d, const int64_t* rowptr,
                     const int32_t* col, const double* val, int64_t m, int s,
                     const int32_t* bucket, const int8_t* sign, double* SA) {
-  for (int64_t q = 0; q < m * d; ++q) SA[q] = 0.0;
-  for (int k = 0; k < s; ++k) {
-    for (int64_t i = 0; i < n; ++i) {
-      int64_t row = bucket[(int64_t)k * n + i];
-      double sg = (double)sign[(int64_t)k * n + i];
-      for (int64_t p = rowptr[i]; p < rowptr[i + 1]; ++p)
-        SA[row * d + col[p]] += sg * val[p];
+#pragma omp parallel
+  {
+    int64_t r0, r1; /* the rows of SA (buckets) this thread owns */
+    owned_range(m, &r0, &r1);
+    for (int64_t q = r0 * d; q < r1 * d; ++q) SA[q] = 0.0;
+    for (int k = 0; k < s; ++k) {
+      for (int64_t i = 0; i < n; ++i) {
+        int64_t row = bucket[(int64_t)k * n + i];
+        if (row < r0 || row >= r1) continue;
+        double sg = (double)sign[(int64_t)k * n + i];
+        for (int64_t p = rowptr[i]; p < rowptr[i + 1]; ++p)
+          SA[row * d + col[p]] += sg * val[p];
+      }
     }
   }
 }
@@ -141,6 +191,7 @@ void orc_sketch_csr(int64_t n, int64_t d, const int64_t* rowptr,
  */
 void orc_gram(int64_t m, int64_t d, const double* SA, double scale,
               double shift, double* H) {
+#pragma omp parallel for schedule(static)
   for (int64_t a = 0; a < d; ++a) {
     for (int64_t c = 0; c < d; ++c) {
       double acc = 0.0;
@@ -153,32 +204,58 @@ void orc_gram(int64_t m, int64_t d, const double* SA, double scale,
 /*
  * Residual and gradient of f(x) = 1/2 ||Ax - b||^2 (Eq. 1): r = b - A x and
  * g = A^T r = -grad f(x), the linear term of the IHS subproblem (Eq. 2).
- * Rows in ascending order; r may be NULL.
+ * Rows in ascending order; r may be NULL.  The residual of every row is
+ * formed first, then g_j = sum_i A_ij r_i over the rows in ascending order
+ * (the same additions, in the same order, as one interleaved pass).
+ * Returns 0, or -1 if the residual buffer could not be allocated.
  */
-void orc_resid_grad_dense(int64_t n, int64_t d, const double* A, int64_t lda,
-                          const double* b, const double* x, double* r,
-                          double* g) {
-  for (int64_t j = 0; j < d; ++j) g[j] = 0.0;
+int orc_resid_grad_dense(int64_t n, int64_t d, const double* A, int64_t lda,
+                         const double* b, const double* x, double* r,
+                         double* g) {
+  double* rr = r ? r : (double*)malloc((size_t)(n > 0 ? n : 1) * sizeof(double));
+  if (!rr) return -1;
+#pragma omp parallel for schedule(static)
   for (int64_t i = 0; i < n; ++i) {
     double ax = 0.0;
     for (int64_t j = 0; j < d; ++j) ax += A[i * lda + j] * x[j];
-    double ri = b[i] - ax;
-    if (r) r[i] = ri;
-    for (int64_t j = 0; j < d; ++j) g[j] += A[i * lda + j] * ri;
+    rr[i] = b[i] - ax;
   }
+#pragma omp parallel
+  {
+    int64_t j0, j1; /* the entries of g this thread owns */
+    owned_range(d, &j0, &j1);
+    for (int64_t j = j0; j < j1; ++j) g[j] = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+      const double ri = rr[i];
+      for (int64_t j = j0; j < j1; ++j) g[j] += A[i * lda + j] * ri;
+    }
+  }
+  if (!r) free(rr);
+  return 0;
 }
 
-void orc_resid_grad_csr(int64_t n, int64_t d, const int64_t* rowptr,
-                        const int32_t* col, const double* val, const double* b,
-                        const double* x, double* r, double* g) {
-  for (int64_t j = 0; j < d; ++j) g[j] = 0.0;
+int orc_resid_grad_csr(int64_t n, int64_t d, const int64_t* rowptr,
+                       const int32_t* col, const double* val, const double* b,
+                       const double* x, double* r, double* g) {
+  double* rr = r ? r : (double*)malloc((size_t)(n > 0 ? n : 1) * sizeof(double));
+  if (!rr) return -1;
+#pragma omp parallel for schedule(static)
   for (int64_t i = 0; i < n; ++i) {
     double ax = 0.0;
     for (int64_t p = rowptr[i]; p < rowptr[i + 1]; ++p) ax += val[p] * x[col[p]];
-    double ri = b[i] - ax;
-    if (r) r[i] = ri;
-    for (int64_t p = rowptr[i]; p < rowptr[i + 1]; ++p) g[col[p]] += val[p] * ri;
+    rr[i] = b[i] - ax;
   }
+#pragma omp parallel
+  {
+    int64_t j0, j1; /* the entries of g this thread owns */
+    owned_range(d, &j0, &j1);
+    for (int64_t j = j0; j < j1; ++j) g[j] = 0.0;
+    for (int64_t i = 0; i < n; ++i)
+      for (int64_t p = rowptr[i]; p < rowptr[i + 1]; ++p)
+        if (col[p] >= j0 && col[p] < j1) g[col[p]] += val[p] * rr[i];
+  }
+  if (!r) free(rr);
+  return 0;
 }
 
 /*
@@ -278,6 +355,7 @@ void orc_gauss_draw(uint64_t seed, int64_t t, int64_t m, int64_t n, double* G) {
   uint64_t key_t = orc_sm64_at(key_seed, (uint64_t)t);
   uint64_t key_t2 = orc_sm64_at(key_t, 2);
   const double two_pi = 6.283185307179586476925286766559;
+#pragma omp parallel for schedule(static)
   for (int64_t r = 0; r < m; ++r)
     for (int64_t i = 0; i < n; ++i) {
       uint64_t w = orc_sm64_at(key_t2, (uint64_t)(r * n + i));

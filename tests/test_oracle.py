@@ -656,3 +656,32 @@ def test_ihs_l2_ball_converges_to_xopt():
     assert O.l2_ball_kkt_residual(G, A.T @ b, np.zeros(20), R, xo) < 1e-12
     xs = O.ihs(A, b, O.L2_BALL, R, 200, 1, 0, 30)
     assert O.err_A(xs[-1], xo, G) < 1e-10
+
+
+# ------------------------------------------------- multi-core oracle build ---
+def test_multicore_oracle_build_is_bit_identical():
+    """The OpenMP build that times the CPU baseline gives every thread its own
+    outputs and sums each one over the same terms in the same order, so it
+    returns exactly what the serial build returns: the draw, SA (dense and
+    CSR, SJLT s = 3 with ragged bucket ranges over 5 threads), the Gram, the
+    residual and gradient (dense and CSR) and the Gaussian G."""
+    rng = np.random.default_rng(4)
+    n, d, m, s = 3001, 23, 93, 3
+    A = rng.standard_normal((n, d))
+    b = rng.standard_normal(n)
+    x = rng.standard_normal(d)
+    rowptr, col, val = synth.csr_uniform(n, d, 4, 3, np.float64)
+    C = O.CSR(n, d, rowptr, col, val)
+    out = {}
+    for threads in (1, 5):
+        O.use_threads(threads)
+        try:
+            bk, sg = O.hash_draw(7, 2, s, m, n)
+            out[threads] = [bk, sg, O.sketch(A, m, s, bk, sg), O.sketch(C, m, s, bk, sg),
+                            O.gram(O.sketch(A, m, s, bk, sg), 1.0 / s, 0.5),
+                            *O.resid_grad(A, b, x, want_r=True), *O.resid_grad(C, b, x, want_r=True),
+                            O.resid_grad(A, b, x), O.gauss_draw(3, 1, 17, 211)]
+        finally:
+            O.use_threads(1)
+    for a, c in zip(out[1], out[5]):
+        assert a.dtype == c.dtype and np.array_equal(a, c)
