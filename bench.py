@@ -39,6 +39,7 @@ import synth  # noqa: E402
 
 METRIC = "IHS time-to-1e-10 rel. error (mixed vs FP64); SA sketch GB/s vs HBM peak"
 FALLBACK_HBM = 6800.0
+FALLBACK_BF16 = 1900.0
 
 
 def peaks():
@@ -47,6 +48,16 @@ def peaks():
         d = json.load(open(p))
         return float(d["hbm_gbs"]), "measured"
     return FALLBACK_HBM, "fallback"
+
+
+def tensor_peak_tf32():
+    """Dense TF32 tensor peak: the measured BF16 burst figure times the
+    nominal TF32 / BF16 ratio (1.1 / 2.25 PFLOP/s), else the fallback."""
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["bf16_tflops"]) * 1.1 / 2.25, "measured bf16 burst x 1.1/2.25"
+    return FALLBACK_BF16 * 1.1 / 2.25, "fallback bf16 x 1.1/2.25"
 
 
 # ---------------------------------------------------------------- clocks ---
@@ -102,40 +113,74 @@ class Clocks:
 
 
 # ------------------------------------------------------------ CPU oracle ---
-def oracle_time_to_tol(w, n_sample, T, seed=0, iters=3):
-    """The FP64 CPU oracle, timed on a bounded sample of the workload: `iters`
-    IHS iterations (sketch draw, SA, gradient, Gram, Cholesky step) on the
-    first n_sample rows (all n by default), with the O(n) passes scaled to the
-    full n when sampled and the O(m d^2) Gram kept whole; the mean iteration
-    times T.  Returns (ms, description, CPU seconds spent)."""
+def host_cpu():
+    """(threads available, CPU model name) of this host, for the CPU baseline."""
+    cores = os.cpu_count() or 1
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return cores, model
+
+
+def oracle_time_to_tol(w, n_sample, T, seed=0, iters=3, threads=1, budget_s=None):
+    """The FP64 CPU oracle, timed on a bounded sample of the workload: IHS
+    iterations (sketch draw, SA, gradient, Gram, Cholesky step) on the first
+    n_sample rows (all n by default), on `threads` host threads (the
+    multi-core build of the same C loops, bit-identical results).  It runs
+    `iters` iterations, or, with budget_s, as many of the T iterations as the
+    first one says fit in budget_s (all T: a measured whole solve).  O(n)
+    passes are scaled to the full n when sampled; the mean iteration times T
+    is the time to 1e-10.  Returns (ms, description, seconds spent, threads,
+    iterations run)."""
     import oracle as O
-    n = w["n"]
-    n_sample = min(n_sample or n, w["A"].shape[0])
-    A = np.ascontiguousarray(w["A"][:n_sample], dtype=np.float64)
-    b = np.ascontiguousarray(w["b"][:n_sample])
-    m, s = w["m"], w["s"]
-    x = np.zeros(A.shape[1])
-    t_n = t_g = 0.0
-    for t in range(iters):
-        t0 = time.perf_counter()
-        bucket, sign = O.hash_draw(seed, t, s, m, n_sample)
-        SA = O.sketch(A, m, s, bucket, sign)
-        g = O.resid_grad(A, b, x)
-        t1 = time.perf_counter()
-        H = O.gram(SA, 1.0 / s)
-        x = x + O.chol_solve(H, g)
-        t2 = time.perf_counter()
-        t_n += t1 - t0
-        t_g += t2 - t1
-    per_iter = (t_n * (n / n_sample) + t_g) / iters
-    ran = "one oracle iteration" if iters == 1 else "%d oracle iterations" % iters
-    if n_sample == n:
-        desc = ("%s on the whole %d-row workload, the mean iteration times %d iterations"
-                % (ran, n, T))
+    used = O.use_threads(threads)
+    try:
+        n = w["n"]
+        n_sample = min(n_sample or n, w["A"].shape[0])
+        if w.get("A64") is not None and w["A64"].shape[0] == n_sample:
+            A = w["A64"]  # promoted once by the caller
+        else:
+            A = np.ascontiguousarray(w["A"][:n_sample], dtype=np.float64)
+        b = np.ascontiguousarray(w["b"][:n_sample])
+        m, s = w["m"], w["s"]
+        x = np.zeros(A.shape[1])
+        t_n = t_g = 0.0
+        it, todo = 0, iters
+        while it < todo:
+            t0 = time.perf_counter()
+            bucket, sign = O.hash_draw(seed, it, s, m, n_sample)
+            SA = O.sketch(A, m, s, bucket, sign)
+            g = O.resid_grad(A, b, x)
+            t1 = time.perf_counter()
+            H = O.gram(SA, 1.0 / s)
+            x = x + O.chol_solve(H, g)
+            t2 = time.perf_counter()
+            t_n += t1 - t0
+            t_g += t2 - t1
+            it += 1
+            if budget_s is not None and it == 1:
+                todo = int(max(1, min(T, budget_s // max(t2 - t0, 1e-9))))
+    finally:
+        O.use_threads(1)
+    per_iter = (t_n * (n / n_sample) + t_g) / it
+    core = "%d thread%s" % (used, "" if used == 1 else "s")
+    if it == T and n_sample == n:
+        desc = ("the whole solve: all %d iterations on the whole %d-row workload, %s"
+                % (T, n, core))
+    elif n_sample == n:
+        desc = ("%d oracle iteration%s on the whole %d-row workload (%s), the mean iteration "
+                "times %d iterations" % (it, "" if it == 1 else "s", n, core, T))
     else:
-        desc = ("%s on the first %d of %d rows (O(n) passes scaled by %.1f, m x d Gram whole), "
-                "the mean iteration times %d iterations" % (ran, n_sample, n, n / n_sample, T))
-    return per_iter * T * 1e3, desc, t_n + t_g
+        desc = ("%d oracle iterations on the first %d of %d rows (O(n) passes scaled by %.1f, "
+                "m x d Gram whole; %s), the mean iteration times %d iterations"
+                % (it, n_sample, n, n / n_sample, core, T))
+    return per_iter * T * 1e3, desc, t_n + t_g, used, it
 
 
 def oracle_iterations_proxy():
@@ -254,26 +299,47 @@ def run_ours(args, rank, world):
             import torch.distributed as dist
             dist.barrier()
 
-    def timed(solver, T, K, W, profile=False):
+    def timed(solver, T, K, W, profile=False, per_step=None):
         solve_steps(solver, T, W)
         if profile:
             solver.profile(True)
         barrier()
         st = torch.cuda.current_stream()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(st)
-        x = solve_steps(solver, T, K)
-        e1.record(st)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(K + 1)]
+        x = torch.zeros(d, dtype=torch.float64, device="cuda")
+        ev[0].record(st)
+        for k in range(K):  # one event between steps: the per-step times for the median
+            x.zero_()
+            solver.solve(x, t0=0, iters=T)
+            ev[k + 1].record(st)
         barrier()
-        ms = e0.elapsed_time(e1) / K
+        ms = ev[0].elapsed_time(ev[K]) / K
+        if per_step is not None:
+            per_step.extend(ev[k].elapsed_time(ev[k + 1]) for k in range(K))
         prof = solver.profile_read() if profile else None
         if profile:
             solver.profile(False)
         return ms, x, prof
 
+    # setup: ihs_create of the benchmark's context (workspaces from the
+    # library's pool, the float-pair copy of b), median of 5 after one
+    setup = []
+    for it in range(6):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sv = ihs.IHS(A, b, kind="ols", m=m, s=s, seed=0, precision=args.precision)
+        torch.cuda.synchronize()
+        if it:
+            setup.append((time.perf_counter() - t0) * 1e3)
+        sv.close()
+        del sv
+    setup_ms = statistics.median(setup)
+
     clocks = Clocks(int(os.environ.get("LOCAL_RANK", "0")))
     clocks.start()
-    ms_mixed, x_m, prof = timed(mixed, T_mixed, args.steps, args.warmup, profile=True)
+    steps_mixed = []
+    ms_mixed, x_m, prof = timed(mixed, T_mixed, args.steps, args.warmup, profile=True,
+                                per_step=steps_mixed)
     clk = clocks.stop()
     ms_plain, x_p, prof_plain = timed(plain, T_plain, max(1, args.steps // 2), 1, profile=True)
     err_final = err_A(x_m, xo, G)
@@ -321,13 +387,82 @@ def run_ours(args, rank, world):
         ms_two, _, _ = timed(two, T_mixed, max(1, args.steps // 2), 1)
         del two
     # the mixed form with the sketched Hessian factored in FP64 instead of FP32
-    ms_f64fac, T_f64fac = None, None
+    ms_f64fac, T_f64fac, errs_f64fac = None, None, None
     if not args.no_two_pass:
         f64f = ihs.IHS(A, b, kind="ols", m=m, s=s, seed=0, precision=args.precision,
                        fp64_factor=True)
-        T_f64fac, _ = iterations_to(f64f, xo, G, 1e-10)
+        T_f64fac, errs_f64fac = iterations_to(f64f, xo, G, 1e-10)
         ms_f64fac, _, _ = timed(f64f, T_f64fac, max(1, args.steps // 2), 1)
         del f64f
+
+    # the sketch stage as one unit: draw + sort, SA, fix-up of split buckets
+    # (the stand-alone sketch kernel, every stage on one stream), and the
+    # pipeline's per-iteration sort + fused pass + fix-up from the timed run
+    sv = ihs.IHS(A, b, kind="ols", m=m, s=s, seed=0, precision=args.precision, serial=True)
+    sv.sketch(0)
+    sv.profile(True)
+    for t in range(1, 6):
+        sv.sketch(t)
+    ms_sk, cnt_sk, _ = sv.profile_read()
+    sv.close()
+    del sv
+    sk_parts = {k: ms_sk[k] / max(1, cnt_sk[k]) for k in ("sort", "sketch", "sketch_fix")}
+    sk_ms = sum(sk_parts.values())
+    sk_bytes = a_bytes + m * d * 4
+    sketch_stage = {"what": "sort (draw + counting sort) + SA kernel + fix-up, one stream",
+                    "ms": round(sk_ms, 4), **{k + "_ms": round(v, 4) for k, v in sk_parts.items()},
+                    "algorithmic_bytes": sk_bytes,
+                    "GB_s": round(sk_bytes / (sk_ms * 1e-3) / 1e9, 1),
+                    "frac": round(sk_bytes / (sk_ms * 1e-3) / 1e9 / hbm, 3)}
+    if lookahead or fused:
+        per = {k: ms_stage[k] / max(1, cnt[k]) for k in ("sort", "grad" if lookahead else "sketch",
+                                                          "sketch_fix")}
+        fb = alg["grad" if lookahead else "sketch"]
+        fms = sum(per.values())
+        sketch_stage["fused_pipeline"] = {
+            "what": "per iteration: sort (on the second stream, overlapped) + fused pass "
+                    "(SA of the next iteration and the gradient) + fix-up",
+            "ms": round(fms, 4), "algorithmic_bytes": fb,
+            "GB_s": round(fb / (fms * 1e-3) / 1e9, 1),
+            "frac": round(fb / (fms * 1e-3) / 1e9 / hbm, 3)}
+
+    # the Gaussian comparison sketch (Sec. 2) on the same data: one sketch
+    # (G generated in the kernel, SA = G A on the tensor cores) and the solve
+    gauss = None
+    if not args.no_extra:
+        tf32_peak, tf32_kind = tensor_peak_tf32()
+        gv = ihs.IHS(A, b, kind="ols", m=m, s=s, seed=0, precision=args.precision,
+                     sketch="gaussian", serial=True)
+        gv.sketch(0)
+        gv.profile(True)
+        for t in range(1, 4):
+            gv.sketch(t)
+        ms_g, cnt_g, _ = gv.profile_read()
+        gms = ms_g["sketch"] / max(1, cnt_g["sketch"])
+        gflop = 2.0 * m * n * d
+        x_g = torch.zeros(d, dtype=torch.float64, device="cuda")
+        gv.solve(x_g, iters=2)  # warm-up of the solve path
+        gtimes = []
+        for _ in range(2):
+            x_g.zero_()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            gv.solve(x_g, iters=T_mixed)
+            e1.record()
+            torch.cuda.synchronize()
+            gtimes.append(e0.elapsed_time(e1))
+        gauss = {"kernel": "k_gauss_tc", "sketch_ms": round(gms, 3),
+                 "flops": gflop, "TFLOP_s": round(gflop / (gms * 1e-3) / 1e12, 1),
+                 "peak_tf32_TFLOP_s": round(tf32_peak, 1), "peak_kind": tf32_kind,
+                 "frac": round(gflop / (gms * 1e-3) / 1e12 / tf32_peak, 3),
+                 "solve_ms": round(min(gtimes), 3), "iters": T_mixed,
+                 "final_err": err_A(x_g, xo, G)}
+        gv.close()
+        del gv
+
+    # the large sparse LASSO workload: solve time and the CSC sketch's bandwidth
+    c5 = c5_record(ihs, hbm) if not args.no_extra and rank == 0 else None
 
     # end to end through the public API with host buffers
     e2e = None
@@ -366,10 +501,14 @@ def run_ours(args, rank, world):
 
     cpu = None
     if rank == 0 and not args.no_cpu:
-        import multiprocessing as mp  # noqa: F401  (oracle runs in this process; no pool)
-        ms_cpu, desc, spent = oracle_time_to_tol(w, args.cpu_rows, T_plain)
-        cpu = {"value": round(ms_cpu, 1), "unit": "ms", "cores": 1, "kind": "oracle",
-               "sample": desc, "cpu_seconds": round(spent, 2)}
+        cores, model = host_cpu()
+        ms_cpu, desc, spent, used, _ = oracle_time_to_tol(w, args.cpu_rows, T_plain,
+                                                          threads=cores, budget_s=args.cpu_budget)
+        cpu = {"value": round(ms_cpu, 1), "unit": "ms", "cores": used, "kind": "oracle",
+               "sample": desc, "cpu_seconds": round(spent, 2), "host_cores": cores,
+               "cpu_model": model,
+               "build": "the oracle's C loops built with OpenMP: each output summed in the "
+                        "serial order, results bit-identical to the one-thread build"}
 
     res = {
         "metric": METRIC,
@@ -382,20 +521,34 @@ def run_ours(args, rank, world):
         "higher_is_better": False,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f32 data; %s Gram; f64-class gradient" % args.precision,
+        "dtype": ("f32 A, f64 b and iterate; SA f32 accumulation; Gram %s inputs, f32 "
+                  "accumulation; Cholesky factor f32 (the f64 factor of the configuration: "
+                  "mixed_fp64_factor_ms); residual and gradient double-float (~48-bit, "
+                  "FP64-class)" % args.precision),
         "data": "synthetic",
-        "config": {"workload": "%s n=%d d=%d m=%d s=%d CountSketch seed 0 (OLS, AR(1) rho=0.5 rows)"
-                   % (args.workload, n, d, m, s),
-                   "precision": args.precision, "l2": "inputs larger than L2 (A = %.2f GB)" % (a_bytes / 1e9),
-                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "config": config_of(args.workload, n, d, m, s, world),
+        "precision": args.precision,
         "iters_to_1e-10": {"mixed": T_mixed, "fp64": T_plain, "mixed_fp64_factor": T_f64fac},
         "final_err": {"mixed": err_final, "fp64": err_final_plain},
+        "err_per_iter": {
+            "what": "||x^t - x_OPT||_A / ||x_OPT||_A after iteration t = 1, 2, ... (x_OPT by "
+                    "FP64 normal equations with refinement)",
+            "mixed": [float("%.3g" % e) for e in errs_mixed],
+            "mixed_fp64_factor": ([float("%.3g" % e) for e in errs_f64fac]
+                                  if errs_f64fac else None),
+            "fp64": [float("%.3g" % e) for e in errs_plain]},
+        "ms_per_step_median": round(statistics.median(steps_mixed), 3),
+        "setup_ms": round(setup_ms, 3),
+        "value_with_setup_ms": round(ms_mixed + setup_ms, 3),
         "fp64_time_to_1e-10_ms": round(ms_plain, 3),
         "mixed_speedup_vs_fp64": round(ms_plain / ms_mixed, 3),
         "mixed_two_pass_ms": round(ms_two, 3) if ms_two else None,
         "mixed_fp64_factor_ms": round(ms_f64fac, 3) if ms_f64fac else None,
         "sketch_GB_s": sk["GB_s"],
         "sketch_frac_of_hbm": sk["frac"],
+        "sketch_stage": sketch_stage,
+        "gaussian_sketch": gauss,
+        "lasso_csr_zipf": c5,
         "kernels": kernels,
         "stage_ms_per_iter": {k: round(v / max(1, cnt[k]), 4) for k, v in ms_stage.items()},
         "stage_ms_per_iter_fp64": {k: round(v / max(1, prof_plain[1][k]), 4)
@@ -409,32 +562,105 @@ def run_ours(args, rank, world):
     return res
 
 
+def config_of(workload, n, d, m, s, world):
+    """The benchmark's workload, named the same way by both arms."""
+    return {"workload": "%s n=%d d=%d m=%d s=%d CountSketch seed 0 (OLS, AR(1) rho=0.5 rows)"
+                        % (workload, n, d, m, s),
+            "l2": "inputs larger than L2 (A = %.2f GB FP32)" % (n * d * 4 / 1e9),
+            "parallelism": "replicas" if world > 1 else "single GPU"}
+
+
+def c5_record(ihs, hbm):
+    """The large sparse LASSO workload (CSR 10,000,000 x 1000, 5 nonzeros a
+    row at Zipf(1.1) columns, FP32 values, SJLT s = 8, m = 10000, l1 ball of
+    radius ||x*||_1 / 2, mixed TF32, 20 iterations): the solve (CUDA events,
+    median of 3 after a warm-up) and, from a one-stream profile of 5 sketches,
+    the CSC sketch kernel's bandwidth on its algorithmic bytes (the column
+    copy's values and row indices read once, SA written once)."""
+    import torch
+    w = synth.make("lasso_csr_zipf", seed=0)
+    n, d, m, s = w["n"], w["d"], w["m"], w["s"]
+    rp, col, val = (torch.from_numpy(w[k]).cuda() for k in ("rowptr", "col", "val"))
+    b = torch.from_numpy(w["b"]).cuda()
+    kw = dict(kind="l1", param=w["param"], m=m, s=s, seed=0, precision=w["precision"],
+              shape=(n, d))
+    t0 = time.perf_counter()
+    sv = ihs.IHS((rp, col, val), b, **kw)
+    torch.cuda.synchronize()
+    create_ms = (time.perf_counter() - t0) * 1e3
+    iters = w["iters"]
+    x0 = torch.zeros(d, dtype=torch.float64, device="cuda")
+    sv.solve(x0.clone(), iters=iters)
+    times = []
+    for _ in range(3):
+        x = x0.clone()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        _, rep = sv.solve(x, iters=iters)
+        e1.record()
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    sv.close()
+    del sv
+    sv = ihs.IHS((rp, col, val), b, serial=True, **kw)
+    sv.sketch(0)
+    sv.profile(True)
+    for t in range(1, 6):
+        sv.sketch(t)
+    ms, cnt, _ = sv.profile_read()
+    sv.close()
+    del sv
+    sk = ms["sketch"] / max(1, cnt["sketch"])
+    nnz = int(val.numel())
+    alg = nnz * (val.element_size() + 4) + m * d * 4
+    return {"workload": "lasso_csr_zipf n=%d d=%d nnz=%d m=%d s=%d l1 ball tf32" % (n, d, nnz, m, s),
+            "iters": iters, "solve_ms_median": round(statistics.median(times), 3),
+            "solve_ms_all": [round(t, 3) for t in times], "status": int(rep.status),
+            "create_ms": round(create_ms, 1),
+            "sketch_kernel": "k_sketch_csc", "sketch_ms": round(sk, 4),
+            "sketch_algorithmic_bytes": alg,
+            "sketch_GB_s": round(alg / (sk * 1e-3) / 1e9, 1),
+            "sketch_frac": round(alg / (sk * 1e-3) / 1e9 / hbm, 3)}
+
+
 def run_reference(args, rank, world):
-    """The oracle (plain FP64 CPU IHS) as the reference arm, on the same
-    workload and metric, each step a bounded sample (see oracle_time_to_tol)."""
+    """The oracle (plain FP64 CPU IHS, the multi-core build of its C loops on
+    every host core) as the reference arm, on the same workload and metric:
+    each timed step runs as many oracle iterations as fit in --ref-step-budget
+    seconds (the mean iteration times the iteration count is the step's time
+    to 1e-10; the iteration count is the oracle's own, from a proxy of the
+    workload with the same m / d and design)."""
     if rank != 0:
         return None
     nrows = args.cpu_rows
     w = synth.make(args.workload, n=nrows, seed=0)
     w["n"] = synth.WORKLOADS[args.workload]["n"] if args.n is None else args.n
+    w["A64"] = np.ascontiguousarray(w["A"], dtype=np.float64)
     T = oracle_iterations_proxy()
+    cores, model = host_cpu()
     vals = []
     spent = 0.0
+    desc, used = "", 1
     for it in range(args.warmup + args.steps):
-        ms, desc, sp = oracle_time_to_tol(w, nrows, T, iters=1)
+        timed_step = it >= args.warmup
+        ms, desc, sp, used, _ = oracle_time_to_tol(
+            w, nrows, T, iters=1, threads=cores,
+            budget_s=args.ref_step_budget if timed_step else None)
         spent += sp
-        if it >= args.warmup:
+        if timed_step:
             vals.append(ms)
     v = round(statistics.mean(vals), 1)
     return {
         "impl": "reference", "metric": METRIC, "value": v, "unit": "ms", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": v, "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "%s n=%d d=%d m=%d s=%d CountSketch seed 0" %
-                   (args.workload, w["n"], w["d"], w["m"], w["s"])},
+        "config": config_of(args.workload, w["n"], w["d"], w["m"], w["s"], world),
+        "precision": "fp64 (the oracle)",
         "iters_to_1e-10": {"oracle_proxy": T},
-        "cpu_baseline": {"value": v, "unit": "ms", "cores": 1, "kind": "oracle", "sample": desc,
-                         "cpu_seconds": round(spent, 2)},
+        "cpu_baseline": {"value": v, "unit": "ms", "cores": used, "kind": "oracle",
+                         "sample": desc, "cpu_seconds": round(spent, 2), "host_cores": cores,
+                         "cpu_model": model},
         "e2e": {"value": v, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
 
@@ -661,6 +887,13 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-two-pass", action="store_true")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the Gaussian-sketch and sparse-LASSO records")
+    ap.add_argument("--ref-step-budget", type=float, default=15.0,
+                    help="reference arm: seconds of oracle iterations per timed step")
+    ap.add_argument("--cpu-budget", type=float, default=40.0,
+                    help="seconds of oracle iterations the CPU baseline may run (whole solve "
+                         "when it fits)")
     ap.add_argument("--only", default=None, help="workloads experiment: comma-separated names")
     ap.add_argument("--experiment", default=None, choices=["sketch-quality", "workloads", "adjoint"],
                     help="run an experiment instead of the benchmark (one JSON line per point)")

@@ -120,9 +120,12 @@ typedef struct {
  *                      form, FP32 in the mixed form).
  *   IHS_SKETCH_GAUSSIAN S = G / sqrt(m) with G_ij iid N(0, 1) (Box-Muller of
  *                      the counter words of block 2), the dense comparison
- *                      whose cost is an O(m n d) product: G is generated in
- *                      column chunks and multiplied in by cuBLAS (TF32 in the
- *                      mixed form, FP64 in the plain form).  Dense A only, s = 1. */
+ *                      whose cost is an O(m n d) product.  G is never stored:
+ *                      the sketch kernel generates each tile of G in shared
+ *                      memory and multiplies it into SA there (tcgen05 tensor
+ *                      cores with TF32 inputs and FP32 accumulation in the
+ *                      mixed form, FP64 SIMT in the plain form); the context
+ *                      holds the split-K partials of SA.  Dense A only, s = 1. */
 enum { IHS_SKETCH_SPARSE = 0, IHS_SKETCH_SRHT = 1, IHS_SKETCH_GAUSSIAN = 2 };
 
 /* Option flags (a bit not listed here makes ihs_create return IHS_ERR_ARG).
@@ -191,6 +194,23 @@ ihs_status ihs_sketch(ihs_ctx* ctx, int64_t t);
  * term of Eq. 2, and optionally r = b - A x.  x: DEVICE d doubles (in);
  * g: DEVICE d doubles (out); r: DEVICE n doubles or NULL.  Asynchronous. */
 ihs_status ihs_gradient(ihs_ctx* ctx, const double* x, double* g, double* r);
+
+/* ihs_sketch_gradient -- both halves of Eq. 2's subproblem, with one read
+ * of A where the fused pass applies: draw S for counter t and form SA, the
+ * Hessian (1/s) (SA)^T SA (+ lambda I) and its factor, as ihs_sketch does,
+ * and the gradient g = A^T (b - A x) (minus lambda x for ridge) at x, as
+ * ihs_gradient does.  SA is the sum over the rows of each bucket (Sec. 2's
+ * streaming update) and the gradient is O(nnz(A)); both stream A, so the
+ * fused pass (dense FP32 A, a mixed precision, CountSketch, d <= 512, ld and
+ * d multiples of 4, IHS_FLAG_NO_FUSE unset) uses each row of A three times
+ * while it is in registers: for SA, for the residual and for the gradient.
+ * It is the kernel ihs_solve runs every iteration, in the same row-chunk
+ * plan.  Other contexts run the sketch chain and then the gradient pass.
+ * x: DEVICE d doubles (in); g: DEVICE d doubles (out), may not alias x.
+ * Afterwards ihs_get_sketch returns this SA and Hessian and ihs_step uses
+ * this factor.  Asynchronous, on the context's stream.  Errors: IHS_ERR_ARG
+ * (NULL, t < 0), IHS_ERR_CUDA. */
+ihs_status ihs_sketch_gradient(ihs_ctx* ctx, int64_t t, const double* x, double* g);
 
 /* ihs_step -- one step of Eq. 2 with the Hessian of the last ihs_sketch:
  * x (DEVICE, d doubles) holds x^t on entry and x^{t+1} on return.  OLS and
@@ -325,16 +345,23 @@ ihs_status ihs_sketch_adjoint(uint64_t seed, int64_t t, int s, int64_t m,
  * allocates nothing (no cudaMalloc, cudaFree or allocating library call).
  * The paper has no counterpart; this is a service of the library.
  *   A: HOST descriptor of a DENSE matrix (IHS_F32 or IHS_F64, DEVICE values,
- *      d <= 1024); b: DEVICE n doubles; x: DEVICE d doubles;
- *   g: DEVICE d doubles (out); stream: cudaStream_t or NULL.
+ *      d <= 1024; n = 0 is allowed, with A->val and b then unused and
+ *      possibly NULL, and gives g = -lambda x); b: DEVICE n doubles;
+ *   x: DEVICE d doubles; g: DEVICE d doubles (out); stream: cudaStream_t or
+ *   NULL.  The types and lengths behind these pointers cannot be checked
+ *   here: a b shorter than n or of another type is read out of bounds.
  * Scratch: a fixed 4 MiB array of per-warp partial gradients inside the
  * library (512 Ki doubles), held by every GPU that loads the library until
  * the process exits; the number of warps is chosen so that warps * d fits.
  * The first call on a device looks up that array's device address (once per
- * device, with that device current); make the first call on each device
- * before any stream capture.  Every call overwrites the slots it uses, so no
- * clearing is needed, but calls that overlap on the GPU (in flight at the
- * same time, e.g. on two streams) race on the shared array.
+ * device, with that device current, together with its SM count, which sets
+ * the number of warps); make the first call on each device before any stream
+ * capture.  The address belongs to the device's current context: if that
+ * context is destroyed and re-created (cudaDeviceReset), the next call sees
+ * a new context id and looks the address up again.  Every call overwrites
+ * the slots it uses, so no clearing is needed, but calls that overlap on the
+ * GPU (in flight at the same time, e.g. on two streams) race on the shared
+ * array.
  * Errors: IHS_ERR_ARG (not dense, bad shape or NULL pointer),
  * IHS_ERR_UNSUPPORTED (d > 1024), IHS_ERR_CUDA.  Asynchronous. */
 ihs_status ihs_gradient_noalloc(const ihs_matrix* A, const double* b, const double* x,

@@ -79,6 +79,7 @@ def _load():
                        ctypes.POINTER(_Constraint), ctypes.POINTER(_Options), vp],
         "ihs_sketch": [vp, i64],
         "ihs_gradient": [vp, vp, vp, vp],
+        "ihs_sketch_gradient": [vp, i64, vp, vp],
         "ihs_step": [vp, vp],
         "ihs_solve": [vp, vp, i64, i32, ctypes.POINTER(_Report)],
         "ihs_sync": [vp],
@@ -108,8 +109,8 @@ def _load():
 _lib = _load()
 LIB_PATH = _build.LIB
 STAGES = ["sort", "sketch", "sketch_fix", "gram", "factor", "grad", "step"]
-EXPORTS = ["ihs_create", "ihs_sketch", "ihs_gradient", "ihs_step", "ihs_solve", "ihs_sync",
-           "ihs_get_sketch", "ihs_adjoint", "ihs_destroy", "ihs_status_str", "ihs_hash",
+EXPORTS = ["ihs_create", "ihs_sketch", "ihs_gradient", "ihs_sketch_gradient", "ihs_step",
+           "ihs_solve", "ihs_sync", "ihs_get_sketch", "ihs_adjoint", "ihs_destroy", "ihs_status_str", "ihs_hash",
            "ihs_sketch_adjoint", "ihs_profile", "ihs_profile_read", "ihs_gradient_noalloc"]
 
 
@@ -156,18 +157,33 @@ def ihs_gradient_noalloc(A, b, x, lam=0.0):
     """g = A^T (b - A x) - lam x for a dense CUDA tensor A, through the entry
     point that allocates no device memory inside the library (its scratch is
     a fixed array in the library; see include/ihs.h).  Only the output g is
-    allocated here, by the caller's side (PyTorch)."""
+    allocated here, by the caller's side (PyTorch).
+
+    The C entry point cannot see tensor types or lengths, so they are checked
+    here before anything is launched: A 2-D float32/float64, b float64 with
+    A.shape[0] entries, x float64 with A.shape[1], all on one device; the call
+    runs with that device current."""
     for t_, nm in ((A, "A"), (b, "b"), (x, "x")):
         _need_cuda(t_, nm)
     if A.dim() != 2 or A.dtype not in (torch.float32, torch.float64):
         raise TypeError("A must be a 2-D float32/float64 tensor")
+    if b.dtype != torch.float64 or x.dtype != torch.float64:
+        raise TypeError("b and x must be float64")
+    if b.dim() != 1 or b.numel() != A.shape[0]:
+        raise ValueError("b must hold A.shape[0] = %d values" % A.shape[0])
+    if x.dim() != 1 or x.numel() != A.shape[1]:
+        raise ValueError("x must hold A.shape[1] = %d values" % A.shape[1])
+    if b.device != A.device or x.device != A.device:
+        raise ValueError("A, b and x must be on one device")
     M = _Matrix()
-    M.kind, M.n, M.d, M.ld = DENSE, A.shape[0], A.shape[1], A.stride(0)
+    M.kind, M.n, M.d, M.ld = DENSE, A.shape[0], A.shape[1], max(A.stride(0), A.shape[1])
     M.dtype = F32 if A.dtype == torch.float32 else F64
-    M.val = A.data_ptr()
-    g = torch.empty(A.shape[1], dtype=torch.float64, device=A.device)
-    _check(_lib.ihs_gradient_noalloc(ctypes.byref(M), _ptr(b), _ptr(x), float(lam), _ptr(g),
-                                     _stream()), "ihs_gradient_noalloc")
+    M.val = A.data_ptr() if A.numel() else None
+    with torch.cuda.device(A.device):
+        g = torch.empty(A.shape[1], dtype=torch.float64, device=A.device)
+        _check(_lib.ihs_gradient_noalloc(ctypes.byref(M), _ptr(b) if b.numel() else None,
+                                         _ptr(x), float(lam), _ptr(g), _stream()),
+               "ihs_gradient_noalloc")
     return g
 
 
@@ -264,6 +280,16 @@ class IHS:
         r = torch.empty(self.n, dtype=torch.float64, device=self.device) if want_r else None
         _check(_lib.ihs_gradient(self._h, _ptr(x), _ptr(g), _ptr(r)), "ihs_gradient")
         return (r, g) if want_r else g
+
+    def sketch_gradient(self, t, x):
+        """Sketch of counter t (SA, Hessian, factor) and g at x from one pass
+        over A where the fused pass applies (ihs_sketch_gradient)."""
+        _need_cuda(x, "x")
+        if x.dtype != torch.float64 or x.numel() != self.d:
+            raise ValueError("x must hold d float64 values")
+        g = torch.empty(self.d, dtype=torch.float64, device=self.device)
+        _check(_lib.ihs_sketch_gradient(self._h, int(t), _ptr(x), _ptr(g)), "ihs_sketch_gradient")
+        return g
 
     def step(self, x):
         _need_cuda(x, "x")

@@ -58,6 +58,7 @@ struct ihs_ctx {
   cudaEvent_t ev_grad = nullptr;  // gradient pass of the current iteration done
   cudaEvent_t ev_sa = nullptr;    // look-ahead: SA of the next counter formed
   cudaEvent_t ev_gram = nullptr;  // look-ahead: the Gram has read SA (SA free)
+  cudaEvent_t ev_tail2 = nullptr; // the tail of the internal stream (joined into the caller's)
   bool prof = false;
   StageEvents pe;
   double prof_ms[IHS_NSTAGES] = {};
@@ -104,11 +105,11 @@ struct ihs_ctx {
   bool srht = false;
   void* srht_T = nullptr;
   int32_t* srht_rows = nullptr;
-  // Gaussian comparison sketch: chunk buffers and the BLAS handle
+  // Gaussian comparison sketch: plan and split partials
   bool gauss = false;
-  void* gauss_G = nullptr;
-  void* gauss_A = nullptr;
-  void* blas = nullptr;
+  GaussPlan gplan{};
+  void* gauss_part = nullptr;
+  void* gauss_At = nullptr;  // mixed form: A^T in TF32, K-major (built at create)
   GramPlan gp{};
   void* gop = nullptr;
   float* gpart_f = nullptr;
@@ -428,12 +429,12 @@ void ihs_destroy(ihs_ctx* c) {
   if (c->ev_grad) cudaEventDestroy(c->ev_grad);
   if (c->ev_sa) cudaEventDestroy(c->ev_sa);
   if (c->ev_gram) cudaEventDestroy(c->ev_gram);
+  if (c->ev_tail2) cudaEventDestroy(c->ev_tail2);
   for (int k = 0; k < 2; ++k) {
     if (c->ev_sort[k]) cudaEventDestroy(c->ev_sort[k]);
     if (c->ev_read[k]) cudaEventDestroy(c->ev_read[k]);
   }
   if (c->st2) cudaStreamDestroy(c->st2);
-  gauss_blas_destroy(c->blas);
   for (void* p : c->allocs) cudaFreeAsync(p, c->st);
   cudaStreamSynchronize(c->st);
   delete c;
@@ -513,7 +514,8 @@ ihs_status ihs_create(ihs_ctx** out, const ihs_matrix* A, const double* b,
   if (cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&c->ev_grad, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&c->ev_sa, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&c->ev_gram, cudaEventDisableTiming) != cudaSuccess)
+      cudaEventCreateWithFlags(&c->ev_gram, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_tail2, cudaEventDisableTiming) != cudaSuccess)
     return fail(IHS_ERR_CUDA);
   for (int k = 0; k < 2; ++k) {
     if (cudaEventCreateWithFlags(&c->ev_sort[k], cudaEventDisableTiming) != cudaSuccess ||
@@ -564,11 +566,13 @@ ihs_status ihs_create(ihs_ctx** out, const ihs_matrix* A, const double* b,
     c->rg_warps = rg_dense_warps(c->n);
     AL2(c->gpart, (size_t)c->rg_warps * c->d * sizeof(double));
     if (c->gauss) {
-      const int64_t nc = gauss_chunk(c->m, c->n);
-      AL2(c->gauss_G, (size_t)c->m * nc * acc_el);
-      AL2(c->gauss_A, (size_t)nc * c->d * acc_el);
-      c->blas = gauss_blas_create();
-      if (!c->blas) return fail(IHS_ERR_CUDA);
+      c->gplan = make_gauss_plan(c->m, c->n, (int)c->d, c->acc64, c->sms);
+      AL2(c->gauss_part, c->gplan.partial_bytes);
+      if (!c->acc64) {
+        AL2(c->gauss_At, c->gplan.at_bytes);
+        if (launch_gauss_operand(c->gplan, c->DA, c->gauss_At, c->st) != cudaSuccess)
+          return fail(IHS_ERR_CUDA);
+      }
     }
     if (c->srht) {
       AL2(c->srht_T, (size_t)srht_n2(c->n) * srht_ldt((int)c->d) * acc_el);
@@ -634,8 +638,8 @@ ihs_status sketch_chain(ihs_ctx* c, int64_t t, int bf, int fac_ctas = 0,
   const SketchKeys K = make_keys(c->opt.seed, t, c->s, c->m);
   if (c->gauss) {
     stage_begin(c, IHS_ST_SKETCH, s2);
-    CK(launch_gauss(c->blas, c->DA, make_keys(c->opt.seed, t, 3, c->m), c->m, c->acc64,
-                    c->gauss_G, c->gauss_A, c->SA, s2));
+    CK(launch_gauss(c->gplan, c->DA, c->gauss_At, make_keys(c->opt.seed, t, 3, c->m).key[2],
+                    c->gauss_part, c->SA, c->status, s2));
     stage_end(c);
   } else if (c->srht) {
     stage_begin(c, IHS_ST_SKETCH, s2);
@@ -886,6 +890,46 @@ ihs_status ihs_sketch(ihs_ctx* c, int64_t t) {
 ihs_status ihs_gradient(ihs_ctx* c, const double* x, double* g, double* r) {
   if (!c || !x || !g) return IHS_ERR_ARG;
   return gradient_on(c, x, g, r, true);
+}
+
+ihs_status ihs_sketch_gradient(ihs_ctx* c, int64_t t, const double* x, double* g) {
+  if (!c || t < 0 || !x || !g) return IHS_ERR_ARG;
+  if (!c->fused) {
+    ihs_status s = ihs_sketch(c, t);
+    if (s != IHS_OK) return s;
+    return gradient_on(c, x, g, nullptr, true);
+  }
+  // Everything on the caller's stream, after what the internal stream holds
+  // (a sketch chain may still be writing the sort buffers or SA).
+  cudaStream_t st = c->st;
+  CK(cudaEventRecord(c->ev_tail2, c->st2));
+  CK(cudaStreamWaitEvent(st, c->ev_tail2, 0));
+  const int bf = c->cur ^ 1;
+  CK(cudaStreamWaitEvent(st, c->ev_use[bf], 0));
+  const double lam = (c->C.kind == IHS_RIDGE) ? c->C.param : 0.0;
+  const SketchKeys K = make_keys(c->opt.seed, t, c->s, c->m);
+  stage_begin(c, IHS_ST_SORT, st);
+  CK(launch_sort_sketch(c->sp, K, c->n, c->sort_ws, c->perm, c->seg, c->chunk_first, st));
+  stage_end(c);
+  stage_begin(c, IHS_ST_SKETCH, st);
+  cudaError_t e = launch_sketch_grad_fused(c->DA, c->sp, c->perm, c->seg, c->chunk_first,
+                                           c->bsplit, x, (float*)c->SA, (float*)c->sk_partial,
+                                           c->gcta, g, lam, st, c->prof ? c : nullptr, true);
+  stage_end(c);
+  CK(e);
+  CK(cudaEventRecord(c->ev_read[0], st));
+  stage_begin(c, IHS_ST_GRAM, st);
+  CK(launch_gram(c->gp, c->SA, c->gop, c->gpart_f, c->gpart_d, gram_scale(c), lam, c->H[bf],
+                 c->status, st));
+  stage_end(c);
+  stage_begin(c, IHS_ST_FACTOR, st);
+  CK(launch_cholesky(c->H[bf], (int)c->d, c->f32fac, c->L[bf], c->Dinv[bf], c->bar, c->status,
+                     st, (c->opt.flags & IHS_FLAG_CLUSTER) != 0));
+  stage_end(c);
+  CK(cudaEventRecord(c->ev_fac[bf], st));
+  c->cur = bf;
+  c->have_sketch = true;
+  return IHS_OK;
 }
 
 ihs_status ihs_step(ihs_ctx* c, double* x) {

@@ -192,14 +192,30 @@ cudaError_t launch_srht(const DenseA& A, const SketchKeys& K, int64_t m, int acc
                         int32_t* rows, void* SA, cudaStream_t st);
 
 // ---- Gaussian sketch (Sec. 2's dense comparison) --------------------------------
-// G generated in chunks of gauss_chunk(m, n) columns into Gbuf (m x nc), A's rows
-// copied into Abuf (nc x d) when their type differs or for the ragged last chunk,
-// SA = G A by cuBLAS (TF32 / FP64).  cublas: a handle from gauss_blas_create().
-int64_t gauss_chunk(int64_t m, int64_t n);
-cudaError_t launch_gauss(void* cublas, const DenseA& A, const SketchKeys& K, int64_t m, int acc64,
-                         void* Gbuf, void* Abuf, void* SA, cudaStream_t st);
-void* gauss_blas_create();
-void gauss_blas_destroy(void* h);
+// SA = G A with G generated tile by tile inside the kernel (never stored):
+// FP64 SIMT tiles (plain form) or a tcgen05 TF32 kernel (mixed forms), split
+// over the rows of A; partial holds partial_bytes, summed in split order.
+struct GaussPlan {
+  int acc64 = 0;
+  int64_t m = 0, n = 0;
+  int d = 0;
+  int mtiles = 0, ntiles = 0, splits = 0;
+  int64_t kchunk = 0;        // plain form: rows of A per split
+  int dn = 0;                // mixed form: columns per N tile (multiple of 64, <= 512)
+  int dpad = 0;              // mixed form: d rounded up to 64 (rows of the A^T operand)
+  int box_rows = 0;          // mixed form: rows of A^T per TMA copy
+  int64_t ldt = 0;           // mixed form: n rounded up to 32 (row length of A^T)
+  size_t at_bytes = 0;       // mixed form: the A^T operand (dpad x ldt TF32)
+  int64_t ldp = 0;           // mixed form: row length of the partials
+  int64_t kb_per_split = 0;  // mixed form: 32-row K blocks per split
+  int stages = 0, tmem_cols = 0, smem = 0;
+  size_t partial_bytes = 0;
+};
+GaussPlan make_gauss_plan(int64_t m, int64_t n, int d, int acc64, int sms);
+// Mixed form: A^T in TF32, K-major, once per context (a no-op in the plain form).
+cudaError_t launch_gauss_operand(const GaussPlan& p, const DenseA& A, void* At, cudaStream_t st);
+cudaError_t launch_gauss(const GaussPlan& p, const DenseA& A, const void* At, uint64_t key,
+                         void* partial, void* SA, int* status, cudaStream_t st);
 
 // ---- p = 2 ball step (host-driven secular iteration; kernels in l2ball.cu) ------
 cudaError_t launch_l2_matvec(const double* H, int d, const double* x, double mu, const double* base,

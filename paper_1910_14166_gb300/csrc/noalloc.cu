@@ -171,24 +171,75 @@ __global__ void k_noalloc_reduce(const double* __restrict__ gpart, int nwarps, i
   }
 }
 
-// Device address of the scratch array, looked up once per device.
+// Device address of the scratch array and the SM count, looked up once per
+// device (with that device current) and cached.  A module's __device__ array
+// lives in a CUDA context: if the device's primary context is destroyed and
+// re-created (cudaDeviceReset), the array is reloaded, possibly at another
+// address.  So each cached entry also records the unique id of the context it
+// was taken in (cuCtxGetId, reached through the runtime's driver entry-point
+// query), and a call made in a different context looks the address up again.
+typedef int (*PFN_ctxGetCurrent)(void**);
+typedef int (*PFN_ctxGetId)(void*, unsigned long long*);
+
 constexpr int kMaxDevices = 64;
-double* g_scratch_addr[kMaxDevices] = {};
+struct ScratchEntry {
+  double* addr = nullptr;
+  unsigned long long ctx_id = 0;
+  int sms = 0;
+};
+ScratchEntry g_scratch[kMaxDevices];
 std::mutex g_scratch_mu;
 
-cudaError_t scratch_for_current_device(double** out) {
+// Unique id of the calling thread's current context (0 when no context is
+// current yet); *known = false if the driver entry points cannot be had, and
+// the cache is then keyed by device alone.
+unsigned long long current_context_id(bool* known) {
+  static PFN_ctxGetCurrent get_cur = nullptr;
+  static PFN_ctxGetId get_id = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPoint("cuCtxGetCurrent", &p, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_cur = (PFN_ctxGetCurrent)p;
+    p = nullptr;
+    if (cudaGetDriverEntryPoint("cuCtxGetId", &p, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_id = (PFN_ctxGetId)p;
+  });
+  *known = get_cur && get_id;
+  if (!*known) return 0;
+  void* ctx = nullptr;
+  unsigned long long id = 0;
+  if (get_cur(&ctx) != 0 || !ctx || get_id(ctx, &id) != 0) return 0;
+  return id;
+}
+
+cudaError_t scratch_for_current_device(double** out, int* sms) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  bool known = false;
+  const unsigned long long id = current_context_id(&known);
   std::lock_guard<std::mutex> lock(g_scratch_mu);
-  if (!g_scratch_addr[dev]) {
+  ScratchEntry& E = g_scratch[dev];
+  // look up on the first call on the device, and again in a new context (or
+  // on a thread with no context current yet: the lookup makes one current)
+  if (!E.addr || (known && (id == 0 || id != E.ctx_id))) {
     void* p = nullptr;
     e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess) return e;
-    g_scratch_addr[dev] = (double*)p;
+    int nsm = 0;
+    if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+      return e;
+    E.addr = (double*)p;
+    E.ctx_id = known ? current_context_id(&known) : 0;
+    E.sms = nsm > 0 ? nsm : 1;
   }
-  *out = g_scratch_addr[dev];
+  *out = E.addr;
+  *sms = E.sms;
   return cudaSuccess;
 }
 
@@ -196,19 +247,23 @@ cudaError_t scratch_for_current_device(double** out) {
 
 extern "C" ihs_status ihs_gradient_noalloc(const ihs_matrix* A, const double* b, const double* x,
                                            double lambda, double* g, void* stream) {
-  if (!A || !b || !x || !g) return IHS_ERR_ARG;
+  if (!A || !x || !g) return IHS_ERR_ARG;
   if (A->kind != IHS_DENSE || (A->dtype != IHS_F32 && A->dtype != IHS_F64)) return IHS_ERR_ARG;
-  if (A->n < 0 || A->d < 1 || A->ld < A->d || A->val == nullptr) return IHS_ERR_ARG;
+  if (A->n < 0 || A->n >= (1ll << 31) || A->d < 1 || A->ld < A->d) return IHS_ERR_ARG;
+  // an empty A (n = 0) needs no values and no b: g = -lambda x
+  if (A->n > 0 && (A->val == nullptr || b == nullptr)) return IHS_ERR_ARG;
   if (A->d > 1024) return IHS_ERR_UNSUPPORTED;
   const int d = (int)A->d;
-  // warps: as many as the scratch holds, at most 16 per SM of a 152-SM part
+  double* scratch = nullptr;
+  int sms = 1;
+  cudaError_t e = scratch_for_current_device(&scratch, &sms);
+  if (e != cudaSuccess) return IHS_ERR_CUDA;
+  // warps: as many as the scratch holds, at most 16 per SM of this device,
+  // and none with fewer than four rows
   const int64_t by_scratch = kNoAllocScratchDoubles / d;
-  int nwarps = (int)std::max<int64_t>(1, std::min<int64_t>({by_scratch, 152 * 16,
+  int nwarps = (int)std::max<int64_t>(1, std::min<int64_t>({by_scratch, (int64_t)sms * 16,
                                                             (A->n + 3) / 4}));
   if ((int64_t)nwarps * d > kNoAllocScratchDoubles) return IHS_ERR_UNSUPPORTED;
-  double* scratch = nullptr;
-  cudaError_t e = scratch_for_current_device(&scratch);
-  if (e != cudaSuccess) return IHS_ERR_CUDA;
   cudaStream_t st = (cudaStream_t)stream;
   const int blocks = (nwarps * 32 + kNaThreads - 1) / kNaThreads;
   if (A->dtype == IHS_F32) {

@@ -328,7 +328,9 @@ __device__ bool face_solve(const double* __restrict__ H, int d, double R, bool p
       su += (sig_src[sh.S[a]] > 0.f ? 1.0 : -1.0) * res[a];
     const double sTu = block_sum(su, sh.redd);
     const double dmu = pen ? 0.0 : (sTu - rb) / sTw;
-    for (int a = threadIdx.x; a < k; a += blockDim.x) sh.z[a] += res[a] - dmu * wv[a];
+    // (the penalised form leaves w unset: it has no border, and dmu = 0)
+    for (int a = threadIdx.x; a < k; a += blockDim.x)
+      sh.z[a] += pen ? res[a] : res[a] - dmu * wv[a];
     if (threadIdx.x == 0) sh.z[k] += dmu;
     __syncthreads();
   }

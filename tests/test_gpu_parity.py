@@ -141,6 +141,44 @@ def test_gradient_csr(cuda_lib):
         assert np.all(np.abs(g - go) <= 1e-12 * scale)
 
 
+# ------------------------------------------- one pass: sketch + gradient ---
+@pytest.mark.parametrize("n,d,m,prec", [(70001, 500, 5000, "tf32"), (20011, 132, 1320, "bf16"),
+                                        (3001, 4, 40, "tf32"), (5003, 36, 64, "fp64")])
+def test_sketch_gradient_one_pass(cuda_lib, n, d, m, prec):
+    """ihs_sketch_gradient: SA of counter 4 and g at x from one read of A (the
+    fused pass for FP32 data in the mixed forms; the sketch chain and the
+    gradient pass for the plain form).  SA: within the FP32 summation bound
+    gamma_{L-1} sum |A_ij| per bucket of L rows (bit-identical to the oracle in
+    FP64); g: within 1e-12 of sum_i |A_i||r_i|; H: the Gram of that SA."""
+    rng = np.random.default_rng(n + m)
+    A = rng.standard_normal((n, d)).astype(np.float32 if prec != "fp64" else np.float64)
+    A64 = A.astype(np.float64)
+    xs = rng.standard_normal(d)
+    b = A64 @ xs + 0.1 * rng.standard_normal(n)
+    sv = cuda_lib.IHS(dev(A), dev(b), m=m, s=1, seed=2, precision=prec)
+    for t in (4, 5):
+        x = xs + 1e-3 * rng.standard_normal(d)
+        g = sv.sketch_gradient(t, dev(x)).cpu().numpy()
+        SA, H, scale = sv.get_sketch()
+        SA = SA.cpu().numpy()
+        bo, so = O.hash_draw(2, t, 1, m, n)
+        SAo = O.sketch(A64, m, 1, bo, so)
+        if prec == "fp64":
+            assert np.array_equal(SA, SAo)
+            assert rel(H.cpu().numpy(), O.gram(SAo, 1.0)) < 1e-13
+        else:
+            absS = O.sketch(np.abs(A64), m, 1, bo, np.ones_like(so))
+            L = np.maximum(np.bincount(bo.ravel(), minlength=m) - 1.0, 0.0)
+            gam = L * 2.0 ** -24 / (1.0 - L * 2.0 ** -24)
+            assert np.all(np.abs(SA - SAo) <= (gam[:, None] + 1e-15) * absS)
+            u = 2.0 ** -11 if prec == "tf32" else 2.0 ** -8
+            SA64 = SA.astype(np.float64)
+            assert np.all(np.abs(H.cpu().numpy() - O.gram(SA64, scale))
+                          <= 4 * u * O.gram(np.abs(SA64), scale))
+        r, go = O.resid_grad(A64, b, x, want_r=True)
+        assert np.all(np.abs(g - go) <= 1e-12 * (np.abs(A64).T @ np.abs(r))), t
+
+
 # ------------------------------------------------------------ full solve ---
 def test_ihs_ols_plain_matches_oracle_every_iteration(cuda_lib):
     """20000 x 50 OLS, CountSketch m = 500, 10 iterations, seed 0: every GPU
@@ -767,6 +805,47 @@ def test_contexts_reuse_pool_memory_and_trim(cuda_lib):
             cuda_lib.trim_memory()
     for x in xs[1:]:
         assert np.array_equal(x, xs[0])
+
+
+@pytest.mark.parametrize("kind", ["l1", "l1pen"])
+def test_l1_contexts_after_poisoned_pool_memory(cuda_lib, kind):
+    """The l1-ball and penalised steps read no workspace before writing it:
+    after contexts of the same shape whose data hold NaN (so every workspace
+    they touched, in the library's pool and in shared memory, is left full of
+    NaN) are destroyed, a fresh context on clean data repeats the iterates of
+    a context created on a trimmed pool bit for bit.  (The penalised face
+    solve once read its border direction, which only the ball form writes,
+    multiplied by zero: 0 * NaN poisoned the step.)"""
+    w, C = _csr_problem("lasso_csr_fp64", 60000, 120, 1200)
+    param = w["param"] if kind == "l1" else _pen_lambda(C, w["b"], 0.02)
+    rp, col, b = dev(w["rowptr"]), dev(w["col"]), dev(w["b"])
+    val = dev(w["val"])
+
+    def run(values, iters=8, **kw):
+        sv = cuda_lib.IHS((rp, col, values), b, kind=kind, param=param, m=1200, s=4, seed=0,
+                          precision="fp64", shape=(w["n"], w["d"]), **kw)
+        try:
+            x, rep = sv.solve(iters=iters)
+            out = (x.cpu().numpy(), rep.status)
+        except cuda_lib.IHSError as e:
+            out = (None, e.status)
+        sv.close()
+        return out
+
+    cuda_lib.trim_memory()
+    x_fresh, st = run(val)
+    assert st == 0
+    bad = val.clone()
+    bad[::7] = float("nan")
+    for k in ("l1", "l1pen"):
+        sv = cuda_lib.IHS((rp, col, bad), b, kind=k, param=param, m=1200, s=4, seed=0,
+                          precision="fp64", shape=(w["n"], w["d"]), qp_max_iter=300)
+        with pytest.raises(cuda_lib.IHSError):
+            sv.solve(iters=2)
+        sv.close()
+    x_again, st = run(val)
+    assert st == 0
+    assert np.array_equal(x_again, x_fresh)
 
 
 def test_bounded_wait_gives_up_and_the_context_stays_usable(cuda_lib):
