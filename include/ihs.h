@@ -160,9 +160,10 @@ enum {
  * Hessian and apply the factor in FP64, as the plain form does, instead of
  * in FP32.  The factor only preconditions the step (the residual, gradient
  * and update that set the attainable accuracy are FP64-class either way), so
- * both reach the same accuracy in the same iterations; the FP64 factor costs
- * more on this GPU's FP64 units and implies IHS_FLAG_NO_LOOKAHEAD (its kernel
- * needs a whole SM's registers, so it cannot run beside the fused pass). */
+ * both reach the same accuracy in the same iterations.  The FP64 factor costs
+ * more on this GPU's FP64 units: with the look-ahead pipeline the pass of
+ * iteration t then forms SA of iteration t + 2 (not t + 1), so each factor
+ * has two passes' time beside them; the context keeps three factors. */
 
 typedef struct {
   int iters;            /* iterations taken                                */

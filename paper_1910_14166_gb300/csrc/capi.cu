@@ -15,9 +15,15 @@
 #include "internal.h"
 
 // CTAs of the factor that runs beside the look-ahead fused pass (the pass
-// leaves these slots free: at d <= 512 the factor on 16 SMs still ends well
-// within one pass).
+// leaves these slots free): 16 for the FP32 factor, which at d <= 512 ends
+// well within one pass on 16 SMs; 32 for the FP64 factor, whose duration on
+// GB300's FP64 units must also fit in one iteration (factors queue on one
+// stream, so the pipeline's depth buys latency, not throughput).
 constexpr int kLookaheadFactorCtas = 16;
+constexpr int kLookaheadFactorCtasF64 = 32;
+// Factor buffers (H, L, D^{-1}): two in rotation, three when the look-ahead
+// pipeline runs two iterations ahead (FP64 factor).
+constexpr int kFacBufs = 3;
 
 static int64_t g_launches = 0;  // kernel launches issued by the library
 void note_launches(int k) { __atomic_add_fetch(&g_launches, (int64_t)k, __ATOMIC_RELAXED); }
@@ -52,8 +58,8 @@ struct StageEvents {
 struct ihs_ctx {
   cudaStream_t st = nullptr;   // caller's stream: gradient, step, adjoint
   cudaStream_t st2 = nullptr;  // internal stream: sketch draw, SA, Gram, factor
-  cudaEvent_t ev_fac[2] = {};  // factor of buffer b ready
-  cudaEvent_t ev_use[2] = {};  // last step reading buffer b done
+  cudaEvent_t ev_fac[kFacBufs] = {};  // factor of buffer b ready
+  cudaEvent_t ev_use[kFacBufs] = {};  // last step reading buffer b done
   cudaEvent_t ev_join = nullptr;
   cudaEvent_t ev_grad = nullptr;  // gradient pass of the current iteration done
   cudaEvent_t ev_sa = nullptr;    // look-ahead: SA of the next counter formed
@@ -114,9 +120,12 @@ struct ihs_ctx {
   void* gop = nullptr;
   float* gpart_f = nullptr;
   double* gpart_d = nullptr;
-  double* H[2] = {};
-  void* L[2] = {};
-  void* Dinv[2] = {};
+  double* H[kFacBufs] = {};
+  void* L[kFacBufs] = {};
+  void* Dinv[kFacBufs] = {};
+  int nbuf = 2;  // factor buffers in rotation (la + 1 in the look-ahead pipeline)
+  int la = 1;    // look-ahead pipeline: the pass of iteration t forms SA of t + la
+  int fac_ctas = kLookaheadFactorCtas;  // look-ahead pipeline: CTAs of the factor
   unsigned* bar = nullptr;
   int cur = 1;  // buffer of the last sketch
   double* g = nullptr;
@@ -421,7 +430,7 @@ void ihs_destroy(ihs_ctx* c) {
   cudaStreamSynchronize(c->st);
   if (c->st2) cudaStreamSynchronize(c->st2);
   for (cudaEvent_t e : c->pe.ev) cudaEventDestroy(e);
-  for (int k = 0; k < 2; ++k) {
+  for (int k = 0; k < kFacBufs; ++k) {
     if (c->ev_fac[k]) cudaEventDestroy(c->ev_fac[k]);
     if (c->ev_use[k]) cudaEventDestroy(c->ev_use[k]);
   }
@@ -506,7 +515,7 @@ ihs_status ihs_create(ihs_ctx** out, const ihs_matrix* A, const double* b,
   } while (0)
   if (cudaStreamCreateWithFlags(&c->st2, cudaStreamNonBlocking) != cudaSuccess)
     return fail(IHS_ERR_CUDA);
-  for (int k = 0; k < 2; ++k) {
+  for (int k = 0; k < kFacBufs; ++k) {
     if (cudaEventCreateWithFlags(&c->ev_fac[k], cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&c->ev_use[k], cudaEventDisableTiming) != cudaSuccess)
       return fail(IHS_ERR_CUDA);
@@ -524,7 +533,7 @@ ihs_status ihs_create(ihs_ctx** out, const ihs_matrix* A, const double* b,
   }
   AL2(c->SA, (size_t)c->m * c->d * acc_el);
   const int dp = chol_padded((int)c->d);
-  for (int k = 0; k < 2; ++k) {
+  for (int k = 0; k < kFacBufs; ++k) {
     AL2(c->H[k], (size_t)c->d * c->d * sizeof(double));
     AL2(c->L[k], (size_t)dp * dp * (c->f32fac ? 4 : 8));
     AL2(c->Dinv[k], chol_dinv_bytes((int)c->d, c->f32fac));
@@ -552,10 +561,18 @@ ihs_status ihs_create(ihs_ctx** out, const ihs_matrix* A, const double* b,
     c->gauss = opt->sketch == IHS_SKETCH_GAUSSIAN;
     c->fused = !c->acc64 && !c->srht && !c->gauss && fused_supported(c->DA, c->s) &&
                !(opt->flags & IHS_FLAG_NO_FUSE);
-    c->lookahead = c->fused && c->f32fac && !(opt->flags & IHS_FLAG_NO_LOOKAHEAD);
+    c->lookahead = c->fused && !(opt->flags & IHS_FLAG_NO_LOOKAHEAD);
+    // The FP64 factor on the look-ahead pipeline's 16 CTAs takes longer than
+    // one pass (GB300's FP64 rate): form SA two iterations ahead, so each
+    // factor has two passes to finish, with a third factor buffer.
+    if (c->lookahead && !c->f32fac) {
+      c->la = 2;
+      c->nbuf = 3;
+      c->fac_ctas = kLookaheadFactorCtasF64;
+    }
     // one warp per chunk; the fused pass runs two CTAs of eight warps per SM,
     // less the SMs' share left to the factor that runs beside it
-    const int warps = c->lookahead ? (2 * c->sms - kLookaheadFactorCtas) * 8 : c->sms * 16;
+    const int warps = c->lookahead ? (2 * c->sms - c->fac_ctas) * 8 : c->sms * 16;
     c->sp = make_sort_plan((int64_t)c->s * c->n, (int)c->m, warps);
     if ((size_t)c->m * sizeof(int32_t) > 200 * 1024) return fail(IHS_ERR_UNSUPPORTED);
     AL2(c->sort_ws, sort_workspace_bytes(c->sp));
@@ -625,6 +642,9 @@ namespace {
 double gram_scale(const ihs_ctx* c) {
   return (c->srht || c->gauss) ? 1.0 / (double)c->m : 1.0 / c->s;
 }
+
+// The factor buffer after b in the rotation.
+int next_buf(const ihs_ctx* c, int b) { return (b + 1) % c->nbuf; }
 
 // The sketch chain of counter t into buffer `bf`, on the internal stream:
 // draw S and sort (dense), SA, Gram (+ lambda I), Cholesky factor.  Waits
@@ -813,32 +833,41 @@ ihs_status fused_iteration(ihs_ctx* c, double* x, int pb, int bf) {
   return step_with(c, x, bf);
 }
 
-// Look-ahead fused pipeline.  Pass k (caller's stream) reads A once for the
-// gradient at x^k and SA of counter t0+k+1; the Gram and factor of t0+k+1
-// then run on the internal stream beside the step of k and the pass of k+1
-// (the factor on kLookaheadFactorCtas CTAs, the slots the pass leaves free),
-// and the sort of counter t0+k+3 follows them there.  Counter t0's SA comes
-// from a sketch-only pass first; the last pass forms the gradient only (in
-// the row order of the last sort), so SA, H and the factor left behind are
-// those of the last iteration, as in the other loops.  Sort buffer u&1 holds
-// counter t0+u; factor buffers alternate as in the other loops.
+// Look-ahead fused pipeline, depth la (1, or 2 with the FP64 factor).  Pass
+// k (caller's stream) reads A once for the gradient at x^k and SA of counter
+// t0+k+la; the Gram and factor of that counter then run on the internal
+// stream beside the steps and passes of the next la iterations (the factor
+// on kLookaheadFactorCtas CTAs, the slots the pass leaves free).  Counters
+// t0 .. t0+la-1 take sketch-only passes first (their chains on the internal
+// stream); the last la passes form the gradient only, in the row order of the
+// last sort, so SA, H and the factor left behind are the last iteration's,
+// as in the other loops.  Sort buffer u&1 holds counter t0+u for u >= la;
+// the sort of t0+k+la+2 follows the Gram and factor of pass k on the
+// internal stream.  Counter t0+j uses factor buffer fb(j) of the rotation.
 ihs_status fused_lookahead(ihs_ctx* c, double* x, int64_t t0, int iters) {
   const bool serial = (c->opt.flags & IHS_FLAG_SERIAL) != 0;
   cudaStream_t s1 = c->st, s2 = serial ? c->st : c->st2;
-  const int fac_ctas = serial ? 0 : kLookaheadFactorCtas;
+  const int fac_ctas = serial ? 0 : c->fac_ctas;
   const double lam = (c->C.kind == IHS_RIDGE) ? c->C.param : 0.0;
+  const int la = c->la;
+  const int b0 = next_buf(c, c->cur);
+  auto fb = [&](int j) { return (b0 + j) % c->nbuf; };
   ihs_status s;
-  int bf = c->cur ^ 1;  // factor buffer of counter t0
-  if ((s = sketch_chain(c, t0, bf, fac_ctas, c->ev_gram)) != IHS_OK) return s;
-  CK(cudaEventRecord(c->ev_read[0], s2));  // the sketch-only pass read sort buffer 0
-  if (iters > 1 && (s = fused_sort(c, t0 + 1, 1)) != IHS_OK) return s;
-  if (iters > 2 && (s = fused_sort(c, t0 + 2, 0)) != IHS_OK) return s;
+  const int pre = std::min(la, iters);
+  for (int j = 0; j < pre; ++j)
+    if ((s = sketch_chain(c, t0 + j, fb(j), fac_ctas, c->ev_gram)) != IHS_OK) return s;
+  CK(cudaEventRecord(c->ev_read[0], s2));  // the sketch-only passes read sort buffer 0
+  for (int u = la; u < std::min(iters, la + 2); ++u)
+    if ((s = fused_sort(c, t0 + u, u & 1)) != IHS_OK) return s;
+  // the gradient-only passes read the last counter's sort (buffer 0 when
+  // every counter came from a sketch-only pass)
+  const int last_pb = iters > la ? (iters - 1) & 1 : 0;
   for (int k = 0; k < iters; ++k) {
-    const bool ahead = k + 1 < iters;
-    const int pb = ahead ? (k + 1) & 1 : k & 1;
-    const int nb = bf ^ 1;  // factor buffer of counter t0+k+1
-    if (k > 0 || ahead) CK(cudaStreamWaitEvent(s1, c->ev_sort[pb], 0));
-    else CK(cudaStreamWaitEvent(s1, c->ev_read[0], 0));  // one pass: counter t0's sort
+    const bool ahead = k + la < iters;
+    const int pb = ahead ? (k + la) & 1 : last_pb;
+    if (ahead) CK(cudaStreamWaitEvent(s1, c->ev_sort[pb], 0));
+    else if (iters > la) CK(cudaStreamWaitEvent(s1, c->ev_sort[pb], 0));
+    else CK(cudaStreamWaitEvent(s1, c->ev_read[0], 0));  // the sketch-only passes' sorts
     CK(cudaStreamWaitEvent(s1, c->ev_gram, 0));  // SA no longer needed by the last Gram
     // timed as the gradient stage: the sketch stage is the sketch-only pass
     stage_begin(c, IHS_ST_GRAD, s1);
@@ -850,9 +879,10 @@ ihs_status fused_lookahead(ihs_ctx* c, double* x, int64_t t0, int iters) {
     CK(e);
     CK(cudaEventRecord(c->ev_read[pb], s1));
     if (ahead) {
+      const int nb = fb(k + la);  // factor buffer of counter t0+k+la
       CK(cudaEventRecord(c->ev_sa, s1));
       CK(cudaStreamWaitEvent(s2, c->ev_sa, 0));
-      CK(cudaStreamWaitEvent(s2, c->ev_use[nb], 0));  // step k-1 read factor buffer nb
+      CK(cudaStreamWaitEvent(s2, c->ev_use[nb], 0));  // the last step that read buffer nb
       stage_begin(c, IHS_ST_GRAM, s2);
       CK(launch_gram(c->gp, c->SA, c->gop, c->gpart_f, c->gpart_d, gram_scale(c), lam,
                      c->H[nb], c->status, s2));
@@ -863,11 +893,10 @@ ihs_status fused_lookahead(ihs_ctx* c, double* x, int64_t t0, int iters) {
                          c->status, s2, (c->opt.flags & IHS_FLAG_CLUSTER) != 0, 0.0, fac_ctas));
       stage_end(c);
       CK(cudaEventRecord(c->ev_fac[nb], s2));
-      if (k + 3 < iters && (s = fused_sort(c, t0 + k + 3, pb)) != IHS_OK) return s;
+      if (k + la + 2 < iters && (s = fused_sort(c, t0 + k + la + 2, pb)) != IHS_OK) return s;
     }
-    if ((s = step_with(c, x, bf)) != IHS_OK) return s;
-    c->cur = bf;
-    bf = nb;
+    if ((s = step_with(c, x, fb(k))) != IHS_OK) return s;
+    c->cur = fb(k);
   }
   return IHS_OK;
 }
@@ -880,7 +909,7 @@ ihs_status ihs_sketch(ihs_ctx* c, int64_t t) {
   if (!c || t < 0) return IHS_ERR_ARG;
   ihs_status s = join_caller(c);
   if (s != IHS_OK) return s;
-  const int bf = c->cur ^ 1;
+  const int bf = next_buf(c, c->cur);
   if ((s = sketch_chain(c, t, bf)) != IHS_OK) return s;
   c->cur = bf;
   c->have_sketch = true;
@@ -904,7 +933,7 @@ ihs_status ihs_sketch_gradient(ihs_ctx* c, int64_t t, const double* x, double* g
   cudaStream_t st = c->st;
   CK(cudaEventRecord(c->ev_tail2, c->st2));
   CK(cudaStreamWaitEvent(st, c->ev_tail2, 0));
-  const int bf = c->cur ^ 1;
+  const int bf = next_buf(c, c->cur);
   CK(cudaStreamWaitEvent(st, c->ev_use[bf], 0));
   const double lam = (c->C.kind == IHS_RIDGE) ? c->C.param : 0.0;
   const SketchKeys K = make_keys(c->opt.seed, t, c->s, c->m);
@@ -969,18 +998,18 @@ ihs_status ihs_solve(ihs_ctx* c, double* x, int64_t t0, int iters, ihs_report* r
   } else if (iters > 0 && c->fused) {
     if ((s = join_caller(c)) != IHS_OK) return s;
     if ((s = fused_sort(c, t0, 0)) != IHS_OK) return s;
-    int bf = c->cur ^ 1;
+    int bf = next_buf(c, c->cur);
     for (int k = 0; k < iters; ++k) {
       const int pb = k & 1;
       if (k + 1 < iters && (s = fused_sort(c, t0 + k + 1, pb ^ 1)) != IHS_OK) return s;
       if ((s = fused_iteration(c, x, pb, bf)) != IHS_OK) return s;
       c->cur = bf;
-      bf ^= 1;
+      bf = next_buf(c, bf);
     }
     c->have_sketch = true;
   } else if (iters > 0) {
     if ((s = join_caller(c)) != IHS_OK) return s;
-    int bf = c->cur ^ 1;
+    int bf = next_buf(c, c->cur);
     if ((s = sketch_chain(c, t0, bf)) != IHS_OK) return s;
     // The chain of t+1 starts once the gradient pass of t is done, and is
     // issued after the step of t: a gradient pass sharing the GPU with a
@@ -995,10 +1024,10 @@ ihs_status ihs_solve(ihs_ctx* c, double* x, int64_t t0, int iters, ihs_report* r
       if ((s = step_with(c, x, bf)) != IHS_OK) return s;
       if (k + 1 < iters) {
         CK(cudaStreamWaitEvent(c->st2, c->ev_grad, 0));
-        if ((s = sketch_chain(c, t0 + k + 1, bf ^ 1)) != IHS_OK) return s;
+        if ((s = sketch_chain(c, t0 + k + 1, next_buf(c, bf))) != IHS_OK) return s;
       }
       c->cur = bf;
-      bf ^= 1;
+      bf = next_buf(c, bf);
     }
     c->have_sketch = true;
   }

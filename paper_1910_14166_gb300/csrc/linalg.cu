@@ -151,6 +151,83 @@ __device__ void panel_sweep(T (*Dk)[33], T (*Ta)[33], bool tall, int* spd) {
   __syncthreads();
 }
 
+// The same sweep spread over warps 0-3 (128 threads), for FP64, where the
+// per-column updates dominate: GB300 issues about one FP64 warp instruction
+// per 64 cycles on each sub-partition, so a one-warp sweep of a 32-column
+// tile (about a thousand DFMA instructions) takes tens of microseconds.
+// Lane r still owns row r; warp w owns the columns c = w (mod 4), eight of
+// the diagonal block and eight of the panel block, so the four sub-partitions
+// share the updates.  At column j the warp that owns it forms the pivot, the
+// scaled column L_rj and the scaled panel entries, publishes them in shared
+// memory (two buffers, alternating by j) and all four warps meet at a named
+// barrier before applying the rank-1 update to their own columns.  Every
+// entry goes through the same operations in the same order as in
+// panel_sweep, so both give the same factor.  All threads must call.
+template <typename T>
+__device__ void panel_sweep4(T (*Dk)[33], T (*Ta)[33], bool tall, int* spd) {
+  __shared__ T colL[2][32], colB[2][32];
+  __shared__ int bad;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (threadIdx.x == 0) bad = 0;
+  __syncthreads();
+  if (threadIdx.x < 128) {
+    T a[8], bb[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int c = w + 4 * u;
+      a[u] = (c <= lane) ? Dk[lane][c] : T(0);
+      bb[u] = tall ? Ta[lane][c] : T(0);
+    }
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+      const int buf = j & 1;
+      if (w == (j & 3)) {
+        const int uj = j >> 2;
+        T pj = __shfl_sync(0xffffffffu, a[uj], j);
+        if (!(pj > T(0))) {
+          if (lane == 0) bad = 1;
+          pj = T(1);
+        }
+        const T rinv = rsqrt(pj);
+        const T lrj = (lane > j) ? a[uj] * rinv : (lane == j ? pj * rinv : T(0));
+        a[uj] = lrj;
+        const T bj = bb[uj] * rinv;
+        bb[uj] = bj;
+        colL[buf][lane] = lrj;
+        colB[buf][lane] = bj;
+      }
+      asm volatile("bar.sync 1, 128;" ::: "memory");
+      const T lrj = colL[buf][lane], bj = colB[buf][lane];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int c = w + 4 * u;
+        if (c > j) {
+          const T lcj = colL[buf][c];
+          if (lane >= c) a[u] -= lrj * lcj;
+          bb[u] -= bj * lcj;
+        }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int c = w + 4 * u;
+      Dk[lane][c] = a[u];
+      if (tall) Ta[lane][c] = bb[u];
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) *spd = bad ? 0 : 1;
+  __syncthreads();
+}
+
+// The factor's panel sweep: four warps in FP64, one warp (no barriers) in
+// FP32, whose FMA rate makes the one-warp sweep short.
+template <typename T>
+__device__ void panel_factor(T (*Dk)[33], T (*Ta)[33], bool tall, int* spd) {
+  if constexpr (sizeof(T) == 8) panel_sweep4<T>(Dk, Ta, tall, spd);
+  else panel_sweep<T>(Dk, Ta, tall, spd);
+}
+
 // C (32 x 32 in smem) -= P Q^T, P, Q 32 x 32 in smem; 256 threads.
 template <typename T>
 __device__ void tile_sub_pqt(T (*C)[33], T (*P)[33], T (*Q)[33]) {
@@ -217,7 +294,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_chol_coop(T* __
           for (int e = tid; e < 1024; e += blockDim.x) Ta[e >> 5][e & 31] = ((e >> 5) == (e & 31)) ? T(1) : T(0);
           __syncthreads();
         }
-        panel_sweep<T>(Dk, Ta, true, &spd);
+        panel_factor<T>(Dk, Ta, true, &spd);
         if (c == 0) {
           // L_kk itself is not stored: the other panel items of this step
           // read the diagonal tile of L concurrently (it must keep the
@@ -359,7 +436,7 @@ __global__ void __launch_bounds__(256) k_chol_cluster(const double* __restrict__
         __syncthreads();
         pan = Ta;
       }
-      panel_sweep<T>(Dk, pan, true, &spd);
+      panel_factor<T>(Dk, pan, true, &spd);
       if (c == 0) {
         if (!spd && tid == 0) set_status(status, DEV_NOT_SPD);
         for (int e = tid; e < 1024; e += blockDim.x) {

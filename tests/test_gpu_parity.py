@@ -397,24 +397,31 @@ def test_fused_pass_agrees_with_two_passes(cuda_lib):
     assert O.err_A(x1.cpu().numpy(), xo, G) < 1e-10 and O.err_A(x2.cpu().numpy(), xo, G) < 1e-10
 
 
-@pytest.mark.parametrize("kind,iters,serial", [
-    ("ols", 1, False), ("ols", 2, False), ("ols", 3, False), ("ols", 7, False), ("ols", 4, True),
-    ("ridge", 5, False), ("l1", 5, False), ("l2", 4, False)])
-def test_lookahead_matches_in_order_fused(cuda_lib, kind, iters, serial):
+@pytest.mark.parametrize("kind,iters,serial,fp64fac", [
+    ("ols", 1, False, False), ("ols", 2, False, False), ("ols", 3, False, False),
+    ("ols", 7, False, False), ("ols", 4, True, False), ("ridge", 5, False, False),
+    ("l1", 5, False, False), ("l2", 4, False, False),
+    ("ols", 1, False, True), ("ols", 2, False, True), ("ols", 3, False, True),
+    ("ols", 4, False, True), ("ols", 7, False, True), ("ols", 5, True, True),
+    ("ridge", 4, False, True), ("l1", 6, False, True)])
+def test_lookahead_matches_in_order_fused(cuda_lib, kind, iters, serial, fp64fac):
     """The look-ahead fused pipeline (SA of iteration t+1 formed in the pass of
-    iteration t, its factor beside the next pass) takes the same sketches as
-    the in-order fused pipeline: the iterates agree to rounding, for 1 to 7
-    iterations (every branch of the sort schedule), serial or overlapped,
-    and a second solve continues to 1e-10.  At this size (fewer than 32 rows
-    per warp slot) both pipelines split the rows into the same chunks, so the
+    iteration t, its factor beside the next pass; t+2 with the FP64 factor,
+    three factors in rotation) takes the same sketches as the in-order fused
+    pipeline: the iterates agree to rounding, for 1 to 7 iterations (every
+    branch of the sort schedule at both depths), serial or overlapped, and a
+    second solve continues to 1e-10.  At this size (fewer than 32 rows per
+    warp slot) both pipelines split the rows into the same chunks, so the
     sketch and Hessian left behind (the last iteration's) are identical bit
     for bit and the iterates differ only by the gradient's summation order."""
-    w = synth.make("ols_dense_ar1", n=70001, d=120, m=1200)
+    # 60001 rows: fewer row pairs than warp slots in every pipeline's plan
+    # (the FP64-factor pipeline leaves 32 CTA slots to the factor)
+    w = synth.make("ols_dense_ar1", n=60001, d=120, m=1200)
     A64 = w["A"].astype(np.float64)
     A, b = dev(w["A"]), dev(w["b"])
     xo = O.x_opt_ols_normal(A64, w["b"])
     G = A64.T @ A64
-    kw = dict(m=1200, precision="tf32", seed=11, serial=serial)
+    kw = dict(m=1200, precision="tf32", seed=11, serial=serial, fp64_factor=fp64fac)
     if kind == "ridge":
         kw.update(kind="ridge", param=3.0)
     elif kind == "l1":
