@@ -9,10 +9,11 @@
 //     for the increment dS = x_S - x^t_S and multiplier mu.  The point is
 //     accepted only if mu >= 0, every x_S keeps its sign and
 //     |(H (x - x^t) - g)_j| <= mu off S -- then it is the unique optimum.
-//  3. Otherwise FISTA (Beck & Teboulle 2009) in FP32 with the exact
-//     Euclidean projection onto the l1 ball (Michelot's fixed-point
-//     threshold, exact after finitely many passes) finds the support, and a
-//     face solve is tried every kFaceEvery iterations.
+//  3. Otherwise FISTA (Beck & Teboulle 2009) in FP32, preconditioned by
+//     diag(H)^{-1}, with the exact projection onto the l1 ball in that
+//     metric (a weighted form of Michelot's fixed-point threshold, exact
+//     after finitely many passes), finds the support, and a face solve is
+//     tried every kFaceEvery iterations.
 // The face system is factored in the factor precision of the mode (FP32 in
 // the mixed form) and refined with FP64 residuals, so dS and mu are FP64
 // accurate.  Failure to certify within the iteration cap records
@@ -22,8 +23,8 @@
 // instead of the ball) takes the same path: the full face first (every index
 // in the support, signs from x^t, else from H^{-1} g: one more solve with the
 // sketched factor, the answer when no sign changes), the previous face (x = 0
-// included), then proximal FISTA (soft threshold at lambda / L) with periodic
-// faces, whose system has no border,
+// included), then proximal FISTA (soft threshold at lambda D_j / L, the same
+// preconditioner) with periodic faces, whose system has no border,
 //     H_SS dS = g_S + H_{S,S^c} x^t_{S^c} - lambda sigma,
 // and whose off-support test is |(H (x - x^t) - g)_j| <= lambda.
 #include <cuda_runtime.h>
@@ -76,6 +77,7 @@ struct QpShared {
   double ra[kQpMaxD + 1];
   float fx[kQpMaxD], fy[kQpMaxD], fv[kQpMaxD];
   float fxt[kQpMaxD];
+  float dg[kQpMaxD];     // FISTA's diagonal preconditioner, 1 / H_jj
   int S[kQpMaxD];
   int k;           // support size
   int accept;
@@ -95,33 +97,46 @@ __device__ void matvec_f(const float* __restrict__ Hf, int d, const float* v, fl
   }
 }
 
-// Euclidean projection of v onto {||x||_1 <= R} in place (Michelot's
-// threshold iteration: theta <- (sum_{|v|>theta} |v| - R) / #{|v| > theta}).
-__device__ void project_l1(float* v, int d, float R, QpShared& sh) {
-  float a = 0.f;
-  for (int j = threadIdx.x; j < d; j += blockDim.x) a += fabsf(v[j]);
+// Projection onto the l1 ball in the metric of diag(D)^{-1}:
+//   argmin_{||y||_1 <= R} sum_j (y_j - v_j)^2 / (2 D_j),
+// y_j = sign(v_j) max(|v_j| - theta D_j, 0) with the theta >= 0 that puts y on
+// the sphere.  theta by the weighted form of Michelot's iteration: on the
+// active set A = {j : |v_j| > theta D_j}, theta = (sum_A |v_j| - R) /
+// sum_A D_j; from the whole set it increases monotonically to the root
+// (each step's theta is at most the root, and the active set shrinks).
+__device__ void project_l1_w(float* v, const float* D, int d, float R, QpShared& sh) {
+  float a = 0.f, w = 0.f;
+  for (int j = threadIdx.x; j < d; j += blockDim.x) {
+    a += fabsf(v[j]);
+    w += D[j];
+  }
   const float tot = block_sum(a, sh.redf);
   if (tot <= R) return;
-  float theta = (tot - R) / (float)d;
+  const float W0 = block_sum(w, sh.redf);
+  float theta = fmaxf((tot - R) / W0, 0.f);
   int prev = d;
   for (int it = 0; it < d + 1; ++it) {
-    float s = 0.f, c = 0.f;
+    float s = 0.f, ws = 0.f, c = 0.f;
     for (int j = threadIdx.x; j < d; j += blockDim.x) {
       const float u = fabsf(v[j]);
-      if (u > theta) { s += u; c += 1.f; }
+      if (u > theta * D[j]) {
+        s += u;
+        ws += D[j];
+        c += 1.f;
+      }
     }
     const float S = block_sum(s, sh.redf);
-    const float C = block_sum(c, sh.redf);
-    const int cnt = (int)C;
-    if (cnt == 0) break;
-    const float nt = (S - R) / C;
+    const float WS = block_sum(ws, sh.redf);
+    const int cnt = (int)block_sum(c, sh.redf);
+    if (cnt == 0 || !(WS > 0.f)) break;
+    const float nt = (S - R) / WS;
     const bool stop = (cnt == prev) || !(nt > theta);
     theta = fmaxf(theta, nt);
     prev = cnt;
     if (stop) break;
   }
   for (int j = threadIdx.x; j < d; j += blockDim.x) {
-    const float u = fabsf(v[j]) - theta;
+    const float u = fabsf(v[j]) - theta * D[j];
     v[j] = u > 0.f ? copysignf(u, v[j]) : 0.f;
   }
   __syncthreads();
@@ -566,7 +581,21 @@ __global__ void __launch_bounds__(kQpThreads, 1) k_l1_step(
   }
   // 3. FISTA + periodic face solves
   if (!done) {
-    // Lipschitz constant by power iteration on Hf.  It starts from the top
+    // FISTA with a diagonal (Jacobi) preconditioner D = diag(H)^{-1}: in the
+    // variables y = D^{-1/2} x the Hessian D^{1/2} H D^{1/2} has a unit
+    // diagonal, which removes the spread of the column scales (a Zipf
+    // column distribution puts H's diagonal over three decades, and plain
+    // FISTA then needs hundreds of iterations).  In x: the step is
+    // x - D (H (x - x^t) - g) / L with L the top eigenvalue of
+    // D^{1/2} H D^{1/2}, and the projection is onto the ball in the metric of
+    // D^{-1} (the penalty's soft threshold scales by D_j likewise).  FISTA
+    // only has to find the face: every accepted point is the face solution
+    // certified by the KKT conditions.
+    for (int j = threadIdx.x; j < d; j += blockDim.x) {
+      const float hjj = Hf[(int64_t)j * d + j];
+      sh.dg[j] = hjj > 0.f ? 1.f / hjj : 1.f;
+    }
+    // L by power iteration on D^{1/2} H D^{1/2}.  It starts from the top
     // eigenvector estimate left by the previous step when there is one: the
     // Hessians of successive steps are sketches of the same A^T A and share
     // their dominant direction up to the sketch's distortion.
@@ -583,10 +612,15 @@ __global__ void __launch_bounds__(kQpThreads, 1) k_l1_step(
     float lam = 1.f;
     const int npow = warm ? 12 : 40;
     for (int it = 0; it < npow; ++it) {
-      matvec_f(Hf, d, sh.fv, sh.fy);
+      for (int j = threadIdx.x; j < d; j += blockDim.x) sh.fx[j] = sqrtf(sh.dg[j]) * sh.fv[j];
+      __syncthreads();
+      matvec_f(Hf, d, sh.fx, sh.fy);
       __syncthreads();
       float a = 0.f;
-      for (int j = threadIdx.x; j < d; j += blockDim.x) a += sh.fy[j] * sh.fy[j];
+      for (int j = threadIdx.x; j < d; j += blockDim.x) {
+        sh.fy[j] *= sqrtf(sh.dg[j]);
+        a += sh.fy[j] * sh.fy[j];
+      }
       const float nrm = sqrtf(block_sum(a, sh.redf));
       float b = 0.f;
       for (int j = threadIdx.x; j < d; j += blockDim.x) b += sh.fy[j] * sh.fv[j];
@@ -599,7 +633,7 @@ __global__ void __launch_bounds__(kQpThreads, 1) k_l1_step(
     const float Rf = (float)R;
     for (int j = threadIdx.x; j < d; j += blockDim.x) sh.fx[j] = sh.fxt[j];
     __syncthreads();
-    if (!pen) project_l1(sh.fx, d, Rf, sh);
+    if (!pen) project_l1_w(sh.fx, sh.dg, d, Rf, sh);
     for (int j = threadIdx.x; j < d; j += blockDim.x) sh.fy[j] = sh.fx[j];
     __syncthreads();
     float tk = 1.f;
@@ -615,18 +649,19 @@ __global__ void __launch_bounds__(kQpThreads, 1) k_l1_step(
       matvec_f(Hf, d, gv, hv);
       __syncthreads();
       for (int j = threadIdx.x; j < d; j += blockDim.x)
-        sh.fv[j] = sh.fy[j] - (hv[j] - (float)sh.gd[j]) / Lip;
+        sh.fv[j] = sh.fy[j] - sh.dg[j] * (hv[j] - (float)sh.gd[j]) / Lip;
       __syncthreads();
       if (pen) {
-        // proximal step of lambda ||.||_1: soft threshold at lambda / L
+        // proximal step of lambda ||.||_1 in the metric of D^{-1}: soft
+        // threshold at lambda D_j / L
         const float tau = Rf / Lip;
         for (int j = threadIdx.x; j < d; j += blockDim.x) {
-          const float u = fabsf(sh.fv[j]) - tau;
+          const float u = fabsf(sh.fv[j]) - tau * sh.dg[j];
           sh.fv[j] = u > 0.f ? copysignf(u, sh.fv[j]) : 0.f;
         }
         __syncthreads();
       } else {
-        project_l1(sh.fv, d, Rf, sh);
+        project_l1_w(sh.fv, sh.dg, d, Rf, sh);
       }
       const float tn = 0.5f * (1.f + sqrtf(1.f + 4.f * tk * tk));
       const float mom = (tk - 1.f) / tn;
