@@ -373,6 +373,20 @@ def run_ours(args, rank, world):
         gbs = alg[k] / (avg * 1e-3) / 1e9 if avg > 0 else 0.0
         kernels[names[k]] = {"ms_avg": round(avg, 4), "algorithmic_bytes": alg[k],
                              "GB_s": round(gbs, 1), "frac": round(gbs / hbm, 3)}
+    # The fused pass is also bound by its FP32 arithmetic: 23 FP32 operations
+    # an element (the sketch's FMA, and TwoProd + TwoSum + the low-part FMA for
+    # the float-pair residual and again for the gradient), against the FP32
+    # peak of 128 operations per clock per SM at the maximum SM clock.
+    if "k_sketch_grad_fused" in kernels:
+        kf = kernels["k_sketch_grad_fused"]
+        sms = torch.cuda.get_device_properties(0).multi_processor_count
+        mhz = (clk.get("sm_max_mhz") or 2070.0) if isinstance(clk, dict) else 2070.0
+        fp32_peak = 128.0 * sms * mhz * 1e6
+        ops = 23.0 * n * d
+        kf["fp32_ops"] = ops
+        kf["fp32_Tops"] = round(ops / (kf["ms_avg"] * 1e-3) / 1e12, 2)
+        kf["fp32_peak_Tops"] = round(fp32_peak / 1e12, 2)
+        kf["fp32_frac"] = round(ops / (kf["ms_avg"] * 1e-3) / fp32_peak, 3)
     dominant = max(alg, key=lambda k: ms_stage[k])
     kd = kernels[names[dominant]]
     roofline = {"kernel": names[dominant], "bound": "hbm", "achieved": kd["GB_s"], "peak": hbm,

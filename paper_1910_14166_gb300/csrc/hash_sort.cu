@@ -186,7 +186,11 @@ SortPlan make_sort_plan(int64_t P, int m, int nchunks_target) {
   SortPlan p;
   p.P = P;
   p.m = m;
+  // tiles of 4096 items; a small problem (under 152 such tiles) takes tiles
+  // of P / 152 rounded up to 256, at least 1024, so that its count and
+  // scatter kernels spread over the SMs instead of running a few long warps
   int64_t tile = 4096;
+  if (P < 4096 * 152) tile = std::max<int64_t>(1024, (P / 152 + 255) / 256 * 256);
   // keep the tile-count matrix under 16M entries
   while ((P + tile - 1) / tile * (int64_t)m > (16ll << 20)) tile *= 2;
   p.tile = (int)tile;

@@ -343,17 +343,22 @@ __global__ void __launch_bounds__(256) k_sketch_csc(
         xq[q] = __ldg(val + e);
       }
     }
+    // the draws of all kU batches first: independent hash chains the
+    // scheduler interleaves, before the scatters, which synchronise the warp
+    int keyq[kU];
+    Tacc vq[kU];
+#pragma unroll
+    for (int q = 0; q < kU; ++q) {
+      int row, neg;
+      sketch_draw(K, k, (uint64_t)rq[q], row, neg);
+      keyq[q] = row - k * mb;
+      vq[q] = neg ? -(Tacc)xq[q] : (Tacc)xq[q];
+    }
 #pragma unroll
     for (int q = 0; q < kU; ++q) {
       const bool valid = base + q * 32 + lane < e1;
-      int key = -1 - lane;
-      Tacc v = Tacc(0);
-      if (valid) {
-        int row, neg;
-        sketch_draw(K, k, (uint64_t)rq[q], row, neg);
-        key = row - k * mb;
-        v = neg ? -(Tacc)xq[q] : (Tacc)xq[q];
-      }
+      const int key = valid ? keyq[q] : -1 - lane;
+      const Tacc v = valid ? vq[q] : Tacc(0);
       if constexpr (MINTAG) {
         // Rounds: every pending lane claims its bucket with a shared-memory
         // atomicMin of its index, so the lowest pending lane of each bucket
