@@ -852,18 +852,22 @@ def run_workloads(args):
         if param_o == "half":  # p = 2 ball of radius ||x*|| / 2 (the constraint active)
             param = 0.5 * float(np.linalg.norm(w["x_star"]))
         iters = w["iters"] or 25
-        times = []
-        for serial in (False, True):
+        times, times_ng, used_graph = [], [], False
+        for serial, graph in ((False, True), (False, False), (True, False)):
+            if not serial and not graph and not used_graph:
+                continue  # the context replays no graph anyway
             sv = ihs.IHS(A, b, kind=kind, param=param, m=w["m"], s=w["s"], seed=0,
-                         precision=w["precision"], shape=shape, serial=serial, sketch=sketch)
+                         precision=w["precision"], shape=shape, serial=serial, sketch=sketch,
+                         graph=graph)
             x0 = torch.zeros(w["d"], dtype=torch.float64, device="cuda")
-            sv.solve(x0.clone(), iters=iters)  # warm-up
+            sv.solve(x0.clone(), iters=iters)  # warm-up (and graph capture)
             if serial:
                 sv.profile(True)
                 sv.solve(x0.clone(), iters=iters)
                 ms, cnt, launches = sv.profile_read()
                 stages = {k: round(v / iters, 4) for k, v in ms.items()}
             else:
+                out = times if graph else times_ng
                 for _ in range(max(1, args.steps)):
                     x = x0.clone()
                     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -872,14 +876,16 @@ def run_workloads(args):
                     _, rep = sv.solve(x, iters=iters)
                     e1.record()
                     torch.cuda.synchronize()
-                    times.append(e0.elapsed_time(e1))
-                    status = rep.status
-                    fista = rep.qp_fista_iters
+                    out.append(e0.elapsed_time(e1))
+                    if graph:
+                        status, fista, used_graph = rep.status, rep.qp_fista_iters, bool(rep.graph)
             del sv
         print(json.dumps({
             "experiment": "workloads", "workload": name, "kind": kind, "param": param, "sketch": sketch,
             "n": w["n"], "d": w["d"], "m": w["m"], "s": w["s"], "precision": w["precision"],
             "iters": iters, "solve_ms_median": statistics.median(times), "solve_ms_all": times,
+            "graph": used_graph,
+            "solve_ms_median_no_graph": statistics.median(times_ng) if times_ng else None,
             "status": status, "qp_fista_iters": fista, "stage_ms_per_iter_serial": stages,
             "launches_per_solve": launches}), flush=True)
         del A, b

@@ -138,7 +138,8 @@ enum {
   IHS_FLAG_SERIAL = 2,
   IHS_FLAG_CLUSTER = 4,
   IHS_FLAG_NO_LOOKAHEAD = 8,
-  IHS_FLAG_FP64_FACTOR = 16
+  IHS_FLAG_FP64_FACTOR = 16,
+  IHS_FLAG_NO_GRAPH = 32
 };
 /* IHS_FLAG_SERIAL: issue the sketch chain (draw, sort, SA, Gram, factor) on
  * the caller's stream too, instead of overlapping it with the gradient and
@@ -163,7 +164,15 @@ enum {
  * both reach the same accuracy in the same iterations.  The FP64 factor costs
  * more on this GPU's FP64 units: with the look-ahead pipeline the pass of
  * iteration t then forms SA of iteration t + 2 (not t + 1), so each factor
- * has two passes' time beside them; the context keeps three factors. */
+ * has two passes' time beside them; the context keeps three factors.
+ * IHS_FLAG_NO_GRAPH: a context whose A takes at most 128 MB (where a solve
+ * is bound by launches, not by the data) replays each ihs_solve as a CUDA
+ * graph: captured on the first call with a given (t0, iters), on an internal
+ * copy of the iterate, and launched as one unit afterwards (the p = 2 ball,
+ * whose step reads scalars on the host, and IHS_FLAG_SERIAL never are).
+ * Same kernels in the same order, so the same results.  This flag turns it
+ * off.  ihs_report.graph tells whether a solve ran as a graph; if a capture
+ * fails, the context falls back to issuing on its streams for good. */
 
 typedef struct {
   int iters;            /* iterations taken                                */
@@ -171,6 +180,7 @@ typedef struct {
   int status;           /* ihs_status of the device status word             */
   double step_norm;     /* ||x^{t+1} - x^t||_inf of the last step            */
   int qp_active_rounds; /* penalised l1: active-set rounds spent, summed     */
+  int graph;            /* ihs_solve: 1 if it ran as a replayed CUDA graph   */
 } ihs_report;
 
 /* ihs_create -- validate (A, b, C, options) and allocate every workspace.

@@ -30,13 +30,15 @@ PREC = {"fp64": 0, "tf32": 1, "bf16": 2}
 KIND = {"ols": OLS, "l1": L1_BALL, "ridge": RIDGE, "l1pen": L1_PENALTY, "l2": L2_BALL}
 SKETCH = {"sparse": 0, "srht": 1, "gaussian": 2}
 FLAG_NO_FUSE, FLAG_SERIAL, FLAG_CLUSTER, FLAG_NO_LOOKAHEAD, FLAG_FP64_FACTOR = 1, 2, 4, 8, 16
+FLAG_NO_GRAPH = 32
 
 
-def option_flags(fuse=True, serial=False, cluster=False, lookahead=True, fp64_factor=False):
+def option_flags(fuse=True, serial=False, cluster=False, lookahead=True, fp64_factor=False,
+                 graph=True):
     """The IHS_FLAG_* word of ihs_options for IHS()'s keyword options."""
     return ((0 if fuse else FLAG_NO_FUSE) | (FLAG_SERIAL if serial else 0)
             | (FLAG_CLUSTER if cluster else 0) | (0 if lookahead else FLAG_NO_LOOKAHEAD)
-            | (FLAG_FP64_FACTOR if fp64_factor else 0))
+            | (FLAG_FP64_FACTOR if fp64_factor else 0) | (0 if graph else FLAG_NO_GRAPH))
 
 
 class IHSError(RuntimeError):
@@ -66,7 +68,7 @@ class _Options(ctypes.Structure):
 class _Report(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("qp_fista_iters", ctypes.c_int),
                 ("status", ctypes.c_int), ("step_norm", ctypes.c_double),
-                ("qp_active_rounds", ctypes.c_int)]
+                ("qp_active_rounds", ctypes.c_int), ("graph", ctypes.c_int)]
 
 
 def _load():
@@ -211,13 +213,13 @@ class IHS:
     precision: 'fp64' (plain), 'tf32' or 'bf16' (mixed).  fuse=False,
     serial=True, cluster=True, lookahead=False and fp64_factor=True set
     IHS_FLAG_NO_FUSE, IHS_FLAG_SERIAL, IHS_FLAG_CLUSTER, IHS_FLAG_NO_LOOKAHEAD
-    and IHS_FLAG_FP64_FACTOR; sketch:
+    and IHS_FLAG_FP64_FACTOR, and graph=False sets IHS_FLAG_NO_GRAPH; sketch:
     'sparse' (CountSketch / SJLT), 'srht' or 'gaussian' (the paper's dense
     comparisons)."""
 
     def __init__(self, A, b, kind="ols", param=0.0, m=None, s=1, seed=0, precision="fp64",
                  shape=None, qp_max_iter=0, qp_tol=0.0, fuse=True, serial=False, cluster=False,
-                 sketch="sparse", lookahead=True, fp64_factor=False):
+                 sketch="sparse", lookahead=True, fp64_factor=False, graph=True):
         self._keep = [A, b]
         _need_cuda(b, "b")
         if b.dtype != torch.float64:
@@ -252,7 +254,8 @@ class IHS:
         self.precision = precision
         C = _Constraint(KIND[kind], float(param))
         O = _Options(self.m, self.s, seed & 0xFFFFFFFFFFFFFFFF, PREC[precision], int(qp_max_iter),
-                     float(qp_tol), option_flags(fuse, serial, cluster, lookahead, fp64_factor),
+                     float(qp_tol), option_flags(fuse, serial, cluster, lookahead, fp64_factor,
+                                                 graph),
                      SKETCH[sketch])
         h = ctypes.c_void_p()
         _check(_lib.ihs_create(ctypes.byref(h), ctypes.byref(M), _ptr(b), ctypes.byref(C),

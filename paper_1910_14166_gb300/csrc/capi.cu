@@ -126,6 +126,17 @@ struct ihs_ctx {
   int nbuf = 2;  // factor buffers in rotation (la + 1 in the look-ahead pipeline)
   int la = 1;    // look-ahead pipeline: the pass of iteration t forms SA of t + la
   int fac_ctas = kLookaheadFactorCtas;  // look-ahead pipeline: CTAs of the factor
+  // CUDA graph of ihs_solve for launch-bound problems: the whole solve for
+  // (t0, iters), captured once and replayed, on an internal copy xg of the
+  // iterate so that the graph does not depend on the caller's pointer
+  bool graphs = false;
+  cudaStream_t gst = nullptr;  // internal stream the graph is captured and launched on
+  double* xg = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  int64_t g_t0 = -1;
+  int g_iters = -1;
+  int g_cur_end = 0;
+  bool last_graph = false;  // the last ihs_solve ran as a CUDA graph
   unsigned* bar = nullptr;
   int cur = 1;  // buffer of the last sketch
   double* g = nullptr;
@@ -443,6 +454,11 @@ void ihs_destroy(ihs_ctx* c) {
     if (c->ev_sort[k]) cudaEventDestroy(c->ev_sort[k]);
     if (c->ev_read[k]) cudaEventDestroy(c->ev_read[k]);
   }
+  if (c->gexec) cudaGraphExecDestroy(c->gexec);
+  if (c->gst) {
+    cudaStreamSynchronize(c->gst);
+    cudaStreamDestroy(c->gst);
+  }
   if (c->st2) cudaStreamDestroy(c->st2);
   for (void* p : c->allocs) cudaFreeAsync(p, c->st);
   cudaStreamSynchronize(c->st);
@@ -462,7 +478,7 @@ ihs_status ihs_create(ihs_ctx** out, const ihs_matrix* A, const double* b,
   if (opt->m < A->d) return IHS_ERR_ARG;
   if (opt->precision < IHS_PREC_FP64 || opt->precision > IHS_PREC_BF16) return IHS_ERR_ARG;
   const int known = IHS_FLAG_NO_FUSE | IHS_FLAG_SERIAL | IHS_FLAG_CLUSTER | IHS_FLAG_NO_LOOKAHEAD |
-                    IHS_FLAG_FP64_FACTOR;
+                    IHS_FLAG_FP64_FACTOR | IHS_FLAG_NO_GRAPH;
   if (opt->flags & ~known) return IHS_ERR_ARG;
   if (C->kind != IHS_OLS && C->kind != IHS_L1_BALL && C->kind != IHS_RIDGE &&
       C->kind != IHS_L1_PENALTY && C->kind != IHS_L2_BALL)
@@ -625,6 +641,22 @@ ihs_status ihs_create(ihs_ctx** out, const ihs_matrix* A, const double* b,
     if (cudaMemsetAsync(c->qw.support, 0, (dd + 4) * sizeof(int), c->st) != cudaSuccess ||
         cudaMemsetAsync(c->qw.evec, 0, dd * sizeof(float), c->st) != cudaSuccess)
       return fail(IHS_ERR_CUDA);
+  }
+  {
+    // launch-bound problems (A up to 128 MB) replay their solves as CUDA
+    // graphs; the p = 2 ball reads scalars on the host inside its step, and
+    // the serial mode exists for stage timing, so neither is captured
+    const size_t el = (A->dtype == IHS_F32) ? 4 : 8;
+    const size_t a_bytes =
+        c->dense ? (size_t)A->n * A->ld * el
+                 : (size_t)A->nnz * (el + 4) + (size_t)(A->n + 1) * (A->rowptr_i64 ? 8 : 4);
+    c->graphs = a_bytes <= (128u << 20) && C->kind != IHS_L2_BALL &&
+                !(opt->flags & (IHS_FLAG_SERIAL | IHS_FLAG_NO_GRAPH));
+    if (c->graphs) {
+      AL2(c->xg, c->d * sizeof(double));
+      if (cudaStreamCreateWithFlags(&c->gst, cudaStreamNonBlocking) != cudaSuccess)
+        return fail(IHS_ERR_CUDA);
+    }
   }
 #undef AL2
   if (cudaStreamSynchronize(c->st) != cudaSuccess) return fail(IHS_ERR_CUDA);
@@ -901,6 +933,139 @@ ihs_status fused_lookahead(ihs_ctx* c, double* x, int64_t t0, int iters) {
   return IHS_OK;
 }
 
+// The solve's work (iterations t0 .. t0+iters-1), issued on the context's
+// streams; ihs_solve synchronises afterwards.
+ihs_status issue_solve(ihs_ctx* c, double* x, int64_t t0, int iters) {
+  if (c->qw.iters) {
+    CK(cudaMemsetAsync(c->qw.iters, 0, sizeof(int), c->st));
+    CK(cudaMemsetAsync(c->qw.need + 1, 0, sizeof(int), c->st));
+  }
+  ihs_status s = IHS_OK;
+  if (iters > 0 && c->lookahead) {
+    if ((s = join_caller(c)) != IHS_OK) return s;
+    if ((s = fused_lookahead(c, x, t0, iters)) != IHS_OK) return s;
+    c->have_sketch = true;
+  } else if (iters > 0 && c->fused) {
+    if ((s = join_caller(c)) != IHS_OK) return s;
+    if ((s = fused_sort(c, t0, 0)) != IHS_OK) return s;
+    int bf = next_buf(c, c->cur);
+    for (int k = 0; k < iters; ++k) {
+      const int pb = k & 1;
+      if (k + 1 < iters && (s = fused_sort(c, t0 + k + 1, pb ^ 1)) != IHS_OK) return s;
+      if ((s = fused_iteration(c, x, pb, bf)) != IHS_OK) return s;
+      c->cur = bf;
+      bf = next_buf(c, bf);
+    }
+    c->have_sketch = true;
+  } else if (iters > 0) {
+    if ((s = join_caller(c)) != IHS_OK) return s;
+    int bf = next_buf(c, c->cur);
+    if ((s = sketch_chain(c, t0, bf)) != IHS_OK) return s;
+    // The chain of t+1 starts once the gradient pass of t is done, and is
+    // issued after the step of t: a gradient pass sharing the GPU with a
+    // full-width sketch kernel runs several times slower, and the one-CTA
+    // l1 step needs a whole SM, which it gets only if launched first.
+    for (int k = 0; k < iters; ++k) {
+      stage_begin(c, IHS_ST_GRAD, c->st);
+      s = gradient_on(c, x, c->g, nullptr, true);
+      stage_end(c);
+      if (s != IHS_OK) return s;
+      CK(cudaEventRecord(c->ev_grad, c->st));
+      if ((s = step_with(c, x, bf)) != IHS_OK) return s;
+      if (k + 1 < iters) {
+        CK(cudaStreamWaitEvent(c->st2, c->ev_grad, 0));
+        if ((s = sketch_chain(c, t0 + k + 1, next_buf(c, bf))) != IHS_OK) return s;
+      }
+      c->cur = bf;
+      bf = next_buf(c, bf);
+    }
+    c->have_sketch = true;
+  }
+  return s;
+}
+
+// Record every event a wait of the solve can name on stream st.  Inside a
+// capture this makes each later wait refer to a record within the graph;
+// outside, it replaces records made inside a capture (which a wait outside
+// the graph may not name) by records ordered after the graph.
+cudaError_t record_solve_events(ihs_ctx* c, cudaStream_t st) {
+  cudaEvent_t evs[] = {c->ev_join, c->ev_grad, c->ev_sa, c->ev_gram, c->ev_tail2,
+                       c->ev_sort[0], c->ev_sort[1], c->ev_read[0], c->ev_read[1]};
+  cudaError_t e = cudaSuccess;
+  for (cudaEvent_t ev : evs)
+    if (e == cudaSuccess) e = cudaEventRecord(ev, st);
+  for (int k = 0; k < kFacBufs && e == cudaSuccess; ++k) {
+    e = cudaEventRecord(c->ev_fac[k], st);
+    if (e == cudaSuccess) e = cudaEventRecord(c->ev_use[k], st);
+  }
+  return e;
+}
+
+// The solve as a CUDA graph: captured on the first call with a given (t0,
+// iters) and replayed afterwards, on the internal copy xg of the iterate and
+// on an internal stream (the caller's may be the legacy default stream,
+// which cannot be captured), ordered after the caller's stream and the
+// internal stream and joined back into the caller's.  Every event a wait in
+// the solve can name is recorded again at the start of the capture, so each
+// wait refers to a record inside the graph.  If the capture or the
+// instantiation fails, graphs are turned off for the context and the solve
+// is issued on the streams.
+ihs_status solve_graph(ihs_ctx* c, double* x, int64_t t0, int iters) {
+  const size_t xb = (size_t)c->d * sizeof(double);
+  cudaStream_t caller = c->st, gs = c->gst;
+  CK(cudaEventRecord(c->ev_join, caller));
+  CK(cudaStreamWaitEvent(gs, c->ev_join, 0));
+  CK(cudaEventRecord(c->ev_tail2, c->st2));
+  CK(cudaStreamWaitEvent(gs, c->ev_tail2, 0));
+  CK(cudaMemcpyAsync(c->xg, x, xb, cudaMemcpyDeviceToDevice, gs));
+  if (!(c->gexec && c->g_t0 == t0 && c->g_iters == iters)) {
+    if (c->gexec) {
+      cudaGraphExecDestroy(c->gexec);
+      c->gexec = nullptr;
+    }
+    const int cur0 = c->cur;
+    c->st = gs;  // the solve's "caller's stream" while capturing
+    bool ok = cudaStreamBeginCapture(gs, cudaStreamCaptureModeRelaxed) == cudaSuccess;
+    if (ok) {
+      ihs_status s = IHS_OK;
+      ok = record_solve_events(c, gs) == cudaSuccess;
+      if (ok) s = issue_solve(c, c->xg, t0, iters);
+      // join the internal stream back
+      ok = ok && s == IHS_OK && cudaEventRecord(c->ev_tail2, c->st2) == cudaSuccess &&
+           cudaStreamWaitEvent(gs, c->ev_tail2, 0) == cudaSuccess;
+      cudaGraph_t g = nullptr;
+      const cudaError_t e = cudaStreamEndCapture(gs, &g);
+      ok = ok && e == cudaSuccess && g != nullptr;
+      if (ok) ok = cudaGraphInstantiate(&c->gexec, g, 0) == cudaSuccess;
+      if (g) cudaGraphDestroy(g);
+    }
+    c->st = caller;
+    if (!ok) {
+      cudaGetLastError();
+      if (c->gexec) cudaGraphExecDestroy(c->gexec);
+      c->gexec = nullptr;
+      c->graphs = false;
+      c->cur = cur0;
+      CK(cudaStreamSynchronize(gs));
+      CK(record_solve_events(c, caller));
+      return issue_solve(c, x, t0, iters);
+    }
+    c->g_t0 = t0;
+    c->g_iters = iters;
+    c->g_cur_end = c->cur;
+  }
+  CK(cudaGraphLaunch(c->gexec, gs));
+  CK(record_solve_events(c, gs));
+  c->last_graph = true;
+  c->cur = c->g_cur_end;
+  c->have_sketch = true;
+  CK(cudaMemcpyAsync(x, c->xg, xb, cudaMemcpyDeviceToDevice, gs));
+  // the caller's stream continues after the graph
+  CK(cudaEventRecord(c->ev_join, gs));
+  CK(cudaStreamWaitEvent(caller, c->ev_join, 0));
+  return IHS_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -986,51 +1151,10 @@ ihs_status ihs_sync(ihs_ctx* c) {
 // the step; double buffering keeps the step's factor intact.
 ihs_status ihs_solve(ihs_ctx* c, double* x, int64_t t0, int iters, ihs_report* rep) {
   if (!c || !x || iters < 0 || t0 < 0) return IHS_ERR_ARG;
-  if (c->qw.iters) {
-    CK(cudaMemsetAsync(c->qw.iters, 0, sizeof(int), c->st));
-    CK(cudaMemsetAsync(c->qw.need + 1, 0, sizeof(int), c->st));
-  }
-  ihs_status s = IHS_OK;
-  if (iters > 0 && c->lookahead) {
-    if ((s = join_caller(c)) != IHS_OK) return s;
-    if ((s = fused_lookahead(c, x, t0, iters)) != IHS_OK) return s;
-    c->have_sketch = true;
-  } else if (iters > 0 && c->fused) {
-    if ((s = join_caller(c)) != IHS_OK) return s;
-    if ((s = fused_sort(c, t0, 0)) != IHS_OK) return s;
-    int bf = next_buf(c, c->cur);
-    for (int k = 0; k < iters; ++k) {
-      const int pb = k & 1;
-      if (k + 1 < iters && (s = fused_sort(c, t0 + k + 1, pb ^ 1)) != IHS_OK) return s;
-      if ((s = fused_iteration(c, x, pb, bf)) != IHS_OK) return s;
-      c->cur = bf;
-      bf = next_buf(c, bf);
-    }
-    c->have_sketch = true;
-  } else if (iters > 0) {
-    if ((s = join_caller(c)) != IHS_OK) return s;
-    int bf = next_buf(c, c->cur);
-    if ((s = sketch_chain(c, t0, bf)) != IHS_OK) return s;
-    // The chain of t+1 starts once the gradient pass of t is done, and is
-    // issued after the step of t: a gradient pass sharing the GPU with a
-    // full-width sketch kernel runs several times slower, and the one-CTA
-    // l1 step needs a whole SM, which it gets only if launched first.
-    for (int k = 0; k < iters; ++k) {
-      stage_begin(c, IHS_ST_GRAD, c->st);
-      s = gradient_on(c, x, c->g, nullptr, true);
-      stage_end(c);
-      if (s != IHS_OK) return s;
-      CK(cudaEventRecord(c->ev_grad, c->st));
-      if ((s = step_with(c, x, bf)) != IHS_OK) return s;
-      if (k + 1 < iters) {
-        CK(cudaStreamWaitEvent(c->st2, c->ev_grad, 0));
-        if ((s = sketch_chain(c, t0 + k + 1, next_buf(c, bf))) != IHS_OK) return s;
-      }
-      c->cur = bf;
-      bf = next_buf(c, bf);
-    }
-    c->have_sketch = true;
-  }
+  c->last_graph = false;
+  ihs_status s = (iters > 0 && c->graphs && !c->prof) ? solve_graph(c, x, t0, iters)
+                                                      : issue_solve(c, x, t0, iters);
+  if (s != IHS_OK) return s;
   ihs_status st = ihs_sync(c);
   if (rep) {
     rep->iters = iters;
@@ -1038,6 +1162,7 @@ ihs_status ihs_solve(ihs_ctx* c, double* x, int64_t t0, int iters, ihs_report* r
     rep->step_norm = 0.0;
     rep->qp_fista_iters = 0;
     rep->qp_active_rounds = 0;
+    rep->graph = c->last_graph ? 1 : 0;
     if (iters > 0) cudaMemcpy(&rep->step_norm, c->step_norm, sizeof(double), cudaMemcpyDeviceToHost);
     if (c->qw.iters) {
       cudaMemcpy(&rep->qp_fista_iters, c->qw.iters, sizeof(int), cudaMemcpyDeviceToHost);
@@ -1172,6 +1297,7 @@ ihs_status ihs_adjoint(ihs_ctx* c, const double* x, const double* dLdx, double* 
     rep->qp_fista_iters = 0;
     rep->qp_active_rounds = 0;
     rep->step_norm = 0.0;
+    rep->graph = 0;
   }
   if (st != IHS_OK) return st;
   return conv ? IHS_OK : IHS_ERR_NOT_CONVERGED;

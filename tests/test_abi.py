@@ -101,6 +101,7 @@ def test_binding_constants_match_the_header():
     assert ihs.option_flags(serial=True) == h["IHS_FLAG_SERIAL"]
     assert ihs.option_flags(cluster=True) == h["IHS_FLAG_CLUSTER"]
     assert ihs.option_flags(lookahead=False) == h["IHS_FLAG_NO_LOOKAHEAD"]
+    assert ihs.option_flags(graph=False) == h["IHS_FLAG_NO_GRAPH"]
     assert ihs.option_flags(fp64_factor=True) == h["IHS_FLAG_FP64_FACTOR"]
     assert ihs.option_flags(False, True, True, False, True) == 31
     stages = [n for n in sorted(h, key=h.get) if n.startswith("IHS_ST_") and n != "IHS_ST_COUNT"]
@@ -127,7 +128,7 @@ def test_create_rejects_invalid_options_before_touching_the_device():
                               ctypes.byref(O), None)
 
     ERR_ARG = 1
-    assert create(flags=32) == ERR_ARG
+    assert create(flags=64) == ERR_ARG
     assert create(flags=1 << 30) == ERR_ARG
     assert create(sketch=3) == ERR_ARG
     assert create(m=101, s=2) == ERR_ARG

@@ -868,3 +868,49 @@ def test_bounded_wait_gives_up_and_the_context_stays_usable(cuda_lib):
     x, rep = solver.solve(iters=3)
     assert rep.status == 0
     assert np.abs(x.cpu().numpy() - xs[-1]).max() <= 1e-12 * np.abs(xs[-1]).max()
+
+
+@pytest.mark.parametrize("case", ["ols_fp64", "l1_csr_fp64", "ols_tf32_lookahead", "ridge_fp64"])
+def test_graph_solve_matches_stream_solve(cuda_lib, case):
+    """Launch-bound contexts (A up to 128 MB) replay ihs_solve as a CUDA
+    graph, captured on the first call with a given (t0, iters).  The graph
+    holds the same kernels in the same order as the streams, so the iterates
+    equal those of a context with graphs off bit for bit.  This holds on the
+    capture, on a replay with another iterate buffer, and across a resume
+    (4 + 6 iterations against 10)."""
+    if case == "l1_csr_fp64":
+        w, C = _csr_problem("lasso_csr_fp64", 60000, 120, 1200)
+        args = ((dev(w["rowptr"]), dev(w["col"]), dev(w["val"])), dev(w["b"]))
+        kw = dict(kind="l1", param=w["param"], m=1200, s=4, precision="fp64",
+                  shape=(w["n"], w["d"]))
+        d = w["d"]
+    else:
+        name = "ridge_dense" if case == "ridge_fp64" else "ols_dense_fp64"
+        w = synth.make(name, n=20000, d=48, m=480)
+        A = w["A"].astype(np.float32 if case == "ols_tf32_lookahead" else np.float64)
+        args = (dev(A), dev(w["b"]))
+        kw = dict(m=480, precision="tf32" if case == "ols_tf32_lookahead" else "fp64")
+        if case == "ridge_fp64":
+            kw.update(kind="ridge", param=w["param"])
+        d = 48
+    gr = cuda_lib.IHS(*args, **kw)
+    st = cuda_lib.IHS(*args, graph=False, **kw)
+    x_s, r_s = st.solve(iters=10)
+    assert r_s.graph == 0
+    for trial in range(2):  # capture, then replay into a fresh buffer
+        x_g = torch.zeros(d, dtype=torch.float64, device="cuda")
+        _, r_g = gr.solve(x_g, iters=10)
+        assert r_g.status == 0 and r_g.graph == 1, trial
+        assert torch.equal(x_g, x_s), trial
+    x4, r4 = gr.solve(iters=4)
+    x10, r10 = gr.solve(x4, t0=4, iters=6)
+    assert r4.graph == 1 and r10.graph == 1
+    if case == "ols_tf32_lookahead":
+        # the look-ahead pipeline's last pass of a solve walks another sort's
+        # row order, so a resumed run agrees to the gradient's rounding
+        assert float((x10 - x_s).abs().max()) <= 1e-11 * float(x_s.abs().max())
+    else:
+        assert torch.equal(x10, x_s)
+    S1, H1, _ = gr.get_sketch()
+    S2, H2, _ = st.get_sketch()
+    assert torch.equal(S1, S2) and torch.equal(H1, H2)
