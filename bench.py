@@ -632,7 +632,8 @@ def c5_record(ihs, hbm):
             "iters": iters, "solve_ms_median": round(statistics.median(times), 3),
             "solve_ms_all": [round(t, 3) for t in times], "status": int(rep.status),
             "create_ms": round(create_ms, 1),
-            "sketch_kernel": "k_sketch_csc", "sketch_ms": round(sk, 4),
+            "sketch_kernel": "k_sketch_csc (+ k_sketch_csc_merge)",
+            "sketch_ms": round(sk, 4),
             "sketch_algorithmic_bytes": alg,
             "sketch_GB_s": round(alg / (sk * 1e-3) / 1e9, 1),
             "sketch_frac": round(alg / (sk * 1e-3) / 1e9 / hbm, 3)}
@@ -915,7 +916,7 @@ def main():
                     help="seconds of oracle iterations the CPU baseline may run (whole solve "
                          "when it fits)")
     ap.add_argument("--only", default=None, help="workloads experiment: comma-separated names")
-    ap.add_argument("--experiment", default=None, choices=["sketch-quality", "workloads", "adjoint"],
+    ap.add_argument("--experiment", default=None, choices=["sketch-quality", "workloads", "adjoint", "c5"],
                     help="run an experiment instead of the benchmark (one JSON line per point)")
     ap.add_argument("--trials", type=int, default=10)
     ap.add_argument("--families", default=None,
@@ -940,6 +941,10 @@ def main():
         return
     if args.experiment == "adjoint":
         run_adjoint(args)
+        return
+    if args.experiment == "c5":  # the large sparse LASSO record of the main line, alone
+        import paper_1910_14166_gb300 as ihs
+        print(json.dumps(dict(experiment="c5", **c5_record(ihs, peaks()[0]))), flush=True)
         return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

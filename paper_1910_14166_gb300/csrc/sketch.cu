@@ -22,6 +22,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <type_traits>
 #include <cmath>
 
 #include "internal.h"
@@ -294,7 +295,64 @@ cudaError_t launch_sketch_dense(const DenseA& A, const SortPlan& p, const uint32
 // ----------------------------------------------------------------------------
 // CSR through the CSC copy
 // ----------------------------------------------------------------------------
-template <typename Tin, typename Tacc, bool MINTAG>
+// Adds v into bucket `key` of a warp-private shared-memory accumulator for
+// every valid lane.  Invalid lanes pass a key distinct from every valid key
+// (-1 - lane) and touch nothing.  Three modes:
+// 2 (FP32 accumulators): one shared-memory atomic add a lane.  Lanes of one
+//   batch that share a bucket add in the order the hardware serialises them
+//   (within the FP32 summation bound, which holds for any order); batches
+//   still add in entry order, and the accumulator is private to the warp.
+// Modes 1 and 0 (FP64, whose sums follow the entries' order exactly, as the
+// oracle's do) add lanes that share a bucket in lane order:
+// 1: one 32-bit claim word a bucket (32 = free).  In rounds, each pending
+//   lane claims its bucket with a shared-memory atomicMin of its index; the
+//   lowest pending lane of each bucket wins, adds, frees the word and leaves.
+//   A batch without collision takes one round; each extra entry in one
+//   bucket, one more.
+// 0: byte tags.  Every valid lane writes its index at its bucket's tag byte and
+//   reads it back; a lane that reads another index shares its bucket.
+//   Whichever write survives, the test is exact.  Without a collision the
+//   lanes add at once; otherwise the warp matches keys (a narrow pipe, so
+//   only for batches that collide) and adds one rank per round.
+template <typename Tacc, int MODE>
+IHS_DEV void warp_bucket_add(Tacc* acc, uint8_t* tag, uint32_t* tag32, int key, Tacc v,
+                             bool valid, int lane, unsigned lt) {
+  if constexpr (MODE == 2) {
+    if (valid) atomicAdd(acc + key, v);
+  } else if constexpr (MODE == 1) {
+    bool pending = valid;
+    while (__any_sync(0xffffffffu, pending)) {
+      if (pending) atomicMin(tag32 + key, (uint32_t)lane);
+      __syncwarp();
+      const bool win = pending && tag32[key] == (uint32_t)lane;
+      __syncwarp();
+      if (win) {
+        acc[key] += v;
+        tag32[key] = 32u;
+        pending = false;
+      }
+      __syncwarp();
+    }
+  } else {
+    if (valid) tag[key] = (uint8_t)lane;
+    __syncwarp();
+    const bool clash = valid && tag[key] != (uint8_t)lane;
+    if (!__any_sync(0xffffffffu, clash)) {
+      if (valid) acc[key] += v;
+    } else {
+      const unsigned peers = __match_any_sync(0xffffffffu, key);
+      const int rank = __popc(peers & lt);
+      const int rounds = (int)__reduce_max_sync(0xffffffffu, (unsigned)__popc(peers));
+      for (int r = 0; r < rounds; ++r) {
+        if (valid && rank == r) acc[key] += v;
+        __syncwarp();
+      }
+    }
+    __syncwarp();
+  }
+}
+
+template <typename Tin, typename Tacc, int MODE>
 __global__ void __launch_bounds__(256) k_sketch_csc(
     const int32_t* __restrict__ rowidx, const Tin* __restrict__ val, int nitems,
     const int32_t* __restrict__ item_col, const int64_t* __restrict__ item_begin,
@@ -306,9 +364,9 @@ __global__ void __launch_bounds__(256) k_sketch_csc(
   const int nw = blockDim.x >> 5;
   const int mb = K.mb;
   Tacc* acc = reinterpret_cast<Tacc*>(smem_raw) + (size_t)wib * mb;
-  // one byte per bucket to detect colliding lanes (after the nw accumulators),
-  // or (MINTAG) one 32-bit word per bucket holding the lowest lane that
-  // claimed it (32: none)
+  // after the nw accumulators: one byte per bucket to detect colliding lanes
+  // (mode 0), or one 32-bit word per bucket holding the lowest lane that
+  // claimed it (mode 1; 32: none); none in mode 2
   uint8_t* tag = reinterpret_cast<uint8_t*>(reinterpret_cast<Tacc*>(smem_raw) + (size_t)nw * mb) +
                  (size_t)wib * mb;
   uint32_t* tag32 = reinterpret_cast<uint32_t*>(reinterpret_cast<Tacc*>(smem_raw) + (size_t)nw * mb) +
@@ -320,7 +378,7 @@ __global__ void __launch_bounds__(256) k_sketch_csc(
   const int k = (int)(unit - (int64_t)it * K.s);
   for (int b = lane; b < mb; b += 32) {
     acc[b] = Tacc(0);
-    if constexpr (MINTAG) tag32[b] = 32u;
+    if constexpr (MODE == 1) tag32[b] = 32u;
   }
   __syncwarp();
   const int64_t e0 = item_begin[it], e1 = item_end[it];
@@ -357,51 +415,8 @@ __global__ void __launch_bounds__(256) k_sketch_csc(
 #pragma unroll
     for (int q = 0; q < kU; ++q) {
       const bool valid = base + q * 32 + lane < e1;
-      const int key = valid ? keyq[q] : -1 - lane;
-      const Tacc v = valid ? vq[q] : Tacc(0);
-      if constexpr (MINTAG) {
-        // Rounds: every pending lane claims its bucket with a shared-memory
-        // atomicMin of its index, so the lowest pending lane of each bucket
-        // wins; winners add (colliding lanes therefore add in lane, i.e.
-        // row, order), release the bucket and leave.  A batch with no
-        // collision takes one round; each extra entry in one bucket, one more.
-        bool pending = valid;
-        while (__any_sync(0xffffffffu, pending)) {
-          if (pending) atomicMin(tag32 + key, (uint32_t)lane);
-          __syncwarp();
-          const bool win = pending && tag32[key] == (uint32_t)lane;
-          __syncwarp();
-          if (win) {
-            acc[key] += v;
-            tag32[key] = 32u;
-            pending = false;
-          }
-          __syncwarp();
-        }
-        continue;
-      }
-      // Collision test: every lane writes its index at its bucket; a lane
-      // that reads back another index shares its bucket.  Whichever lane's
-      // write survives, the test is exact, and without a collision the
-      // adds below touch distinct buckets.  (Matching keys across the warp
-      // occupies a narrow pipe, so it is kept for batches that collide,
-      // about one in three at 1250 buckets.)
-      if (valid) tag[key] = (uint8_t)lane;
-      __syncwarp();
-      const bool clash = valid && tag[key] != (uint8_t)lane;
-      if (!__any_sync(0xffffffffu, clash)) {
-        if (valid) acc[key] += v;
-      } else {
-        const unsigned peers = __match_any_sync(0xffffffffu, key);
-        const int rank = __popc(peers & lt);
-        // max multiplicity in this batch
-        const int rounds = (int)__reduce_max_sync(0xffffffffu, (unsigned)__popc(peers));
-        for (int r = 0; r < rounds; ++r) {
-          if (valid && rank == r) acc[key] += v;
-          __syncwarp();
-        }
-      }
-      __syncwarp();
+      warp_bucket_add<Tacc, MODE>(acc, tag, tag32, valid ? keyq[q] : -1 - lane,
+                                    valid ? vq[q] : Tacc(0), valid, lane, lt);
     }
   }
   // write block k's rows of column item_col[it]
@@ -432,43 +447,58 @@ __global__ void k_sketch_csc_merge(const int32_t* __restrict__ col_first_item,
   }
 }
 
-template <typename Tin, typename Tacc>
-static cudaError_t run_csc(const CscA& A, const SketchKeys& K, int64_t m, void* SA, void* partial,
-                           cudaStream_t st) {
-  // 32-bit claim words when a CTA of eight warps' accumulators and words
-  // stays within 56 KB (four CTAs an SM); the byte tags (collisions resolved
-  // by key matching) otherwise, where the claim words would cost occupancy
-  // (measured: 1250 FP32 buckets a block, 1.40 ms with byte tags against
-  // 1.99 ms with claim words at two CTAs an SM; 500 FP64 buckets, 0.152
-  // against 0.118 ms)
-  const bool mintag = (size_t)K.mb * (sizeof(Tacc) + 4) * 8 <= 56 * 1024;
-  const size_t per_warp = (size_t)K.mb * (sizeof(Tacc) + (mintag ? 4 : 1));
-  int nw = (int)std::min<size_t>(8, (200 * 1024) / per_warp);
-  if (nw < 1) return cudaErrorInvalidValue;
-  const size_t smem = per_warp * nw;
-  const void* fn = mintag ? (const void*)k_sketch_csc<Tin, Tacc, true>
-                          : (const void*)k_sketch_csc<Tin, Tacc, false>;
-  if (smem > 48 * 1024) {
-    cudaError_t e = ensure_smem(fn, (int)smem);
-    if (e != cudaSuccess) return e;
-  }
-  const int64_t units = (int64_t)A.nitems * K.s;
-  const unsigned grid = (unsigned)((units + nw - 1) / nw);
-  if (mintag)
-    k_sketch_csc<Tin, Tacc, true><<<grid, nw * 32, smem, st>>>(
-        A.rowidx, (const Tin*)A.val, A.nitems, A.item_col, A.item_begin, A.item_end, A.item_slot,
-        K, (int)A.d, (Tacc*)SA, (Tacc*)partial);
-  else
-    k_sketch_csc<Tin, Tacc, false><<<grid, nw * 32, smem, st>>>(
-        A.rowidx, (const Tin*)A.val, A.nitems, A.item_col, A.item_begin, A.item_end, A.item_slot,
-        K, (int)A.d, (Tacc*)SA, (Tacc*)partial);
-  note_launches(1);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess || A.nsplit_slots == 0) return e;
+template <typename Tacc>
+static cudaError_t merge_csc(const CscA& A, const SketchKeys& K, int64_t m, void* SA,
+                             const void* partial, cudaStream_t st) {
+  if (A.nsplit_slots == 0) return cudaSuccess;
   dim3 g((unsigned)std::min<int64_t>((m + 255) / 256, 64), (unsigned)A.d);
   { k_sketch_csc_merge<Tacc><<<g, 256, 0, st>>>(A.col_first_item, A.item_slot, (int)A.d, (int)m,
                                               K.s, K.mb, (const Tacc*)partial, (Tacc*)SA); note_launches(1); }
   return cudaGetLastError();
+}
+
+template <typename Tin, typename Tacc, int MODE>
+static cudaError_t launch_csc_warp(const CscA& A, const SketchKeys& K, int nw, size_t smem,
+                                   cudaStream_t st, void* SA, void* partial) {
+  cudaError_t e = cudaSuccess;
+  if (smem > 48 * 1024 &&
+      (e = ensure_smem((const void*)k_sketch_csc<Tin, Tacc, MODE>, (int)smem)) != cudaSuccess)
+    return e;
+  const int64_t units = (int64_t)A.nitems * K.s;
+  const unsigned grid = (unsigned)((units + nw - 1) / nw);
+  k_sketch_csc<Tin, Tacc, MODE><<<grid, nw * 32, smem, st>>>(
+      A.rowidx, (const Tin*)A.val, A.nitems, A.item_col, A.item_begin, A.item_end, A.item_slot, K,
+      (int)A.d, (Tacc*)SA, (Tacc*)partial);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+template <typename Tin, typename Tacc>
+static cudaError_t run_csc(const CscA& A, const SketchKeys& K, int64_t m, void* SA, void* partial,
+                           cudaStream_t st) {
+  // Scatter mode.  FP32 accumulators: shared-memory atomic adds (measured on
+  // 1250 FP32 buckets a block: 1.03 ms against 1.38 ms with byte tags).
+  // FP64 (whose sums must follow the entries' order): 32-bit claim words
+  // when a CTA of eight warps' accumulators and words stays within 56 KB
+  // (four CTAs an SM), the byte tags otherwise, where the claim words would
+  // cost occupancy (500 FP64 buckets a block: 0.118 ms with claim words
+  // against 0.152 ms with byte tags).
+  const int mode = std::is_same<Tacc, float>::value
+                       ? 2
+                       : ((size_t)K.mb * (sizeof(Tacc) + 4) * 8 <= 56 * 1024 ? 1 : 0);
+  const size_t per_warp = (size_t)K.mb * (sizeof(Tacc) + (mode == 1 ? 4 : (mode == 0 ? 1 : 0)));
+  const int nw = (int)std::min<size_t>(8, (200 * 1024) / per_warp);
+  if (nw < 1) return cudaErrorInvalidValue;
+  const size_t smem = per_warp * nw;
+  cudaError_t e = cudaSuccess;
+  if constexpr (std::is_same<Tacc, float>::value) {
+    e = launch_csc_warp<Tin, Tacc, 2>(A, K, nw, smem, st, SA, partial);
+  } else {
+    e = mode == 1 ? launch_csc_warp<Tin, Tacc, 1>(A, K, nw, smem, st, SA, partial)
+                  : launch_csc_warp<Tin, Tacc, 0>(A, K, nw, smem, st, SA, partial);
+  }
+  if (e != cudaSuccess) return e;
+  return merge_csc<Tacc>(A, K, m, SA, partial, st);
 }
 
 cudaError_t launch_sketch_csc(const CscA& A, const SketchKeys& K, int64_t m, int acc64, void* SA,

@@ -105,6 +105,38 @@ def test_sketch_csr(cuda_lib, dt, prec, s, n, d, m):
         assert rel(SA.cpu().numpy(), SAo) < 1e-5
 
 
+def test_sketch_csr_fp32_repeats_bit_for_bit(cuda_lib):
+    """With FP32 accumulators the CSC sketch adds the lanes of a batch with
+    shared-memory atomic adds, so lanes that share a bucket add in the order
+    the hardware serialises them, not in lane order.  The accumulator is
+    private to one warp and batches add in entry order, so the same sketch
+    must give the same bits again: in one context, in a second context, and
+    after other sketches.  100 buckets a block make collisions in most
+    batches.  The values stay within the FP32 bar of the oracle's sum."""
+    n, d, m, s = 200003, 16, 800, 8
+    rowptr, col, val = synth.csr_uniform(n, d, 5, 3, np.float32)
+    b = np.random.default_rng(1).standard_normal(n)
+    args = ((dev(rowptr), dev(col), dev(val)), dev(b))
+    kw = dict(m=m, s=s, seed=4, precision="tf32", shape=(n, d))
+    one, two = cuda_lib.IHS(*args, **kw), cuda_lib.IHS(*args, **kw)
+    one.sketch(7)
+    SA1 = one.get_sketch()[0].clone()
+    one.sketch(8)
+    one.sketch(7)
+    two.sketch(7)
+    assert torch.equal(one.get_sketch()[0], SA1)
+    assert torch.equal(two.get_sketch()[0], SA1)
+    bo, so = O.hash_draw(4, 7, s, m, n)
+    SAo = O.sketch(O.CSR(n, d, rowptr, col, val.astype(np.float64)), m, s, bo, so)
+    # FP32 sums of at most L terms: |err| <= gamma_L sum |terms|, L the
+    # longest column chunk (16384 entries) plus the merge of a column's chunks
+    absS = O.sketch(O.CSR(n, d, rowptr, col, np.abs(val.astype(np.float64))), m, s, bo,
+                    np.ones_like(so))
+    L = 16384 + n * 5 // d // 16384 + 1
+    u = 2.0 ** -24
+    assert np.all(np.abs(SA1.cpu().numpy() - SAo) <= (L * u / (1 - L * u)) * absS + 1e-30)
+
+
 # -------------------------------------------------------------- gradient ---
 @pytest.mark.parametrize("n,d,dt", [(20000, 50, np.float64), (30001, 500, np.float32),
                                     (5000, 37, np.float32), (7000, 1000, np.float32),
