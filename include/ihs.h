@@ -269,6 +269,17 @@ ihs_status ihs_trim_memory(void);
  * (NULL = legacy default stream); synchronises it. */
 ihs_status ihs_selftest_wait(void* stream);
 
+/* ihs_selftest_rsqrt -- evaluates, for each of the n doubles p[i] (DEVICE),
+ * the reciprocal square root the FP64 Cholesky factor uses for its pivots
+ * (Newton-Raphson from an FP32 seed; the pivots of the factor of Eq. 2's
+ * sketched Hessian) into out[i], and CUDA's rsqrt(p[i]) into ref[i] (both
+ * DEVICE, n doubles), so that tests can bound the first against the second.
+ * Positive finite p only (the factor records a non-positive pivot as
+ * IHS_ERR_NOT_SPD before it takes the root).  n <= 0 does nothing.  stream:
+ * a cudaStream_t (NULL = legacy default stream); not synchronised.  Errors:
+ * IHS_ERR_ARG (null pointer with n > 0), IHS_ERR_CUDA. */
+ihs_status ihs_selftest_rsqrt(const double* p, double* out, double* ref, int64_t n, void* stream);
+
 /* ihs_exact_gram -- G = A^T A in FP64 (DEVICE, d x d doubles, row-major,
  * both triangles), the reference of the sketch-quality experiment (App. B:
  * the empirical error ||A^T S^T S A - A^T A||_F / ||A^T A||_F).  Dense A: an

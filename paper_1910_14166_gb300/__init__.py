@@ -95,6 +95,7 @@ def _load():
         "ihs_exact_gram": [vp, vp],
         "ihs_trim_memory": [],
         "ihs_selftest_wait": [vp],
+        "ihs_selftest_rsqrt": [vp, vp, vp, i64, vp],
         "ihs_sketch_error": [vp, i64, vp, ctypes.POINTER(f64)],
     }
     for name, args in sig.items():
@@ -193,6 +194,20 @@ def trim_memory():
     """Return the library's cached device workspace memory to the device
     (contexts keep reusing it otherwise; see ihs_trim_memory)."""
     _check(_lib.ihs_trim_memory(), "ihs_trim_memory")
+
+
+def selftest_rsqrt(p):
+    """The FP64 Cholesky's pivot reciprocal square root and CUDA's rsqrt of
+    each entry of p (a CUDA float64 tensor of positive finite values), as two
+    new tensors (ours, CUDA's)."""
+    _need_cuda(p, "p")
+    if p.dtype != torch.float64:
+        raise TypeError("p must be float64")
+    p = p.contiguous()
+    out, ref = torch.empty_like(p), torch.empty_like(p)
+    _check(_lib.ihs_selftest_rsqrt(_ptr(p), _ptr(out), _ptr(ref), p.numel(), _stream()),
+           "ihs_selftest_rsqrt")
+    return out, ref
 
 
 def selftest_wait():

@@ -597,7 +597,7 @@ ihs_status ihs_create(ihs_ctx** out, const ihs_matrix* A, const double* b,
     AL2(c->chunk_first, c->sp.nchunks * sizeof(int32_t));
     AL2(c->sk_partial, (size_t)2 * c->sp.nchunks * c->d * acc_el);
     c->rg_warps = rg_dense_warps(c->n);
-    AL2(c->gpart, (size_t)c->rg_warps * c->d * sizeof(double));
+    AL2(c->gpart, rg_partial_bytes(c->rg_warps, c->d));
     if (c->gauss) {
       c->gplan = make_gauss_plan(c->m, c->n, (int)c->d, c->acc64, c->sms);
       AL2(c->gauss_part, c->gplan.partial_bytes);
@@ -1201,6 +1201,15 @@ ihs_status ihs_selftest_wait(void* stream) {
   cudaFree(bar);
   if (e != cudaSuccess) return IHS_ERR_CUDA;
   return (ihs_status)h;
+}
+
+ihs_status ihs_selftest_rsqrt(const double* p, double* out, double* ref, int64_t n,
+                              void* stream) {
+  if (n <= 0) return IHS_OK;
+  if (!p || !out || !ref) return IHS_ERR_ARG;
+  if (launch_selftest_rsqrt(p, out, ref, n, (cudaStream_t)stream) != cudaSuccess)
+    return IHS_ERR_CUDA;
+  return IHS_OK;
 }
 
 ihs_status ihs_trim_memory(void) {

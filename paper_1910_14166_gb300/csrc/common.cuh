@@ -133,6 +133,37 @@ IHS_DEV T warp_sum(T v) {
   return v;
 }
 
+// 1/sqrt(p) in FP64 with a short dependency chain, for the Cholesky pivots
+// (each column of a sweep waits on one).  Newton-Raphson for f(y) = 1/y^2 - p:
+// y <- y + (y/2)(1 - p y^2), which squares the relative error each step.  The
+// seed is the FP32 reciprocal square root of p truncated to FP32 (relative
+// error about 2^-21); two steps bring it to about 2^-84 before rounding, so
+// the result is within about an ulp of 1/sqrt(p).  Each step is three
+// dependent FP64 operations, six in all, where the FP64 library routine's
+// chain is several times longer (GB300 issues one FP64 warp instruction per
+// 64 cycles a sub-partition, so chain length sets a sweep's time).  The
+// conversions between FP64 and FP32 go through the bit patterns (integer
+// operations).  p outside FP32's normal exponent range takes rsqrt().
+IHS_DEV double rsqrt_nr(double p) {
+  const int hi = __double2hiint(p);
+  const int E = (hi >> 20) & 0x7ff;
+  if (hi < 0 || E < 1023 - 126 || E > 1023 + 127) return rsqrt(p);
+  // p truncated to FP32: exponent rebased from 1023 to 127, top 23 mantissa bits
+  const unsigned fb = ((unsigned)(hi - ((1023 - 127) << 20)) << 3) |
+                      ((unsigned)__double2loint(p) >> 29);
+  const float yf = rsqrtf(__uint_as_float(fb));
+  // yf widened to FP64 exactly (a positive normal FP32 value)
+  const unsigned yb = __float_as_uint(yf);
+  double y = __hiloint2double((int)((yb >> 3) + ((1023 - 127) << 20)), (int)(yb << 29));
+#pragma unroll
+  for (int it = 0; it < 2; ++it) {
+    const double h = 0.5 * y;
+    const double e = fma(-(p * y), y, 1.0);  // 1 - p y^2
+    y = fma(h, e, y);
+  }
+  return y;
+}
+
 // Load / store helpers with a compile-time vector width.
 template <typename T, int V> struct VecT;
 template <> struct VecT<float, 4> { using type = float4; };
@@ -172,4 +203,28 @@ constexpr long long kSpinLimit = 1ll << 26;
 
 IHS_DEV uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// mbarrier primitives (shared memory, CTA scope): init with an arrival
+// count, arrive (release), and one test of a phase's completion (acquire).
+IHS_DEV void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+               : "memory");
+}
+IHS_DEV void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+IHS_DEV bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+IHS_DEV void mbar_inval(uint64_t* bar) {
+  asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
 }

@@ -280,24 +280,53 @@ __global__ void __launch_bounds__(kRgThreads) k_rg_dense_f64(
     if (colq[q] < d) gp[colq[q]] = g[q];
 }
 
-// g[c] = sum_w gpart[w][c] (fixed order: 8 interleaved warps then a fixed
-// combine) - lam * x[c].
-__global__ void k_reduce_gpart(const double* __restrict__ gpart, int nwarps, int d,
-                               const double* __restrict__ x, double lam, double* __restrict__ g) {
+// g[c] = sum_w gpart[w][c] - lam * x[c], in two levels when there are many
+// warp partials: CTA (column block, part p) sums the partials of its slice
+// [p W / P, (p + 1) W / P) (eight interleaved warps, then a fixed combine)
+// into g2[p][c], and a second kernel adds the P slice sums in order.  One
+// level (P = 1) writes g directly.  Either way the order is fixed, so the
+// gradient is reproducible.  The split puts the FP64 additions (about two
+// lanes a clock an SM on GB300) on P times more SMs.
+int rg_reduce_split(int nwarps) { return std::min(32, std::max(1, nwarps / 64)); }
+
+size_t rg_partial_bytes(int nwarps, int64_t d) {
+  const int P = rg_reduce_split(nwarps);
+  return (size_t)(nwarps + (P > 1 ? P : 0)) * (size_t)d * sizeof(double);
+}
+
+__global__ void k_reduce_gpart(const double* __restrict__ gpart, int nwarps, int d, int P,
+                               const double* __restrict__ x, double lam, double* __restrict__ g,
+                               double* __restrict__ g2) {
   __shared__ double part[8][32];
   const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
   const int c = blockIdx.x * 32 + lane;
+  const int p = blockIdx.y;
+  const int w0 = (int)((int64_t)p * nwarps / P), w1 = (int)((int64_t)(p + 1) * nwarps / P);
   double acc = 0.0;
   if (c < d)
-    for (int w = wi; w < nwarps; w += 8) acc += gpart[(int64_t)w * d + c];
+    for (int w = w0 + wi; w < w1; w += 8) acc += gpart[(int64_t)w * d + c];
   part[wi][lane] = acc;
   __syncthreads();
   if (wi == 0 && c < d) {
     double s = 0.0;
     for (int k = 0; k < 8; ++k) s += part[k][lane];
-    if (lam != 0.0) s -= lam * x[c];
-    g[c] = s;
+    if (P > 1) {
+      g2[(int64_t)p * d + c] = s;
+    } else {
+      if (lam != 0.0) s -= lam * x[c];
+      g[c] = s;
+    }
   }
+}
+
+__global__ void k_reduce_gpart2(const double* __restrict__ g2, int P, int d,
+                                const double* __restrict__ x, double lam, double* __restrict__ g) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= d) return;
+  double s = 0.0;
+  for (int p = 0; p < P; ++p) s += g2[(int64_t)p * d + c];
+  if (lam != 0.0) s -= lam * x[c];
+  g[c] = s;
 }
 
 cudaError_t launch_resid_grad_dense(const DenseA& A, const double* b, const float2* bsplit,
@@ -358,7 +387,14 @@ cudaError_t launch_resid_grad_dense(const DenseA& A, const double* b, const floa
   } else {
     cudaMemsetAsync(gpart, 0, (size_t)nwarps * d * sizeof(double), st);
   }
-  { k_reduce_gpart<<<(d + 31) / 32, 256, 0, st>>>(gpart, nwarps, d, x, lam, g); note_launches(1); }
+  const int P = rg_reduce_split(nwarps);
+  double* g2 = gpart + (int64_t)nwarps * d;  // P x d slice sums (P > 1)
+  { k_reduce_gpart<<<dim3((d + 31) / 32, P), 256, 0, st>>>(gpart, nwarps, d, P, x, lam, g, g2); note_launches(1); }
+  if (P > 1) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    { k_reduce_gpart2<<<(d + 127) / 128, 128, 0, st>>>(g2, P, d, x, lam, g); note_launches(1); }
+  }
   return cudaGetLastError();
 }
 
@@ -517,7 +553,7 @@ cudaError_t launch_split_b(const double* b, int64_t n, float2* out, cudaStream_t
 
 cudaError_t launch_reduce_partials(const double* part, int nparts, int d, const double* x,
                                    double lam, double* g, cudaStream_t st) {
-  k_reduce_gpart<<<(d + 31) / 32, 256, 0, st>>>(part, nparts, d, x, lam, g);
+  k_reduce_gpart<<<(d + 31) / 32, 256, 0, st>>>(part, nparts, d, 1, x, lam, g, nullptr);
   note_launches(1);
   return cudaGetLastError();
 }

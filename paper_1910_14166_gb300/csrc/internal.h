@@ -93,6 +93,9 @@ cudaError_t launch_sketch_adjoint(const SketchKeys& K, int64_t n, int64_t d, con
 // ---- residual and gradient ----------------------------------------------------
 // Dense: g = A^T (b - A x) with FP64-class accuracy; gpart has nwarps*d doubles.
 int rg_dense_warps(int64_t n);
+// bytes of the dense gradient's partial buffer for nwarps warps (the warp
+// partials, then the reduce's slice sums)
+size_t rg_partial_bytes(int nwarps, int64_t d);
 cudaError_t launch_resid_grad_dense(const DenseA& A, const double* b, const float2* bsplit,
                                     const double* x, double* r, double* gpart, int nwarps,
                                     double* g, double lam, cudaStream_t st);
@@ -145,6 +148,8 @@ size_t chol_dinv_bytes(int d, int f32);
 // the cooperative grid kernel (the two give identical factors).  max_ctas > 0
 // caps the grid kernel's CTAs (the factor then leaves the other SMs to a
 // kernel running beside it).
+cudaError_t launch_selftest_rsqrt(const double* p, double* out, double* ref, int64_t n,
+                                  cudaStream_t st);
 cudaError_t launch_cholesky(const double* H, int d, int f32, void* Lbuf, void* Dinv, unsigned* bar,
                             int* status, cudaStream_t st, int allow_cluster, double shift = 0.0,
                             int max_ctas = 0);

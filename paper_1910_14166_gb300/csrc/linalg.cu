@@ -12,7 +12,9 @@
 //              the unused upper triangle, tile (k, i);
 //   update(k-1) every trailing lower tile (i, j), k < j <= i:
 //              A_ij -= L_{i,k-1} L_{j,k-1}^T,
-// so a step costs one grid barrier.  The item that owns the diagonal tile
+// so a step costs one grid barrier (FP32; in FP64, where a tile update is
+// slow, k_chol_coop2 takes two barriers a step and spreads the updates over
+// the grid).  The item that owns the diagonal tile
 // sweeps the identity alongside it, which yields D_k = L_kk^{-1} for the
 // solve in the same 32 steps; L_kk itself is never written back (every panel
 // item of step k reads the diagonal tile while the step runs, and the solve
@@ -102,15 +104,39 @@ cudaError_t launch_barrier_selftest(unsigned* bar, int* status, cudaStream_t st)
   return cudaGetLastError();
 }
 
+__global__ void k_selftest_rsqrt(const double* __restrict__ p, double* __restrict__ out,
+                                 double* __restrict__ ref, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    out[i] = rsqrt_nr(p[i]);
+    ref[i] = rsqrt(p[i]);
+  }
+}
+
+cudaError_t launch_selftest_rsqrt(const double* p, double* out, double* ref, int64_t n,
+                                  cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  { k_selftest_rsqrt<<<(unsigned)std::min<int64_t>((n + 255) / 256, 1024), 256, 0, st>>>(p, out, ref, n); note_launches(1); }
+  return cudaGetLastError();
+}
+
+// Reciprocal square root of a pivot: FP32 through the hardware's rsqrtf,
+// FP64 through rsqrt_nr (six dependent FP64 operations on the pivot chain).
+IHS_DEV float pivot_rsqrt(float p) { return rsqrtf(p); }
+IHS_DEV double pivot_rsqrt(double p) { return rsqrt_nr(p); }
+
 // Panel sweep with warp 0 over the tall block [Dk; Ta] (Ta optional): lane r
 // holds row r of the diagonal tile and row r of the panel tile in registers.
 // Column j: the pivot comes from lane j by a shuffle, the diagonal rows below
 // and every panel row are scaled by 1/L_jj, and the trailing columns of both
 // are updated with L_cj fetched from lane c.  This factors Dk = L_kk L_kk^T
 // and solves Ta <- Ta L_kk^{-T} in the same 32 steps, with no block-wide
-// barrier inside.  All threads of the CTA must call.
+// barrier inside.  Only the first ncols columns are swept: in the last tile
+// the columns past d are identity padding (pivot 1, and every L entry that
+// would update them is 0), so they end as they start.  All threads of the
+// CTA must call.
 template <typename T>
-__device__ void panel_sweep(T (*Dk)[33], T (*Ta)[33], bool tall, int* spd) {
+__device__ void panel_sweep(T (*Dk)[33], T (*Ta)[33], bool tall, int* spd, int ncols) {
   const int lane = threadIdx.x & 31;
   if (threadIdx.x < 32) {
     T a[32], bb[32];
@@ -122,12 +148,13 @@ __device__ void panel_sweep(T (*Dk)[33], T (*Ta)[33], bool tall, int* spd) {
     bool good = true;
 #pragma unroll
     for (int j = 0; j < 32; ++j) {
+      if (j >= ncols) break;  // identity padding past d: nothing to do
       T pj = __shfl_sync(0xffffffffu, a[j], j);
       if (!(pj > T(0))) {
         good = false;
         pj = T(1);
       }
-      const T rinv = rsqrt(pj);
+      const T rinv = pivot_rsqrt(pj);
       const T lrj = (lane > j) ? a[j] * rinv : (lane == j ? pj * rinv : T(0));
       a[j] = lrj;
       const T bj = bb[j] * rinv;
@@ -157,18 +184,31 @@ __device__ void panel_sweep(T (*Dk)[33], T (*Ta)[33], bool tall, int* spd) {
 // tile (about a thousand DFMA instructions) takes tens of microseconds.
 // Lane r still owns row r; warp w owns the columns c = w (mod 4), eight of
 // the diagonal block and eight of the panel block, so the four sub-partitions
-// share the updates.  At column j the warp that owns it forms the pivot, the
-// scaled column L_rj and the scaled panel entries, publishes them in shared
-// memory (two buffers, alternating by j) and all four warps meet at a named
-// barrier before applying the rank-1 update to their own columns.  Every
-// entry goes through the same operations in the same order as in
-// panel_sweep, so both give the same factor.  All threads must call.
+// share the updates.  Column j is published by its owner warp (j mod 4): the
+// scaled column L_rj and the scaled panel entries go to shared-memory slot j
+// and each lane arrives on mbarrier j (32 arrivals complete it); a warp that
+// needs column j waits on that mbarrier alone, so it is never held up by
+// another warp's unfinished updates.  Each warp copies column j to registers,
+// then the owner of column j + 1 applies column j's update to column j + 1
+// first and publishes column j + 1 at once, before its other updates: the
+// pivot chain runs from one column to the next without waiting for the rest
+// of the rank-1 update.  Waits are bounded (kSpinLimit polls); one that runs
+// out marks the sweep as timed out and the warp goes on, so no wait can hang
+// the CTA.  Every entry goes through the same operations in the same order
+// as in panel_sweep, so both give the same factor; columns from ncols on are
+// skipped as there.  *spd: 1, 0 if a pivot was not positive, -1 if a wait
+// timed out.  All threads must call.
 template <typename T>
-__device__ void panel_sweep4(T (*Dk)[33], T (*Ta)[33], bool tall, int* spd) {
-  __shared__ T colL[2][32], colB[2][32];
-  __shared__ int bad;
+__device__ void panel_sweep4(T (*Dk)[33], T (*Ta)[33], bool tall, int* spd, int ncols) {
+  __shared__ T colL[32][32], colB[32][32];
+  __shared__ __align__(8) uint64_t ready[32];
+  __shared__ int bad, late;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  if (threadIdx.x == 0) bad = 0;
+  if (threadIdx.x == 0) {
+    bad = 0;
+    late = 0;
+    for (int j = 0; j < 32; ++j) mbar_init(&ready[j], 32);
+  }
   __syncthreads();
   if (threadIdx.x < 128) {
     T a[8], bb[8];
@@ -178,33 +218,55 @@ __device__ void panel_sweep4(T (*Dk)[33], T (*Ta)[33], bool tall, int* spd) {
       a[u] = (c <= lane) ? Dk[lane][c] : T(0);
       bb[u] = tall ? Ta[lane][c] : T(0);
     }
+    // the owner's publication of column j (a[j >> 2], bb[j >> 2] final)
+    auto publish = [&](const int j) {
+      const int uj = j >> 2;
+      T pj = __shfl_sync(0xffffffffu, a[uj], j);
+      if (!(pj > T(0))) {
+        if (lane == 0) bad = 1;
+        pj = T(1);
+      }
+      const T rinv = pivot_rsqrt(pj);
+      const T lrj = (lane > j) ? a[uj] * rinv : (lane == j ? pj * rinv : T(0));
+      a[uj] = lrj;
+      const T bj = bb[uj] * rinv;
+      bb[uj] = bj;
+      colL[j][lane] = lrj;
+      colB[j][lane] = bj;
+      __syncwarp();
+      mbar_arrive(&ready[j]);
+    };
+    if (w == 0) publish(0);
 #pragma unroll
     for (int j = 0; j < 32; ++j) {
-      const int buf = j & 1;
-      if (w == (j & 3)) {
-        const int uj = j >> 2;
-        T pj = __shfl_sync(0xffffffffu, a[uj], j);
-        if (!(pj > T(0))) {
-          if (lane == 0) bad = 1;
-          pj = T(1);
+      if (j >= ncols) break;  // identity padding past d: nothing to do
+      if (w != (j & 3)) {
+        long long it = 0;
+        while (!mbar_try_wait(&ready[j], 0)) {
+          if (++it > kSpinLimit) {
+            late = 1;
+            break;
+          }
         }
-        const T rinv = rsqrt(pj);
-        const T lrj = (lane > j) ? a[uj] * rinv : (lane == j ? pj * rinv : T(0));
-        a[uj] = lrj;
-        const T bj = bb[uj] * rinv;
-        bb[uj] = bj;
-        colL[buf][lane] = lrj;
-        colB[buf][lane] = bj;
       }
-      asm volatile("bar.sync 1, 128;" ::: "memory");
-      const T lrj = colL[buf][lane], bj = colB[buf][lane];
+      const T lrj = colL[j][lane], bj = colB[j][lane];
+      T lc[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) lc[u] = colL[j][w + 4 * u];
+      const int jn = j + 1;
+      const bool next = jn < ncols && w == (jn & 3);
+      if (next) {
+        const int un = jn >> 2;
+        if (lane >= jn) a[un] -= lrj * lc[un];
+        bb[un] -= bj * lc[un];
+        publish(jn);
+      }
 #pragma unroll
       for (int u = 0; u < 8; ++u) {
         const int c = w + 4 * u;
-        if (c > j) {
-          const T lcj = colL[buf][c];
-          if (lane >= c) a[u] -= lrj * lcj;
-          bb[u] -= bj * lcj;
+        if (c > j && !(next && c == jn)) {
+          if (lane >= c) a[u] -= lrj * lc[u];
+          bb[u] -= bj * lc[u];
         }
       }
     }
@@ -216,16 +278,28 @@ __device__ void panel_sweep4(T (*Dk)[33], T (*Ta)[33], bool tall, int* spd) {
     }
   }
   __syncthreads();
-  if (threadIdx.x == 0) *spd = bad ? 0 : 1;
+  if (threadIdx.x == 0) {
+    *spd = late ? -1 : (bad ? 0 : 1);
+    for (int j = 0; j < 32; ++j) mbar_inval(&ready[j]);
+  }
   __syncthreads();
+}
+
+// Records a sweep's outcome: a pivot that was not positive (reported by the
+// item of the diagonal tile) or a wait that ran out (any item).
+IHS_DEV void note_sweep(int spd, bool diag, int* status) {
+  if (threadIdx.x == 0) {
+    if (spd < 0) set_status(status, DEV_TIMEOUT);
+    else if (spd == 0 && diag) set_status(status, DEV_NOT_SPD);
+  }
 }
 
 // The factor's panel sweep: four warps in FP64, one warp (no barriers) in
 // FP32, whose FMA rate makes the one-warp sweep short.
 template <typename T>
-__device__ void panel_factor(T (*Dk)[33], T (*Ta)[33], bool tall, int* spd) {
-  if constexpr (sizeof(T) == 8) panel_sweep4<T>(Dk, Ta, tall, spd);
-  else panel_sweep<T>(Dk, Ta, tall, spd);
+__device__ void panel_factor(T (*Dk)[33], T (*Ta)[33], bool tall, int* spd, int ncols) {
+  if constexpr (sizeof(T) == 8) panel_sweep4<T>(Dk, Ta, tall, spd, ncols);
+  else panel_sweep<T>(Dk, Ta, tall, spd, ncols);
 }
 
 // C (32 x 32 in smem) -= P Q^T, P, Q 32 x 32 in smem; 256 threads.
@@ -256,7 +330,7 @@ __device__ void tile_sub_pqt(T (*C)[33], T (*P)[33], T (*Q)[33]) {
 // a CTA of the fused pass (256 threads x 128 registers): the look-ahead
 // pipeline runs the two together.
 template <typename T>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_chol_coop(T* __restrict__ L, T* __restrict__ Dinv, int dp,
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_chol_coop(T* __restrict__ L, T* __restrict__ Dinv, int d, int dp,
                                                    int Tt, unsigned* bar, int* status) {
   __shared__ T Dk[32][33];
   __shared__ T Ta[32][33];
@@ -294,13 +368,13 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_chol_coop(T* __
           for (int e = tid; e < 1024; e += blockDim.x) Ta[e >> 5][e & 31] = ((e >> 5) == (e & 31)) ? T(1) : T(0);
           __syncthreads();
         }
-        panel_factor<T>(Dk, Ta, true, &spd);
+        panel_factor<T>(Dk, Ta, true, &spd, min(32, d - k0));
+        note_sweep(spd, c == 0, status);
         if (c == 0) {
           // L_kk itself is not stored: the other panel items of this step
           // read the diagonal tile of L concurrently (it must keep the
           // updated Hessian tile until the next barrier), and the solve
           // only needs D_k = L_kk^{-1}.
-          if (!spd && tid == 0) set_status(status, DEV_NOT_SPD);
           for (int e = tid; e < 1024; e += blockDim.x) {
             const int r = e >> 5, q = e & 31;
             Dinv[(int64_t)k * 1024 + e] = (q <= r) ? Ta[q][r] : T(0);  // (L_kk^{-T})^T
@@ -342,6 +416,89 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_chol_coop(T* __
       }
     }
     if (k + 1 < Tt && !grid_barrier(bar, nb, status)) return;
+  }
+}
+
+// FP64 schedule: two phases a step, each ended by a grid barrier.
+//   P(k)  panel(k) items, tile rows k..Tt-1 of column k: the tiles already
+//         carry every update of steps < k, so an item only sweeps;
+//   U(k)  the rank-32 update of step k on every trailing lower tile (i, j),
+//         k < j <= i, split into four items of eight rows each.
+// At GB300's FP64 rate (about two FMA lanes a clock an SM) a 32 x 32 rank-32
+// tile update takes about 8 us on one SM; in k_chol_coop's one-barrier
+// schedule each panel item applied two of them (its diagonal and its own
+// tile) before its sweep, on the critical path of every step.  Here the
+// update is spread over the grid as 2 us items and the step's critical path
+// is sweep + barrier + quarter update + barrier.  Every entry goes through
+// the same operations in the same order as in k_chol_coop (the same 32-term
+// product sums, subtracted once a step), so the factor is the same bit for
+// bit.  The updated diagonal tiles are written back to L (nothing reads
+// them: the solve and the inverse use D_k).
+template <typename T>
+__global__ void __launch_bounds__(256, 1) k_chol_coop2(T* __restrict__ L, T* __restrict__ Dinv,
+                                                       int d, int dp, int Tt, unsigned* bar,
+                                                       int* status) {
+  __shared__ T Dk[32][33];
+  __shared__ T Ta[32][33];
+  __shared__ T Pq[8][33];
+  __shared__ int spd;
+  const int tid = threadIdx.x;
+  const unsigned nb = gridDim.x;
+  for (int k = 0; k < Tt; ++k) {
+    const int k0 = k * 32;
+    const int npanel = Tt - k;
+    for (int c = blockIdx.x; c < npanel; c += gridDim.x) {
+      const int i0 = (k + c) * 32;
+      for (int e = tid; e < 1024; e += blockDim.x) {
+        const int r = e >> 5, q = e & 31;
+        Dk[r][q] = __ldcg(L + (int64_t)(k0 + r) * dp + k0 + q);
+        // sweeping the identity alongside the diagonal item gives L_kk^{-T}
+        Ta[r][q] = (c > 0) ? __ldcg(L + (int64_t)(i0 + r) * dp + k0 + q) : (r == q ? T(1) : T(0));
+      }
+      __syncthreads();
+      panel_factor<T>(Dk, Ta, true, &spd, min(32, d - k0));
+      note_sweep(spd, c == 0, status);
+      if (c == 0) {
+        for (int e = tid; e < 1024; e += blockDim.x) {
+          const int r = e >> 5, q = e & 31;
+          Dinv[(int64_t)k * 1024 + e] = (q <= r) ? Ta[q][r] : T(0);  // (L_kk^{-T})^T
+        }
+      } else {
+        for (int e = tid; e < 1024; e += blockDim.x) {
+          const int a = e >> 5, b = e & 31;
+          L[(int64_t)(i0 + a) * dp + k0 + b] = Ta[a][b];
+          L[(int64_t)(k0 + a) * dp + i0 + b] = Ta[b][a];  // transpose into tile (k, i)
+        }
+      }
+      __syncthreads();
+    }
+    if (k + 1 == Tt) break;
+    if (!grid_barrier(bar, nb, status)) return;
+    // U(k): tile (i, j) = (k + 1 + ii, k + 1 + jj), rows 8 qr .. 8 qr + 7
+    const int u = Tt - k - 1;
+    const int nitems = 4 * (u * (u + 1) / 2);
+    for (int item = blockIdx.x; item < nitems; item += gridDim.x) {
+      const int q = item >> 2, qr = item & 3;
+      int ii = (int)((sqrtf(8.0f * q + 1.0f) - 1.0f) * 0.5f);
+      while ((ii + 1) * (ii + 2) / 2 <= q) ++ii;
+      while (ii * (ii + 1) / 2 > q) --ii;
+      const int jj = q - ii * (ii + 1) / 2;
+      const int i0 = (k + 1 + ii) * 32 + qr * 8, j0 = (k + 1 + jj) * 32;
+      for (int e = tid; e < 1024; e += blockDim.x) {
+        const int r = e >> 5, cc = e & 31;
+        Ta[r][cc] = __ldcg(L + (int64_t)(j0 + r) * dp + k0 + cc);  // L_{j,k}
+        if (r < 8) Pq[r][cc] = __ldcg(L + (int64_t)(i0 + r) * dp + k0 + cc);  // rows of L_{i,k}
+      }
+      __syncthreads();
+      const int a = tid >> 5, b = tid & 31;
+      T acc = T(0);
+#pragma unroll 8
+      for (int cc = 0; cc < 32; ++cc) acc += Pq[a][cc] * Ta[b][cc];
+      T* out = L + (int64_t)(i0 + a) * dp + j0 + b;
+      __stcg(out, __ldcg(out) - acc);
+      __syncthreads();
+    }
+    if (!grid_barrier(bar, nb, status)) return;
   }
 }
 
@@ -436,9 +593,9 @@ __global__ void __launch_bounds__(256) k_chol_cluster(const double* __restrict__
         __syncthreads();
         pan = Ta;
       }
-      panel_factor<T>(Dk, pan, true, &spd);
+      panel_factor<T>(Dk, pan, true, &spd, min(32, d - k0));
+      note_sweep(spd, c == 0, status);
       if (c == 0) {
-        if (!spd && tid == 0) set_status(status, DEV_NOT_SPD);
         for (int e = tid; e < 1024; e += blockDim.x) {
           const int r = e >> 5, q = e & 31;
           Dinv[(int64_t)k * 1024 + e] = (q <= r) ? Ta[q][r] : T(0);  // (L_kk^{-T})^T
@@ -544,16 +701,22 @@ static cudaError_t chol_impl(const double* H, int d, double shift, T* L, T* Dinv
   if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
   if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
     return e;
-  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_chol_coop<T>, 256, 0)) !=
-      cudaSuccess)
+  constexpr bool two_phase = sizeof(T) == 8;
+  const void* fn;
+  if constexpr (two_phase) fn = (const void*)k_chol_coop2<T>;
+  else fn = (const void*)k_chol_coop<T>;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, 256, 0)) != cudaSuccess)
     return e;
   if (per < 1) return cudaErrorCooperativeLaunchTooLarge;
   // one CTA per SM at most; no more CTAs than the largest phase has items
-  int grid = std::min(sms, std::max(Tt, Tt + (Tt - 2) * (Tt - 1) / 2));
+  const int most = two_phase ? std::max(Tt, 2 * Tt * (Tt - 1))
+                             : std::max(Tt, Tt + (Tt - 2) * (Tt - 1) / 2);
+  int grid = std::min(sms, most);
   if (max_ctas > 0) grid = std::min(grid, max_ctas);
   grid = std::max(grid, 1);
-  void* args[] = {(void*)&L, (void*)&Dinv, (void*)&dp, (void*)&Tt, (void*)&bar, (void*)&status};
-  e = cudaLaunchCooperativeKernel((const void*)k_chol_coop<T>, dim3(grid), dim3(256), args, 0, st);
+  void* args[] = {(void*)&L,  (void*)&Dinv, (void*)&d,     (void*)&dp,
+                  (void*)&Tt, (void*)&bar,  (void*)&status};
+  e = cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(256), args, 0, st);
   note_launches(1);
   if (e != cudaSuccess) return e;
   return cudaGetLastError();

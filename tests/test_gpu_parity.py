@@ -887,6 +887,26 @@ def test_l1_contexts_after_poisoned_pool_memory(cuda_lib, kind):
     assert np.array_equal(x_again, x_fresh)
 
 
+def test_pivot_rsqrt_matches_cuda_rsqrt(cuda_lib):
+    """The FP64 factor takes its pivots' reciprocal square roots by two
+    Newton-Raphson steps from an FP32 seed.  Against CUDA's rsqrt and a
+    long-double evaluation, on 200,000 values over exponents 2^-300..2^300
+    (outside FP32's range the routine falls back to rsqrt), powers of two,
+    and the ends of FP32's exponent range: within 2 ulp of both."""
+    rng = np.random.default_rng(11)
+    p = np.ldexp(1.0 + rng.random(200000), rng.integers(-300, 300, size=200000))
+    edge = [1.0, 2.0, 4.0, 0.5, 3.0, 2.0 ** -126, 2.0 ** -125 * 1.5, 2.0 ** 127,
+            2.0 ** 127 * 1.9999999, 2.0 ** 128, 2.0 ** -127, 1e-310, 1.7e308]
+    p = np.concatenate([p, np.array(edge), 2.0 ** np.arange(-200, 200, dtype=np.float64)])
+    out, ref = cuda_lib.selftest_rsqrt(torch.from_numpy(p).cuda())
+    out, ref = out.cpu().numpy(), ref.cpu().numpy()
+    ulp = np.spacing(np.abs(ref))
+    assert np.all(np.abs(out - ref) <= 2 * ulp)
+    exact = (1 / np.sqrt(p.astype(np.longdouble))).astype(np.longdouble)
+    err = np.abs(out.astype(np.longdouble) - exact) / np.spacing(np.abs(exact).astype(np.float64))
+    assert float(err.max()) <= 2.0
+
+
 def test_bounded_wait_gives_up_and_the_context_stays_usable(cuda_lib):
     """Failure detection on the GPU without a fault: a grid barrier that can
     never complete (two CTAs waiting for three) gives up after its poll limit
