@@ -16,14 +16,20 @@
 
 // CTAs of the factor that runs beside the look-ahead fused pass (the pass
 // leaves these slots free): 16 for the FP32 factor, which at d <= 512 ends
-// well within one pass on 16 SMs; 32 for the FP64 factor, whose duration on
-// GB300's FP64 units must also fit in one iteration (factors queue on one
-// stream, so the pipeline's depth buys latency, not throughput).
+// well within one pass on 16 SMs.  The FP64 factor takes a few passes' time
+// on GB300's FP64 units, so the pass of iteration t forms SA of t +
+// kFp64Depth and kFp64Depth factors run at once, each on 16 CTAs and a stream
+// of its own (on one stream they would queue, and depth would buy latency,
+// not throughput).  Measured on the 1,048,576 x 500 OLS workload (25
+// iterations): one factor stream, sorts on st2, 32 CTAs: 29.6 ms; sorts on a
+// stream of their own: 26.8 ms; two factor streams of 16 CTAs (depth 2):
+// 24.0 ms; three (depth 3, 48 slots taken from the pass): 26.5 ms.
 constexpr int kLookaheadFactorCtas = 16;
-constexpr int kLookaheadFactorCtasF64 = 32;
-// Factor buffers (H, L, D^{-1}): two in rotation, three when the look-ahead
-// pipeline runs two iterations ahead (FP64 factor).
-constexpr int kFacBufs = 3;
+constexpr int kLookaheadFactorCtasF64 = 16;
+constexpr int kFp64Depth = 2;
+// Factor buffers (H, L, D^{-1}): two in rotation, kFp64Depth + 1 when the
+// look-ahead pipeline runs kFp64Depth iterations ahead (FP64 factor).
+constexpr int kFacBufs = kFp64Depth + 1;
 
 static int64_t g_launches = 0;  // kernel launches issued by the library
 void note_launches(int k) { __atomic_add_fetch(&g_launches, (int64_t)k, __ATOMIC_RELAXED); }
@@ -65,6 +71,18 @@ struct ihs_ctx {
   cudaEvent_t ev_sa = nullptr;    // look-ahead: SA of the next counter formed
   cudaEvent_t ev_gram = nullptr;  // look-ahead: the Gram has read SA (SA free)
   cudaEvent_t ev_tail2 = nullptr; // the tail of the internal stream (joined into the caller's)
+  // FP64-factor look-ahead pipeline: a third internal stream for the sorts,
+  // so that a sort does not queue behind a factor on st2 (neither needs the
+  // other), and kFp64Depth factor streams, each with its own grid-barrier
+  // words (fbar[0] is bar); ev_s3 starts these streams after st2 and ev_fgo
+  // hands a Gram's result to a factor stream; ev_s3 and ev_fend join them
+  // back into st2 at the end of a solve
+  cudaStream_t st3 = nullptr;
+  cudaEvent_t ev_s3 = nullptr;
+  cudaStream_t fst[kFp64Depth] = {};
+  cudaEvent_t ev_fgo[kFp64Depth] = {};
+  cudaEvent_t ev_fend[kFp64Depth] = {};
+  unsigned* fbar[kFp64Depth] = {};
   bool prof = false;
   StageEvents pe;
   double prof_ms[IHS_NSTAGES] = {};
@@ -126,6 +144,7 @@ struct ihs_ctx {
   int nbuf = 2;  // factor buffers in rotation (la + 1 in the look-ahead pipeline)
   int la = 1;    // look-ahead pipeline: the pass of iteration t forms SA of t + la
   int fac_ctas = kLookaheadFactorCtas;  // look-ahead pipeline: CTAs of the factor
+  int fac_slots = kLookaheadFactorCtas;  // CTA slots the fused pass leaves to factors
   // CUDA graph of ihs_solve for launch-bound problems: the whole solve for
   // (t0, iters), captured once and replayed, on an internal copy xg of the
   // iterate so that the graph does not depend on the caller's pointer
@@ -450,6 +469,15 @@ void ihs_destroy(ihs_ctx* c) {
   if (c->ev_sa) cudaEventDestroy(c->ev_sa);
   if (c->ev_gram) cudaEventDestroy(c->ev_gram);
   if (c->ev_tail2) cudaEventDestroy(c->ev_tail2);
+  if (c->ev_s3) cudaEventDestroy(c->ev_s3);
+  for (int i = 0; i < kFp64Depth; ++i) {
+    if (c->fst[i]) {
+      cudaStreamSynchronize(c->fst[i]);
+      cudaStreamDestroy(c->fst[i]);
+    }
+    if (c->ev_fgo[i]) cudaEventDestroy(c->ev_fgo[i]);
+    if (c->ev_fend[i]) cudaEventDestroy(c->ev_fend[i]);
+  }
   for (int k = 0; k < 2; ++k) {
     if (c->ev_sort[k]) cudaEventDestroy(c->ev_sort[k]);
     if (c->ev_read[k]) cudaEventDestroy(c->ev_read[k]);
@@ -460,6 +488,10 @@ void ihs_destroy(ihs_ctx* c) {
     cudaStreamDestroy(c->gst);
   }
   if (c->st2) cudaStreamDestroy(c->st2);
+  if (c->st3) {
+    cudaStreamSynchronize(c->st3);
+    cudaStreamDestroy(c->st3);
+  }
   for (void* p : c->allocs) cudaFreeAsync(p, c->st);
   cudaStreamSynchronize(c->st);
   delete c;
@@ -578,17 +610,30 @@ ihs_status ihs_create(ihs_ctx** out, const ihs_matrix* A, const double* b,
     c->fused = !c->acc64 && !c->srht && !c->gauss && fused_supported(c->DA, c->s) &&
                !(opt->flags & IHS_FLAG_NO_FUSE);
     c->lookahead = c->fused && !(opt->flags & IHS_FLAG_NO_LOOKAHEAD);
-    // The FP64 factor on the look-ahead pipeline's 16 CTAs takes longer than
-    // one pass (GB300's FP64 rate): form SA two iterations ahead, so each
-    // factor has two passes to finish, with a third factor buffer.
+    // The FP64 factor beside the pass takes a few passes' time (GB300's FP64
+    // rate): form SA kFp64Depth iterations ahead, so each factor has that many
+    // passes to finish, with kFp64Depth factors in flight on streams of their
+    // own and kFp64Depth + 1 factor buffers.
     if (c->lookahead && !c->f32fac) {
-      c->la = 2;
-      c->nbuf = 3;
+      c->la = kFp64Depth;
+      c->nbuf = kFp64Depth + 1;
       c->fac_ctas = kLookaheadFactorCtasF64;
+      c->fac_slots = kFp64Depth * kLookaheadFactorCtasF64;
+      if (cudaStreamCreateWithFlags(&c->st3, cudaStreamNonBlocking) != cudaSuccess ||
+          cudaEventCreateWithFlags(&c->ev_s3, cudaEventDisableTiming) != cudaSuccess)
+        return fail(IHS_ERR_CUDA);
+      for (int i = 0; i < kFp64Depth; ++i) {
+        if (i > 0) AL2(c->fbar[i], 4 * sizeof(unsigned));
+        if (cudaStreamCreateWithFlags(&c->fst[i], cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&c->ev_fgo[i], cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&c->ev_fend[i], cudaEventDisableTiming) != cudaSuccess)
+          return fail(IHS_ERR_CUDA);
+      }
+      c->fbar[0] = c->bar;
     }
     // one warp per chunk; the fused pass runs two CTAs of eight warps per SM,
-    // less the SMs' share left to the factor that runs beside it
-    const int warps = c->lookahead ? (2 * c->sms - c->fac_ctas) * 8 : c->sms * 16;
+    // less the SMs' share left to the factors that run beside it
+    const int warps = c->lookahead ? (2 * c->sms - c->fac_slots) * 8 : c->sms * 16;
     c->sp = make_sort_plan((int64_t)c->s * c->n, (int)c->m, warps);
     if ((size_t)c->m * sizeof(int32_t) > 200 * 1024) return fail(IHS_ERR_UNSUPPORTED);
     AL2(c->sort_ws, sort_workspace_bytes(c->sp));
@@ -827,8 +872,8 @@ ihs_status step_with(ihs_ctx* c, double* x, int bf) {
 
 // Fused pipeline, sort half: draw and sort the pairs of counter t into sort
 // buffer pb on the internal stream, after the fused pass that last read it.
-ihs_status fused_sort(ihs_ctx* c, int64_t t, int pb) {
-  cudaStream_t s2 = (c->opt.flags & IHS_FLAG_SERIAL) ? c->st : c->st2;
+ihs_status fused_sort(ihs_ctx* c, int64_t t, int pb, cudaStream_t on = nullptr) {
+  cudaStream_t s2 = (c->opt.flags & IHS_FLAG_SERIAL) ? c->st : (on ? on : c->st2);
   CK(cudaStreamWaitEvent(s2, c->ev_read[pb], 0));
   const SketchKeys K = make_keys(c->opt.seed, t, c->s, c->m);
   stage_begin(c, IHS_ST_SORT, s2);
@@ -889,8 +934,20 @@ ihs_status fused_lookahead(ihs_ctx* c, double* x, int64_t t0, int iters) {
   for (int j = 0; j < pre; ++j)
     if ((s = sketch_chain(c, t0 + j, fb(j), fac_ctas, c->ev_gram)) != IHS_OK) return s;
   CK(cudaEventRecord(c->ev_read[0], s2));  // the sketch-only passes read sort buffer 0
+  // FP64 factors (depth kFp64Depth): the sorts on st3 and the factors going
+  // round fst[0 .. la-1], so that neither a sort nor the next factor queues
+  // behind a factor; those streams start after everything on st2 so far.
+  // Depth 1 keeps the sorts and the factors on st2 (a concurrent sort slows
+  // the pass more than it gains).
+  const bool multi = !serial && la >= 2 && c->fst[la - 1];
+  cudaStream_t s3 = multi ? c->st3 : s2;
+  if (multi) {
+    CK(cudaEventRecord(c->ev_s3, s2));
+    CK(cudaStreamWaitEvent(s3, c->ev_s3, 0));
+    for (int i = 0; i < la; ++i) CK(cudaStreamWaitEvent(c->fst[i], c->ev_s3, 0));
+  }
   for (int u = la; u < std::min(iters, la + 2); ++u)
-    if ((s = fused_sort(c, t0 + u, u & 1)) != IHS_OK) return s;
+    if ((s = fused_sort(c, t0 + u, u & 1, s3)) != IHS_OK) return s;
   // the gradient-only passes read the last counter's sort (buffer 0 when
   // every counter came from a sketch-only pass)
   const int last_pb = iters > la ? (iters - 1) & 1 : 0;
@@ -920,15 +977,32 @@ ihs_status fused_lookahead(ihs_ctx* c, double* x, int64_t t0, int iters) {
                      c->H[nb], c->status, s2));
       stage_end(c);
       CK(cudaEventRecord(c->ev_gram, s2));
-      stage_begin(c, IHS_ST_FACTOR, s2);
-      CK(launch_cholesky(c->H[nb], (int)c->d, c->f32fac, c->L[nb], c->Dinv[nb], c->bar,
-                         c->status, s2, (c->opt.flags & IHS_FLAG_CLUSTER) != 0, 0.0, fac_ctas));
+      cudaStream_t sf = s2;
+      unsigned* fbar = c->bar;
+      if (multi) {
+        const int q = k % la;
+        sf = c->fst[q];
+        fbar = c->fbar[q];
+        CK(cudaEventRecord(c->ev_fgo[q], s2));
+        CK(cudaStreamWaitEvent(sf, c->ev_fgo[q], 0));
+      }
+      stage_begin(c, IHS_ST_FACTOR, sf);
+      CK(launch_cholesky(c->H[nb], (int)c->d, c->f32fac, c->L[nb], c->Dinv[nb], fbar,
+                         c->status, sf, (c->opt.flags & IHS_FLAG_CLUSTER) != 0, 0.0, fac_ctas));
       stage_end(c);
-      CK(cudaEventRecord(c->ev_fac[nb], s2));
-      if (k + la + 2 < iters && (s = fused_sort(c, t0 + k + la + 2, pb)) != IHS_OK) return s;
+      CK(cudaEventRecord(c->ev_fac[nb], sf));
+      if (k + la + 2 < iters && (s = fused_sort(c, t0 + k + la + 2, pb, s3)) != IHS_OK) return s;
     }
     if ((s = step_with(c, x, fb(k))) != IHS_OK) return s;
     c->cur = fb(k);
+  }
+  if (multi) {  // st2 ends after the last sort and factors (every join of st2 covers them)
+    CK(cudaEventRecord(c->ev_s3, s3));
+    CK(cudaStreamWaitEvent(s2, c->ev_s3, 0));
+    for (int i = 0; i < la; ++i) {
+      CK(cudaEventRecord(c->ev_fend[i], c->fst[i]));
+      CK(cudaStreamWaitEvent(s2, c->ev_fend[i], 0));
+    }
   }
   return IHS_OK;
 }
@@ -989,11 +1063,15 @@ ihs_status issue_solve(ihs_ctx* c, double* x, int64_t t0, int iters) {
 // outside, it replaces records made inside a capture (which a wait outside
 // the graph may not name) by records ordered after the graph.
 cudaError_t record_solve_events(ihs_ctx* c, cudaStream_t st) {
-  cudaEvent_t evs[] = {c->ev_join, c->ev_grad, c->ev_sa, c->ev_gram, c->ev_tail2,
-                       c->ev_sort[0], c->ev_sort[1], c->ev_read[0], c->ev_read[1]};
+  cudaEvent_t evs[] = {c->ev_join,    c->ev_grad,    c->ev_sa,      c->ev_gram,   c->ev_tail2,
+                       c->ev_s3,      c->ev_sort[0], c->ev_sort[1], c->ev_read[0], c->ev_read[1]};
   cudaError_t e = cudaSuccess;
-  for (cudaEvent_t ev : evs)
-    if (e == cudaSuccess) e = cudaEventRecord(ev, st);
+  for (cudaEvent_t ev : evs)  // (the FP64-factor pipeline's events exist only there)
+    if (ev && e == cudaSuccess) e = cudaEventRecord(ev, st);
+  for (int i = 0; i < kFp64Depth && e == cudaSuccess; ++i) {
+    if (c->ev_fgo[i]) e = cudaEventRecord(c->ev_fgo[i], st);
+    if (c->ev_fend[i] && e == cudaSuccess) e = cudaEventRecord(c->ev_fend[i], st);
+  }
   for (int k = 0; k < kFacBufs && e == cudaSuccess; ++k) {
     e = cudaEventRecord(c->ev_fac[k], st);
     if (e == cudaSuccess) e = cudaEventRecord(c->ev_use[k], st);
