@@ -97,13 +97,19 @@ uint64_t orc_sm64_at(uint64_t state, uint64_t j) {
  * for a uniformly random row h(i) per column i of S and a sign that is +1 or
  * -1 with probability 1/2, and builds an SJLT from s independent CountSketches
  * of m/s rows each.  It names no generator; this library's reading is a
- * counter-based SplitMix64 chain:
- *     key_seed = out(seed, 0);  key_t = out(key_seed, t);  key_tk = out(key_t, k);
- *     w = out(key_tk, i)
- * where out(x, j) = orc_sm64_at(x, j).  The bucket within block k is the
- * multiply-shift range reduction of the high 32 bits, floor(hi32(w) * mb / 2^32)
- * with mb = m / s (Lemire 2019), and the sign is -1 when bit 0 of w is set.
- * The global row of S is k * mb + bucket.
+ * counter-based SplitMix64 chain, one 64-bit output per row and PAIR of
+ * blocks (2p, 2p + 1):
+ *     key_seed = out(seed, 0);  key_t = out(key_seed, t);  key_tp = out(key_t, p);
+ *     w = out(key_tp, i)
+ * where out(x, j) = orc_sm64_at(x, j).  Block 2p takes the high 32 bits of w
+ * and block 2p + 1 the low 32 bits: the bucket within the block is the
+ * multiply-shift range reduction floor(h32 * mb / 2^32) of that half, with
+ * mb = m / s (Lemire 2019), and the sign is -1 when bit 0 of the OTHER half
+ * is set (bit 0 of w for block 2p, bit 32 for block 2p + 1).  A bucket is
+ * set by its half's high bits, so a sign (the other half's lowest bit) is
+ * independent of it up to mb / 2^32.  The global row of S is k * mb + bucket.
+ * With s = 1 (CountSketch) only block 0 exists and the draw is the high half
+ * and bit 0 of w.
  *
  * Output layout: bucket[k * n + i] (int32, global row in [0, m)),
  *                sign[k * n + i]   (int8, +1 or -1).
@@ -116,15 +122,20 @@ int orc_hash(uint64_t seed, int64_t t, int s, int64_t m, int64_t n,
   if (mb > 2147483647LL) return -1;
   uint64_t key_seed = orc_sm64_at(seed, 0);
   uint64_t key_t = orc_sm64_at(key_seed, (uint64_t)t);
-  for (int k = 0; k < s; ++k) {
-    uint64_t key_tk = orc_sm64_at(key_t, (uint64_t)k);
+  for (int p = 0; 2 * p < s; ++p) {
+    uint64_t key_tp = orc_sm64_at(key_t, (uint64_t)p);
 #pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < n; ++i) {
-      uint64_t w = orc_sm64_at(key_tk, (uint64_t)i);
-      uint64_t hi = w >> 32;
-      uint64_t b = (hi * (uint64_t)mb) >> 32;
-      bucket[(int64_t)k * n + i] = (int32_t)((int64_t)k * mb + (int64_t)b);
-      sign[(int64_t)k * n + i] = (w & 1ULL) ? (int8_t)-1 : (int8_t)1;
+      uint64_t w = orc_sm64_at(key_tp, (uint64_t)i);
+      uint64_t hi = w >> 32, lo = w & 0xFFFFFFFFULL;
+      int k = 2 * p;
+      bucket[(int64_t)k * n + i] = (int32_t)((int64_t)k * mb + (int64_t)((hi * (uint64_t)mb) >> 32));
+      sign[(int64_t)k * n + i] = (lo & 1ULL) ? (int8_t)-1 : (int8_t)1;
+      if (k + 1 < s) {
+        bucket[(int64_t)(k + 1) * n + i] =
+            (int32_t)((int64_t)(k + 1) * mb + (int64_t)((lo * (uint64_t)mb) >> 32));
+        sign[(int64_t)(k + 1) * n + i] = (hi & 1ULL) ? (int8_t)-1 : (int8_t)1;
+      }
     }
   }
   return 0;

@@ -35,7 +35,8 @@ __host__ __device__ __forceinline__ uint64_t sm64_out(uint64_t state, uint64_t j
   return sm64_finalise(state + (j + 1) * kSmGamma);
 }
 
-// Keys of one sketch draw: key[k] for block k of iteration t (at most 64 blocks).
+// Keys of one sketch draw: key[p] for the block pair (2p, 2p + 1) of
+// iteration t (at most 64 blocks; the first ceil(s / 2) keys are used).
 constexpr int kMaxBlocks = 64;
 struct SketchKeys {
   uint64_t key[kMaxBlocks];
@@ -43,13 +44,32 @@ struct SketchKeys {
   int mb;  // rows per block, m / s
 };
 
-// Global row of S and sign for (block k, row i): the multiply-shift range
-// reduction of the high 32 bits, sign from bit 0.
+// The draw of Sec. 2's CountSketch / SJLT for row i (the paper names no
+// generator): one SplitMix64 output w = out(key[p], i) per row and block pair
+// (2p, 2p + 1).  Block 2p takes the high 32 bits of w, block 2p + 1 the low
+// 32 bits; a block's bucket is the multiply-shift range reduction of its
+// half, floor(h32 * mb / 2^32), and its sign is -1 when bit 0 of the other
+// half is set.  With s = 1 only block 0 exists.
+IHS_DEV int draw_bucket(uint32_t h32, int mb) {
+  return (int)(((uint64_t)h32 * (uint64_t)(uint32_t)mb) >> 32);
+}
+// Global row of S and sign for (block k, row i).
 IHS_DEV void sketch_draw(const SketchKeys& K, int k, uint64_t i, int& row, int& neg) {
-  uint64_t w = sm64_out(K.key[k], i);
-  uint32_t b = (uint32_t)(((w >> 32) * (uint64_t)(uint32_t)K.mb) >> 32);
-  row = k * K.mb + (int)b;
-  neg = (int)(w & 1ULL);
+  const uint64_t w = sm64_out(K.key[k >> 1], i);
+  const uint32_t hi = (uint32_t)(w >> 32), lo = (uint32_t)w;
+  row = k * K.mb + draw_bucket((k & 1) ? lo : hi, K.mb);
+  neg = (int)(((k & 1) ? hi : lo) & 1u);
+}
+// Both blocks of pair p for row i from one output: bucket within the block
+// (b0 for block 2p, b1 for block 2p + 1) and sign bits.
+IHS_DEV void sketch_draw_pair(const SketchKeys& K, int p, uint64_t i, int& b0, int& neg0,
+                              int& b1, int& neg1) {
+  const uint64_t w = sm64_out(K.key[p], i);
+  const uint32_t hi = (uint32_t)(w >> 32), lo = (uint32_t)w;
+  b0 = draw_bucket(hi, K.mb);
+  neg0 = (int)(lo & 1u);
+  b1 = draw_bucket(lo, K.mb);
+  neg1 = (int)(hi & 1u);
 }
 
 // ---------------------------------------------------------------------------

@@ -65,6 +65,32 @@ def test_hash_independent_across_iterations_and_blocks():
         assert abs(v - 1 / mb) < 6 * np.sqrt(1 / mb / n)
 
 
+def test_hash_block_pair_halves_independent():
+    """Blocks 2p and 2p + 1 of a row take the high and low halves of one
+    SplitMix64 output (bucket by multiply-shift of the half, sign from bit 0
+    of the other half; the paper names no generator).  They must still behave
+    as independent draws: the two buckets agree on about 1/mb of the rows, and
+    no sign is correlated with the other sign or with either bucket's upper
+    half (a sign taken from the same bits as a bucket, or two blocks taken
+    from one half, fails this)."""
+    n, m, s = 40000, 96, 6
+    mb = m // s
+    b, sg = O.hash_draw(3, 1, s, m, n)
+    tol = 6 / np.sqrt(n)
+    for p in range(s // 2):
+        k0, k1 = 2 * p, 2 * p + 1
+        u0, u1 = b[k0] - k0 * mb, b[k1] - k1 * mb
+        same = (u0 == u1).mean()
+        assert abs(same - 1 / mb) < 6 * np.sqrt(1 / mb / n)
+        s0, s1 = sg[k0].astype(float), sg[k1].astype(float)
+        h0, h1 = np.where(u0 >= mb // 2, 1.0, -1.0), np.where(u1 >= mb // 2, 1.0, -1.0)
+        for a, c in ((s0, s1), (s0, h0), (s0, h1), (s1, h0), (s1, h1)):
+            assert abs(np.mean(a * c) - np.mean(a) * np.mean(c)) < tol
+    # s = 1 keeps the high half and bit 0: the same draw as block 0 of any s
+    b1, sg1 = O.hash_draw(3, 1, 1, mb, n)
+    assert np.array_equal(b1[0], b[0]) and np.array_equal(sg1[0], sg[0])
+
+
 def test_countsketch_rows_orthogonal_lemma():
     """Lemma (orthogonal rows): S S^T is diagonal with (S S^T)_ii = N_i, the
     number of nonzeros in row i; for CountSketch sum_i N_i = n."""
