@@ -518,13 +518,19 @@ __global__ void __launch_bounds__(256) k_sketch_csc_cta(
   for (int64_t base = e0; base < e1; base += B) {
     vals[tid] = x;
 #pragma unroll
-    for (int p = 0; p < 4; ++p) {
-      if (2 * p < s) {
-        int b0, n0, b1, n1;
-        sketch_draw_pair(K, p, (uint64_t)r, b0, n0, b1, n1);
-        codes[(2 * p) * B + tid] = (uint16_t)((uint32_t)b0 | ((uint32_t)n0 << 15));
-        if (2 * p + 1 < s)
-          codes[(2 * p + 1) * B + tid] = (uint16_t)((uint32_t)b1 | ((uint32_t)n1 << 15));
+    {
+      // out(key_p, r) = mix(key_p + (r + 1) gamma): the counter term once
+      const uint64_t ig = ((uint64_t)r + 1) * kSmGamma;
+#pragma unroll
+      for (int p = 0; p < 4; ++p) {
+        if (2 * p < s) {
+          const uint64_t w = sm64_finalise(K.key[p] + ig);
+          const uint32_t hi = (uint32_t)(w >> 32), lo = (uint32_t)w;
+          codes[(2 * p) * B + tid] = (uint16_t)((uint32_t)draw_bucket(hi, mb) | ((lo & 1u) << 15));
+          if (2 * p + 1 < s)
+            codes[(2 * p + 1) * B + tid] =
+                (uint16_t)((uint32_t)draw_bucket(lo, mb) | ((hi & 1u) << 15));
+        }
       }
     }
     __syncthreads();
@@ -538,6 +544,17 @@ __global__ void __launch_bounds__(256) k_sketch_csc_cta(
     // block k over this batch, 32 entries at a time in entry order
     const int nbt = (int)((e1 - base < (int64_t)B) ? (e1 - base) : (int64_t)B);
     const uint16_t* ck = codes + k * B;
+    if constexpr (MODE == 2 && sizeof(Tin) == 4) {
+      if (nbt == B) {  // a full batch: every lane valid, sign as a sign-bit flip
+        for (int q = lane; q < B; q += 32) {
+          const uint32_t c = ck[q];
+          const float v = __uint_as_float(__float_as_uint((float)vals[q]) ^ ((c & 0x8000u) << 16));
+          atomicAdd(reinterpret_cast<float*>(acc) + (c & 0x7fffu), v);
+        }
+        __syncthreads();
+        continue;
+      }
+    }
     for (int q = 0; q < nbt; q += 32) {
       const int idx = q + lane;
       const bool valid = idx < nbt;
