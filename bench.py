@@ -253,7 +253,7 @@ def iterations_to(solver, xo, G, tol, cap=80):
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("sketch.cu", "grad.cu", "fused.cu", "common.cuh", "hash_sort.cu"):
+    for f in ("fused.cu", "common.cuh"):  # the fused pass's source and its inline helpers
         h.update(open(os.path.join(ROOT, "paper_1910_14166_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 

@@ -169,7 +169,9 @@ enum {
  * is bound by launches, not by the data) replays each ihs_solve as a CUDA
  * graph: captured on the first call with a given (t0, iters), on an internal
  * copy of the iterate, and launched as one unit afterwards (the p = 2 ball,
- * whose step reads scalars on the host, and IHS_FLAG_SERIAL never are).
+ * whose step reads scalars on the host, the l1 penalty, whose one-CTA step
+ * kernels must be issued ahead of the sketch chain's full-width kernels to
+ * get an SM, and IHS_FLAG_SERIAL never are).
  * Same kernels in the same order, so the same results.  This flag turns it
  * off.  ihs_report.graph tells whether a solve ran as a graph; if a capture
  * fails, the context falls back to issuing on its streams for good. */

@@ -922,6 +922,21 @@ def test_bounded_wait_gives_up_and_the_context_stays_usable(cuda_lib):
     assert np.abs(x.cpu().numpy() - xs[-1]).max() <= 1e-12 * np.abs(xs[-1]).max()
 
 
+def test_graph_not_used_for_l2_ball_and_l1_penalty(cuda_lib):
+    """The p = 2 ball (its step reads scalars on the host) and the l1 penalty
+    (its one-CTA step kernels need to be issued ahead of the sketch chain)
+    run on the streams even for a small A; the ball and OLS forms of the same
+    data replay graphs."""
+    w, C = _csr_problem("lasso_csr_fp64", 30000, 60, 600)
+    args = ((dev(w["rowptr"]), dev(w["col"]), dev(w["val"])), dev(w["b"]))
+    base = dict(m=600, s=4, precision="fp64", shape=(w["n"], w["d"]))
+    for kind, param, graph in (("l1pen", 1.0, 0), ("l2", 0.5, 0), ("l1", w["param"], 1)):
+        sv = cuda_lib.IHS(*args, kind=kind, param=param, **base)
+        for _ in range(2):
+            _, rep = sv.solve(iters=3)
+            assert rep.status == 0 and rep.graph == graph, (kind, rep.graph)
+
+
 @pytest.mark.parametrize("case", ["ols_fp64", "l1_csr_fp64", "ols_tf32_lookahead", "ridge_fp64"])
 def test_graph_solve_matches_stream_solve(cuda_lib, case):
     """Launch-bound contexts (A up to 128 MB) replay ihs_solve as a CUDA
