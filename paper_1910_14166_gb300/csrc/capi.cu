@@ -79,6 +79,10 @@ struct ihs_ctx {
   // back into st2 at the end of a solve
   cudaStream_t st3 = nullptr;
   cudaEvent_t ev_s3 = nullptr;
+  // the in-order (non-fused) pipeline: the chain's factor on a stream of its
+  // own, so that the next chain's sketch does not queue behind it
+  cudaStream_t fchain = nullptr;
+  cudaEvent_t ev_fc_go = nullptr, ev_fc_end = nullptr;
   cudaStream_t fst[kFp64Depth] = {};
   cudaEvent_t ev_fgo[kFp64Depth] = {};
   cudaEvent_t ev_fend[kFp64Depth] = {};
@@ -470,6 +474,12 @@ void ihs_destroy(ihs_ctx* c) {
   if (c->ev_gram) cudaEventDestroy(c->ev_gram);
   if (c->ev_tail2) cudaEventDestroy(c->ev_tail2);
   if (c->ev_s3) cudaEventDestroy(c->ev_s3);
+  if (c->ev_fc_go) cudaEventDestroy(c->ev_fc_go);
+  if (c->ev_fc_end) cudaEventDestroy(c->ev_fc_end);
+  if (c->fchain) {
+    cudaStreamSynchronize(c->fchain);
+    cudaStreamDestroy(c->fchain);
+  }
   for (int i = 0; i < kFp64Depth; ++i) {
     if (c->fst[i]) {
       cudaStreamSynchronize(c->fst[i]);
@@ -561,7 +571,10 @@ ihs_status ihs_create(ihs_ctx** out, const ihs_matrix* A, const double* b,
   do {                                                    \
     if ((s = dalloc(c, &(ptr), (size_t)(bytes))) != IHS_OK) return fail(s); \
   } while (0)
-  if (cudaStreamCreateWithFlags(&c->st2, cudaStreamNonBlocking) != cudaSuccess)
+  if (cudaStreamCreateWithFlags(&c->st2, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&c->fchain, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_fc_go, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->ev_fc_end, cudaEventDisableTiming) != cudaSuccess)
     return fail(IHS_ERR_CUDA);
   for (int k = 0; k < kFacBufs; ++k) {
     if (cudaEventCreateWithFlags(&c->ev_fac[k], cudaEventDisableTiming) != cudaSuccess ||
@@ -732,9 +745,11 @@ int next_buf(const ihs_ctx* c, int b) { return (b + 1) % c->nbuf; }
 // draw S and sort (dense), SA, Gram (+ lambda I), Cholesky factor.  Waits
 // for the last step that read buffer `bf`; records ev_fac[bf] (and
 // after_gram, if given, once the Gram has read SA).  fac_ctas > 0 caps the
-// factor's grid.
+// factor's grid.  fstream, if given, takes the factor (after the Gram), so
+// that the internal stream is free for the next chain's sketch; ev_fac[bf]
+// is then recorded there.
 ihs_status sketch_chain(ihs_ctx* c, int64_t t, int bf, int fac_ctas = 0,
-                        cudaEvent_t after_gram = nullptr) {
+                        cudaEvent_t after_gram = nullptr, cudaStream_t fstream = nullptr) {
   cudaStream_t s2 = (c->opt.flags & IHS_FLAG_SERIAL) ? c->st : c->st2;
   CK(cudaStreamWaitEvent(s2, c->ev_use[bf], 0));
   const SketchKeys K = make_keys(c->opt.seed, t, c->s, c->m);
@@ -767,11 +782,17 @@ ihs_status sketch_chain(ihs_ctx* c, int64_t t, int bf, int fac_ctas = 0,
                  c->status, s2));
   stage_end(c);
   if (after_gram) CK(cudaEventRecord(after_gram, s2));
-  stage_begin(c, IHS_ST_FACTOR, s2);
+  cudaStream_t sf = s2;
+  if (fstream) {
+    CK(cudaEventRecord(c->ev_fc_go, s2));
+    CK(cudaStreamWaitEvent(fstream, c->ev_fc_go, 0));
+    sf = fstream;
+  }
+  stage_begin(c, IHS_ST_FACTOR, sf);
   CK(launch_cholesky(c->H[bf], (int)c->d, c->f32fac, c->L[bf], c->Dinv[bf], c->bar, c->status,
-                     s2, (c->opt.flags & IHS_FLAG_CLUSTER) != 0, 0.0, fac_ctas));
+                     sf, (c->opt.flags & IHS_FLAG_CLUSTER) != 0, 0.0, fac_ctas));
   stage_end(c);
-  CK(cudaEventRecord(c->ev_fac[bf], s2));
+  CK(cudaEventRecord(c->ev_fac[bf], sf));
   return IHS_OK;
 }
 
@@ -1038,12 +1059,16 @@ ihs_status issue_solve(ihs_ctx* c, double* x, int64_t t0, int iters) {
     c->have_sketch = true;
   } else if (iters > 0) {
     if ((s = join_caller(c)) != IHS_OK) return s;
+    // the factors on their own stream (joined back into st2 at the end)
+    cudaStream_t fs = (c->opt.flags & IHS_FLAG_SERIAL) ? nullptr : c->fchain;
     int bf = next_buf(c, c->cur);
-    if ((s = sketch_chain(c, t0, bf)) != IHS_OK) return s;
+    if ((s = sketch_chain(c, t0, bf, 0, nullptr, fs)) != IHS_OK) return s;
     // The chain of t+1 starts once the gradient pass of t is done, and is
     // issued after the step of t: a gradient pass sharing the GPU with a
     // full-width sketch kernel runs several times slower, and the one-CTA
-    // l1 step needs a whole SM, which it gets only if launched first.
+    // l1 step needs a whole SM, which it gets only if launched first
+    // (measured again with the one-CTA-per-chunk CSC sketch: without this
+    // wait the 1e7 x 1000 LASSO solve takes 65.9 ms against 42.5 ms).
     for (int k = 0; k < iters; ++k) {
       stage_begin(c, IHS_ST_GRAD, c->st);
       s = gradient_on(c, x, c->g, nullptr, true);
@@ -1053,10 +1078,15 @@ ihs_status issue_solve(ihs_ctx* c, double* x, int64_t t0, int iters) {
       if ((s = step_with(c, x, bf)) != IHS_OK) return s;
       if (k + 1 < iters) {
         CK(cudaStreamWaitEvent(c->st2, c->ev_grad, 0));
-        if ((s = sketch_chain(c, t0 + k + 1, next_buf(c, bf))) != IHS_OK) return s;
+        if ((s = sketch_chain(c, t0 + k + 1, next_buf(c, bf), 0, nullptr, fs)) != IHS_OK)
+          return s;
       }
       c->cur = bf;
       bf = next_buf(c, bf);
+    }
+    if (fs) {
+      CK(cudaEventRecord(c->ev_fc_end, fs));
+      CK(cudaStreamWaitEvent(c->st2, c->ev_fc_end, 0));
     }
     c->have_sketch = true;
   }
@@ -1069,7 +1099,8 @@ ihs_status issue_solve(ihs_ctx* c, double* x, int64_t t0, int iters) {
 // the graph may not name) by records ordered after the graph.
 cudaError_t record_solve_events(ihs_ctx* c, cudaStream_t st) {
   cudaEvent_t evs[] = {c->ev_join,    c->ev_grad,    c->ev_sa,      c->ev_gram,   c->ev_tail2,
-                       c->ev_s3,      c->ev_sort[0], c->ev_sort[1], c->ev_read[0], c->ev_read[1]};
+                       c->ev_s3,      c->ev_sort[0], c->ev_sort[1], c->ev_read[0], c->ev_read[1],
+                       c->ev_fc_go,   c->ev_fc_end};
   cudaError_t e = cudaSuccess;
   for (cudaEvent_t ev : evs)  // (the FP64-factor pipeline's events exist only there)
     if (ev && e == cudaSuccess) e = cudaEventRecord(ev, st);

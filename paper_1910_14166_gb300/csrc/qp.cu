@@ -30,6 +30,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 
 #include "internal.h"
@@ -85,15 +86,121 @@ struct QpShared {
   float redf[33];
 };
 
-// y = Hf * v (FP32, warp per row)
-__device__ void matvec_f(const float* __restrict__ Hf, int d, const float* v, float* out) {
+// ---- the FP32 product Hf v, on one CTA or spread over a cluster ----------
+// One CTA reads the d x d matrix (4 MB at d = 1000) from L2 for every product
+// at about 64 bytes a clock, some 30 us a product, and the l1 step's power
+// iteration and FISTA take tens to hundreds of them.  When the step is
+// launched as a thread-block cluster, rank 0 runs the step alone and the
+// other CTAs only serve its products: rank 0 posts the command (the shared
+// addresses of v and out) and meets the cluster at a barrier; every CTA then
+// computes a contiguous slice of the rows, the helpers reading v from rank
+// 0's shared memory and storing their results into rank 0's out through
+// distributed shared memory, and a second barrier publishes them.  Each row
+// is still summed by one warp in the same order, so a product is the same
+// bit for bit on one CTA or on a cluster.  Rank 0 posts an exit command when
+// its step ends, whichever way it ends, and stays resident through one more
+// barrier, until every helper has read it.  Every barrier is passed by every
+// thread of every CTA: rank 0 calls matvec_f (two barriers) only from
+// block-uniform code, and the exit takes two barriers on both sides.
+struct MvCmd {
+  int op;  // 1: product, 0: exit
+  uint32_t v_off, out_off;  // shared-window addresses of v and out in rank 0
+};
+__shared__ MvCmd g_mvcmd;
+
+IHS_DEV uint32_t cl_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+IHS_DEV uint32_t cl_size() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+  return r;
+}
+// Every thread of every CTA of the cluster arrives (release) and waits (acquire).
+IHS_DEV void cl_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::
+                   : "memory");
+}
+// A shared-window address of this CTA mapped to the same offset in CTA `rank`.
+IHS_DEV uint32_t cl_map(uint32_t addr, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
+  return r;
+}
+IHS_DEV float cl_ld_f32(uint32_t a) {
+  float v;
+  asm volatile("ld.shared::cluster.f32 %0, [%1];" : "=f"(v) : "r"(a) : "memory");
+  return v;
+}
+IHS_DEV uint32_t cl_ld_u32(uint32_t a) {
+  uint32_t v;
+  asm volatile("ld.shared::cluster.u32 %0, [%1];" : "=r"(v) : "r"(a) : "memory");
+  return v;
+}
+IHS_DEV void cl_st_f32(uint32_t a, float v) {
+  asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(a), "f"(v) : "memory");
+}
+
+// Rows [r0, r1) of Hf v, a warp a row, v in this CTA's shared memory.
+__device__ void matvec_rows(const float* __restrict__ Hf, int d, const float* v, int r0, int r1,
+                            float* out) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  for (int i = w; i < d; i += (int)(blockDim.x >> 5)) {
+  for (int i = r0 + w; i < r1; i += (int)(blockDim.x >> 5)) {
     const float* row = Hf + (int64_t)i * d;
     float s = 0.f;
     for (int j = lane; j < d; j += 32) s = fmaf(row[j], v[j], s);
     s = warp_sum(s);
     if (lane == 0) out[i] = s;
+  }
+}
+
+// y = Hf * v (FP32, warp per row).  All threads of the CTA call it; in a
+// cluster launch only rank 0 runs the step and calls it (see above).
+__device__ void matvec_f(const float* __restrict__ Hf, int d, const float* v, float* out) {
+  const int C = (int)cl_size();
+  if (C == 1) {
+    matvec_rows(Hf, d, v, 0, d, out);
+    return;
+  }
+  if (threadIdx.x == 0) g_mvcmd = MvCmd{1, smem_u32(v), smem_u32(out)};
+  cl_sync();  // the command and v are visible to the helpers
+  matvec_rows(Hf, d, v, 0, (int)((int64_t)d / C), out);
+  cl_sync();  // every slice of out is written
+}
+
+// The helpers' side (ranks 1 .. C-1): serve rank 0's products until it exits.
+__device__ void matvec_helper(const float* __restrict__ Hf, int d) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t c = cl_rank(), C = cl_size();
+  const int r0 = (int)((int64_t)d * c / C), r1 = (int)((int64_t)d * (c + 1) / C);
+  const uint32_t cmd0 = cl_map(smem_u32(&g_mvcmd), 0);
+  for (;;) {
+    cl_sync();  // a command is posted
+    if (cl_ld_u32(cmd0) == 0u) {
+      cl_sync();  // rank 0 stays resident until every helper has read it
+      break;
+    }
+    const uint32_t v0 = cl_map(cl_ld_u32(cmd0 + 4), 0), out0 = cl_map(cl_ld_u32(cmd0 + 8), 0);
+    // lane l keeps v[l + 32 q] (read from rank 0) in vr[q]; each row is
+    // summed in the same order as matvec_rows
+    float vr[32];
+#pragma unroll
+    for (int q = 0; q < 32; ++q)
+      vr[q] = (lane + 32 * q < d) ? cl_ld_f32(v0 + 4u * (uint32_t)(lane + 32 * q)) : 0.f;
+    for (int i = r0 + (int)(threadIdx.x >> 5); i < r1; i += (int)(blockDim.x >> 5)) {
+      const float* row = Hf + (int64_t)i * d;
+      float s = 0.f;
+#pragma unroll
+      for (int q = 0; q < 32; ++q) {
+        const int j = lane + 32 * q;
+        if (j < d) s = fmaf(row[j], vr[q], s);
+      }
+      s = warp_sum(s);
+      if (lane == 0) cl_st_f32(out0 + 4u * (uint32_t)i, s);
+    }
+    cl_sync();  // this slice of out is written
   }
 }
 
@@ -496,7 +603,7 @@ __device__ unsigned long long support_of(const float* v, int d, QpShared& sh) {
 }
 
 template <typename TF>
-__global__ void __launch_bounds__(kQpThreads, 1) k_l1_step(
+__device__ void l1_step_body(
     const double* __restrict__ H, const float* __restrict__ Hf, int d,
     const double* __restrict__ g, const double* __restrict__ du, const double* __restrict__ uvec,
     double R, int pen, int phase, int* __restrict__ need, int max_iter,
@@ -701,6 +808,32 @@ __global__ void __launch_bounds__(kQpThreads, 1) k_l1_step(
   __syncthreads();
   qp_epilogue(x, sh.xt, d, R, pen, step_norm, support, sh.redd);
   if (threadIdx.x == 0 && need) *need = 0;
+}
+
+// The l1 step: one CTA, or a cluster whose ranks 1 .. C-1 only serve rank
+// 0's FP32 products (matvec_f).  Rank 0 posts the exit command once the step
+// has ended, on every path out of l1_step_body.
+template <typename TF>
+__global__ void __launch_bounds__(kQpThreads, 1) k_l1_step(
+    const double* __restrict__ H, const float* __restrict__ Hf, int d,
+    const double* __restrict__ g, const double* __restrict__ du, const double* __restrict__ uvec,
+    double R, int pen, int phase, int* __restrict__ need, int max_iter,
+    double tol, double* __restrict__ x, double* __restrict__ step_norm, int* __restrict__ support,
+    int* __restrict__ iters, double* __restrict__ wv, TF* __restrict__ Ls, int ld,
+    float* __restrict__ evec, int* status) {
+  const bool clustered = cl_size() > 1;
+  if (clustered && cl_rank() != 0) {
+    matvec_helper(Hf, d);
+    return;
+  }
+  l1_step_body<TF>(H, Hf, d, g, du, uvec, R, pen, phase, need, max_iter, tol, x, step_norm,
+                   support, iters, wv, Ls, ld, evec, status);
+  if (clustered) {
+    __syncthreads();
+    if (threadIdx.x == 0) g_mvcmd.op = 0;
+    cl_sync();  // the exit command is posted
+    cl_sync();  // every helper has read it (rank 0's shared memory stays valid until then)
+  }
 }
 
 // ----------------------------------------------------------------------------
@@ -924,6 +1057,70 @@ __global__ void k_to_float(const double* __restrict__ a, int64_t n, float* __res
     b[i] = (float)a[i];
 }
 
+// The l1 step's launch: for d >= kL1ClusterMinD a cluster of kL1Cluster
+// CTAs (one SM each), rank 0 running the step and the others serving its
+// FP32 products, where this GPU can hold such a cluster at this shared-memory
+// size (checked once per device and size class); one CTA otherwise.
+constexpr int kL1Cluster = 8;
+constexpr int kL1ClusterMinD = 512;
+
+template <typename TF, typename... Args>
+static cudaError_t launch_l1_kernel(size_t smem, int d, cudaStream_t st, Args... args) {
+  const void* fn = (const void*)k_l1_step<TF>;
+  cudaError_t e = ensure_smem(fn, (int)smem);
+  if (e != cudaSuccess) return e;
+  int C = 1;
+  if (d >= kL1ClusterMinD) {
+    static std::atomic<int> ok_dev[64][2];  // [device][TF is double]: 0 unknown, 1 yes, 2 no
+    int dev = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    const int ti = sizeof(TF) == 8 ? 1 : 0;
+    if (dev < 64) {
+      if (ok_dev[dev][ti].load() == 0) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(kL1Cluster);
+        cfg.blockDim = dim3(kQpThreads);
+        cfg.dynamicSmemBytes = smem;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = kL1Cluster;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        int nclusters = 0;
+        const cudaError_t q = cudaOccupancyMaxActiveClusters(&nclusters, k_l1_step<TF>, &cfg);
+        if (q != cudaSuccess) cudaGetLastError();
+        ok_dev[dev][ti].store(q == cudaSuccess && nclusters >= 1 ? 1 : 2);
+      }
+      if (ok_dev[dev][ti].load() == 1) C = kL1Cluster;
+    }
+  }
+  // The step is on the solve's critical path while the next iteration's
+  // sketch chain runs beside it: launch it at the device's highest priority,
+  // so that SMs freed by the chain's kernels go to the step first.
+  int lo = 0, hi = 0;
+  if ((e = cudaDeviceGetStreamPriorityRange(&lo, &hi)) != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(C);
+  cfg.blockDim = dim3(kQpThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[2];
+  at[0].id = cudaLaunchAttributePriority;
+  at[0].val.priority = hi;
+  at[1].id = cudaLaunchAttributeClusterDimension;
+  at[1].val.clusterDim.x = C;
+  at[1].val.clusterDim.y = 1;
+  at[1].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = C > 1 ? 2 : 1;
+  e = cudaLaunchKernelEx(&cfg, k_l1_step<TF>, args...);
+  note_launches(1);
+  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
 cudaError_t launch_l1_step(const double* H, const void* Lbuf, const void* Dinv, int f32, int d,
                            const double* g,
                            double R, int pen, int max_iter, double tol, QpWork w, double* x,
@@ -957,22 +1154,15 @@ cudaError_t launch_l1_step(const double* H, const void* Lbuf, const void* Dinv, 
   // phase 1 (FISTA) -- each of the later ones exits at once if the step is done
   const bool active = pen && w.Hinv && chol_inverse_smem_bytes(d, f32) <= 220 * 1024;
   auto l1 = [&](int phase) -> cudaError_t {
-    cudaError_t e2;
-    if (f32) {
-      if ((e2 = ensure_smem((const void*)k_l1_step<float>, (int)smem)) != cudaSuccess) return e2;
-      k_l1_step<float><<<1, kQpThreads, smem, st>>>(H, w.Hf, d, g, du, uvec, R, pen, phase, need,
-                                                    max_iter, tl, x, step_norm, w.support, w.iters,
-                                                    wv, (float*)w.Ls, ld, w.evec, status);
-    } else {
-      if ((e2 = ensure_smem((const void*)k_l1_step<double>, (int)smem)) != cudaSuccess)
-        return e2;
-      k_l1_step<double><<<1, kQpThreads, smem, st>>>(H, w.Hf, d, g, du, uvec, R, pen, phase, need,
-                                                     max_iter, tl, x, step_norm, w.support,
-                                                     w.iters, wv, (double*)w.Ls, ld, w.evec,
-                                                     status);
-    }
-    note_launches(1);
-    return cudaGetLastError();
+    if (f32)
+      return launch_l1_kernel<float>(smem, d, st, H, (const float*)w.Hf, d, g, (const double*)du,
+                                     (const double*)uvec, R, pen, phase, need, max_iter, tl, x,
+                                     step_norm, w.support, w.iters, wv, (float*)w.Ls, ld, w.evec,
+                                     status);
+    return launch_l1_kernel<double>(smem, d, st, H, (const float*)w.Hf, d, g, (const double*)du,
+                                    (const double*)uvec, R, pen, phase, need, max_iter, tl, x,
+                                    step_norm, w.support, w.iters, wv, (double*)w.Ls, ld, w.evec,
+                                    status);
   };
   if ((e = l1(0)) != cudaSuccess) return e;
   if (!pen) return cudaSuccess;

@@ -287,13 +287,16 @@ def _csr_problem(name, n, d, m, seed=0):
     return w, C
 
 
-def test_l1_qp_step_matches_oracle_qp(cuda_lib):
+@pytest.mark.parametrize("n,d,m", [(40000, 60, 600), (120000, 600, 3000)])
+def test_l1_qp_step_matches_oracle_qp(cuda_lib, n, d, m):
     """One l1-ball step of Eq. 2 on the GPU equals the oracle's exact QP on the
-    same H and g (from the same sketch): the QP solution is unique."""
-    w, C = _csr_problem("lasso_csr_fp64", 40000, 60, 600)
+    same H and g (from the same sketch): the QP solution is unique.  At
+    d = 600 the step runs as a thread-block cluster whose helper CTAs form
+    the FP32 products of the power iteration and FISTA."""
+    w, C = _csr_problem("lasso_csr_fp64", n, d, m)
     R = w["param"]
     solver = cuda_lib.IHS((dev(w["rowptr"]), dev(w["col"]), dev(w["val"])), dev(w["b"]), kind="l1",
-                          param=R, m=600, s=4, seed=0, precision="fp64", shape=(w["n"], w["d"]))
+                          param=R, m=m, s=4, seed=0, precision="fp64", shape=(w["n"], w["d"]))
     x = torch.zeros(w["d"], dtype=torch.float64, device="cuda")
     xo = np.zeros(w["d"])
     for t in range(4):
