@@ -632,7 +632,7 @@ def c5_record(ihs, hbm):
             "iters": iters, "solve_ms_median": round(statistics.median(times), 3),
             "solve_ms_all": [round(t, 3) for t in times], "status": int(rep.status),
             "create_ms": round(create_ms, 1),
-            "sketch_kernel": "k_sketch_csc (+ k_sketch_csc_merge)",
+            "sketch_kernel": "k_sketch_csc_cta (+ k_sketch_csc_merge)",
             "sketch_ms": round(sk, 4),
             "sketch_algorithmic_bytes": alg,
             "sketch_GB_s": round(alg / (sk * 1e-3) / 1e9, 1),
