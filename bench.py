@@ -680,6 +680,44 @@ def run_reference(args, rank, world):
     }
 
 
+def run_oracle_timing(args):
+    """The FP64 oracle timed on this host's cores, config by config: the
+    20000 x 50 OLS and 1,000,000 x 200 LASSO solves in full; the
+    1,048,576 x 500 OLS, 262,144 x 256 ridge and 10,000,000 x 1000 LASSO ones
+    over their first two iterations, extrapolated to the iteration count (an
+    iteration's cost does not depend on t).  Each runs on one thread and on
+    every host core (the OpenMP build of the oracle's C loops, bit-identical
+    results); the l1 QP and the d x d solves are numpy's, on whatever threads
+    its BLAS uses.  One JSON line per (workload, threads)."""
+    import oracle as O
+    cores, model = host_cpu()
+    plan = [("ols_dense_fp64", None), ("lasso_csr_fp64", None), ("ols_dense_ar1", 2),
+            ("ridge_dense", 2), ("lasso_csr_zipf", 2)]
+    if args.only:
+        plan = [p for p in plan if p[0] in args.only.split(",")]
+    for name, part in plan:
+        w = synth.make(name, seed=0)
+        if "A" in w:
+            A = np.ascontiguousarray(w["A"], dtype=np.float64)
+        else:
+            A = O.CSR(w["n"], w["d"], w["rowptr"], w["col"], np.asarray(w["val"], dtype=np.float64))
+        kind = {"ols": O.OLS, "l1": O.L1_BALL, "ridge": O.RIDGE}[w["kind"]]
+        T = w["iters"] or 25
+        run = T if part is None else part
+        for threads in sorted({1, cores}):
+            used = O.use_threads(threads)
+            t0 = time.perf_counter()
+            O.ihs(A, w["b"], kind, w["param"], w["m"], w["s"], 0, run)
+            sec = time.perf_counter() - t0
+            print(json.dumps({
+                "experiment": "oracle_timing", "workload": name, "n": w["n"], "d": w["d"],
+                "m": w["m"], "s": w["s"], "threads": used, "host_cores": cores, "cpu_model": model,
+                "iters_run": run, "iters_total": T, "ms_per_iter": round(sec * 1e3 / run, 1),
+                "ms_solve": round(sec * 1e3 / run * T, 1),
+                "how": "measured whole solve" if part is None else "two iterations, extrapolated"}),
+                flush=True)
+
+
 def run_iters_only(args):
     """Profiling driver: create the solver on the workload and run exactly
     args.ncu_iters iterations (no x_OPT, no timing).  Used under ncu."""
@@ -916,7 +954,7 @@ def main():
                     help="seconds of oracle iterations the CPU baseline may run (whole solve "
                          "when it fits)")
     ap.add_argument("--only", default=None, help="workloads experiment: comma-separated names")
-    ap.add_argument("--experiment", default=None, choices=["sketch-quality", "workloads", "adjoint", "c5"],
+    ap.add_argument("--experiment", default=None, choices=["sketch-quality", "workloads", "adjoint", "c5", "oracle-timing"],
                     help="run an experiment instead of the benchmark (one JSON line per point)")
     ap.add_argument("--trials", type=int, default=10)
     ap.add_argument("--families", default=None,
@@ -941,6 +979,9 @@ def main():
         return
     if args.experiment == "adjoint":
         run_adjoint(args)
+        return
+    if args.experiment == "oracle-timing":
+        run_oracle_timing(args)
         return
     if args.experiment == "c5":  # the large sparse LASSO record of the main line, alone
         import paper_1910_14166_gb300 as ihs

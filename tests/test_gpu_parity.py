@@ -79,14 +79,18 @@ def test_sketch_dense(cuda_lib, n, d, m, s, dt, prec):
     (np.float64, "fp64", 4, 30011, 40, 400), (np.float32, "tf32", 8, 30011, 40, 400),
     (np.float64, "fp64", 1, 30011, 40, 400), (np.float64, "fp64", 2, 30011, 40, 400),
     (np.float64, "fp64", 3, 30011, 40, 402), (np.float64, "fp64", 8, 100003, 8, 800),
-    (np.float32, "tf32", 1, 30011, 40, 40000)])
+    (np.float32, "tf32", 1, 30011, 40, 40000), (np.float64, "fp64", 8, 30011, 40, 10000),
+    (np.float32, "tf32", 2, 30011, 40, 80000)])
 def test_sketch_csr(cuda_lib, dt, prec, s, n, d, m):
     """CSR sketch through the column copy; FP64 exact vs the oracle's
     ascending-row order.  Cases cover s = 1, 2, 3, 4, 8, columns split into
     several items (100003 rows over 8 columns: partial columns merged in
     item order, so a bucket's sum is associated by item and agrees with the
-    oracle's entry-by-entry sum to rounding), and m/s = 40000 buckets (one
-    warp's accumulator fills the shared memory of its CTA)."""
+    oracle's entry-by-entry sum to rounding), m/s = 40000 buckets (one
+    warp's accumulator fills the shared memory of its CTA; with s = 2 this
+    is the one-warp-per-block kernel taking its half of the pair draw), and
+    FP64 with 1250 buckets a block (the one-CTA-per-chunk kernel with byte
+    tags, bit for bit)."""
     rowptr, col, val = synth.csr_uniform(n, d, 3, 1, dt)
     b = np.random.default_rng(0).standard_normal(n)
     solver = cuda_lib.IHS((dev(rowptr), dev(col), dev(val)), dev(b), m=m, s=s, seed=9,
