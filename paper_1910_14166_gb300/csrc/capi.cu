@@ -23,7 +23,8 @@
 // not throughput).  Measured on the 1,048,576 x 500 OLS workload (25
 // iterations): one factor stream, sorts on st2, 32 CTAs: 29.6 ms; sorts on a
 // stream of their own: 26.8 ms; two factor streams of 16 CTAs (depth 2):
-// 24.0 ms; three (depth 3, 48 slots taken from the pass): 26.5 ms.
+// 24.0 ms; three (depth 3, 48 slots taken from the pass): 26.5 ms; three of
+// 11 CTAs (33 slots): 27.0 ms.
 constexpr int kLookaheadFactorCtas = 16;
 constexpr int kLookaheadFactorCtasF64 = 16;
 constexpr int kFp64Depth = 2;
