@@ -14,11 +14,15 @@
 // accumulation keeps whole buckets per warp (k_sketch_dense_units) so the
 // result is bit-identical to the sequential definition.
 //
-// CSR A: a column-major (CSC) copy is built once at create.  One warp owns
-// (column chunk, SJLT block k) and keeps that block's m/s accumulators in
-// shared memory; entries arrive in ascending row order, buckets are drawn
-// on the fly, and lanes that hit the same bucket add in lane (= row) order
-// through __match_any_sync rounds, so again no atomics and a fixed order.
+// CSR A: a column-major (CSC) copy is built once at create.  For 2 <= s <= 8
+// one CTA of s warps owns a column chunk: each thread loads one entry and
+// draws its row once per SJLT block pair (two blocks per SplitMix64 output),
+// and warp k keeps block k's m/s accumulators in shared memory
+// (k_sketch_csc_cta).  Otherwise one warp owns (column chunk, block k)
+// (k_sketch_csc).  Entries arrive in ascending row order.  FP64 accumulators
+// add lanes that hit the same bucket in lane (= row) order, so the sums have
+// the sequential order; FP32 accumulators use shared-memory atomic adds, in
+// a warp-private accumulator (see warp_bucket_add).
 #include <cuda_runtime.h>
 
 #include <algorithm>
