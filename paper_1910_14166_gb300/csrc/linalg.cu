@@ -754,33 +754,106 @@ __global__ void __launch_bounds__(1024) k_chol_solve(const T* __restrict__ L,
     for (int e = tid; e < Tt * 1024; e += blockDim.x) Ds[e] = Dinv[e];
   const T* Dk = dinv_in_smem ? Ds : Dinv;
   __syncthreads();
-  // forward: y_k = D_k (v_k - sum_{j < k} L_kj y_j)
-  for (int k = 0; k < Tt; ++k) {
-    const int k0 = k * 32, r = k0 + w;
-    const T* Lr = L + (int64_t)r * dp;
-    T s = T(0);
-    for (int c = lane; c < k0; c += 32) s += Lr[c] * y[c];
-    s = warp_sum(s);
-    if (lane == 0) t[w] = y[r] - s;
-    __syncthreads();
-    T yv = Dk[(int64_t)k * 1024 + w * 32 + lane] * t[lane];
-    yv = warp_sum(yv);
-    if (lane == 0) y[r] = yv;
-    __syncthreads();
-  }
-  // backward: z_k = D_k^T (y_k - sum_{j > k} (L^T)_kj z_j), (L^T)_kj stored in tile (k, j)
-  for (int k = Tt - 1; k >= 0; --k) {
-    const int k0 = k * 32, r = k0 + w;
-    const T* Ur = L + (int64_t)r * dp;
-    T s = T(0);
-    for (int c = k0 + 32 + lane; c < dp; c += 32) s += Ur[c] * y[c];
-    s = warp_sum(s);
-    if (lane == 0) t[w] = y[r] - s;
-    __syncthreads();
-    T zv = Dk[(int64_t)k * 1024 + lane * 32 + w] * t[lane];
-    zv = warp_sum(zv);
-    if (lane == 0) y[r] = zv;
-    __syncthreads();
+  if constexpr (sizeof(T) == 8) {
+    // FP64 (a few tiles at the plain form's sizes): the plain left-looking
+    // sweeps; the prefetch below measured slower there (d = 50 / 200).
+    // forward: y_k = D_k (v_k - sum_{j < k} L_kj y_j)
+    for (int k = 0; k < Tt; ++k) {
+      const int k0 = k * 32, r = k0 + w;
+      const T* Lr = L + (int64_t)r * dp;
+      T s = T(0);
+      for (int c = lane; c < k0; c += 32) s += Lr[c] * y[c];
+      s = warp_sum(s);
+      if (lane == 0) t[w] = y[r] - s;
+      __syncthreads();
+      T yv = Dk[(int64_t)k * 1024 + w * 32 + lane] * t[lane];
+      yv = warp_sum(yv);
+      if (lane == 0) y[r] = yv;
+      __syncthreads();
+    }
+    // backward: z_k = D_k^T (y_k - sum_{j > k} (L^T)_kj z_j), (L^T)_kj stored in tile (k, j)
+    for (int k = Tt - 1; k >= 0; --k) {
+      const int k0 = k * 32, r = k0 + w;
+      const T* Ur = L + (int64_t)r * dp;
+      T s = T(0);
+      for (int c = k0 + 32 + lane; c < dp; c += 32) s += Ur[c] * y[c];
+      s = warp_sum(s);
+      if (lane == 0) t[w] = y[r] - s;
+      __syncthreads();
+      T zv = Dk[(int64_t)k * 1024 + lane * 32 + w] * t[lane];
+      zv = warp_sum(zv);
+      if (lane == 0) y[r] = zv;
+      __syncthreads();
+    }
+  } else {
+    // FP32: both sweeps are software-pipelined: in step k each warp issues the loads
+    // of the next step's row over the tiles whose solution is already known
+    // (up to kPre tiles in registers, the rest loaded after the step) and adds
+    // them up after the step's barriers, so their L2 latency overlaps the
+    // step's dependent chain; the row of step k then only adds its last tile.
+    // A lane adds its tiles in a fixed order (ascending forward, descending
+    // backward), the same whichever step prefetched them.
+    constexpr int kPre = 16;
+    // forward: y_k = D_k (v_k - sum_{j < k} L_kj y_j)
+    T part = T(0);  // row k0 + w: this lane's sum over tiles j < k - 1
+    for (int k = 0; k < Tt; ++k) {
+      const int k0 = k * 32, r = k0 + w;
+      const bool nxt = k + 1 < Tt;
+      const T* Ln = L + (int64_t)(r + 32) * dp;  // the next step's row
+      T nl[kPre];
+#pragma unroll
+      for (int q = 0; q < kPre; ++q) nl[q] = (nxt && q < k) ? Ln[lane + 32 * q] : T(0);
+      T s = part;
+      if (k >= 1) s += L[(int64_t)r * dp + k0 - 32 + lane] * y[k0 - 32 + lane];
+      s = warp_sum(s);
+      if (lane == 0) t[w] = y[r] - s;
+      __syncthreads();
+      T yv = Dk[(int64_t)k * 1024 + w * 32 + lane] * t[lane];
+      yv = warp_sum(yv);
+      if (lane == 0) y[r] = yv;
+      __syncthreads();
+      T pn = T(0);
+      if (nxt) {
+#pragma unroll
+        for (int q = 0; q < kPre; ++q)
+          if (q < k) pn += nl[q] * y[lane + 32 * q];
+        for (int q = kPre; q < k; ++q) pn += Ln[lane + 32 * q] * y[lane + 32 * q];
+      }
+      part = pn;
+    }
+    // backward: z_k = D_k^T (y_k - sum_{j > k} (L^T)_kj z_j), (L^T)_kj stored in
+    // tile (k, j); a lane adds the tiles j = Tt-1, Tt-2, ..., k+1 in that order
+    part = T(0);  // row k0 + w: this lane's sum over tiles j > k + 1
+    for (int k = Tt - 1; k >= 0; --k) {
+      const int k0 = k * 32, r = k0 + w;
+      const bool nxt = k >= 1;
+      const T* Un = L + (int64_t)(r - 32) * dp;  // the next step's row (tile k - 1)
+      const int known = Tt - 1 - k;                // tiles Tt-1 .. k+1 are solved
+      T nl[kPre];
+#pragma unroll
+      for (int q = 0; q < kPre; ++q)
+        nl[q] = (nxt && q < known) ? Un[(Tt - 1 - q) * 32 + lane] : T(0);
+      T s = part;
+      if (k + 1 < Tt) s += L[(int64_t)r * dp + k0 + 32 + lane] * y[k0 + 32 + lane];
+      s = warp_sum(s);
+      if (lane == 0) t[w] = y[r] - s;
+      __syncthreads();
+      T zv = Dk[(int64_t)k * 1024 + lane * 32 + w] * t[lane];
+      zv = warp_sum(zv);
+      if (lane == 0) y[r] = zv;
+      __syncthreads();
+      T pn = T(0);
+      if (nxt) {
+#pragma unroll
+        for (int q = 0; q < kPre; ++q)
+          if (q < known) pn += nl[q] * y[(Tt - 1 - q) * 32 + lane];
+        for (int q = kPre; q < known; ++q) {
+          const int c = (Tt - 1 - q) * 32 + lane;
+          pn += Un[c] * y[c];
+        }
+      }
+      part = pn;
+    }
   }
   double mx = 0.0;
   for (int i = tid; i < d; i += blockDim.x) {
