@@ -60,17 +60,6 @@ IHS_DEV void sketch_draw(const SketchKeys& K, int k, uint64_t i, int& row, int& 
   row = k * K.mb + draw_bucket((k & 1) ? lo : hi, K.mb);
   neg = (int)(((k & 1) ? hi : lo) & 1u);
 }
-// Both blocks of pair p for row i from one output: bucket within the block
-// (b0 for block 2p, b1 for block 2p + 1) and sign bits.
-IHS_DEV void sketch_draw_pair(const SketchKeys& K, int p, uint64_t i, int& b0, int& neg0,
-                              int& b1, int& neg1) {
-  const uint64_t w = sm64_out(K.key[p], i);
-  const uint32_t hi = (uint32_t)(w >> 32), lo = (uint32_t)w;
-  b0 = draw_bucket(hi, K.mb);
-  neg0 = (int)(lo & 1u);
-  b1 = draw_bucket(lo, K.mb);
-  neg1 = (int)(hi & 1u);
-}
 
 // ---------------------------------------------------------------------------
 // Double-float ("float-float") arithmetic from error-free transformations:
