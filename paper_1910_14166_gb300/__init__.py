@@ -137,6 +137,22 @@ def _need_cuda(t, name):
         raise ValueError("%s must be contiguous" % name)
 
 
+def _need(t, name, shape, dtypes, device):
+    """Checks the C ABI cannot make (it sees bare pointers): a contiguous CUDA
+    tensor of this shape, one of these dtypes, on this device."""
+    _need_cuda(t, name)
+    if t.dtype not in dtypes:
+        raise TypeError("%s must be %s" % (name, "/".join(str(x).replace("torch.", "")
+                                                           for x in dtypes)))
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError("%s must have shape %s, not %s" % (name, tuple(shape), tuple(t.shape)))
+    if t.device != device:
+        raise ValueError("%s must be on %s, not %s" % (name, device, t.device))
+
+
+_F64 = (torch.float64,)
+
+
 def ihs_hash(seed, t, s, m, n):
     """Sketch draw of Sec. 2 on the GPU: (bucket int32 [s, n], sign int8 [s, n])."""
     bucket = torch.empty((s, n), dtype=torch.int32, device="cuda")
@@ -147,12 +163,16 @@ def ihs_hash(seed, t, s, m, n):
 
 
 def ihs_sketch_adjoint(seed, t, s, m, n, G):
-    """S^T G (n x d FP64) for the normalised sketch of counter t."""
+    """S^T G (n x d FP64) for the normalised sketch of counter t; G is m x d
+    (its rows are gathered by bucket, so it must hold all m of them)."""
     _need_cuda(G, "G")
+    if G.dim() != 2 or G.shape[0] != m:
+        raise ValueError("G must be a 2-D tensor with m = %d rows" % m)
     G = G.to(torch.float64)
-    out = torch.empty((n, G.shape[1]), dtype=torch.float64, device=G.device)
-    _check(_lib.ihs_sketch_adjoint(seed & 0xFFFFFFFFFFFFFFFF, t, s, m, n, G.shape[1], _ptr(G),
-                                   _ptr(out), _stream()), "ihs_sketch_adjoint")
+    with torch.cuda.device(G.device):
+        out = torch.empty((n, G.shape[1]), dtype=torch.float64, device=G.device)
+        _check(_lib.ihs_sketch_adjoint(seed & 0xFFFFFFFFFFFFFFFF, t, s, m, n, G.shape[1],
+                                       _ptr(G), _ptr(out), _stream()), "ihs_sketch_adjoint")
     return out
 
 
@@ -237,13 +257,14 @@ class IHS:
                  sketch="sparse", lookahead=True, fp64_factor=False, graph=True):
         self._keep = [A, b]
         _need_cuda(b, "b")
-        if b.dtype != torch.float64:
-            raise TypeError("b must be float64")
+        if b.dtype != torch.float64 or b.dim() != 1:
+            raise TypeError("b must be a float64 vector")
         M = _Matrix()
         if isinstance(A, torch.Tensor):
             _need_cuda(A, "A")
             if A.dim() != 2 or A.dtype not in (torch.float32, torch.float64):
                 raise TypeError("dense A must be a 2-D float32/float64 tensor")
+            _need(b, "b", (A.shape[0],), _F64, A.device)
             M.kind, M.n, M.d = DENSE, A.shape[0], A.shape[1]
             M.ld = A.stride(0)
             M.dtype = F32 if A.dtype == torch.float32 else F64
@@ -253,10 +274,12 @@ class IHS:
             M.nnz = A.numel()
         else:
             rowptr, col, val = A
-            for t_, nm in ((rowptr, "rowptr"), (col, "col"), (val, "val")):
-                _need_cuda(t_, nm)
             if shape is None:
                 raise ValueError("CSR input needs shape=(n, d)")
+            _need(b, "b", (shape[0],), _F64, b.device)
+            _need(rowptr, "rowptr", (shape[0] + 1,), (torch.int32, torch.int64), b.device)
+            _need(val, "val", (val.numel(),), (torch.float32, torch.float64), b.device)
+            _need(col, "col", (val.numel(),), (torch.int32,), b.device)
             M.kind, M.n, M.d, M.ld = CSR, shape[0], shape[1], shape[1]
             M.dtype = F32 if val.dtype == torch.float32 else F64
             M.val, M.col, M.rowptr = val.data_ptr(), col.data_ptr(), rowptr.data_ptr()
@@ -273,10 +296,12 @@ class IHS:
                                                  graph),
                      SKETCH[sketch])
         h = ctypes.c_void_p()
-        _check(_lib.ihs_create(ctypes.byref(h), ctypes.byref(M), _ptr(b), ctypes.byref(C),
-                               ctypes.byref(O), _stream()), "ihs_create")
-        self._h = h
         self.device = b.device
+        # the context keeps the stream current at creation: take b's device's
+        with torch.cuda.device(self.device):
+            _check(_lib.ihs_create(ctypes.byref(h), ctypes.byref(M), _ptr(b), ctypes.byref(C),
+                                   ctypes.byref(O), _stream()), "ihs_create")
+        self._h = h
 
     def close(self):
         if getattr(self, "_h", None):
@@ -289,65 +314,78 @@ class IHS:
         except Exception:
             pass
 
+    def _x(self, x, name="x"):
+        _need(x, name, (self.d,), _F64, self.device)
+
     def sketch(self, t):
-        _check(_lib.ihs_sketch(self._h, int(t)), "ihs_sketch")
+        with torch.cuda.device(self.device):
+            _check(_lib.ihs_sketch(self._h, int(t)), "ihs_sketch")
 
     def gradient(self, x, want_r=False):
-        _need_cuda(x, "x")
-        g = torch.empty(self.d, dtype=torch.float64, device=self.device)
-        r = torch.empty(self.n, dtype=torch.float64, device=self.device) if want_r else None
-        _check(_lib.ihs_gradient(self._h, _ptr(x), _ptr(g), _ptr(r)), "ihs_gradient")
+        self._x(x)
+        with torch.cuda.device(self.device):
+            g = torch.empty(self.d, dtype=torch.float64, device=self.device)
+            r = torch.empty(self.n, dtype=torch.float64, device=self.device) if want_r else None
+            _check(_lib.ihs_gradient(self._h, _ptr(x), _ptr(g), _ptr(r)), "ihs_gradient")
         return (r, g) if want_r else g
 
     def sketch_gradient(self, t, x):
         """Sketch of counter t (SA, Hessian, factor) and g at x from one pass
         over A where the fused pass applies (ihs_sketch_gradient)."""
-        _need_cuda(x, "x")
-        if x.dtype != torch.float64 or x.numel() != self.d:
-            raise ValueError("x must hold d float64 values")
-        g = torch.empty(self.d, dtype=torch.float64, device=self.device)
-        _check(_lib.ihs_sketch_gradient(self._h, int(t), _ptr(x), _ptr(g)), "ihs_sketch_gradient")
+        self._x(x)
+        with torch.cuda.device(self.device):
+            g = torch.empty(self.d, dtype=torch.float64, device=self.device)
+            _check(_lib.ihs_sketch_gradient(self._h, int(t), _ptr(x), _ptr(g)),
+                   "ihs_sketch_gradient")
         return g
 
     def step(self, x):
-        _need_cuda(x, "x")
-        _check(_lib.ihs_step(self._h, _ptr(x)), "ihs_step")
+        self._x(x)
+        with torch.cuda.device(self.device):
+            _check(_lib.ihs_step(self._h, _ptr(x)), "ihs_step")
 
     def sync(self):
-        _check(_lib.ihs_sync(self._h), "ihs_sync")
+        with torch.cuda.device(self.device):
+            _check(_lib.ihs_sync(self._h), "ihs_sync")
 
     def solve(self, x=None, t0=0, iters=10):
         if x is None:
             x = torch.zeros(self.d, dtype=torch.float64, device=self.device)
-        _need_cuda(x, "x")
+        self._x(x)
         rep = _Report()
-        _check(_lib.ihs_solve(self._h, _ptr(x), int(t0), int(iters), ctypes.byref(rep)), "ihs_solve")
+        with torch.cuda.device(self.device):
+            _check(_lib.ihs_solve(self._h, _ptr(x), int(t0), int(iters), ctypes.byref(rep)),
+                   "ihs_solve")
         return x, rep
 
     def get_sketch(self):
         dt = ctypes.c_int()
         scale = ctypes.c_double()
-        _check(_lib.ihs_get_sketch(self._h, None, ctypes.byref(dt), None, ctypes.byref(scale)),
-               "ihs_get_sketch")
-        SA = torch.empty((self.m, self.d), dtype=torch.float64 if dt.value == F64 else torch.float32,
-                         device=self.device)
-        H = torch.empty((self.d, self.d), dtype=torch.float64, device=self.device)
-        _check(_lib.ihs_get_sketch(self._h, _ptr(SA), ctypes.byref(dt), _ptr(H),
-                                   ctypes.byref(scale)), "ihs_get_sketch")
+        with torch.cuda.device(self.device):
+            _check(_lib.ihs_get_sketch(self._h, None, ctypes.byref(dt), None,
+                                       ctypes.byref(scale)), "ihs_get_sketch")
+            SA = torch.empty((self.m, self.d),
+                             dtype=torch.float64 if dt.value == F64 else torch.float32,
+                             device=self.device)
+            H = torch.empty((self.d, self.d), dtype=torch.float64, device=self.device)
+            _check(_lib.ihs_get_sketch(self._h, _ptr(SA), ctypes.byref(dt), _ptr(H),
+                                       ctypes.byref(scale)), "ihs_get_sketch")
         return SA, H, scale.value
 
     def exact_gram(self):
         """A^T A in FP64 (d x d CUDA tensor), computed by the library."""
-        G = torch.empty((self.d, self.d), dtype=torch.float64, device=self.device)
-        _check(_lib.ihs_exact_gram(self._h, _ptr(G)), "ihs_exact_gram")
+        with torch.cuda.device(self.device):
+            G = torch.empty((self.d, self.d), dtype=torch.float64, device=self.device)
+            _check(_lib.ihs_exact_gram(self._h, _ptr(G)), "ihs_exact_gram")
         return G
 
     def sketch_error(self, t, G):
         """||(1/s)(S_t A)^T (S_t A) - G||_F / ||G||_F for the sketch of counter t."""
-        _need_cuda(G, "G")
+        _need(G, "G", (self.d, self.d), _F64, self.device)
         err = ctypes.c_double()
-        _check(_lib.ihs_sketch_error(self._h, int(t), _ptr(G), ctypes.byref(err)),
-               "ihs_sketch_error")
+        with torch.cuda.device(self.device):
+            _check(_lib.ihs_sketch_error(self._h, int(t), _ptr(G), ctypes.byref(err)),
+                   "ihs_sketch_error")
         return err.value
 
     def profile(self, enable=True):
@@ -365,12 +403,13 @@ class IHS:
                 launches.value)
 
     def adjoint(self, x, dLdx, want_A=True):
-        _need_cuda(x, "x")
-        _need_cuda(dLdx, "dLdx")
-        dLdb = torch.empty(self.n, dtype=torch.float64, device=self.device)
+        self._x(x)
+        self._x(dLdx, "dLdx")
         A = self._keep[0]
-        dLdA = torch.empty_like(A) if (want_A and isinstance(A, torch.Tensor)) else None
         rep = _Report()
-        _check(_lib.ihs_adjoint(self._h, _ptr(x), _ptr(dLdx), _ptr(dLdb), _ptr(dLdA),
-                                ctypes.byref(rep)), "ihs_adjoint")
+        with torch.cuda.device(self.device):
+            dLdb = torch.empty(self.n, dtype=torch.float64, device=self.device)
+            dLdA = torch.empty_like(A) if (want_A and isinstance(A, torch.Tensor)) else None
+            _check(_lib.ihs_adjoint(self._h, _ptr(x), _ptr(dLdx), _ptr(dLdb), _ptr(dLdA),
+                                    ctypes.byref(rep)), "ihs_adjoint")
         return dLdb, dLdA, rep

@@ -272,6 +272,48 @@ def test_invalid_arguments_are_rejected(cuda_lib):
         cuda_lib.ihs_hash(0, 0, 3, 10, 5)
 
 
+def test_binding_rejects_mismatched_tensors(cuda_lib):
+    """The C ABI sees bare pointers, so the binding checks every tensor's
+    dtype, length and device before it calls into the library: a short or
+    float32 b, a CSR triple with a short rowptr or int64 columns, an x of the
+    wrong type or length, a Gram of the wrong shape and an S^T G operand
+    without m rows are refused with nothing launched for them."""
+    n, d, m = 200, 8, 40
+    A = torch.randn((n, d), dtype=torch.float64, device="cuda")
+    b = torch.randn(n, dtype=torch.float64, device="cuda")
+    with pytest.raises(ValueError):
+        cuda_lib.IHS(A, b[:-1], m=m)
+    with pytest.raises(TypeError):
+        cuda_lib.IHS(A, b.float(), m=m)
+    rowptr, col, val = synth.csr_uniform(n, d, 3, 1)
+    csr = (dev(rowptr), dev(col), dev(val))
+    with pytest.raises(ValueError):
+        cuda_lib.IHS((csr[0][:-1], csr[1], csr[2]), b, m=m, shape=(n, d))
+    with pytest.raises(TypeError):
+        cuda_lib.IHS((csr[0], csr[1].long(), csr[2]), b, m=m, shape=(n, d))
+    with pytest.raises(ValueError):
+        cuda_lib.IHS((csr[0], csr[1][:-1], csr[2]), b, m=m, shape=(n, d))
+    sv = cuda_lib.IHS(A, b, m=m)
+    x = torch.zeros(d, dtype=torch.float64, device="cuda")
+    with pytest.raises(TypeError):
+        sv.solve(x.float(), iters=1)
+    with pytest.raises(ValueError):
+        sv.solve(torch.zeros(d + 1, dtype=torch.float64, device="cuda"), iters=1)
+    with pytest.raises(ValueError):
+        sv.gradient(x[:-1])
+    with pytest.raises(ValueError):
+        sv.step(x[:-1])
+    with pytest.raises(ValueError):
+        sv.sketch_error(0, torch.zeros((d, d + 1), dtype=torch.float64, device="cuda"))
+    with pytest.raises(ValueError):
+        cuda_lib.ihs_sketch_adjoint(0, 0, 1, m, n,
+                                    torch.zeros((m - 1, d), dtype=torch.float64, device="cuda"))
+    # the context still works after the refusals
+    x, rep = sv.solve(x, iters=3)
+    assert rep.status == 0 and torch.isfinite(x).all().item()
+    sv.close()
+
+
 def test_not_spd_is_reported(cuda_lib):
     """A rank-deficient sketch (m >= d but zero columns in A) makes the
     Hessian singular; the factor reports it through the status word."""
