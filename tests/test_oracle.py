@@ -65,6 +65,25 @@ def test_hash_independent_across_iterations_and_blocks():
         assert abs(v - 1 / mb) < 6 * np.sqrt(1 / mb / n)
 
 
+def _pair_draws_independent(b, sg, mb):
+    """For every block pair (2p, 2p + 1) of a draw over n rows: the buckets
+    agree on 1/mb of the rows within 6 sigma, and no sign is correlated with
+    the other sign or with either bucket's upper half (6 / sqrt(n))."""
+    s, n = b.shape
+    tol = 6 / np.sqrt(n)
+    for p in range(s // 2):
+        k0, k1 = 2 * p, 2 * p + 1
+        u0, u1 = b[k0] - k0 * mb, b[k1] - k1 * mb
+        if abs((u0 == u1).mean() - 1 / mb) >= 6 * np.sqrt(1 / mb / n):
+            return False
+        s0, s1 = sg[k0].astype(float), sg[k1].astype(float)
+        h0, h1 = np.where(u0 >= mb // 2, 1.0, -1.0), np.where(u1 >= mb // 2, 1.0, -1.0)
+        for a, c in ((s0, s1), (s0, h0), (s0, h1), (s1, h0), (s1, h1)):
+            if abs(np.mean(a * c) - np.mean(a) * np.mean(c)) >= tol:
+                return False
+    return True
+
+
 def test_hash_block_pair_halves_independent():
     """Blocks 2p and 2p + 1 of a row take the high and low halves of one
     SplitMix64 output (bucket by multiply-shift of the half, sign from bit 0
@@ -76,16 +95,7 @@ def test_hash_block_pair_halves_independent():
     n, m, s = 40000, 96, 6
     mb = m // s
     b, sg = O.hash_draw(3, 1, s, m, n)
-    tol = 6 / np.sqrt(n)
-    for p in range(s // 2):
-        k0, k1 = 2 * p, 2 * p + 1
-        u0, u1 = b[k0] - k0 * mb, b[k1] - k1 * mb
-        same = (u0 == u1).mean()
-        assert abs(same - 1 / mb) < 6 * np.sqrt(1 / mb / n)
-        s0, s1 = sg[k0].astype(float), sg[k1].astype(float)
-        h0, h1 = np.where(u0 >= mb // 2, 1.0, -1.0), np.where(u1 >= mb // 2, 1.0, -1.0)
-        for a, c in ((s0, s1), (s0, h0), (s0, h1), (s1, h0), (s1, h1)):
-            assert abs(np.mean(a * c) - np.mean(a) * np.mean(c)) < tol
+    assert _pair_draws_independent(b, sg, mb)
     # s = 1 keeps the high half and bit 0: the same draw as block 0 of any s
     b1, sg1 = O.hash_draw(3, 1, 1, mb, n)
     assert np.array_equal(b1[0], b[0]) and np.array_equal(sg1[0], sg[0])
@@ -272,18 +282,25 @@ def test_l1_projection_properties():
     """Projection onto the l1 ball (Duchi et al. 2008): feasible, idempotent,
     on the boundary when the input is outside, and the variational
     inequality <v - p, y - p> <= 0 for feasible y."""
+    assert _l1_projection_pins_hold(O.project_l1_ball)
+
+
+def _l1_projection_pins_hold(proj):
+    """The properties above for 50 seeded (v, R), each with 5 feasible y."""
     rng = np.random.default_rng(6)
     for _ in range(50):
         v = rng.standard_normal(9) * 3
         R = rng.random() * 4 + 0.1
-        p = O.project_l1_ball(v, R)
-        assert np.abs(p).sum() <= R * (1 + 1e-12)
-        assert np.allclose(O.project_l1_ball(p, R), p)
-        if np.abs(v).sum() > R:
-            assert abs(np.abs(p).sum() - R) < 1e-12
+        p = proj(v, R)
+        if np.abs(p).sum() > R * (1 + 1e-12) or not np.allclose(proj(p, R), p):
+            return False
+        if np.abs(v).sum() > R and abs(np.abs(p).sum() - R) >= 1e-12:
+            return False
         for _ in range(5):
-            y = O.project_l1_ball(rng.standard_normal(9) * 5, R)
-            assert (v - p) @ (y - p) <= 1e-10
+            y = proj(rng.standard_normal(9) * 5, R)
+            if (v - p) @ (y - p) > 1e-10:
+                return False
+    return True
 
 
 def test_l1_qp_kkt_at_dimension_200():
@@ -361,6 +378,15 @@ def test_resume_is_exact():
 def test_ridge_adjoint_against_central_differences():
     """dL/db = A v and dL/dA = r v^T - (A v) x^T for L = ||x(A, b) - x_t||^2,
     x = (A^T A + lam I)^{-1} A^T b; central differences h = 1e-6 in FP64."""
+    A, b, lam, dLdx, fd_b, fd_A = _ridge_fd_case()
+    x, dLdb, dLdA = O.ridge_adjoint(A, b, lam, dLdx)
+    assert np.linalg.norm(fd_b - dLdb) <= 1e-6 * np.linalg.norm(dLdb)
+    assert np.linalg.norm(fd_A - dLdA) <= 1e-6 * np.linalg.norm(dLdA)
+
+
+def _ridge_fd_case():
+    """A 60 x 5 ridge problem, dL/dx at its solution for L = ||x - x_t||^2,
+    and central differences (h = 1e-6) of L in every entry of b and of A."""
     rng = np.random.default_rng(8)
     n, d, lam = 60, 5, 1e-3
     A = rng.standard_normal((n, d))
@@ -371,17 +397,16 @@ def test_ridge_adjoint_against_central_differences():
         x = np.linalg.solve(A_.T @ A_ + lam * np.eye(d), A_.T @ b_)
         return np.sum((x - xt) ** 2)
 
-    x, dLdb, dLdA = O.ridge_adjoint(A, b, lam, None if False else 2 * (np.linalg.solve(A.T @ A + lam * np.eye(d), A.T @ b) - xt))
+    dLdx = 2 * (np.linalg.solve(A.T @ A + lam * np.eye(d), A.T @ b) - xt)
     h = 1e-6
     fd_b = np.array([(loss(A, b + h * e) - loss(A, b - h * e)) / (2 * h) for e in np.eye(n)])
-    assert np.linalg.norm(fd_b - dLdb) <= 1e-6 * np.linalg.norm(dLdb)
     fd_A = np.zeros_like(A)
     for i in range(n):
         for j in range(d):
             E = np.zeros_like(A)
             E[i, j] = h
             fd_A[i, j] = (loss(A + E, b) - loss(A - E, b)) / (2 * h)
-    assert np.linalg.norm(fd_A - dLdA) <= 1e-6 * np.linalg.norm(dLdA)
+    return A, b, lam, dLdx, fd_b, fd_A
 
 
 # ----------------------------------------------- planted-mistake checks ----
@@ -421,6 +446,126 @@ def test_pins_catch_planted_mistakes(monkeypatch):
     except RuntimeError:
         bad = None  # no face passed the acceptance test: caught
     assert bad is None or not np.allclose(bad, good)
+
+
+def test_pair_pin_catches_shared_halves():
+    """Planted on the CPU: block 2p + 1 drawn from the same half as block 2p,
+    or every sign taken from the top bit of its own bucket, fails the
+    block-pair independence pin."""
+    n, m, s = 40000, 96, 6
+    mb = m // s
+    b, sg = O.hash_draw(3, 1, s, m, n)
+    same = b.copy()
+    for p in range(s // 2):
+        same[2 * p + 1] = b[2 * p] + mb
+    assert not _pair_draws_independent(same, sg, mb)
+    own = np.stack([np.where(b[k] - k * mb >= mb // 2, -1, 1) for k in range(s)]).astype(np.int8)
+    assert not _pair_draws_independent(b, own, mb)
+
+
+def test_projection_pins_catch_an_off_by_one_threshold():
+    """Planted on the CPU: the sort-based l1 projection with its threshold
+    divided by rho instead of rho + 1 fails the projection pins."""
+    def proj_bad(v, R):
+        if np.abs(v).sum() <= R:
+            return v.copy()
+        u = np.sort(np.abs(v))[::-1]
+        css = np.cumsum(u)
+        rho = np.nonzero(u - (css - R) / np.arange(1, v.size + 1) > 0)[0][-1]
+        theta = (css[rho] - R) / max(rho, 1)
+        return np.sign(v) * np.maximum(np.abs(v) - theta, 0.0)
+
+    assert not _l1_projection_pins_hold(proj_bad)
+
+
+def test_srht_pins_catch_planted_mistakes():
+    """Planted on the CPU: the SRHT without its diagonal D, and a fast
+    transform whose butterfly writes (u + v, v - u), each fail the
+    materialised-Hadamard pins."""
+    from scipy.linalg import hadamard
+    rng = np.random.default_rng(21)
+    n, m = 100, 12
+    A = rng.standard_normal((n, 3))
+    rows, sign = O.srht_draw(3, 5, m, n)
+    want = (hadamard(O.srht_n2(n))[rows][:, :n] * sign[None, :].astype(float)) @ A
+    assert np.allclose(O.srht_sketch(A, m, rows, sign), want, rtol=0, atol=1e-12)
+    assert not np.allclose(O.srht_sketch(A, m, rows, np.ones_like(sign)), want, rtol=0,
+                           atol=1e-12)
+
+    def fwht_reversed(X):
+        Y = np.array(X, dtype=np.float64, copy=True)
+        h = 1
+        while h < Y.shape[0]:
+            Y = Y.reshape(Y.shape[0] // (2 * h), 2, h, -1)
+            u, v = Y[:, 0].copy(), Y[:, 1].copy()
+            Y[:, 0], Y[:, 1] = u + v, v - u
+            Y = Y.reshape(-1, Y.shape[-1])
+            h *= 2
+        return Y
+
+    X = rng.standard_normal((256, 4))
+    assert not np.allclose(fwht_reversed(X), hadamard(256) @ X, atol=1e-11)
+
+
+def _sm64_np(state, j):
+    """SplitMix64 output j (uint64 array) of the generator started at
+    `state` (Steele, Lea & Flood 2014), vectorised for the planted draws."""
+    z = np.uint64(state) + (j.astype(np.uint64) + np.uint64(1)) * np.uint64(0x9E3779B97F4A7C15)
+    z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+    z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+    return z ^ (z >> np.uint64(31))
+
+
+def test_gauss_pins_catch_planted_mistakes():
+    """Planted on the CPU in a restatement of the oracle's Box-Muller draw
+    (which first reproduces gauss_draw): a missing factor 2 under the root, a
+    missing 2 pi in the angle, or one uniform for both factors, each fail the
+    standard-normal pins."""
+    seed, t, m, n = 5, 0, 200, 1000
+    key = O.sm64_at(O.sm64_at(O.sm64_at(seed, 0), t), 2)
+    assert int(_sm64_np(key, np.array([7], dtype=np.uint64))[0]) == O.sm64_at(key, 7)
+    w = _sm64_np(key, np.arange(m * n, dtype=np.uint64))
+    u1 = ((w >> np.uint64(32)).astype(np.float64) + 0.5) / 4294967296.0
+    u2 = ((w & np.uint64(0xFFFFFFFF)).astype(np.float64) + 0.5) / 4294967296.0
+    good = np.sqrt(-2.0 * np.log(u1)) * np.cos(2.0 * np.pi * u2)
+    assert np.allclose(good, O.gauss_draw(seed, t, m, n).ravel(), rtol=0, atol=1e-12)
+    assert _standard_normal_pins_hold(good)
+    assert not _standard_normal_pins_hold(np.sqrt(-np.log(u1)) * np.cos(2.0 * np.pi * u2))
+    assert not _standard_normal_pins_hold(np.sqrt(-2.0 * np.log(u1)) * np.cos(u2))
+    assert not _standard_normal_pins_hold(np.sqrt(-2.0 * np.log(u1)) * np.cos(2.0 * np.pi * u1))
+
+
+def test_l2_ball_pin_catches_a_transposed_eigenbasis(monkeypatch):
+    """Planted on the CPU: the p = 2 ball solver using its eigenbasis
+    transposed fails the KKT pin (d = 6, the ball constraint active)."""
+    rng = np.random.default_rng(33)
+    d = 6
+    M = rng.standard_normal((10, d))
+    H = M.T @ M + 0.1 * np.eye(d)
+    xt = rng.standard_normal(d)
+    g = 4 * rng.standard_normal(d)
+    R = 0.5 * np.linalg.norm(np.linalg.solve(H, H @ xt + g))
+    assert O.l2_ball_kkt_residual(H, g, xt, R, O.l2_ball_qp(H, g, xt, R)) < 1e-12
+    eigh = np.linalg.eigh
+
+    def eigh_transposed(a):
+        lam, Q = eigh(a)
+        return lam, Q.T
+
+    monkeypatch.setattr(O.np.linalg, "eigh", eigh_transposed)
+    assert O.l2_ball_kkt_residual(H, g, xt, R, O.l2_ball_qp(H, g, xt, R)) > 1e-6
+
+
+def test_adjoint_pin_catches_planted_mistakes():
+    """Planted on the CPU: dL/dA with the sign of its (A v) x^T term flipped,
+    or v solved without the ridge shift lam I, fails the central-difference
+    pin."""
+    A, b, lam, dLdx, fd_b, fd_A = _ridge_fd_case()
+    x, dLdb, dLdA = O.ridge_adjoint(A, b, lam, dLdx)
+    flipped = dLdA + 2 * np.outer(dLdb, x)
+    assert np.linalg.norm(fd_A - flipped) > 1e-6 * np.linalg.norm(flipped)
+    v0 = np.linalg.solve(A.T @ A, dLdx)
+    assert np.linalg.norm(fd_b - A @ v0) > 1e-6 * np.linalg.norm(A @ v0)
 
 
 # --------------------------------------------------------------- synth ----
@@ -594,16 +739,20 @@ def test_ihs_srht_converges_to_xopt():
 
 
 # ------------------------------------------------------------ Gaussian ----
+def _standard_normal_pins_hold(z):
+    """Mean 0 and variance 1 within 5 standard errors, and a
+    Kolmogorov-Smirnov p-value above 1e-3 against N(0, 1)."""
+    from scipy.stats import kstest
+    return (abs(z.mean()) < 5 / np.sqrt(z.size)
+            and abs(z.var() - 1.0) < 5 * np.sqrt(2.0 / z.size)
+            and kstest(z, "norm").pvalue > 1e-3)
+
+
 def test_gauss_draw_is_standard_normal():
     """The Gaussian sketch's entries (Box-Muller of the counter words) have
     mean 0, variance 1 and pass a Kolmogorov-Smirnov test against N(0, 1);
     E[S^T S] = I for S = G / sqrt(m) (5 standard errors entrywise)."""
-    from scipy.stats import kstest
-    G = O.gauss_draw(5, 0, 200, 1000)
-    z = G.ravel()
-    assert abs(z.mean()) < 5 / np.sqrt(z.size)
-    assert abs(z.var() - 1.0) < 5 * np.sqrt(2.0 / z.size)
-    assert kstest(z, "norm").pvalue > 1e-3
+    assert _standard_normal_pins_hold(O.gauss_draw(5, 0, 200, 1000).ravel())
     n, m, T = 6, 4, 3000
     acc = np.zeros((n, n)); acc2 = np.zeros((n, n))
     for t in range(T):
