@@ -279,8 +279,9 @@ def test_binding_rejects_mismatched_tensors(cuda_lib):
     wrong type or length, a Gram of the wrong shape and an S^T G operand
     without m rows are refused with nothing launched for them."""
     n, d, m = 200, 8, 40
-    A = torch.randn((n, d), dtype=torch.float64, device="cuda")
-    b = torch.randn(n, dtype=torch.float64, device="cuda")
+    rng = np.random.default_rng(12)
+    A = dev(rng.standard_normal((n, d)))
+    b = dev(rng.standard_normal(n))
     with pytest.raises(ValueError):
         cuda_lib.IHS(A, b[:-1], m=m)
     with pytest.raises(TypeError):
