@@ -136,3 +136,57 @@ def test_create_rejects_invalid_options_before_touching_the_device():
     assert create(kind=7) == ERR_ARG
     assert create(kind=ihs.L1_BALL, param=0.0) == ERR_ARG
     assert create(sketch=1, s=2, m=100) == ERR_ARG
+
+
+def test_entry_points_reject_bad_arguments_before_touching_the_device():
+    """Every entry point checks its arguments on the host before its first
+    CUDA call: a null context, a negative counter or size, s not dividing m,
+    more than 2^31 buckets and null buffers return IHS_ERR_ARG (1), and an
+    oversize d returns IHS_ERR_UNSUPPORTED (8), with no device in this
+    process.  A null context passed to ihs_destroy is a no-op."""
+    import paper_1910_14166_gb300 as ihs
+    lib = ihs._lib
+    ERR_ARG, UNSUPPORTED = 1, 8
+    buf = ctypes.c_void_p(0x1000)  # never dereferenced: each call fails a host check first
+    dbl, i32, i64 = ctypes.c_double(), ctypes.c_int(), ctypes.c_int64()
+    rep = ihs._Report()
+    ms = (ctypes.c_double * 8)()
+
+    assert lib.ihs_sketch(None, 0) == ERR_ARG
+    assert lib.ihs_gradient(None, buf, buf, None) == ERR_ARG
+    assert lib.ihs_sketch_gradient(None, 0, buf, buf) == ERR_ARG
+    assert lib.ihs_step(None, buf) == ERR_ARG
+    assert lib.ihs_sync(None) == ERR_ARG
+    assert lib.ihs_solve(None, buf, 0, 1, ctypes.byref(rep)) == ERR_ARG
+    assert lib.ihs_get_sketch(None, None, ctypes.byref(i32), None, ctypes.byref(dbl)) == ERR_ARG
+    assert lib.ihs_exact_gram(None, buf) == ERR_ARG
+    assert lib.ihs_sketch_error(None, 0, buf, ctypes.byref(dbl)) == ERR_ARG
+    assert lib.ihs_adjoint(None, buf, buf, buf, None, ctypes.byref(rep)) == ERR_ARG
+    assert lib.ihs_profile(None, 1) == ERR_ARG
+    assert lib.ihs_profile_read(None, ms, None, ctypes.byref(i64)) == ERR_ARG
+    lib.ihs_destroy(None)
+
+    # stateless draw and gather: (seed, t, s, m, n)
+    for s, m, n, t in ((0, 10, 5, 0), (65, 130, 5, 0), (3, 10, 5, 0), (1, 10, -1, 0),
+                       (1, 10, 5, -1), (1, 1 << 31, 5, 0)):
+        assert lib.ihs_hash(0, t, s, m, n, buf, buf, None) == ERR_ARG, (s, m, n, t)
+    assert lib.ihs_hash(0, 0, 1, 10, 5, None, buf, None) == ERR_ARG
+    assert lib.ihs_sketch_adjoint(0, 0, 1, 10, 5, 0, buf, buf, None) == ERR_ARG
+    assert lib.ihs_sketch_adjoint(0, 0, 2, 10, 5, 3, None, buf, None) == ERR_ARG
+    assert lib.ihs_sketch_adjoint(0, 0, 3, 10, 5, 3, buf, buf, None) == ERR_ARG
+
+    # self-test of the pivot root: nothing to do for n = 0, null buffers refused
+    assert lib.ihs_selftest_rsqrt(None, None, None, 0, None) == 0
+    assert lib.ihs_selftest_rsqrt(None, buf, buf, 4, None) == ERR_ARG
+
+    # no-allocation gradient
+    M = ihs._Matrix()
+    M.kind, M.dtype, M.n, M.d, M.ld, M.val = ihs.DENSE, ihs.F32, 100, 8, 8, 0x1000
+    assert lib.ihs_gradient_noalloc(None, buf, buf, 0.0, buf, None) == ERR_ARG
+    assert lib.ihs_gradient_noalloc(ctypes.byref(M), None, buf, 0.0, buf, None) == ERR_ARG
+    M.ld = 7
+    assert lib.ihs_gradient_noalloc(ctypes.byref(M), buf, buf, 0.0, buf, None) == ERR_ARG
+    M.ld, M.kind = 8, ihs.CSR
+    assert lib.ihs_gradient_noalloc(ctypes.byref(M), buf, buf, 0.0, buf, None) == ERR_ARG
+    M.kind, M.d, M.ld = ihs.DENSE, 1025, 1025
+    assert lib.ihs_gradient_noalloc(ctypes.byref(M), buf, buf, 0.0, buf, None) == UNSUPPORTED
