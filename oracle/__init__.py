@@ -160,6 +160,7 @@ class CSR:
         return out
 
     def matvec(self, x):
+        """A x (the residual's product in Eq. 2's gradient)."""
         rows = np.repeat(np.arange(self.n), np.diff(self.rowptr))
         out = np.zeros(self.n)
         np.add.at(out, rows, self.val * x[self.col])
@@ -183,6 +184,7 @@ class CSR:
             return G
 
     def rmatvec(self, r):
+        """A^T r (the gradient of Eq. 2)."""
         out = np.zeros(self.d)
         rows = np.repeat(np.arange(self.n), np.diff(self.rowptr))
         np.add.at(out, self.col, self.val * r[rows])
@@ -260,7 +262,8 @@ def resid_grad(A, b, x, want_r: bool = False):
 
 
 def sketch_adjoint(G, n: int, s: int, bucket, sign):
-    """S^T G for the normalised sketch (entries sign/sqrt(s)), n x d FP64."""
+    """S^T G for the normalised sketch (entries sign/sqrt(s), App. A), n x d
+    FP64: the adjoint of the streaming product of Sec. 2, a gather by bucket."""
     G = np.ascontiguousarray(G, dtype=np.float64)
     m, d = G.shape
     out = np.empty((n, d))
@@ -271,7 +274,8 @@ def sketch_adjoint(G, n: int, s: int, bucket, sign):
 
 
 def sketch_matrix(m: int, s: int, bucket, sign):
-    """Dense S (m x n) with entries sign/sqrt(s): only for brute-force pins on tiny n."""
+    """Dense S (m x n) of Sec. 2 with entries sign/sqrt(s) (App. A): only for
+    brute-force pins on tiny n."""
     n = bucket.shape[1]
     S = np.zeros((m, n))
     for k in range(s):
@@ -306,7 +310,8 @@ def project_l1_ball(v, R):
 
 def _l1_face_solve(H, c, R, S, sgn):
     """Minimise 1/2 x^T H x - c^T x on {x_S^T sgn = R, x_{S^c} = 0}: the
-    bordered KKT system [H_SS sgn; sgn^T 0][z; mu] = [c_S; R]."""
+    bordered KKT system [H_SS sgn; sgn^T 0][z; mu] = [c_S; R] (one face of the
+    l1 ball in Eq. 2's subproblem, solved exactly as Sec. 3 asks)."""
     k = len(S)
     K = np.zeros((k + 1, k + 1))
     K[:k, :k] = H[np.ix_(S, S)]
@@ -318,7 +323,8 @@ def _l1_face_solve(H, c, R, S, sgn):
 
 
 def l1_kkt_residual(H, g, xt, R, x):
-    """Relative KKT violation of x for the l1-ball QP (0 at the exact solution)."""
+    """Relative KKT violation of x for the l1-ball QP of Eq. 2 (0 at the exact
+    solution, the certificate of Sec. 3's "solved exactly")."""
     c = H @ xt + g
     grad = H @ x - c
     scale = max(np.abs(c).max(), 1e-300)
@@ -377,8 +383,9 @@ def l1_ball_qp(H, g, xt, R, tol=1e-13, max_rounds=200, inner=200):
 
 
 def l1_ball_qp_bruteforce(H, g, xt, R):
-    """Brute force for tiny d: the unconstrained point if feasible, else the
-    best point over every face of the l1 ball (all sign patterns in {-1,0,1}^d)."""
+    """Eq. 2's l1-ball subproblem by brute force for tiny d: the unconstrained
+    point if feasible, else the best point over every face of the ball (all
+    sign patterns in {-1,0,1}^d)."""
     import itertools
     d = H.shape[0]
     c = H @ xt + g
@@ -403,24 +410,28 @@ def l1_ball_qp_bruteforce(H, g, xt, R):
 
 
 def soft_threshold(v, tau):
-    """Proximal map of tau ||.||_1: sign(v) max(|v| - tau, 0)."""
+    """Proximal map of tau ||.||_1 (the penalised LASSO of Sec. 3's
+    experiments): sign(v) max(|v| - tau, 0)."""
     return np.sign(v) * np.maximum(np.abs(v) - tau, 0.0)
 
 
 def _pen_face_solve(H, c, lam, S, sgn):
     """Stationary point of 1/2 x^T H x - c^T x + lam sgn^T x_S on {x_{S^c} = 0}:
-    H_SS x_S = c_S - lam sgn."""
+    H_SS x_S = c_S - lam sgn (one face of the penalised form of Eq. 2's
+    subproblem, Sec. 3's experiments)."""
     return np.linalg.solve(H[np.ix_(S, S)], c[S] - lam * sgn)
 
 
 def l1_penalty_objective(H, g, xt, lam, x):
-    """1/2 (x - xt)^T H (x - xt) - g^T (x - xt) + lam ||x||_1."""
+    """Eq. 2's subproblem with the penalty of Sec. 3's experiments:
+    1/2 (x - xt)^T H (x - xt) - g^T (x - xt) + lam ||x||_1."""
     e = np.asarray(x) - xt
     return float(0.5 * e @ H @ e - g @ e + lam * np.abs(x).sum())
 
 
 def l1_penalty_kkt_residual(H, g, xt, lam, x):
-    """Relative violation of 0 in H (x - xt) - g + lam d||x||_1 (0 at the optimum)."""
+    """Relative violation of 0 in H (x - xt) - g + lam d||x||_1 for the
+    penalised subproblem of Eq. 2 (0 at the optimum)."""
     c = H @ xt + g
     grad = H @ x - c
     scale = max(np.abs(c).max(), lam, 1e-300)
@@ -469,8 +480,9 @@ def l1_penalty_qp(H, g, xt, lam, tol=1e-13, max_rounds=200, inner=200):
 
 
 def l1_penalty_qp_bruteforce(H, g, xt, lam):
-    """Brute force for tiny d: the best stationary point over every support and
-    sign pattern in {-1,0,1}^d (x = 0 included)."""
+    """The penalised subproblem of Eq. 2 by brute force for tiny d: the best
+    stationary point over every support and sign pattern in {-1,0,1}^d
+    (x = 0 included)."""
     import itertools
     d = H.shape[0]
     best, bq = np.zeros(d), l1_penalty_objective(H, g, xt, lam, np.zeros(d))
@@ -519,8 +531,9 @@ def l2_ball_qp(H, g, xt, R, iters: int = 400):
 
 
 def l2_ball_kkt_residual(H, g, xt, R, x):
-    """Relative KKT violation of x for the p = 2 ball subproblem: stationarity
-    H (x - xt) - g + mu x = 0 with mu >= 0, and mu (||x|| - R) = 0."""
+    """Relative KKT violation of x for the p = 2 ball subproblem (Sec. 1's
+    norm balls, Eq. 2): stationarity H (x - xt) - g + mu x = 0 with mu >= 0,
+    and mu (||x|| - R) = 0."""
     c = H @ xt + g
     grad = H @ x - c
     scale = max(np.abs(c).max(), 1e-300)
@@ -583,6 +596,7 @@ def ihs(A, b, kind: int, param: float, m: int, s: int, seed: int, iters: int, x0
 
 
 def ata(A):
+    """A^T A in FP64: the Hessian of Eq. 1 (x_OPT, the norm ||.||_A)."""
     A = as_f64(A)
     if isinstance(A, CSR):
         return A.gram()
@@ -590,6 +604,7 @@ def ata(A):
 
 
 def atb(A, b):
+    """A^T b in FP64: the linear term of Eq. 1."""
     A = as_f64(A)
     if isinstance(A, CSR):
         return A.rmatvec(b)
@@ -604,8 +619,9 @@ def x_opt_ols_qr(A, b):
 
 
 def x_opt_ols_normal(A, b, lam: float = 0.0, refine: int = 3):
-    """x_OPT from the normal equations (A^T A + lam I) x = A^T b, Cholesky in
-    FP64 plus `refine` rounds of iterative refinement with FP64 residuals."""
+    """x_OPT of Eq. 1 with C = R^d (lam > 0: ridge, not in the paper) from the
+    normal equations (A^T A + lam I) x = A^T b, Cholesky in FP64 plus `refine`
+    rounds of iterative refinement with FP64 residuals."""
     A = as_f64(A)
     G = ata(A) + lam * np.eye(A.shape[1])
     x = chol_solve(G, atb(A, b))
@@ -623,8 +639,9 @@ def x_opt_l1(A, b, R):
 
 
 def x_opt_l1_penalty(A, b, lam):
-    """x_OPT of the penalised LASSO 1/2 ||Ax - b||^2 + lam ||x||_1: the
-    subproblem above with H = A^T A, x^t = 0, g = A^T b."""
+    """x_OPT of the penalised LASSO of Sec. 3's experiments,
+    1/2 ||Ax - b||^2 + lam ||x||_1: the subproblem above with H = A^T A,
+    x^t = 0, g = A^T b."""
     A = as_f64(A)
     return l1_penalty_qp(ata(A), atb(A, b), np.zeros(A.shape[1]), lam)
 
@@ -643,9 +660,11 @@ def err_A(x, xopt, G):
 
 
 def ridge_adjoint(A, b, lam, dLdx):
-    """Exact gradients of L(x(A, b)) for x = (A^T A + lam I)^{-1} A^T b:
-    v = (A^T A + lam I)^{-1} dL/dx,  dL/db = A v,  dL/dA = r v^T - (A v) x^T
-    with r = b - A x.  Dense FP64 solves."""
+    """Exact gradients of L(x(A, b)) for the ridge solution
+    x = (A^T A + lam I)^{-1} A^T b (ridge is not in the paper; its nearest
+    constraint is Sec. 1's p = 2 ball): v = (A^T A + lam I)^{-1} dL/dx,
+    dL/db = A v,  dL/dA = r v^T - (A v) x^T with r = b - A x.  Dense FP64
+    solves."""
     A = np.ascontiguousarray(A, dtype=np.float64)
     G = A.T @ A + lam * np.eye(A.shape[1])
     x = chol_solve(G, A.T @ b)
@@ -656,7 +675,8 @@ def ridge_adjoint(A, b, lam, dLdx):
 
 
 def srht_n2(n: int) -> int:
-    """Rows of the Hadamard transform: the least power of two >= n (A is padded with zero rows)."""
+    """Rows of the SRHT's Hadamard transform (Sec. 2): the least power of two
+    >= n (A is padded with zero rows)."""
     return 1 << max(0, (int(n) - 1).bit_length())
 
 
@@ -684,8 +704,8 @@ def srht_sketch(A, m: int, rows, sign):
 
 
 def fwht_rows(X):
-    """Unnormalised Walsh-Hadamard transform along axis 0 (length a power of
-    two), by the recursive definition H_{2k} = [H_k H_k; H_k -H_k]: stage h
+    """Unnormalised Walsh-Hadamard transform (the H of Sec. 2's SRHT) along
+    axis 0 (length a power of two), by the recursive definition H_{2k} = [H_k H_k; H_k -H_k]: stage h
     replaces each pair (u, v) at distance h by (u + v, u - v)."""
     Y = np.array(X, dtype=np.float64, copy=True)
     n2 = Y.shape[0]
@@ -702,8 +722,9 @@ def fwht_rows(X):
 
 
 def srht_sketch_fast(A, m: int, rows, sign):
-    """P H D A through the fast transform (the same numbers as srht_sketch up
-    to the order of the additions): pad D A to n2 rows, transform, take rows."""
+    """P H D A of Sec. 2's SRHT through the fast transform (the same numbers
+    as srht_sketch up to the order of the additions): pad D A to n2 rows,
+    transform, take rows."""
     A = as_f64(A)
     n, d = A.shape
     X = np.zeros((srht_n2(n), d))
@@ -719,7 +740,8 @@ def gauss_draw(seed: int, t: int, m: int, n: int):
 
 
 def gauss_sketch(A, m: int, seed: int, t: int):
-    """Raw G A (m x d, FP64) for the Gaussian sketch of counter t (Gram scale 1/m)."""
+    """Raw G A (m x d, FP64) for Sec. 2's Gaussian sketch of counter t (Gram
+    scale 1/m)."""
     A = as_f64(A)
     return gauss_draw(seed, t, m, A.shape[0]) @ A
 
