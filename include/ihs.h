@@ -185,7 +185,9 @@ typedef struct {
   int graph;            /* ihs_solve: 1 if it ran as a replayed CUDA graph   */
 } ihs_report;
 
-/* ihs_create -- validate (A, b, C, options) and allocate every workspace.
+/* ihs_create -- validate (A, b, C, options) and allocate every workspace:
+ * the problem (A, b, C) of Eq. 1 with the sketch of Sec. 2 (m rows, s
+ * blocks, seed).
  * A: matrix descriptor (HOST struct; its arrays are DEVICE, borrowed).
  * b: DEVICE, n doubles, borrowed.  C, opt: HOST structs, copied.
  * stream: a cudaStream_t (NULL = legacy default stream).  For CSR input a
@@ -231,7 +233,7 @@ ihs_status ihs_sketch_gradient(ihs_ctx* ctx, int64_t t, const double* x, double*
  * Asynchronous; device failures surface at the next synchronising call. */
 ihs_status ihs_step(ihs_ctx* ctx, double* x);
 
-/* ihs_solve -- iterations t = t0 .. t0+iters-1 of ihs_sketch + ihs_step from
+/* ihs_solve -- iterations t = t0 .. t0+iters-1 of Eq. 2 (ihs_sketch + ihs_step) from
  * the x given (DEVICE, d doubles; in: x^{t0}, out: x^{t0+iters}).  The run
  * is a pure function of (A, b, C, options, x, t0), so stopping after k
  * iterations and resuming with t0 + k reproduces it exactly.  rep: HOST,
@@ -240,10 +242,12 @@ ihs_status ihs_solve(ihs_ctx* ctx, double* x, int64_t t0, int iters,
                      ihs_report* rep);
 
 /* ihs_sync -- wait for the context's stream and return the device status
- * word (then clear it). */
+ * word (then clear it).  A service of the library (no counterpart in the
+ * paper). */
 ihs_status ihs_sync(ihs_ctx* ctx);
 
-/* ihs_get_sketch -- copy the last sketch out, for inspection and tests.
+/* ihs_get_sketch -- copy the last sketch out, for inspection and tests: SA of
+ * Sec. 2 and the approximate Hessian of Sec. 1.
  * SA_out: DEVICE buffer for the m x d row-major raw sketch SA (entries +-1,
  * SJLT normalisation not applied), FP64 for precision FP64 and FP32 for the
  * mixed modes (*SA_dtype, HOST, gets IHS_F64 or IHS_F32).  H_out: DEVICE
@@ -253,7 +257,8 @@ ihs_status ihs_sync(ihs_ctx* ctx);
 ihs_status ihs_get_sketch(ihs_ctx* ctx, void* SA_out, int* SA_dtype, double* H_out,
                           double* scale);
 
-/* ihs_trim_memory -- contexts take their device workspaces from a
+/* ihs_trim_memory -- a service of the library (no counterpart in the
+ * paper).  Contexts take their device workspaces from a
  * library-owned memory pool per device that keeps what ihs_destroy frees, so
  * that creating the next context does not map new device memory.  This call
  * returns every pool's unused memory to the device.  Call it with no context
@@ -261,7 +266,8 @@ ihs_status ihs_get_sketch(ihs_ctx* ctx, void* SA_out, int* SA_dtype, double* H_o
  * IHS_ERR_CUDA. */
 ihs_status ihs_trim_memory(void);
 
-/* ihs_selftest_wait -- exercises the bounded device wait used by the
+/* ihs_selftest_wait -- a self-test of the library (no counterpart in the
+ * paper): exercises the bounded device wait used by the
  * library's grid barriers without faulting or hanging the GPU: two CTAs wait
  * at a barrier that expects three (nothing ever completes it), each gives up
  * after 4096 polls (well under a millisecond) and records the timeout in a
@@ -292,7 +298,8 @@ ihs_status ihs_selftest_rsqrt(const double* p, double* out, double* ref, int64_t
  * first use.  Errors: IHS_ERR_ARG (null), IHS_ERR_OOM, IHS_ERR_CUDA. */
 ihs_status ihs_exact_gram(ihs_ctx* ctx, double* G);
 
-/* ihs_sketch_error -- form the sketch of counter t as ihs_sketch does, then
+/* ihs_sketch_error -- App. B's empirical sketch error: form the sketch of
+ * counter t as ihs_sketch does, then
  * err (HOST) = ||H_t - G||_F / ||G||_F with H_t = (1/s) (S_t A)^T (S_t A)
  * (+ lambda I for ridge) and G (DEVICE, d x d) normally from
  * ihs_exact_gram.  Synchronises; returns the device status. */
@@ -323,19 +330,23 @@ enum { IHS_ST_SORT = 0, IHS_ST_SKETCH, IHS_ST_SKETCH_FIX, IHS_ST_GRAM, IHS_ST_FA
        IHS_ST_GRAD, IHS_ST_STEP, IHS_NSTAGES };
 
 /* ihs_profile -- enable (1) or disable (0) stage timing; enabling clears
- * the totals and the launch count. */
+ * the totals and the launch count.  A service of the library (no
+ * counterpart in the paper), like ihs_profile_read. */
 ihs_status ihs_profile(ihs_ctx* ctx, int enable);
 
 /* ihs_profile_read -- synchronise and report, per stage, the summed event
  * time in ms (ms[IHS_NSTAGES], HOST) and the number of timed instances
  * (count[IHS_NSTAGES], HOST, nullable), and the kernel launches issued by the
- * library since ihs_profile(ctx, 1) (launches, HOST, nullable). */
+ * library since ihs_profile(ctx, 1) (launches, HOST, nullable).  A service of
+ * the library (no counterpart in the paper). */
 ihs_status ihs_profile_read(ihs_ctx* ctx, double* ms, int* count, int64_t* launches);
 
-/* ihs_destroy -- free every workspace (NULL is a no-op).  Synchronises. */
+/* ihs_destroy -- free every workspace (NULL is a no-op).  Synchronises.
+ * A service of the library (no counterpart in the paper). */
 void ihs_destroy(ihs_ctx* ctx);
 
-/* ihs_status_str -- static text for a status code. */
+/* ihs_status_str -- static text for a status code (a service of the
+ * library). */
 const char* ihs_status_str(ihs_status st);
 
 /* ---------------------------------------------------------------------
@@ -361,8 +372,8 @@ ihs_status ihs_sketch_adjoint(uint64_t seed, int64_t t, int s, int64_t m,
                               int64_t n, int64_t d, const double* G,
                               double* out, void* stream);
 
-/* ihs_gradient_noalloc -- g = A^T (b - A x) - lambda x for a DENSE A, the
- * same quantity as ihs_gradient, for callers that cannot allocate device
+/* ihs_gradient_noalloc -- g = A^T (b - A x) - lambda x for a DENSE A (the
+ * linear term of Eq. 2), the same quantity as ihs_gradient, for callers that cannot allocate device
  * memory when they call: code whose device memory is all handed to its own
  * pool allocator, or latency-critical loops that cannot afford the implicit
  * device-wide synchronisation of cudaMalloc.  It needs no context and
