@@ -1,5 +1,6 @@
 // noalloc.cu -- ihs_gradient_noalloc: the dense residual/gradient pass
-// g = A^T (b - A x) - lambda x for callers that cannot allocate device memory.
+// g = A^T (b - A x) - lambda x (the linear term of Eq. 2) for callers that
+// cannot allocate device memory.
 //
 // It is a variant of the dense gradient kernels in grad.cu whose per-warp
 // partial gradients live in a fixed file-scope device array instead of a
