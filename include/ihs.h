@@ -23,6 +23,10 @@
  *     device status word and returned by the next call that synchronises
  *     (ihs_solve, ihs_sync, ihs_adjoint).
  *   - Sizes: n < 2^31 rows, 1 <= d <= 1024 columns, s divides m, m >= d.
+ *     Dense A: m <= 51200 (the bucket sort counts in 200 KB of shared
+ *     memory) and s * n < 2^31.  CSR A: nnz < 2^31, m / s <= 51200 with FP32
+ *     accumulators, <= 25600 with FP64 (a block's buckets in 200 KB of
+ *     shared memory).
  */
 #ifndef IHS_H_
 #define IHS_H_
@@ -194,8 +198,9 @@ typedef struct {
  * column-major (CSC) copy of A is built once here and owned by the context.
  * Workspaces come from a library-owned device memory pool (see
  * ihs_trim_memory).
- * Synchronises.  Errors: IHS_ERR_ARG for shapes (m % s != 0, m < d, d > 1024,
- * n >= 2^31, bad kind/dtype), IHS_ERR_OOM, IHS_ERR_CUDA. */
+ * Synchronises.  Errors: IHS_ERR_ARG for shapes (m % s != 0, m < d,
+ * n >= 2^31, bad kind/dtype/flags), IHS_ERR_UNSUPPORTED for d > 1024 and
+ * the m, s * n and nnz limits above, IHS_ERR_OOM, IHS_ERR_CUDA. */
 ihs_status ihs_create(ihs_ctx** out, const ihs_matrix* A, const double* b,
                       const ihs_constraint* C, const ihs_options* opt,
                       void* stream);
