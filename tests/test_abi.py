@@ -190,3 +190,28 @@ def test_entry_points_reject_bad_arguments_before_touching_the_device():
     assert lib.ihs_gradient_noalloc(ctypes.byref(M), buf, buf, 0.0, buf, None) == ERR_ARG
     M.kind, M.d, M.ld = ihs.DENSE, 1025, 1025
     assert lib.ihs_gradient_noalloc(ctypes.byref(M), buf, buf, 0.0, buf, None) == UNSUPPORTED
+
+
+def test_create_reports_unsupported_sizes_before_touching_the_device():
+    """Sizes the library does not handle return IHS_ERR_UNSUPPORTED (8) from
+    ihs_create's host-side checks: d > 1024, a dense s * n of 2^31 or more,
+    and the SRHT over a CSR matrix (no device in this process)."""
+    import paper_1910_14166_gb300 as ihs
+    lib = ihs._lib
+    UNSUPPORTED = 8
+    b = ctypes.c_void_p(0x2000)
+
+    def create(M, m, s, sketch=0):
+        C = ihs._Constraint(ihs.OLS, 0.0)
+        O = ihs._Options(m, s, 0, 1, 0, 0.0, 0, sketch)
+        h = ctypes.c_void_p()
+        return lib.ihs_create(ctypes.byref(h), ctypes.byref(M), b, ctypes.byref(C),
+                              ctypes.byref(O), None)
+
+    M = ihs._Matrix()
+    M.kind, M.dtype, M.n, M.d, M.ld, M.val = ihs.DENSE, ihs.F32, 1000, 1025, 1025, 0x1000
+    assert create(M, 2050, 1) == UNSUPPORTED
+    M.n, M.d, M.ld = 1 << 26, 10, 10
+    assert create(M, 640, 64) == UNSUPPORTED
+    M.kind, M.n, M.col, M.rowptr, M.nnz = ihs.CSR, 1000, 0x3000, 0x4000, 2000
+    assert create(M, 100, 1, sketch=1) == UNSUPPORTED
