@@ -67,3 +67,31 @@ def test_both_arms_name_the_workload_alike():
     assert one["parallelism"] == "single GPU"
     assert "2.10 GB" in one["l2"]
     assert bench.config_of("ols_dense_ar1", 1048576, 500, 5000, 1, 4)["parallelism"] == "replicas"
+
+
+def test_reference_arm_runs_on_rank_zero_only():
+    """Under a 2-rank launch, the reference arm (the oracle on the host
+    cores) runs and prints one JSON line on rank 0 only; rank 1 exits 0
+    without work or output.  The line carries the contract's keys: impl,
+    the same metric and workload as this library's arm, a cpu_baseline of
+    kind oracle, and an e2e object with no host-device bytes."""
+    import subprocess
+    base = [sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+            "--warmup", "0", "--cpu-rows", "20000", "--ref-step-budget", "1"]
+    outs = {}
+    for rank in (1, 0):
+        env = dict(os.environ, RANK=str(rank), WORLD_SIZE="2", LOCAL_RANK=str(rank))
+        p = subprocess.run(base, capture_output=True, text=True, env=env, timeout=600)
+        assert p.returncode == 0, p.stderr[-2000:]
+        outs[rank] = p.stdout.strip()
+    assert outs[1] == ""
+    lines = outs[0].splitlines()
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["metric"] == bench.METRIC
+    assert d["n_gpus"] == 2 and d["steps"] == 1 and d["higher_is_better"] is False
+    assert d["config"]["workload"] == bench.config_of("ols_dense_ar1", 1048576, 500, 5000, 1,
+                                                      2)["workload"]
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}
