@@ -7,12 +7,27 @@ import os
 import shutil
 import sys
 
+import pytest
+
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-sys.path.insert(0, ROOT)
-
-import bench  # noqa: E402
-
 CSRC = os.path.join("paper_1910_14166_gb300", "csrc")
+_THREAD_VARS = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
+
+
+@pytest.fixture(scope="module")
+def bench():
+    """bench.py as a module, imported only when these tests run (it sets the
+    BLAS/OpenMP thread variables for its own process on import; they are
+    put back so that the rest of the session keeps its threads)."""
+    saved = {k: os.environ.get(k) for k in _THREAD_VARS}
+    sys.path.insert(0, ROOT)
+    import bench as b
+    for k, v in saved.items():
+        if v is None:
+            os.environ.pop(k, None)
+        else:
+            os.environ[k] = v
+    return b
 
 
 def _copy_sources(dst):
@@ -21,7 +36,7 @@ def _copy_sources(dst):
         shutil.copy(os.path.join(ROOT, CSRC, f), os.path.join(dst, CSRC, f))
 
 
-def test_source_hash_changes_with_either_fused_pass_source(monkeypatch, tmp_path):
+def test_source_hash_changes_with_either_fused_pass_source(bench, monkeypatch, tmp_path):
     real = bench.kernel_source_hash()
     _copy_sources(str(tmp_path))
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
@@ -35,7 +50,7 @@ def test_source_hash_changes_with_either_fused_pass_source(monkeypatch, tmp_path
         assert bench.kernel_source_hash() == real
 
 
-def test_traffic_is_reported_only_for_the_sources_it_was_taken_on(monkeypatch, tmp_path):
+def test_traffic_is_reported_only_for_the_sources_it_was_taken_on(bench, monkeypatch, tmp_path):
     (tmp_path / "profiles").mkdir()
     rec = {"source_hash": "0123456789abcdef", "kernels": {"k_sketch_grad_fused": 2223404032}}
     (tmp_path / "profiles" / "traffic.json").write_text(json.dumps(rec))
@@ -49,7 +64,7 @@ def test_traffic_is_reported_only_for_the_sources_it_was_taken_on(monkeypatch, t
     assert bench.traffic_for("k_sketch_grad_fused") is None
 
 
-def test_peaks_measured_else_fallback(monkeypatch, tmp_path):
+def test_peaks_measured_else_fallback(bench, monkeypatch, tmp_path):
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     assert bench.peaks() == (bench.FALLBACK_HBM, "fallback")
     tf, kind = bench.tensor_peak_tf32()
@@ -61,7 +76,7 @@ def test_peaks_measured_else_fallback(monkeypatch, tmp_path):
     assert abs(tf - 2000.0 * 1.1 / 2.25) < 1e-9 and kind.startswith("measured")
 
 
-def test_both_arms_name_the_workload_alike():
+def test_both_arms_name_the_workload_alike(bench):
     one = bench.config_of("ols_dense_ar1", 1048576, 500, 5000, 1, 1)
     assert one["workload"].startswith("ols_dense_ar1 n=1048576 d=500 m=5000 s=1")
     assert one["parallelism"] == "single GPU"
@@ -69,7 +84,7 @@ def test_both_arms_name_the_workload_alike():
     assert bench.config_of("ols_dense_ar1", 1048576, 500, 5000, 1, 4)["parallelism"] == "replicas"
 
 
-def test_reference_arm_runs_on_rank_zero_only():
+def test_reference_arm_runs_on_rank_zero_only(bench):
     """Under a 2-rank launch, the reference arm (the oracle on the host
     cores) runs and prints one JSON line on rank 0 only; rank 1 exits 0
     without work or output.  The line carries the contract's keys: impl,
